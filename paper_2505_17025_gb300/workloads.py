@@ -1,0 +1,148 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, tests and bench.
+
+This module only builds inputs: grids, bathymetry, slide parameters, initial
+states and time steps.  It holds none of the method's arithmetic (no fluxes,
+criteria, elliptic coefficients or corrections) and imports neither the CUDA
+binding nor the oracle.
+
+Workloads (sizes are those of the synthetic configurations the library is
+measured on; the paper's own runs are quoted where they are used):
+
+* ``solitary_1d`` -- Green-Naghdi / Serre solitary wave over a flat bottom
+  (Sec. 4.1, Eq. 18): eta = a sech^2(K (x - c t - x0)), u = c eta / (d + eta),
+  c = sqrt(g (d + a)), K = sqrt(3 a / (4 d^2 (d + a))); the initial hw follows
+  from the constraint (Eq. 4) for a flat, static bottom, hw = -h^2 u_x / 2.
+* ``slide_1d`` -- still water over a plane slope d0 = min(h_min + s x, h_max)
+  with a Gaussian mound of height A and width L moving down-slope as
+  s(t) = s0 ln cosh(t / t0); per-member A, L, s0 drawn from a seeded uniform
+  +-30 % band around the nominal values.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+G = 9.81
+
+
+# ---------------------------------------------------------------- closed form
+
+def solitary_fields(x, t, a, d, x0, g=G):
+    """(eta, u, hw) of the solitary wave of Eq. 18 at positions x, time t."""
+    c = math.sqrt(g * (d + a))
+    K = math.sqrt(3.0 * a / (4.0 * d * d * (d + a)))
+    xi = K * (np.asarray(x, dtype=np.float64) - c * t - x0)
+    sech2 = 1.0 / np.cosh(xi) ** 2
+    eta = a * sech2
+    u = c * eta / (d + eta)
+    eta_x = -2.0 * K * eta * np.tanh(xi)
+    u_x = c * d * eta_x / (d + eta) ** 2
+    h = d + eta
+    hw = -0.5 * h * h * u_x
+    return eta, u, hw
+
+
+def solitary_speed(a, d, g=G):
+    return math.sqrt(g * (d + a))
+
+
+def cfl_dt(T, cfl, dx, speed):
+    """Fixed step dt = T / ceil(T / dt_cfl), dt_cfl = cfl dx / speed."""
+    n = int(math.ceil(T / (cfl * dx / speed) - 1e-9))
+    return T / n, n
+
+
+# ------------------------------------------------------------------ workloads
+
+@dataclass
+class Member1D:
+    """One 1D problem: grid, bottom, slide and initial state."""
+    nx: int
+    dx: float
+    xl: float
+    d0: np.ndarray
+    h: np.ndarray
+    hu: np.ndarray
+    hw: np.ndarray
+    slide: int = 0           # 0 static bottom, 1 Gaussian mound, s0 ln cosh(t/t0)
+    A: float = 0.0
+    L: float = 1.0
+    xc0: float = 0.0
+    s0: float = 0.0
+    t0: float = 1.0
+
+    @property
+    def x(self):
+        return self.xl + (np.arange(self.nx) + 0.5) * self.dx
+
+
+@dataclass
+class Workload1D:
+    name: str
+    members: list
+    dt: float
+    n_steps: int
+    T: float
+    bc: int = 0              # 0 wall, 1 periodic
+    amplitude: float = 0.0   # wave amplitude a used in error bounds
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nx(self):
+        return self.members[0].nx
+
+
+def solitary_1d(nx=2000, length=200.0, depth=1.0, a=0.1, x0=None, T=20.0, cfl=0.5, g=G):
+    """1D solitary wave, flat bottom, walls (default: h = 1 m, a/h = 0.1,
+    [0, 200] m, dx = 0.1 m, CFL 0.5, T = 20 s)."""
+    dx = length / nx
+    x0 = length / 4.0 if x0 is None else x0
+    x = (np.arange(nx) + 0.5) * dx
+    eta, u, hw = solitary_fields(x, 0.0, a, depth, x0, g)
+    h = depth + eta
+    d0 = np.full(nx, depth)
+    speed = float(np.max(np.abs(u) + np.sqrt(g * h)))
+    dt, n = cfl_dt(T, cfl, dx, speed)
+    m = Member1D(nx=nx, dx=dx, xl=0.0, d0=d0, h=h, hu=h * u, hw=hw)
+    return Workload1D("solitary_1d", [m], dt, n, T, amplitude=a,
+                      meta={"depth": depth, "a": a, "x0": x0, "length": length})
+
+
+def slide_1d(n_members=64, nx=50000, length=40.0, h_min=0.05, h_max=1.0, slope=0.25,
+             A=0.05, L=0.5, s0=2.0, t0=1.0, xc0=1.0, spread=0.3, T=2.0, cfl=0.5,
+             seed0=0, g=G):
+    """Batch of 1D moving-bottom slides; member k uses numpy default_rng(seed0 + k)
+    to scale A, L, s0 by U(1 - spread, 1 + spread)."""
+    dx = length / nx
+    x = (np.arange(nx) + 0.5) * dx
+    d0 = np.minimum(h_min + slope * x, h_max)
+    members = []
+    for k in range(n_members):
+        rng = np.random.default_rng(seed0 + k)
+        fa, fl, fs = rng.uniform(1.0 - spread, 1.0 + spread, size=3)
+        Ak, Lk, sk = A * fa, L * fl, s0 * fs
+        xi = (x - xc0) / Lk
+        d = d0 - Ak * np.exp(-xi * xi)
+        members.append(Member1D(nx=nx, dx=dx, xl=0.0, d0=d0.copy(), h=d.copy(),
+                                hu=np.zeros(nx), hw=np.zeros(nx), slide=1,
+                                A=Ak, L=Lk, xc0=xc0, s0=sk, t0=t0))
+    speed = math.sqrt(g * h_max)
+    dt, n = cfl_dt(T, cfl, dx, speed)
+    return Workload1D("slide_1d", members, dt, n, T, amplitude=A,
+                      meta={"h_min": h_min, "h_max": h_max, "slope": slope, "A": A, "L": L,
+                            "s0": s0, "t0": t0, "xc0": xc0, "spread": spread, "seed0": seed0})
+
+
+def standing_wave_1d(nx=128, depth=1.0, kh=1.0, amp=1e-4, modes=1, g=G):
+    """Small-amplitude standing wave eta = amp cos(k x) in a walled basin of
+    length modes * pi / k (k = kh / depth), at rest."""
+    k = kh / depth
+    length = modes * math.pi / k
+    dx = length / nx
+    x = (np.arange(nx) + 0.5) * dx
+    h = depth + amp * np.cos(k * x)
+    m = Member1D(nx=nx, dx=dx, xl=0.0, d0=np.full(nx, depth), h=h,
+                 hu=np.zeros(nx), hw=np.zeros(nx))
+    return m, k, length
