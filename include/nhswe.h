@@ -1,0 +1,186 @@
+/*
+ * nhswe.h -- C ABI of the GB300 (sm_103a) locally adaptive non-hydrostatic
+ * shallow-water library.
+ *
+ * The library advances the one-dimensional non-hydrostatic extension of the
+ * shallow-water equations with a moving bottom (Firdaus & Behrens, Sec. 2,
+ * Eqs. 1-5) by the projection method of Sec. 3: a hydrostatic predictor
+ * (Sec. 3.1), a criterion on the predicted state that marks the
+ * non-hydrostatic cells (Sec. 5.1, enlarged by whole cells as in Sec. 5.2),
+ * an elliptic solve for the non-hydrostatic pressure on the marked cells only
+ * (Sec. 3.2, Eqs. 12-13, zero Dirichlet data on the sub-domain boundary), and
+ * the backward-Euler correction of hu and hw (Eqs. 10-11; h is not corrected).
+ *
+ * One handle holds a batch of `nbatch` independent members that share the grid
+ * geometry (cell count, spacing, boundary kind) but each have their own static
+ * depth, slide motion and state; every kernel processes the whole batch.
+ *
+ * Conventions for every entry point:
+ *  - Host arrays are FP64, member-major: element (b, i) of a field is at
+ *    [b * nx + i]; cell i of a member spans [x0 + i dx, x0 + (i+1) dx].
+ *  - Device memory is never allocated by the library.  All of it lives in the
+ *    caller's workspace (`ws`, `ws_bytes` from nh_workspace_bytes()), which
+ *    must stay valid and untouched until nh_destroy().
+ *  - All GPU work is ordered on the caller's stream (`stream`, a
+ *    cudaStream_t, NULL = legacy default stream).  Calls that return data to
+ *    the host (nh_get_*), nh_step and nh_run synchronise that stream.
+ *  - Errors are returned as nh_status, never thrown; nh_status_string()
+ *    names them.  A handle is used by one host thread at a time.
+ *  - The library computes on the GPU only.  There is no CPU fallback; a
+ *    missing or unusable device is reported as NH_ERR_CUDA.
+ */
+#ifndef NHSWE_H
+#define NHSWE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nh_grid nh_grid;   /* opaque, created by nh_create_grid */
+
+typedef enum {
+    NH_OK = 0,
+    NH_ERR_ARG = 1,            /* invalid argument or descriptor            */
+    NH_ERR_CUDA = 2,           /* a CUDA runtime call failed                */
+    NH_ERR_NOT_CONVERGED = 3,  /* Krylov solve hit max_iter; step rolled back */
+    NH_ERR_NONFINITE = 4,      /* NaN/Inf in a residual norm; step rolled back */
+    NH_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up        */
+    NH_ERR_STATE = 6           /* call out of order (e.g. no state set)     */
+} nh_status;
+
+enum { NH_BC_WALL = 0, NH_BC_PERIODIC = 1 };
+/* NH_FP64: every field, coefficient, vector and sum in FP64.
+   NH_MIXED: state, predictor, coefficients and Krylov vectors in FP32;
+   inner products, norms, mass sums and the iterative-refinement residual in
+   FP64. */
+enum { NH_FP64 = 0, NH_MIXED = 1 };
+/* Slope limiter of the piecewise-linear reconstruction of eta, u, w. */
+enum { NH_LIM_NONE = 0, NH_LIM_CENTRAL = 1, NH_LIM_MINMOD = 2, NH_LIM_MC = 3 };
+/* Sec. 5.1 criteria.  GLOBAL = every cell (the global model of Sec. 4);
+   HYDROSTATIC = no cell (plain SWE). */
+enum { NH_CRIT_GLOBAL = 0, NH_CRIT_HYDROSTATIC = 1, NH_CRIT_ETA_D = 2,
+       NH_CRIT_ETA_X = 3, NH_CRIT_U = 4, NH_CRIT_U_X = 5, NH_CRIT_W = 6,
+       NH_CRIT_W_X = 7 };
+/* AUTO: CG when the reaction term gamma is > 0 on every active cell of a
+   member (the operator is then symmetric positive definite), else BiCGStab. */
+enum { NH_SOLVER_AUTO = 0, NH_SOLVER_CG = 1, NH_SOLVER_BICGSTAB = 2 };
+enum { NH_GUESS_ZERO = 0, NH_GUESS_PREV = 1 };
+enum { NH_SLIDE_NONE = 0, NH_SLIDE_GAUSS_LNCOSH = 1 };
+
+typedef struct {
+    int    dim;        /* 1                                                 */
+    int    nx;         /* cells per member, 4 <= nx <= 2^26                  */
+    int    nbatch;     /* members, >= 1                                     */
+    int    bc;         /* NH_BC_WALL or NH_BC_PERIODIC (both ends)          */
+    int    precision;  /* NH_FP64 or NH_MIXED                               */
+    int    limiter;    /* NH_LIM_*                                          */
+    double dx;         /* cell width (m), > 0                               */
+    double x0;         /* left end of the domain (m)                        */
+    double g;          /* gravity (m/s^2), > 0                              */
+    double rho;        /* density (kg/m^3), > 0; scales p^nh only           */
+} nh_grid_desc;
+
+/* Moving bottom of one member: d(x,t) = d0(x) - A exp(-((x - xc0 - s(t))/L)^2)
+   with s(t) = s0 ln cosh(t / t0) (a Gaussian mound sliding down-slope).  The
+   static part d0 is sampled per cell; its x-derivatives are central
+   differences; the mound's value and derivatives are analytic. */
+typedef struct {
+    int    shape;      /* NH_SLIDE_NONE or NH_SLIDE_GAUSS_LNCOSH            */
+    double A, L, xc0;  /* height (m), width (m, > 0), start position (m)    */
+    double s0, t0;     /* travel scale (m), time scale (s, > 0)             */
+} nh_slide_desc;
+
+typedef struct {
+    long long step;        /* steps taken since the state was set              */
+    double    t;           /* model time after the step (s)                    */
+    long long n_active;    /* active (non-hydrostatic) cells, all members      */
+    int       n_active_max;/* largest per-member active count                  */
+    int       iters;       /* Krylov iterations, maximum over members          */
+    int       ir_passes;   /* refinement passes (NH_MIXED), maximum over members */
+    int       solver;      /* NH_SOLVER_CG if every solved member used CG,
+                              NH_SOLVER_BICGSTAB if any used BiCGStab, -1 none */
+    int       status;      /* nh_status of the step                             */
+    double    rel_res;     /* max over members of ||R - A q|| / ||R||           */
+    double    min_gamma;   /* min over active cells of the scaled reaction term */
+    double    mass;        /* sum over members and cells of h dx (FP64)         */
+} nh_step_info;
+
+typedef struct {
+    long long steps;         /* steps completed                                */
+    long long iters_total;   /* sum over steps of nh_step_info.iters           */
+    long long active_total;  /* sum over steps of nh_step_info.n_active        */
+    nh_step_info last;       /* the last completed step                        */
+} nh_run_info;
+
+/* Bytes of device workspace nh_create_grid needs for `desc` (0 if invalid). */
+size_t nh_workspace_bytes(const nh_grid_desc* desc);
+
+/* Create a handle over the caller's workspace and upload the static depth.
+   d0_host: nbatch * nx FP64 depths d0 > 0 (m), member-major.  The workspace
+   must be 256-byte aligned and at least nh_workspace_bytes(desc) long.
+   The new handle has no state (nh_set_state must come before stepping), no
+   bottom motion, criterion GLOBAL with k_nh = 1e-3 and one enlarging cell,
+   and solver AUTO, rtol 1e-12, max_iter 20000, warm start PREV.
+   Errors: NH_ERR_ARG (bad descriptor, NULL pointer, short or misaligned
+   workspace), NH_ERR_CUDA. */
+nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host,
+                         void* ws, size_t ws_bytes, void* stream, nh_grid** out);
+
+/* Bottom motion per member (Sec. 4.2-4.3 describe the paper's own moving
+   bottoms; this library moves a Gaussian mound, see nh_slide_desc).
+   slides: nbatch entries, or NULL for a static bottom.  Errors: NH_ERR_ARG. */
+nh_status nh_set_bottom_motion(nh_grid* g, const nh_slide_desc* slides);
+
+/* Adaptivity (Sec. 5.1, 5.2): cells whose criterion value on the predicted
+   state exceeds k_nh (strictly) are marked, then the set is enlarged by
+   `enlarge` cells on each side (0 <= enlarge <= 16).  first_step_global != 0
+   applies the model on every cell in the first step after nh_set_state (the
+   rule Sec. 5.1.2 gives for the |w| and |w_x| criteria).  Errors: NH_ERR_ARG. */
+nh_status nh_set_criterion(nh_grid* g, int kind, double k_nh, int enlarge,
+                           int first_step_global);
+
+/* Elliptic solve on the marked cells (Sec. 3.2).  rtol: stop when
+   ||R - A q||_2 <= rtol ||R||_2 per member (FP64 norms).  max_iter >= 1.
+   guess: NH_GUESS_PREV starts from the previous step's pressure on cells
+   active in both steps (zero elsewhere).  NH_MIXED only: ir_max >= 1 outer
+   refinement passes with an FP64 residual, each an FP32 Krylov solve to
+   inner_rtol (relative to its own right-hand side).  Errors: NH_ERR_ARG. */
+nh_status nh_set_solver(nh_grid* g, int kind, double rtol, int max_iter, int guess,
+                        int ir_max, double inner_rtol);
+
+/* Upload a state (host FP64, nbatch * nx each): h > 0 (m), hu (m^2/s),
+   hw (m^2/s) at model time t; the step counter restarts at 0 and the
+   previous pressure is cleared.  Errors: NH_ERR_ARG, NH_ERR_CUDA. */
+nh_status nh_set_state(nh_grid* g, const double* h, const double* hu, const double* hw,
+                       double t);
+
+/* Download the state (host FP64, nbatch * nx each; any pointer may be NULL):
+   h, hu, hw, and p_nh = the non-hydrostatic pressure of the last step
+   (Pa; zero on cells that were hydrostatic).  Errors: NH_ERR_STATE, NH_ERR_CUDA. */
+nh_status nh_get_state(nh_grid* g, double* h, double* hu, double* hw, double* p_nh);
+
+/* Download the last step's non-hydrostatic mask (nbatch * nx bytes, 1 =
+   corrected cell) and per-member Krylov iterations / relative residuals
+   (nbatch entries each; any pointer may be NULL). */
+nh_status nh_get_mask(nh_grid* g, unsigned char* mask, int* iters, double* rel_res);
+
+/* One step of size dt > 0: predictor, criterion and mask, elliptic solve on
+   the mask, correction.  On NH_ERR_NOT_CONVERGED or NH_ERR_NONFINITE the
+   state is left as it was before the step.  info may be NULL. */
+nh_status nh_step(nh_grid* g, double dt, nh_step_info* info);
+
+/* n_steps steps of size dt; stops at the first failing step (whose status is
+   returned; info->last describes it).  info may be NULL. */
+nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info);
+
+/* Release the handle (the workspace stays the caller's). */
+void nh_destroy(nh_grid* g);
+
+const char* nh_status_string(nh_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NHSWE_H */

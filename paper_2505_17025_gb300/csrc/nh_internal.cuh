@@ -1,0 +1,189 @@
+// nh_internal.cuh -- device-side building blocks of the 1D library path.
+//
+// Unknown used on the GPU: psi = (dt / rho) h~ p^nh.  With this scaling the
+// elliptic problem of Sec. 3.2 (Eqs. 10-13 with the constraint Eq. 4
+// eliminated) reads
+//     -(Kc psi_x)_x + gam psi = R,
+//     Kc  = 4 / (h D),  D = 4 + d_x^2,
+//     gam = beta_x + 12 (1 + d_x^2) / (h^3 D),   beta = 6 d_x / (h^2 D),
+//     R   = -[(U0/h)_x + 2 d_x U0 / h^2 + 2 hw~ / h^2 + 2 phi' / h^2 + 2 d_t / h],
+//     U0  = hu~ + phi' d_x,
+//     phi'= dt h / D (g d_x eta_x - d_tt - 2 u d_xt - u^2 d_xx)   (= dt phi / rho, Eq. 5),
+// and the correction (Eqs. 10-11) is
+//     P'  = 6 psi / (h D) + d_x psi_x / D + phi',
+//     hu  = hu~ - psi_x + d_x P',   hw = hw~ + P',   h = h~.
+// rho only rescales the reported pressure p^nh = rho psi / (dt h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nhswe.h"
+
+namespace nh {
+
+constexpr int kPredTile = 256;   // cells per predictor CTA (multiple of 32)
+constexpr int kPredHalo = 5;     // two Heun stages + one cell for the criterion
+constexpr int kChunk = 256;      // active cells per solver work item (= blockDim)
+constexpr int kCompactThreads = 1024;
+
+// Per-member slide parameters (device copy of nh_slide_desc, FP64).
+struct Slide {
+    double A, L, xc0, s0, t0;
+    int shape;
+    int pad;
+};
+
+// Per-member slide kinematics at t^n and t^{n+1}: position s and, at t^{n+1},
+// its first and second time derivatives.
+struct Kin {
+    double s_n, s_n1, sd_n1, sdd_n1;
+};
+
+// Per-member solver scalars (FP64) and bookkeeping.
+struct MState {
+    double bnorm2;     // ||R||^2
+    double bnorm;      // ||R||
+    double rr;         // CG: <r,r>; BiCGStab: rho = <rhat, r>
+    double alpha, beta, omega;
+    double rel_res;
+    double min_gamma;
+    double snorm;      // BiCGStab: ||s|| of the current iteration
+    int status;        // nh_status
+    int iters;
+    int done;          // 1 once converged / failed
+    int kind;          // NH_SOLVER_CG or NH_SOLVER_BICGSTAB
+    int zero_sol;      // R == 0: solution is exactly zero
+    int s_conv;        // BiCGStab: converged on s this iteration
+    int n_active;
+    int nchunks;
+};
+
+// Counters shared by all members (device).
+struct Ctl {
+    int not_done;      // members still iterating
+    int n_cg, n_bicg;  // members per solver kind after set-up
+    int pad;
+};
+
+__device__ __forceinline__ int resolve(int j, int n, int bc, int* sgn)
+{
+    // In-domain cell for index j (|j| small beyond the ends); *sgn = -1 when a
+    // wall mirror flips odd quantities (u, hu, d_x, ...).
+    if (j >= 0 && j < n) { *sgn = 1; return j; }
+    if (bc == NH_BC_PERIODIC) { *sgn = 1; int r = j % n; return r < 0 ? r + n : r; }
+    *sgn = -1;
+    return j < 0 ? (-1 - j) : (2 * n - 1 - j);
+}
+
+template <typename T> __device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
+__device__ __forceinline__ double texp(double v) { return exp(v); }
+__device__ __forceinline__ float texp(float v) { return expf(v); }
+__device__ __forceinline__ double tsqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float tsqrt(float v) { return sqrtf(v); }
+
+// Depth at the centre of cell c (already resolved) with the mound at
+// displacement s: d = d0 - A exp(-xi^2), xi = (x_c - xc0 - s) / L.
+template <typename T>
+__device__ __forceinline__ T depth_at(const T* __restrict__ d0m, int c, double x0, double dx,
+                                      const Slide& sl, double s)
+{
+    T d = d0m[c];
+    if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
+        double xc = x0 + (c + 0.5) * dx;
+        T xi = T((xc - sl.xc0 - s) / sl.L);
+        d -= T(sl.A) * texp(-xi * xi);
+    }
+    return d;
+}
+
+template <typename T>
+struct Bottom {
+    T d, d_x, d_xx, d_t, d_xt, d_tt;
+};
+
+// Depth and its x/t derivatives at cell i (in the domain) at t^{n+1}: central
+// differences of d0 (ghosts mirrored or wrapped), analytic mound terms.
+template <typename T>
+__device__ __forceinline__ Bottom<T> bottom_full(const T* __restrict__ d0m, int i, int nx, int bc,
+                                                 double x0, double dx, const Slide& sl, const Kin& k)
+{
+    int sg;
+    int im = resolve(i - 1, nx, bc, &sg), ip = resolve(i + 1, nx, bc, &sg);
+    const T dxT = T(dx);
+    Bottom<T> B;
+    T a = d0m[im], c = d0m[i], e = d0m[ip];
+    B.d = c;
+    B.d_x = (e - a) / (T(2) * dxT);
+    B.d_xx = (e - T(2) * c + a) / (dxT * dxT);
+    B.d_t = T(0); B.d_xt = T(0); B.d_tt = T(0);
+    if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
+        const T L = T(sl.L);
+        double xc = x0 + (i + 0.5) * dx;
+        T xi = T((xc - sl.xc0 - k.s_n1) / sl.L);
+        T m = T(sl.A) * texp(-xi * xi);
+        T sd = T(k.sd_n1), sdd = T(k.sdd_n1);
+        T two_xi2m1 = T(2) * xi * xi - T(1);
+        T m_x = m * (T(-2) * xi / L);
+        T m_xx = m * (T(4) * xi * xi - T(2)) / (L * L);
+        T m_t = m * (T(2) * xi / L) * sd;
+        T m_xt = -m * (T(2) / (L * L)) * two_xi2m1 * sd;
+        T m_tt = m * (T(2) / (L * L)) * (two_xi2m1 * sd * sd + xi * L * sdd);
+        B.d -= m; B.d_x -= m_x; B.d_xx -= m_xx;
+        B.d_t = -m_t; B.d_xt = -m_xt; B.d_tt = -m_tt;
+    }
+    return B;
+}
+
+// Reductions ---------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum of NV doubles; result valid in thread 0.  `sh` needs
+// NV * 32 doubles.  Ends with __syncthreads() so `sh` can be reused.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = warp_sum(v[q]);
+        if (lane == 0) sh[q * 32 + wid] = s;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = (lane < nw) ? sh[q * 32 + lane] : 0.0;
+            v[q] = warp_sum(s);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_min(double v, double* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double s = warp_min(v);
+    if (lane == 0) sh[wid] = s;
+    __syncthreads();
+    if (wid == 0) {
+        double t = (lane < nw) ? sh[lane] : INFINITY;
+        v = warp_min(t);
+    }
+    __syncthreads();
+    return v;
+}
+
+}  // namespace nh

@@ -1,0 +1,260 @@
+"""Thin ctypes binding of the C ABI in ``include/nhswe.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The functions keep the C names (``nh_create_grid``, ``nh_step``, ...); the
+``Grid`` class adds the one thing Python must supply -- device memory for the
+workspace and the CUDA stream, both taken from PyTorch.
+
+``load()`` raises ``RuntimeError`` if the library is missing or no CUDA device
+is present: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# enums (mirror include/nhswe.h)
+NH_OK, NH_ERR_ARG, NH_ERR_CUDA, NH_ERR_NOT_CONVERGED, NH_ERR_NONFINITE, NH_ERR_TIMEOUT, NH_ERR_STATE = range(7)
+NH_BC_WALL, NH_BC_PERIODIC = 0, 1
+NH_FP64, NH_MIXED = 0, 1
+NH_LIM_NONE, NH_LIM_CENTRAL, NH_LIM_MINMOD, NH_LIM_MC = range(4)
+(NH_CRIT_GLOBAL, NH_CRIT_HYDROSTATIC, NH_CRIT_ETA_D, NH_CRIT_ETA_X, NH_CRIT_U, NH_CRIT_U_X,
+ NH_CRIT_W, NH_CRIT_W_X) = range(8)
+NH_SOLVER_AUTO, NH_SOLVER_CG, NH_SOLVER_BICGSTAB = range(3)
+NH_GUESS_ZERO, NH_GUESS_PREV = 0, 1
+NH_SLIDE_NONE, NH_SLIDE_GAUSS_LNCOSH = 0, 1
+
+# every exported symbol of the ABI (checked by the CPU test suite)
+EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion",
+           "nh_set_solver", "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run",
+           "nh_destroy", "nh_status_string")
+
+
+class nh_grid_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("nbatch", C.c_int), ("bc", C.c_int),
+                ("precision", C.c_int), ("limiter", C.c_int), ("dx", C.c_double),
+                ("x0", C.c_double), ("g", C.c_double), ("rho", C.c_double)]
+
+
+class nh_slide_desc(C.Structure):
+    _fields_ = [("shape", C.c_int), ("A", C.c_double), ("L", C.c_double), ("xc0", C.c_double),
+                ("s0", C.c_double), ("t0", C.c_double)]
+
+
+class nh_step_info(C.Structure):
+    _fields_ = [("step", C.c_longlong), ("t", C.c_double), ("n_active", C.c_longlong),
+                ("n_active_max", C.c_int), ("iters", C.c_int), ("ir_passes", C.c_int),
+                ("solver", C.c_int), ("status", C.c_int), ("rel_res", C.c_double),
+                ("min_gamma", C.c_double), ("mass", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class nh_run_info(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("iters_total", C.c_longlong),
+                ("active_total", C.c_longlong), ("last", nh_step_info)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+_D = C.POINTER(C.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_symbols_only(path: str | None = None):
+    """Open the shared library without touching a GPU (symbol checks)."""
+    return C.CDLL(path or _build.build())
+
+
+def load():
+    """Build (if needed) and load the CUDA library; raises without a GPU."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2505_17025_gb300 needs a CUDA GPU; no CPU fallback exists")
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = C.CDLL(path)
+        L.nh_workspace_bytes.argtypes = [C.POINTER(nh_grid_desc)]
+        L.nh_workspace_bytes.restype = C.c_size_t
+        L.nh_create_grid.argtypes = [C.POINTER(nh_grid_desc), _D, C.c_void_p, C.c_size_t, C.c_void_p,
+                                     C.POINTER(C.c_void_p)]
+        L.nh_set_bottom_motion.argtypes = [C.c_void_p, C.POINTER(nh_slide_desc)]
+        L.nh_set_criterion.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int]
+        L.nh_set_solver.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
+                                    C.c_double]
+        L.nh_set_state.argtypes = [C.c_void_p, _D, _D, _D, C.c_double]
+        L.nh_get_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
+        L.nh_get_mask.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), C.POINTER(C.c_int), _D]
+        L.nh_step.argtypes = [C.c_void_p, C.c_double, C.POINTER(nh_step_info)]
+        L.nh_run.argtypes = [C.c_void_p, C.c_double, C.c_longlong, C.POINTER(nh_run_info)]
+        L.nh_destroy.argtypes = [C.c_void_p]
+        L.nh_destroy.restype = None
+        L.nh_status_string.argtypes = [C.c_int]
+        L.nh_status_string.restype = C.c_char_p
+        for f in ("nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
+                  "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run"):
+            getattr(L, f).restype = C.c_int
+        _LIB = L
+        return L
+
+
+class NHError(RuntimeError):
+    def __init__(self, status, where):
+        msg = load().nh_status_string(status).decode()
+        super().__init__(f"{where}: {msg}")
+        self.status = status
+
+
+def _check(status, where):
+    if status != NH_OK:
+        raise NHError(status, where)
+    return status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+class Grid:
+    """A batch of 1D members on one GPU, stepping through the C ABI.
+
+    Parameters mirror ``nh_grid_desc``; ``d0`` is (nbatch, nx) or (nx,).
+    The workspace is a ``torch.uint8`` tensor on the current CUDA device and the
+    stream is ``torch.cuda.current_stream()`` unless one is given.
+    """
+
+    def __init__(self, nx, dx, d0, nbatch=1, x0=0.0, bc=NH_BC_WALL, precision=NH_FP64,
+                 limiter=NH_LIM_CENTRAL, g=9.81, rho=1000.0, stream=None):
+        import torch
+        self.L = load()
+        self.desc = nh_grid_desc(1, int(nx), int(nbatch), int(bc), int(precision), int(limiter),
+                                 float(dx), float(x0), float(g), float(rho))
+        self.nx, self.nb = int(nx), int(nbatch)
+        nbytes = self.L.nh_workspace_bytes(C.byref(self.desc))
+        if nbytes == 0:
+            raise NHError(NH_ERR_ARG, "nh_workspace_bytes")
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.ws.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d0 = np.broadcast_to(np.asarray(d0, dtype=np.float64).reshape(-1, self.nx), (self.nb, self.nx))
+        d0 = np.ascontiguousarray(d0)
+        h = C.c_void_p()
+        _check(self.L.nh_create_grid(C.byref(self.desc), _dptr(d0), C.c_void_p(self._ws_ptr),
+                                     C.c_size_t(nbytes), C.c_void_p(self.stream.cuda_stream),
+                                     C.byref(h)), "nh_create_grid")
+        self.h = h
+        self.workspace_bytes = nbytes
+
+    # -- configuration
+    def set_bottom_motion(self, slides):
+        """slides: list of dicts (shape, A, L, xc0, s0, t0) per member, or None."""
+        if slides is None:
+            _check(self.L.nh_set_bottom_motion(self.h, None), "nh_set_bottom_motion")
+            return
+        arr = (nh_slide_desc * self.nb)()
+        for b, s in enumerate(slides):
+            arr[b] = nh_slide_desc(int(s.get("shape", NH_SLIDE_GAUSS_LNCOSH)), float(s["A"]),
+                                   float(s["L"]), float(s["xc0"]), float(s["s0"]), float(s["t0"]))
+        _check(self.L.nh_set_bottom_motion(self.h, arr), "nh_set_bottom_motion")
+
+    def set_criterion(self, kind, k_nh=1e-3, enlarge=1, first_step_global=False):
+        _check(self.L.nh_set_criterion(self.h, int(kind), float(k_nh), int(enlarge),
+                                       int(bool(first_step_global))), "nh_set_criterion")
+
+    def set_solver(self, kind=NH_SOLVER_AUTO, rtol=1e-12, max_iter=20000, guess=NH_GUESS_PREV,
+                   ir_max=8, inner_rtol=1e-5):
+        _check(self.L.nh_set_solver(self.h, int(kind), float(rtol), int(max_iter), int(guess),
+                                    int(ir_max), float(inner_rtol)), "nh_set_solver")
+
+    # -- state
+    def set_state(self, h, hu, hw, t=0.0):
+        n = self.nx * self.nb
+        h, hu, hw = _f64(h, n), _f64(hu, n), _f64(hw, n)
+        _check(self.L.nh_set_state(self.h, _dptr(h), _dptr(hu), _dptr(hw), float(t)), "nh_set_state")
+
+    def set_state_ptr(self, h_ptr, hu_ptr, hw_ptr, t=0.0):
+        """Same as set_state from raw host addresses (e.g. pinned tensors)."""
+        _check(self.L.nh_set_state(self.h, C.cast(C.c_void_p(h_ptr), _D), C.cast(C.c_void_p(hu_ptr), _D),
+                                   C.cast(C.c_void_p(hw_ptr), _D), float(t)), "nh_set_state")
+
+    def get_state(self):
+        n = self.nx * self.nb
+        h, hu, hw, p = (np.empty(n) for _ in range(4))
+        _check(self.L.nh_get_state(self.h, _dptr(h), _dptr(hu), _dptr(hw), _dptr(p)), "nh_get_state")
+        sh = (self.nb, self.nx)
+        return h.reshape(sh), hu.reshape(sh), hw.reshape(sh), p.reshape(sh)
+
+    def get_state_ptr(self, h_ptr, hu_ptr=0, hw_ptr=0, p_ptr=0):
+        cast = lambda p: C.cast(C.c_void_p(p), _D) if p else None
+        _check(self.L.nh_get_state(self.h, cast(h_ptr), cast(hu_ptr), cast(hw_ptr), cast(p_ptr)),
+               "nh_get_state")
+
+    def get_mask(self):
+        m = np.empty(self.nx * self.nb, dtype=np.uint8)
+        it = np.empty(self.nb, dtype=np.int32)
+        rr = np.empty(self.nb)
+        _check(self.L.nh_get_mask(self.h, m.ctypes.data_as(C.POINTER(C.c_ubyte)),
+                                  it.ctypes.data_as(C.POINTER(C.c_int)), _dptr(rr)), "nh_get_mask")
+        return m.reshape(self.nb, self.nx), it, rr
+
+    # -- stepping
+    def step(self, dt, check=True):
+        info = nh_step_info()
+        st = self.L.nh_step(self.h, float(dt), C.byref(info))
+        if check:
+            _check(st, "nh_step")
+        return st, info.as_dict()
+
+    def run(self, dt, n_steps, check=True):
+        info = nh_run_info()
+        st = self.L.nh_run(self.h, float(dt), int(n_steps), C.byref(info))
+        if check:
+            _check(st, "nh_run")
+        return st, {"steps": info.steps, "iters_total": info.iters_total,
+                    "active_total": info.active_total, "last": info.last.as_dict()}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.nh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid_from_workload(wl, precision=NH_FP64, limiter=NH_LIM_CENTRAL, bc=None, **kw):
+    """A Grid holding every member of a ``workloads.Workload1D`` with its
+    bottom motion and initial state set."""
+    ms = wl.members
+    m0 = ms[0]
+    G = Grid(m0.nx, m0.dx, np.stack([m.d0 for m in ms]), nbatch=len(ms), x0=m0.xl,
+             bc=wl.bc if bc is None else bc, precision=precision, limiter=limiter, **kw)
+    if any(m.slide for m in ms):
+        G.set_bottom_motion([dict(shape=m.slide, A=m.A, L=m.L, xc0=m.xc0, s0=m.s0, t0=m.t0) for m in ms])
+    G.set_state(np.stack([m.h for m in ms]), np.stack([m.hu for m in ms]), np.stack([m.hw for m in ms]))
+    return G

@@ -1,0 +1,49 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/nhswe.h declares (no GPU needed: symbols only, no compute call)."""
+import ctypes
+import os
+import re
+
+from paper_2505_17025_gb300 import build as B
+from paper_2505_17025_gb300 import nhswe
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(nh_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(B.build())
+    declared = _declared()
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(nhswe.EXPORTS) <= declared
+
+
+def test_workspace_size_needs_no_gpu():
+    lib = ctypes.CDLL(B.build())
+    lib.nh_workspace_bytes.argtypes = [ctypes.POINTER(nhswe.nh_grid_desc)]
+    lib.nh_workspace_bytes.restype = ctypes.c_size_t
+    d = nhswe.nh_grid_desc(1, 50000, 64, 0, 0, 1, 8e-4, 0.0, 9.81, 1000.0)
+    n = lib.nh_workspace_bytes(ctypes.byref(d))
+    assert n > 64 * 50000 * 8 * 20
+    bad = nhswe.nh_grid_desc(1, 4, 1, 0, 0, 1, 8e-4, 0.0, 9.81, 1000.0)   # nx < 8
+    assert lib.nh_workspace_bytes(ctypes.byref(bad)) == 0
+    bad = nhswe.nh_grid_desc(1, 100, 1, 0, 0, 1, -1.0, 0.0, 9.81, 1000.0)  # dx <= 0
+    assert lib.nh_workspace_bytes(ctypes.byref(bad)) == 0
+
+
+def test_status_strings_need_no_gpu():
+    lib = ctypes.CDLL(B.build())
+    lib.nh_status_string.restype = ctypes.c_char_p
+    for s in range(7):
+        assert lib.nh_status_string(s).startswith(b"NH_")
