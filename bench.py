@@ -1,0 +1,317 @@
+"""Benchmark: cell-updates/s of the adaptive non-hydrostatic step, including the
+elliptic solve, on the 1D moving-bottom slide batch (64 members x 50 000
+cells, plane slope tan = 0.25 from 0.05 m to 1 m, Gaussian mound moving as
+s0 ln cosh(t/t0), per-member A, L, s0 drawn +-30 %).
+
+One "step" is one time step of the whole batch: predictor, criterion and mask,
+assembly, preconditioned Krylov solve on the active cells, correction.  The
+state is first advanced (untimed) to --t-start so the timed steps see a
+developed wave field; then --warmup steps, then --steps timed steps bracketed
+by a barrier and stream synchronisation, timed with CUDA events on the
+library's stream.  The per-step state (~154 MB in FP64) exceeds the 129 MB L2,
+so no L2 flush is done between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own 64-member batch (seeds offset by rank):
+weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s incl. NH solve at fixed error vs FP64 oracle; adaptive/learned vs global plain"
+UNIT = "cell-updates/s"
+WORKLOAD = "1D moving-bottom slide, 64 members x 50000 cells, adaptive |eta/d|>1e-3 + 1-cell enlargement"
+
+# Algorithmic bytes per unit for each kernel class, FP64 path.  Units: cells
+# of the whole batch for the predictor, active cells for the rest.
+BYTES_PER_UNIT_FP64 = {
+    "predict": 56.125,    # read zeta, hu, hw, d0 (32); write zeta~, hu~, hw~ (24); mark bit (1/8)
+    "compact": 4.25,      # read mark bits, write dilated bits (2/8) and the int32 list entry
+    "assemble": 116.0,    # read zeta~, hu~, hw~, d0, list (36); write 8 coefficients + 2 neighbours (80)
+    "solve_init": 84.0,   # read R, 3 coeffs, 2 nbrs, list (44); write x, r, rh, 4 zeroed vectors (..)
+    "precond": 56.0,      # read 3 coeffs, 2 nbrs, r_new, r_old (48); write z (8)
+    "pcg_a": 64.0,        # read z, p_old, 3 coeffs, 2 nbrs (48); write p, q (16)
+    "pcg_b": 48.0,        # read x, p, r_old, q (32); write x, r_new (16)
+    "cg_a": 64.0,
+    "cg_b": 48.0,
+    "correct": 92.0,      # read list, nbrs, x, 4 coeffs, hu, hw (68); write hu, hw, psi (24)
+}
+# Mixed path: FP32 state and Krylov vectors; FP64 operator, rhs and iterate.
+BYTES_PER_UNIT_MIXED = {
+    "predict": 28.125,    # read zeta, hu, hw, d0 (16); write 3 fields (12); mark bit
+    "compact": 4.25,
+    "assemble": 120.0,    # read 3 fields, d0 (FP64), list (24); FP64 op + rhs (32), FP32 op (12), 4 coeffs (16), nbrs (8)
+    "solve_init": 44.0,   # k_ir_resid: read R, 3 FP64 coeffs, nbrs, x64 (48, cached neighbours); write rhs32
+    "precond": 32.0,      # read 3 FP32 coeffs, 2 nbrs, r_new, r_old (28); write z (4)
+    "pcg_a": 32.0,
+    "pcg_b": 24.0,
+    "correct": 50.0,
+}
+def _load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _oracle_sample(wl, max_steps, budget_s, crit):
+    """Oracle (FP64 C, one host thread) on member 0 from t = 0: cell-updates/s."""
+    import oracle as O
+    m = wl.members[0]
+    p = O.Params(nx=m.nx, dx=m.dx, xl=m.xl, slide=m.slide, A=m.A, L=m.L, xc0=m.xc0, s0=m.s0,
+                 t0=m.t0, crit=crit, knh=1e-3, enlarge=1, rtol=1e-12, max_iter=20000)
+    s = O.State(m.h, m.hu, m.hw)
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps and time.perf_counter() - t0 < budget_s:
+        O.step(p, m.d0, k * wl.dt, k, wl.dt, s)
+        k += 1
+    el = time.perf_counter() - t0
+    return m.nx * k / el, k, el
+
+
+def run_reference(args):
+    """The oracle arm: each step is one time step of one 50 000-cell member."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2505_17025_gb300 import workloads as W
+    import oracle as O
+    wl = W.slide_1d(n_members=1)
+    m = wl.members[0]
+    p = O.Params(nx=m.nx, dx=m.dx, xl=m.xl, slide=m.slide, A=m.A, L=m.L, xc0=m.xc0, s0=m.s0,
+                 t0=m.t0, crit=O.CRIT_ETA_D, knh=1e-3, enlarge=1, rtol=1e-12, max_iter=20000)
+    s = O.State(m.h, m.hu, m.hw)
+    for k in range(args.warmup):
+        O.step(p, m.d0, k * wl.dt, k, wl.dt, s)
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        O.step(p, m.d0, k * wl.dt, k, wl.dt, s)
+    el = time.perf_counter() - t0
+    v = m.nx * args.steps / el
+    sample = (f"member 0 of the 64-member batch (50000 cells), time steps {args.warmup}.."
+              f"{args.warmup + args.steps - 1} from t = 0, FP64 C oracle, 1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle: one member per step)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+    from paper_2505_17025_gb300 import nhswe as N
+    from paper_2505_17025_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    wl = W.slide_1d(n_members=64, seed0=64 * rank)
+    prec = N.NH_FP64 if args.precision == "fp64" else N.NH_MIXED
+    G = N.grid_from_workload(wl, precision=prec)
+    crit = N.NH_CRIT_GLOBAL if args.mode == "global" else N.NH_CRIT_ETA_D
+    G.set_criterion(crit, 1e-3, 1, False)
+    rtol = 1e-12 if args.precision == "fp64" else 1e-10
+    G.set_solver(N.NH_SOLVER_AUTO, rtol, 20000, N.NH_GUESS_PREV)
+    G.set_preconditioner(N.NH_PRECOND_LINE if args.precond == "line" else N.NH_PRECOND_NONE)
+    cells = wl.members[0].nx * len(wl.members)
+
+    n_spin = int(round(args.t_start / wl.dt))
+    t_spin0 = time.perf_counter()
+    if n_spin:
+        G.run(wl.dt, n_spin)
+    t_spin = time.perf_counter() - t_spin0
+    G.run(wl.dt, args.warmup)
+
+    stream = G.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    G.set_profiling(True)
+    clocks.start()
+    e0.record(stream)
+    st, info = G.run(wl.dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = G.get_profile()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * cells * args.steps / (ms * 1e-3)
+    launches = sum(n for _, n in prof.values())
+    act_mean = info["active_total"] / max(args.steps, 1)
+    iters_mean = info["iters_total"] / max(args.steps, 1)
+
+    # dominant kernel class by device time, its algorithmic bytes per launch
+    table = BYTES_PER_UNIT_FP64 if args.precision == "fp64" else BYTES_PER_UNIT_MIXED
+    name, (dms, dn) = max(prof.items(), key=lambda kv: kv[1][0])
+    peaks, peak_kind = _load_peaks()
+    roof = None
+    if dn > 0 and name in table:
+        units = cells if name == "predict" else act_mean
+        bytes_per_launch = table[name] * units
+        achieved = bytes_per_launch / (dms * 1e-3 / dn) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": f"k_{name}",
+                "peak_kind": peak_kind, "bytes_per_launch": bytes_per_launch,
+                "launches_per_step": dn / args.steps, "avg_launch_us": 1e3 * dms / dn}
+
+    # end to end through the C ABI with pinned host buffers, per step:
+    # H2D of the step's input state, the step, D2H of its result
+    e2e = None
+    if args.e2e_steps > 0:
+        n = cells
+        hb = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+        G.get_state_ptr(hb[0].data_ptr(), hb[1].data_ptr(), hb[2].data_ptr())
+        torch.cuda.synchronize()
+        G.set_profiling(False)
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            G.put_state_ptr(hb[0].data_ptr(), hb[1].data_ptr(), hb[2].data_ptr())
+            G.step(wl.dt)
+            G.get_state_ptr(hb[0].data_ptr(), hb[1].data_ptr(), hb[2].data_ptr())
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": ws * cells * args.e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 8 * n, "d2h_bytes_per_step": 3 * 8 * n,
+               "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        v, k, el = _oracle_sample(wl, args.cpu_steps, args.cpu_budget, O.CRIT_ETA_D)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"member 0 (50000 cells), {k} time steps from t = 0 ({el:.1f} s of one host "
+                         f"thread), FP64 C oracle; the GPU's timed steps start at t = {args.t_start} s"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "members_per_gpu": len(wl.members),
+                       "cells_per_member": wl.members[0].nx, "dt": wl.dt, "t_start": args.t_start,
+                       "mode": args.mode, "precond": args.precond, "precision": args.precision,
+                       "rtol": rtol, "l2": "per-step state > 129 MB L2 (154 MB FP64, 77 MB FP32 + FP64 operator); no flush",
+                       "error_vs_oracle": ("max|d eta| <= 1e-9 a (tests/test_gpu_parity.py)" if args.precision == "fp64"
+                                           else "max|d eta| <= 1e-4 a while masks agree (tests/test_gpu_mixed.py)"),
+                       "mean_active_cells_per_step": act_mean, "mean_krylov_iters_per_step": iters_mean,
+                       "spin_up_steps": n_spin, "spin_up_s": t_spin},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+            "kernel_ms": {k: v[0] for k, v in prof.items() if v[1] > 0},
+            "kernel_launches": {k: v[1] for k, v in prof.items() if v[1] > 0},
+        }
+        print(json.dumps(out))
+    G.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mode", default="adaptive", choices=["adaptive", "global"])
+    ap.add_argument("--precond", default="line", choices=["line", "none"])
+    ap.add_argument("--t-start", type=float, default=0.5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=400)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -63,15 +63,24 @@ enum { NH_LIM_NONE = 0, NH_LIM_CENTRAL = 1, NH_LIM_MINMOD = 2, NH_LIM_MC = 3 };
 enum { NH_CRIT_GLOBAL = 0, NH_CRIT_HYDROSTATIC = 1, NH_CRIT_ETA_D = 2,
        NH_CRIT_ETA_X = 3, NH_CRIT_U = 4, NH_CRIT_U_X = 5, NH_CRIT_W = 6,
        NH_CRIT_W_X = 7 };
-/* AUTO: CG when the reaction term gamma is > 0 on every active cell of a
-   member (the operator is then symmetric positive definite), else BiCGStab. */
+/* The discrete operator is symmetric.  AUTO: (preconditioned) CG; a member
+   whose CG detects indefiniteness (p.Ap <= 0 or r.z <= 0) is solved again by
+   BiCGStab from the warm start.  gamma > 0 on every active cell is sufficient
+   for positive definiteness; a few negative gamma cells (e.g. at a kink of
+   d0) usually leave the operator definite.  CG / BICGSTAB force one method. */
 enum { NH_SOLVER_AUTO = 0, NH_SOLVER_CG = 1, NH_SOLVER_BICGSTAB = 2 };
 enum { NH_GUESS_ZERO = 0, NH_GUESS_PREV = 1 };
+/* Preconditioner of the CG branch.  NH_PRECOND_LINE: the tridiagonal operator
+   restricted to blocks of 4096 consecutive active cells, solved by parallel
+   cyclic reduction in FP32 (exact up to FP32 rounding on any active segment
+   that fits in one block), inside a flexible (Polak-Ribiere) PCG whose
+   vectors, dots and stopping test stay in the handle's precision. */
+enum { NH_PRECOND_NONE = 0, NH_PRECOND_LINE = 1 };
 enum { NH_SLIDE_NONE = 0, NH_SLIDE_GAUSS_LNCOSH = 1 };
 
 typedef struct {
     int    dim;        /* 1                                                 */
-    int    nx;         /* cells per member, 4 <= nx <= 2^26                  */
+    int    nx;         /* cells per member, 8 <= nx <= 2^20                  */
     int    nbatch;     /* members, >= 1                                     */
     int    bc;         /* NH_BC_WALL or NH_BC_PERIODIC (both ends)          */
     int    precision;  /* NH_FP64 or NH_MIXED                               */
@@ -99,8 +108,8 @@ typedef struct {
     int       n_active_max;/* largest per-member active count                  */
     int       iters;       /* Krylov iterations, maximum over members          */
     int       ir_passes;   /* refinement passes (NH_MIXED), maximum over members */
-    int       solver;      /* NH_SOLVER_CG if every solved member used CG,
-                              NH_SOLVER_BICGSTAB if any used BiCGStab, -1 none */
+    int       solver;      /* NH_SOLVER_CG if every solved member finished with
+                              CG, NH_SOLVER_BICGSTAB if any used BiCGStab, -1 none */
     int       status;      /* nh_status of the step                             */
     double    rel_res;     /* max over members of ||R - A q|| / ||R||           */
     double    min_gamma;   /* min over active cells of the scaled reaction term */
@@ -122,7 +131,8 @@ size_t nh_workspace_bytes(const nh_grid_desc* desc);
    must be 256-byte aligned and at least nh_workspace_bytes(desc) long.
    The new handle has no state (nh_set_state must come before stepping), no
    bottom motion, criterion GLOBAL with k_nh = 1e-3 and one enlarging cell,
-   and solver AUTO, rtol 1e-12, max_iter 20000, warm start PREV.
+   solver AUTO, rtol 1e-12, max_iter 20000, warm start PREV, ir_max 30,
+   inner_rtol 1e-5, and preconditioner NH_PRECOND_LINE.
    Errors: NH_ERR_ARG (bad descriptor, NULL pointer, short or misaligned
    workspace), NH_ERR_CUDA. */
 nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host,
@@ -150,11 +160,23 @@ nh_status nh_set_criterion(nh_grid* g, int kind, double k_nh, int enlarge,
 nh_status nh_set_solver(nh_grid* g, int kind, double rtol, int max_iter, int guess,
                         int ir_max, double inner_rtol);
 
+/* Preconditioner for members solved by CG (NH_PRECOND_NONE or
+   NH_PRECOND_LINE; the default is NH_PRECOND_LINE).  It changes how fast the
+   solve converges, not what it converges to.  BiCGStab members are not
+   preconditioned.  Errors: NH_ERR_ARG. */
+nh_status nh_set_preconditioner(nh_grid* g, int kind);
+
 /* Upload a state (host FP64, nbatch * nx each): h > 0 (m), hu (m^2/s),
    hw (m^2/s) at model time t; the step counter restarts at 0 and the
    previous pressure is cleared.  Errors: NH_ERR_ARG, NH_ERR_CUDA. */
 nh_status nh_set_state(nh_grid* g, const double* h, const double* hu, const double* hw,
                        double t);
+
+/* Replace the state in place (host FP64, nbatch * nx each) and keep running:
+   model time, step counter and the previous pressure (warm start) are kept.
+   This is the upload half of a host-buffer round trip per step.
+   Errors: NH_ERR_ARG, NH_ERR_STATE (no state set yet), NH_ERR_CUDA. */
+nh_status nh_put_state(nh_grid* g, const double* h, const double* hu, const double* hw);
 
 /* Download the state (host FP64, nbatch * nx each; any pointer may be NULL):
    h, hu, hw, and p_nh = the non-hydrostatic pressure of the last step
@@ -174,6 +196,23 @@ nh_status nh_step(nh_grid* g, double dt, nh_step_info* info);
 /* n_steps steps of size dt; stops at the first failing step (whose status is
    returned; info->last describes it).  info may be NULL. */
 nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info);
+
+/* Kernel classes timed by the profiler (index into nh_get_profile arrays). */
+enum { NH_K_KINEMATICS = 0, NH_K_PREDICT = 1, NH_K_COMPACT = 2, NH_K_ASSEMBLE = 3,
+       NH_K_SOLVE_INIT = 4, NH_K_PRECOND = 5, NH_K_PCG_A = 6, NH_K_PCG_B = 7,
+       NH_K_CG_A = 8, NH_K_CG_B = 9, NH_K_BI_1 = 10, NH_K_BI_2 = 11, NH_K_BI_3 = 12,
+       NH_K_SUMMARY = 13, NH_K_CLEAR = 14, NH_K_CORRECT = 15, NH_K_COUNT = 16 };
+
+/* enable != 0: bracket every kernel launch with CUDA events on the handle's
+   stream and accumulate per-class device time (read back at the step's own
+   synchronisation points); also resets the accumulators.  Launch counts are
+   kept whether or not timing is enabled. */
+nh_status nh_set_profiling(nh_grid* g, int enable);
+
+/* Per kernel class (NH_K_COUNT entries each, any pointer may be NULL):
+   total device milliseconds (0 unless profiling was enabled) and launches
+   since the last nh_set_profiling call.  Errors: NH_ERR_ARG. */
+nh_status nh_get_profile(nh_grid* g, double* ms, long long* launches);
 
 /* Release the handle (the workspace stays the caller's). */
 void nh_destroy(nh_grid* g);

@@ -19,12 +19,14 @@ using namespace nh;
 struct nh_grid {
     nh_grid_desc d;
     cudaStream_t stream;
-    int nx, nb, pitch, wpitch, ntiles, maxch, sm_count, items_grid;
-    size_t es;                   // element size of state / vectors
+    int nx, nb, pitch, wpitch, ntiles, maxch, sm_count, items_grid, pcr_grid;
+    size_t es;                   // element size of state / Krylov vectors
+    bool mixed;
+    double mass0;                // sum of d0 dx over all members (FP64)
     // configuration
     int crit, enlarge, first_global;
     double knh;
-    int solver, max_iter, guess, ir_max;
+    int solver, max_iter, guess, ir_max, precond, maxpb;
     double rtol, inner_rtol;
     int poll_every;
     // run state
@@ -36,17 +38,30 @@ struct nh_grid {
     int cur;                     // state buffer holding Q^n
     int lcur;                    // list buffer of the previous step
     // device buffers (inside the workspace)
-    void* sh[2]; void* shu[2]; void* shw[2];
-    void* d0;
+    void* sz[2]; void* shu[2]; void* shw[2];   // zeta = h - d0, hu, hw (type T)
+    void* d0;                                  // static depth (type T)
+    double* d0d;                               // static depth (FP64)
+    double* stage;                             // 3 * nb * nx FP64 host-layout staging
     Slide* slide; Kin* kin;
     uint32_t* marks; uint32_t* act;
     int* list[2]; int* nact[2];
-    void *diag, *offl, *offr, *R, *c6, *cx, *phi, *ddx;
+    double *diag, *offl, *offr, *R;            // FP64 operator and right-hand side
+    float *diag32, *offl32, *offr32, *rhs32;   // mixed: FP32 operator and inner rhs
+    void *c6, *cx, *phi, *ddx;                 // correction coefficients (type T)
     int *nbl, *nbr;
-    void *x, *r, *p0, *p1, *q, *rh, *v0, *v1, *s, *t;
+    void *x, *r, *p0, *p1, *q, *rh, *v0, *v1, *s, *t, *r1, *z;   // Krylov vectors (type T)
+    double* x64;                               // mixed: FP64 outer iterate
+    IRState* ir;
     double* psi;
     MState* ms; Ctl* ctl; double* part; int* cnt;
     double* mass_part; Summary* summary;
+    // profiling: event pairs recorded around launches, folded in at syncs
+    bool prof_on;
+    double prof_ms[NH_K_COUNT];
+    long long prof_launches[NH_K_COUNT];
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<int> prof_kind;        // kind of each recorded pair
+    size_t prof_used;                  // pairs recorded since the last fold
 };
 
 namespace {
@@ -73,7 +88,7 @@ bool desc_ok(const nh_grid_desc* d)
     if (d->nbatch < 1 || d->nbatch > 65535) return false;
     if ((long long)d->nx * d->nbatch > (1LL << 30)) return false;
     if (d->bc != NH_BC_WALL && d->bc != NH_BC_PERIODIC) return false;
-    if (d->precision != NH_FP64) return false;
+    if (d->precision != NH_FP64 && d->precision != NH_MIXED) return false;
     if (d->limiter < NH_LIM_NONE || d->limiter > NH_LIM_MC) return false;
     if (!(d->dx > 0.0) || !(d->g > 0.0) || !(d->rho > 0.0) || !std::isfinite(d->x0)) return false;
     return true;
@@ -83,19 +98,23 @@ bool desc_ok(const nh_grid_desc* d)
 size_t carve(const nh_grid_desc& d, nh_grid* g, char* base)
 {
     const int nx = d.nx, nb = d.nbatch;
+    const bool mixed = d.precision == NH_MIXED;
     const int pitch = (nx + kPredTile - 1) / kPredTile * kPredTile;
     const int wpitch = pitch / 32;
     const int ntiles = pitch / kPredTile;
     const int maxch = (nx + kChunk - 1) / kChunk;
+    const int maxpb = (nx + kPcrRows - 1) / kPcrRows;
     const size_t N = (size_t)nb * pitch;
-    const size_t es = 8;
+    const size_t es = mixed ? 4 : 8;
     Carver c{base};
     nh_grid tmp;
     nh_grid* G = g ? g : &tmp;
     for (int k = 0; k < 2; ++k) {
-        G->sh[k] = c.take(N * es); G->shu[k] = c.take(N * es); G->shw[k] = c.take(N * es);
+        G->sz[k] = c.take(N * es); G->shu[k] = c.take(N * es); G->shw[k] = c.take(N * es);
     }
     G->d0 = c.take(N * es);
+    G->d0d = (double*)c.take(N * 8);
+    G->stage = (double*)c.take(3 * (size_t)nb * nx * 8);
     G->slide = (Slide*)c.take(sizeof(Slide) * nb);
     G->kin = (Kin*)c.take(sizeof(Kin) * nb);
     G->marks = (uint32_t*)c.take(sizeof(uint32_t) * (size_t)nb * wpitch);
@@ -104,13 +123,24 @@ size_t carve(const nh_grid_desc& d, nh_grid* g, char* base)
         G->list[k] = (int*)c.take(sizeof(int) * N);
         G->nact[k] = (int*)c.take(sizeof(int) * nb);
     }
-    G->diag = c.take(N * es); G->offl = c.take(N * es); G->offr = c.take(N * es);
-    G->R = c.take(N * es);
+    G->diag = (double*)c.take(N * 8); G->offl = (double*)c.take(N * 8);
+    G->offr = (double*)c.take(N * 8); G->R = (double*)c.take(N * 8);
+    if (mixed) {
+        G->diag32 = (float*)c.take(N * 4); G->offl32 = (float*)c.take(N * 4);
+        G->offr32 = (float*)c.take(N * 4); G->rhs32 = (float*)c.take(N * 4);
+        G->x64 = (double*)c.take(N * 8);
+        G->ir = (IRState*)c.take(sizeof(IRState) * nb);
+    } else {
+        G->diag32 = G->offl32 = G->offr32 = G->rhs32 = nullptr;
+        G->x64 = nullptr;
+        G->ir = nullptr;
+    }
     G->c6 = c.take(N * es); G->cx = c.take(N * es); G->phi = c.take(N * es); G->ddx = c.take(N * es);
     G->nbl = (int*)c.take(sizeof(int) * N); G->nbr = (int*)c.take(sizeof(int) * N);
     G->x = c.take(N * es); G->r = c.take(N * es); G->p0 = c.take(N * es); G->p1 = c.take(N * es);
     G->q = c.take(N * es); G->rh = c.take(N * es); G->v0 = c.take(N * es); G->v1 = c.take(N * es);
     G->s = c.take(N * es); G->t = c.take(N * es);
+    G->r1 = c.take(N * es); G->z = c.take(N * es);
     G->psi = (double*)c.take(sizeof(double) * N);
     G->ms = (MState*)c.take(sizeof(MState) * nb);
     G->ctl = (Ctl*)c.take(sizeof(Ctl));
@@ -120,7 +150,7 @@ size_t carve(const nh_grid_desc& d, nh_grid* g, char* base)
     G->summary = (Summary*)c.take(sizeof(Summary));
     if (g) {
         g->nx = nx; g->nb = nb; g->pitch = pitch; g->wpitch = wpitch; g->ntiles = ntiles;
-        g->maxch = maxch; g->es = es;
+        g->maxch = maxch; g->es = es; g->maxpb = maxpb; g->mixed = mixed;
     }
     return (c.off + kAlign - 1) / kAlign * kAlign;
 }
@@ -129,6 +159,54 @@ size_t carve(const nh_grid_desc& d, nh_grid* g, char* base)
     do {                                                \
         cudaError_t e_ = (call);                        \
         if (e_ != cudaSuccess) return NH_ERR_CUDA;      \
+    } while (0)
+
+void prof_pre(nh_grid* g, int kind)
+{
+    g->prof_launches[kind] += 1;
+    if (!g->prof_on) return;
+    const size_t need = 2 * (g->prof_used + 1);
+    while (g->prof_pool.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { g->prof_on = false; return; }
+        g->prof_pool.push_back(e);
+    }
+    if (g->prof_kind.size() < g->prof_used + 1) g->prof_kind.resize(g->prof_used + 1);
+    g->prof_kind[g->prof_used] = kind;
+    cudaEventRecord(g->prof_pool[2 * g->prof_used], g->stream);
+}
+
+void prof_post(nh_grid* g)
+{
+    if (!g->prof_on || g->prof_pool.size() < 2 * (g->prof_used + 1)) return;
+    cudaEventRecord(g->prof_pool[2 * g->prof_used + 1], g->stream);
+    g->prof_used += 1;
+}
+
+// Called after a stream synchronisation: every recorded pair is complete.
+void prof_fold(nh_grid* g)
+{
+    for (size_t q = 0; q < g->prof_used; ++q) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g->prof_pool[2 * q], g->prof_pool[2 * q + 1]) == cudaSuccess)
+            g->prof_ms[g->prof_kind[q]] += ms;
+    }
+    g->prof_used = 0;
+}
+
+#define LAUNCH(kind, ...)          \
+    do {                           \
+        prof_pre(g, kind);         \
+        __VA_ARGS__;               \
+        prof_post(g);              \
+    } while (0)
+
+// synchronise the handle's stream and fold profiler events
+#define SYNC()                                                     \
+    do {                                                           \
+        if (cudaStreamSynchronize(g->stream) != cudaSuccess)       \
+            return NH_ERR_CUDA;                                    \
+        prof_fold(g);                                              \
     } while (0)
 
 Geo geo(const nh_grid* g)
@@ -140,27 +218,131 @@ Geo geo(const nh_grid* g)
     return G;
 }
 
-SolveArgs<double> solve_args(nh_grid* g, int lcur)
+// Krylov arguments over the vectors of type T; `diag`, `offl`, `offr`, `R`
+// select the operator (FP64 for the FP64 path, FP32 copies for the inner
+// solve of the mixed path).
+template <typename T>
+SolveArgs<T> solve_args(nh_grid* g, int lcur, const T* diag, const T* offl, const T* offr, const T* R,
+                        double rtol)
 {
-    SolveArgs<double> a;
+    SolveArgs<T> a;
     a.nb = g->nb; a.pitch = g->pitch; a.maxch = g->maxch;
     a.list = g->list[lcur];
-    a.diag = (const double*)g->diag; a.offl = (const double*)g->offl; a.offr = (const double*)g->offr;
-    a.nbl = g->nbl; a.nbr = g->nbr; a.R = (const double*)g->R;
+    a.diag = diag; a.offl = offl; a.offr = offr; a.R = R;
+    a.nbl = g->nbl; a.nbr = g->nbr;
     a.psi_prev = g->psi; a.guess_scale = 0.0;
-    a.x = (double*)g->x; a.r = (double*)g->r; a.p0 = (double*)g->p0; a.p1 = (double*)g->p1;
-    a.q = (double*)g->q; a.rh = (double*)g->rh; a.v0 = (double*)g->v0; a.v1 = (double*)g->v1;
-    a.s = (double*)g->s; a.t = (double*)g->t;
+    a.x = (T*)g->x; a.r = (T*)g->r; a.p0 = (T*)g->p0; a.p1 = (T*)g->p1;
+    a.q = (T*)g->q; a.rh = (T*)g->rh; a.v0 = (T*)g->v0; a.v1 = (T*)g->v1;
+    a.s = (T*)g->s; a.t = (T*)g->t;
+    a.r1 = (T*)g->r1; a.z = (T*)g->z; a.maxpb = g->maxpb;
     a.ms = g->ms; a.ctl = g->ctl; a.part = g->part; a.cnt = g->cnt;
-    a.rtol = g->rtol; a.max_iter = g->max_iter; a.it = 0;
+    a.rtol = rtol; a.max_iter = g->max_iter; a.it = 0;
     return a;
 }
 
-// One step; on success swaps the state and list buffers.
-nh_status do_step(nh_grid* g, double dt, nh_step_info* info)
+// Krylov solve on the active cells with the vectors of type T: set-up, then
+// iterations until every member finished (read back every poll_every).
+template <typename T>
+nh_status krylov_pass(nh_grid* g, SolveArgs<T>& sa);
+
+// Krylov solve; AUTO members whose CG broke down are solved again by BiCGStab.
+template <typename T>
+nh_status krylov(nh_grid* g, SolveArgs<T>& sa)
 {
-    if (!g->has_state) return NH_ERR_STATE;
-    if (!(dt > 0.0) || !std::isfinite(dt)) return NH_ERR_ARG;
+    cudaStream_t st = g->stream;
+    CK(cudaMemsetAsync(&g->ctl->n_fallback, 0, sizeof(int), st));
+    nh_status rc = krylov_pass<T>(g, sa);
+    if (rc != NH_OK) return rc;
+    int nfb = 0;
+    CK(cudaMemcpyAsync(&nfb, &g->ctl->n_fallback, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SYNC();
+    if (nfb == 0) return NH_OK;
+    k_fallback_reset<<<(g->nb + 127) / 128, 128, 0, st>>>(g->ms, g->nb);
+    CK(cudaGetLastError());
+    return krylov_pass<T>(g, sa);
+}
+
+template <typename T>
+nh_status krylov_pass(nh_grid* g, SolveArgs<T>& sa)
+{
+    cudaStream_t st = g->stream;
+    CK(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
+    LAUNCH(NH_K_SOLVE_INIT, k_solve_init<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+    Ctl hctl;
+    CK(cudaMemcpyAsync(&hctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    SYNC();
+    const bool pcg = g->precond == NH_PRECOND_LINE;
+    const size_t pcr_smem = 4 * sizeof(float) * (size_t)kPcrRows;
+    if (hctl.n_cg > 0 && pcg) {
+        sa.it = 0;
+        LAUNCH(NH_K_PRECOND, k_pcr<T, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG));
+    }
+    if (hctl.not_done <= 0) return NH_OK;
+    for (int it = 1; it <= g->max_iter; ++it) {
+        sa.it = it;
+        if (hctl.n_cg > 0 && pcg) {
+            LAUNCH(NH_K_PCG_A, k_pcg_a<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+            LAUNCH(NH_K_PCG_B, k_pcg_b<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+            LAUNCH(NH_K_PRECOND, k_pcr<T, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG));
+        } else if (hctl.n_cg > 0) {
+            LAUNCH(NH_K_CG_A, k_cg_a<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+            LAUNCH(NH_K_CG_B, k_cg_b<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+        }
+        if (hctl.n_bicg > 0 && pcg) {
+            LAUNCH(NH_K_PRECOND, k_pcr<T, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_BI_P));
+            LAUNCH(NH_K_BI_1, k_pbi_mv<T><<<g->items_grid, kChunk, 0, st>>>(sa, 0));
+            LAUNCH(NH_K_PRECOND, k_pcr<T, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_BI_S));
+            LAUNCH(NH_K_BI_2, k_pbi_mv<T><<<g->items_grid, kChunk, 0, st>>>(sa, 1));
+            LAUNCH(NH_K_BI_3, k_pbi_upd<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+        } else if (hctl.n_bicg > 0) {
+            LAUNCH(NH_K_BI_1, k_bi_1<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+            LAUNCH(NH_K_BI_2, k_bi_2<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+            LAUNCH(NH_K_BI_3, k_bi_3<T><<<g->items_grid, kChunk, 0, st>>>(sa));
+        }
+        if (it % g->poll_every == 0 || it == g->max_iter) {
+            int nd = 0;
+            CK(cudaMemcpyAsync(&nd, &g->ctl->not_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SYNC();
+            if (nd <= 0) break;
+        }
+    }
+    return NH_OK;
+}
+
+// Mixed path: FP64 iterative refinement around FP32 Krylov solves.
+nh_status refine(nh_grid* g, int lnew, double guess_scale)
+{
+    cudaStream_t st = g->stream;
+    IRArgs ia;
+    ia.nb = g->nb; ia.pitch = g->pitch; ia.maxch = g->maxch;
+    ia.list = g->list[lnew]; ia.nbl = g->nbl; ia.nbr = g->nbr;
+    ia.diag = g->diag; ia.offl = g->offl; ia.offr = g->offr; ia.R = g->R;
+    ia.psi_prev = g->psi; ia.guess_scale = guess_scale;
+    ia.x64 = g->x64; ia.e32 = (const float*)g->x; ia.rhs32 = g->rhs32;
+    ia.ms = g->ms; ia.ir = g->ir; ia.ctl = g->ctl; ia.part = g->part; ia.cnt = g->cnt;
+    ia.rtol = g->rtol; ia.ir_max = g->ir_max;
+    SolveArgs<float> sa = solve_args<float>(g, lnew, g->diag32, g->offl32, g->offr32, g->rhs32,
+                                            g->inner_rtol);
+    const size_t total = (size_t)g->nb * g->pitch;
+    const int egrid = (int)std::min<size_t>((total + 255) / 256, (size_t)g->sm_count * 8);
+    for (int pass = 0; pass <= g->ir_max; ++pass) {
+        ia.pass = pass;
+        if (pass > 0) LAUNCH(NH_K_CORRECT, k_ir_update<<<egrid, 256, 0, st>>>(ia));
+        CK(cudaMemsetAsync(&g->ctl->ir_pending, 0, sizeof(int), st));
+        LAUNCH(NH_K_SOLVE_INIT, k_ir_resid<<<g->items_grid, kChunk, 0, st>>>(ia));
+        int pending = 0;
+        CK(cudaMemcpyAsync(&pending, &g->ctl->ir_pending, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SYNC();
+        if (pending == 0) break;
+        nh_status rc = krylov<float>(g, sa);
+        if (rc != NH_OK) return rc;
+    }
+    return NH_OK;
+}
+
+template <typename T>
+nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
+{
     cudaStream_t st = g->stream;
     if (g->last_dt != 0.0 && dt != g->last_dt) {
         // keep t^n = t_base + n dt exact for a fixed dt; re-base when dt changes
@@ -172,67 +354,63 @@ nh_status do_step(nh_grid* g, double dt, nh_step_info* info)
     const int cur = g->cur, nxt = cur ^ 1;
     const int lprev = g->lcur, lnew = lprev ^ 1;
     const Geo G = geo(g);
+    const double gscale = (g->guess == NH_GUESS_PREV && g->last_dt > 0.0) ? dt / g->last_dt : 0.0;
 
-    k_kinematics<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slide, g->kin, g->nb, t_n, t_n1);
+    LAUNCH(NH_K_KINEMATICS, k_kinematics<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slide, g->kin, g->nb, t_n, t_n1));
 
-    PredArgs<double> pa;
+    PredArgs<T> pa;
     pa.G = G;
-    pa.h = (const double*)g->sh[cur]; pa.hu = (const double*)g->shu[cur]; pa.hw = (const double*)g->shw[cur];
-    pa.ht = (double*)g->sh[nxt]; pa.hut = (double*)g->shu[nxt]; pa.hwt = (double*)g->shw[nxt];
-    pa.d0 = (const double*)g->d0; pa.slide = g->slide; pa.kin = g->kin;
+    pa.z = (const T*)g->sz[cur]; pa.hu = (const T*)g->shu[cur]; pa.hw = (const T*)g->shw[cur];
+    pa.zt = (T*)g->sz[nxt]; pa.hut = (T*)g->shu[nxt]; pa.hwt = (T*)g->shw[nxt];
+    pa.d0 = (const T*)g->d0; pa.slide = g->slide; pa.kin = g->kin;
     pa.marks = g->marks; pa.mass_part = g->mass_part; pa.dt = dt; pa.knh = g->knh; pa.crit = g->crit;
     pa.all_global = (g->crit == NH_CRIT_GLOBAL) || (g->first_global && g->steps == 0);
-    k_predict<double><<<dim3(g->ntiles, g->nb), kPredTile, 0, st>>>(pa);
+    LAUNCH(NH_K_PREDICT, k_predict<T><<<dim3(g->ntiles, g->nb), kPredTile, 0, st>>>(pa));
 
     CompactArgs ca;
     ca.nx = g->nx; ca.pitch = g->pitch; ca.wpitch = g->wpitch; ca.bc = g->d.bc; ca.enlarge = g->enlarge;
     ca.marks = g->marks; ca.act = g->act; ca.list = g->list[lnew]; ca.nact = g->nact[lnew];
     ca.ms = g->ms; ca.ctl = g->ctl;
     const size_t csm = sizeof(uint32_t) * (size_t)((g->nx + 31) / 32);
-    k_compact<<<g->nb, kCompactThreads, csm, st>>>(ca);
+    LAUNCH(NH_K_COMPACT, k_compact<<<g->nb, kCompactThreads, csm, st>>>(ca));
 
-    AsmArgs<double> aa;
+    AsmArgs<T> aa;
     aa.G = G;
-    aa.ht = (const double*)g->sh[nxt]; aa.hut = (const double*)g->shu[nxt]; aa.hwt = (const double*)g->shw[nxt];
-    aa.d0 = (const double*)g->d0; aa.slide = g->slide; aa.kin = g->kin;
+    aa.zt = (const T*)g->sz[nxt]; aa.hut = (const T*)g->shu[nxt]; aa.hwt = (const T*)g->shw[nxt];
+    aa.d0 = g->d0d; aa.slide = g->slide; aa.kin = g->kin;
     aa.list = g->list[lnew]; aa.act = g->act; aa.ms = g->ms;
-    aa.diag = (double*)g->diag; aa.offl = (double*)g->offl; aa.offr = (double*)g->offr; aa.R = (double*)g->R;
+    aa.diag = g->diag; aa.offl = g->offl; aa.offr = g->offr; aa.R = g->R;
+    aa.diag32 = g->diag32; aa.offl32 = g->offl32; aa.offr32 = g->offr32;
     aa.nbl = g->nbl; aa.nbr = g->nbr;
-    aa.c6 = (double*)g->c6; aa.cx = (double*)g->cx; aa.phi = (double*)g->phi; aa.ddx = (double*)g->ddx;
+    aa.c6 = (T*)g->c6; aa.cx = (T*)g->cx; aa.phi = (T*)g->phi; aa.ddx = (T*)g->ddx;
     aa.part = g->part; aa.cnt = g->cnt; aa.dt = dt; aa.solver = g->solver;
-    k_assemble<double><<<g->items_grid, kChunk, 0, st>>>(aa);
+    LAUNCH(NH_K_ASSEMBLE, k_assemble<T><<<g->items_grid, kChunk, 0, st>>>(aa));
 
-    SolveArgs<double> sa = solve_args(g, lnew);
-    sa.guess_scale = (g->guess == NH_GUESS_PREV && g->last_dt > 0.0) ? dt / g->last_dt : 0.0;
-    k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa);
-    Ctl hctl;
-    CK(cudaMemcpyAsync(&hctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (hctl.not_done > 0) {
-        for (int it = 1; it <= g->max_iter; ++it) {
-            sa.it = it;
-            if (hctl.n_cg > 0) {
-                k_cg_a<double><<<g->items_grid, kChunk, 0, st>>>(sa);
-                k_cg_b<double><<<g->items_grid, kChunk, 0, st>>>(sa);
-            }
-            if (hctl.n_bicg > 0) {
-                k_bi_1<double><<<g->items_grid, kChunk, 0, st>>>(sa);
-                k_bi_2<double><<<g->items_grid, kChunk, 0, st>>>(sa);
-                k_bi_3<double><<<g->items_grid, kChunk, 0, st>>>(sa);
-            }
-            if (it % g->poll_every == 0 || it == g->max_iter) {
-                int nd = 0;
-                CK(cudaMemcpyAsync(&nd, &g->ctl->not_done, sizeof(int), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                if (nd <= 0) break;
-            }
-        }
+    const double* xfinal;
+    if (g->mixed) {
+        nh_status rc = refine(g, lnew, gscale);
+        if (rc != NH_OK) return rc;
+        xfinal = g->x64;
+    } else {
+        SolveArgs<double> sa = solve_args<double>(g, lnew, g->diag, g->offl, g->offr, g->R, g->rtol);
+        sa.guess_scale = gscale;
+        nh_status rc = krylov<double>(g, sa);
+        if (rc != NH_OK) return rc;
+        xfinal = (const double*)g->x;
     }
-    k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->ntiles, g->d.dx, g->summary);
+
+    LAUNCH(NH_K_SUMMARY, k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->ntiles, g->d.dx, g->summary));
     Summary S;
     CK(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    SYNC();
     CK(cudaGetLastError());
+    int ir_passes = 0;
+    if (g->mixed) {
+        std::vector<IRState> irs(g->nb);
+        CK(cudaMemcpyAsync(irs.data(), g->ir, sizeof(IRState) * g->nb, cudaMemcpyDeviceToHost, st));
+        SYNC();
+        for (const auto& q : irs) ir_passes = std::max(ir_passes, q.passes);
+    }
     nh_status status = (nh_status)S.status;
     if (status == NH_OK) {
         ClearArgs cl;
@@ -240,14 +418,14 @@ nh_status do_step(nh_grid* g, double dt, nh_step_info* info)
         cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi;
         const size_t total = (size_t)g->nb * g->pitch;
         int cgrid = (int)std::min<size_t>((total + 255) / 256, (size_t)g->sm_count * 8);
-        k_clear_prev<<<cgrid, 256, 0, st>>>(cl);
-        CorrArgs<double> co;
+        LAUNCH(NH_K_CLEAR, k_clear_prev<<<cgrid, 256, 0, st>>>(cl));
+        CorrArgs<T> co;
         co.nb = g->nb; co.pitch = g->pitch; co.maxch = g->maxch; co.dx = g->d.dx;
-        co.list = g->list[lnew]; co.nbl = g->nbl; co.nbr = g->nbr; co.x = (const double*)g->x;
-        co.c6 = (const double*)g->c6; co.cx = (const double*)g->cx; co.phi = (const double*)g->phi;
-        co.ddx = (const double*)g->ddx; co.ms = g->ms;
-        co.hu = (double*)g->shu[nxt]; co.hw = (double*)g->shw[nxt]; co.psi = g->psi;
-        k_correct<double><<<g->items_grid, kChunk, 0, st>>>(co);
+        co.list = g->list[lnew]; co.nbl = g->nbl; co.nbr = g->nbr; co.x = xfinal;
+        co.c6 = (const T*)g->c6; co.cx = (const T*)g->cx; co.phi = (const T*)g->phi;
+        co.ddx = (const T*)g->ddx; co.ms = g->ms;
+        co.hu = (T*)g->shu[nxt]; co.hw = (T*)g->shw[nxt]; co.psi = g->psi;
+        LAUNCH(NH_K_CORRECT, k_correct<T><<<g->items_grid, kChunk, 0, st>>>(co));
         CK(cudaGetLastError());
         g->cur = nxt;
         g->lcur = lnew;
@@ -261,14 +439,59 @@ nh_status do_step(nh_grid* g, double dt, nh_step_info* info)
         info->n_active = S.n_active;
         info->n_active_max = S.n_active_max;
         info->iters = S.iters;
-        info->ir_passes = 0;
+        info->ir_passes = ir_passes;
         info->solver = S.n_active == 0 ? -1 : (S.any_bicg ? NH_SOLVER_BICGSTAB : NH_SOLVER_CG);
         info->status = status;
         info->rel_res = S.rel_res;
         info->min_gamma = S.min_gamma;
-        info->mass = S.mass;
+        info->mass = S.mass + g->mass0;
     }
     return status;
+}
+
+nh_status do_step(nh_grid* g, double dt, nh_step_info* info)
+{
+    if (!g->has_state) return NH_ERR_STATE;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return NH_ERR_ARG;
+    return g->mixed ? step_t<float>(g, dt, info) : step_t<double>(g, dt, info);
+}
+
+template <typename T>
+nh_status upload_state(nh_grid* g, const double* h, const double* hu, const double* hw)
+{
+    cudaStream_t st = g->stream;
+    const size_t n = (size_t)g->nb * g->nx;
+    CK(cudaMemcpyAsync(g->stage, h, n * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g->stage + n, hu, n * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g->stage + 2 * n, hw, n * 8, cudaMemcpyHostToDevice, st));
+    const int c = g->cur;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sm_count * 8);
+    k_state_in<T><<<grid, 256, 0, st>>>(g->stage, g->stage + n, g->stage + 2 * n, g->d0d,
+                                       (T*)g->sz[c], (T*)g->shu[c], (T*)g->shw[c], g->nb, g->nx, g->pitch);
+    CK(cudaGetLastError());
+    return NH_OK;
+}
+
+template <typename T>
+nh_status download_state(nh_grid* g, double* h, double* hu, double* hw, double* p)
+{
+    cudaStream_t st = g->stream;
+    const size_t n = (size_t)g->nb * g->nx;
+    const int c = g->cur;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sm_count * 8);
+    const double sc = g->last_dt > 0.0 ? g->d.rho / g->last_dt : 0.0;
+    // p is formed in an FP64-sized solver vector: those are scratch between steps
+    double* p_dev = g->es == 8 ? (double*)g->r1 : g->x64;
+    k_state_out<T><<<grid, 256, 0, st>>>((const T*)g->sz[c], (const T*)g->shu[c], (const T*)g->shw[c],
+                                        g->d0d, g->psi, g->stage, g->stage + n, g->stage + 2 * n, p_dev,
+                                        sc, g->nb, g->nx, g->pitch);
+    CK(cudaGetLastError());
+    if (h) CK(cudaMemcpyAsync(h, g->stage, n * 8, cudaMemcpyDeviceToHost, st));
+    if (hu) CK(cudaMemcpyAsync(hu, g->stage + n, n * 8, cudaMemcpyDeviceToHost, st));
+    if (hw) CK(cudaMemcpyAsync(hw, g->stage + 2 * n, n * 8, cudaMemcpyDeviceToHost, st));
+    if (p) CK(cudaMemcpyAsync(p, p_dev, n * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return NH_OK;
 }
 
 }  // namespace
@@ -304,25 +527,45 @@ nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host, void* 
     g->sm_count = sms;
     g->items_grid = (int)std::min<long long>((long long)g->nb * g->maxch, (long long)sms * 8);
     if (g->items_grid < 1) g->items_grid = 1;
+    g->pcr_grid = (int)std::min<long long>((long long)g->nb * g->maxpb, (long long)sms * 2);
+    if (g->pcr_grid < 1) g->pcr_grid = 1;
     g->crit = NH_CRIT_GLOBAL; g->knh = 1e-3; g->enlarge = 1; g->first_global = 0;
     g->solver = NH_SOLVER_AUTO; g->rtol = 1e-12; g->max_iter = 20000; g->guess = NH_GUESS_PREV;
-    g->ir_max = 8; g->inner_rtol = 1e-5; g->poll_every = 16;
+    g->ir_max = 30; g->inner_rtol = 1e-5; g->poll_every = 4; g->precond = NH_PRECOND_LINE;
     g->has_state = false; g->t_base = 0.0; g->n_since = 0; g->steps = 0; g->last_dt = 0.0;
     g->cur = 0; g->lcur = 0;
+    g->prof_on = false; g->prof_used = 0;
+    for (int k = 0; k < NH_K_COUNT; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
     cudaStream_t st = g->stream;
     const size_t hp = (size_t)g->nx * sizeof(double), dp = (size_t)g->pitch * sizeof(double);
     nh_status rc = NH_OK;
     do {
         if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess) { rc = NH_ERR_CUDA; break; }
-        if (cudaMemcpy2DAsync(g->d0, dp, d0_host, hp, hp, g->nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        if (cudaMemcpy2DAsync(g->d0d, dp, d0_host, hp, hp, g->nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
         }
+        const size_t N = (size_t)g->nb * g->pitch;
+        if (g->mixed) {
+            k_to_float<<<(int)std::min<size_t>((N + 255) / 256, (size_t)sms * 8), 256, 0, st>>>(g->d0d, (float*)g->d0, N);
+            if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; break; }
+        } else if (cudaMemcpyAsync(g->d0, g->d0d, N * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            rc = NH_ERR_CUDA; break;
+        }
+        double m0 = 0.0;
+        for (size_t q = 0; q < (size_t)g->nx * g->nb; ++q) m0 += d0_host[q];
+        g->mass0 = m0 * g->d.dx;
         std::vector<Slide> sl(g->nb);
         for (auto& s : sl) { s.A = 0; s.L = 1; s.xc0 = 0; s.s0 = 0; s.t0 = 1; s.shape = NH_SLIDE_NONE; s.pad = 0; }
         if (cudaMemcpyAsync(g->slide, sl.data(), sizeof(Slide) * g->nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; break; }
+        if (cudaFuncSetAttribute(k_pcr<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess ||
+            cudaFuncSetAttribute(k_pcr<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess) {
+            rc = NH_ERR_CUDA; break;
+        }
         if (cudaFuncSetAttribute(k_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(uint32_t) * ((g->nx + 31) / 32))) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
@@ -377,16 +620,25 @@ nh_status nh_set_solver(nh_grid* g, int kind, double rtol, int max_iter, int gue
     return NH_OK;
 }
 
+nh_status nh_set_preconditioner(nh_grid* g, int kind)
+{
+    if (!g) return NH_ERR_ARG;
+    if (kind != NH_PRECOND_NONE && kind != NH_PRECOND_LINE) return NH_ERR_ARG;
+    g->precond = kind;
+    return NH_OK;
+}
+
 nh_status nh_set_state(nh_grid* g, const double* h, const double* hu, const double* hw, double t)
 {
     if (!g || !h || !hu || !hw || !std::isfinite(t)) return NH_ERR_ARG;
+    for (size_t q = 0; q < (size_t)g->nx * g->nb; ++q)
+        if (!(h[q] > 0.0) || !std::isfinite(h[q]) || !std::isfinite(hu[q]) || !std::isfinite(hw[q]))
+            return NH_ERR_ARG;
     cudaStream_t st = g->stream;
-    const size_t hp = (size_t)g->nx * sizeof(double), dp = (size_t)g->pitch * sizeof(double);
     g->cur = 0;
     g->lcur = 0;
-    CK(cudaMemcpy2DAsync(g->sh[0], dp, h, hp, hp, g->nb, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpy2DAsync(g->shu[0], dp, hu, hp, hp, g->nb, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpy2DAsync(g->shw[0], dp, hw, hp, hp, g->nb, cudaMemcpyHostToDevice, st));
+    nh_status rc = g->mixed ? upload_state<float>(g, h, hu, hw) : upload_state<double>(g, h, hu, hw);
+    if (rc != NH_OK) return rc;
     CK(cudaMemsetAsync(g->psi, 0, sizeof(double) * (size_t)g->nb * g->pitch, st));
     CK(cudaMemsetAsync(g->nact[0], 0, sizeof(int) * g->nb, st));
     CK(cudaMemsetAsync(g->nact[1], 0, sizeof(int) * g->nb, st));
@@ -396,31 +648,40 @@ nh_status nh_set_state(nh_grid* g, const double* h, const double* hu, const doub
     return NH_OK;
 }
 
+nh_status nh_put_state(nh_grid* g, const double* h, const double* hu, const double* hw)
+{
+    if (!g || !h || !hu || !hw) return NH_ERR_ARG;
+    if (!g->has_state) return NH_ERR_STATE;
+    return g->mixed ? upload_state<float>(g, h, hu, hw) : upload_state<double>(g, h, hu, hw);
+}
+
+nh_status nh_set_profiling(nh_grid* g, int enable)
+{
+    if (!g) return NH_ERR_ARG;
+    CK(cudaStreamSynchronize(g->stream));
+    g->prof_used = 0;
+    g->prof_on = enable != 0;
+    for (int k = 0; k < NH_K_COUNT; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
+    return NH_OK;
+}
+
+nh_status nh_get_profile(nh_grid* g, double* ms, long long* launches)
+{
+    if (!g) return NH_ERR_ARG;
+    CK(cudaStreamSynchronize(g->stream));
+    prof_fold(g);
+    for (int k = 0; k < NH_K_COUNT; ++k) {
+        if (ms) ms[k] = g->prof_ms[k];
+        if (launches) launches[k] = g->prof_launches[k];
+    }
+    return NH_OK;
+}
+
 nh_status nh_get_state(nh_grid* g, double* h, double* hu, double* hw, double* p_nh)
 {
     if (!g) return NH_ERR_ARG;
     if (!g->has_state) return NH_ERR_STATE;
-    cudaStream_t st = g->stream;
-    const size_t hp = (size_t)g->nx * sizeof(double), dp = (size_t)g->pitch * sizeof(double);
-    const int c = g->cur;
-    if (h) CK(cudaMemcpy2DAsync(h, hp, g->sh[c], dp, hp, g->nb, cudaMemcpyDeviceToHost, st));
-    if (hu) CK(cudaMemcpy2DAsync(hu, hp, g->shu[c], dp, hp, g->nb, cudaMemcpyDeviceToHost, st));
-    if (hw) CK(cudaMemcpy2DAsync(hw, hp, g->shw[c], dp, hp, g->nb, cudaMemcpyDeviceToHost, st));
-    std::vector<double> hh;
-    if (p_nh) {
-        CK(cudaMemcpy2DAsync(p_nh, hp, g->psi, dp, hp, g->nb, cudaMemcpyDeviceToHost, st));
-        if (!h) {
-            hh.resize((size_t)g->nx * g->nb);
-            CK(cudaMemcpy2DAsync(hh.data(), hp, g->sh[c], dp, hp, g->nb, cudaMemcpyDeviceToHost, st));
-        }
-    }
-    CK(cudaStreamSynchronize(st));
-    if (p_nh) {
-        const double* H = h ? h : hh.data();
-        const double sc = g->last_dt > 0.0 ? g->d.rho / g->last_dt : 0.0;
-        for (size_t q = 0; q < (size_t)g->nx * g->nb; ++q) p_nh[q] = sc * p_nh[q] / H[q];
-    }
-    return NH_OK;
+    return g->mixed ? download_state<float>(g, h, hu, hw, p_nh) : download_state<double>(g, h, hu, hw, p_nh);
 }
 
 nh_status nh_get_mask(nh_grid* g, unsigned char* mask, int* iters, double* rel_res)
@@ -477,6 +738,7 @@ void nh_destroy(nh_grid* g)
 {
     if (!g) return;
     cudaStreamSynchronize(g->stream);
+    for (cudaEvent_t e : g->prof_pool) cudaEventDestroy(e);
     delete g;
 }
 

@@ -1,5 +1,10 @@
 // nh_internal.cuh -- device-side building blocks of the 1D library path.
 //
+// State on the GPU: zeta = h - d0 (deviation of the thickness from the static
+// depth), hu, hw.  eta = zeta + m and h = zeta + d0, where m is the moving
+// mound (d = d0 - m), so the surface is formed from two small numbers and an
+// FP32 state keeps sub-nanometre resolution of eta.
+//
 // Unknown used on the GPU: psi = (dt / rho) h~ p^nh.  With this scaling the
 // elliptic problem of Sec. 3.2 (Eqs. 10-13 with the constraint Eq. 4
 // eliminated) reads
@@ -26,6 +31,8 @@ constexpr int kPredTile = 256;   // cells per predictor CTA (multiple of 32)
 constexpr int kPredHalo = 5;     // two Heun stages + one cell for the criterion
 constexpr int kChunk = 256;      // active cells per solver work item (= blockDim)
 constexpr int kCompactThreads = 1024;
+constexpr int kPcrThreads = 1024;     // preconditioner CTA
+constexpr int kPcrRows = 4096;        // active cells per preconditioner block (power of 2)
 
 // Per-member slide parameters (device copy of nh_slide_desc, FP64).
 struct Slide {
@@ -49,6 +56,7 @@ struct MState {
     double rel_res;
     double min_gamma;
     double snorm;      // BiCGStab: ||s|| of the current iteration
+    double rz;         // PCG: <r, z>
     int status;        // nh_status
     int iters;
     int done;          // 1 once converged / failed
@@ -57,13 +65,21 @@ struct MState {
     int s_conv;        // BiCGStab: converged on s this iteration
     int n_active;
     int nchunks;
+    int auto_kind;     // AUTO: CG first, BiCGStab if CG detects indefiniteness
+    int pad;
 };
+
+// MState.status value (never returned): CG broke down on an AUTO member,
+// which is then solved again by BiCGStab.
+constexpr int kStatusFallback = 100;
 
 // Counters shared by all members (device).
 struct Ctl {
     int not_done;      // members still iterating
     int n_cg, n_bicg;  // members per solver kind after set-up
-    int pad;
+    int ir_pending;    // mixed path: members needing another refinement pass
+    int n_fallback;    // AUTO members whose CG broke down in this solve
+    int pad[3];
 };
 
 __device__ __forceinline__ int resolve(int j, int n, int bc, int* sgn)
@@ -82,19 +98,23 @@ __device__ __forceinline__ float texp(float v) { return expf(v); }
 __device__ __forceinline__ double tsqrt(double v) { return sqrt(v); }
 __device__ __forceinline__ float tsqrt(float v) { return sqrtf(v); }
 
-// Depth at the centre of cell c (already resolved) with the mound at
-// displacement s: d = d0 - A exp(-xi^2), xi = (x_c - xc0 - s) / L.
+// Height of the moving mound at the centre of cell c (already resolved) at
+// displacement s: m = A exp(-xi^2), xi = (x_c - xc0 - s) / L; the depth is
+// d = d0 - m.
+template <typename T>
+__device__ __forceinline__ T mound_at(int c, double x0, double dx, const Slide& sl, double s)
+{
+    if (sl.shape != NH_SLIDE_GAUSS_LNCOSH) return T(0);
+    const double xc = x0 + (c + 0.5) * dx;
+    const T xi = T((xc - sl.xc0 - s) / sl.L);
+    return T(sl.A) * texp(-xi * xi);
+}
+
 template <typename T>
 __device__ __forceinline__ T depth_at(const T* __restrict__ d0m, int c, double x0, double dx,
                                       const Slide& sl, double s)
 {
-    T d = d0m[c];
-    if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
-        double xc = x0 + (c + 0.5) * dx;
-        T xi = T((xc - sl.xc0 - s) / sl.L);
-        d -= T(sl.A) * texp(-xi * xi);
-    }
-    return d;
+    return d0m[c] - mound_at<T>(c, x0, dx, sl, s);
 }
 
 template <typename T>

@@ -63,30 +63,40 @@ __device__ __forceinline__ T limited_slope(int lim, T vm, T v0, T vp)
     }
 }
 
-// Local Lax-Friedrichs (Rusanov) flux of (hu, hu^2 + g h^2 / 2, huw).
+// Local Lax-Friedrichs (Rusanov) flux of (hu, hu^2 + g h^2 / 2, huw) at a face
+// with continuous depth d_f, from left / right states (eta, u, w).  The
+// momentum flux is returned split as F1 = A1 + (g/4)(hL^2 + hR^2), with the
+// convective / dissipative part A1 and the jump part
+// G1 = (g/4)(hR + hL)(etaR - etaL) = (g/4)(hR^2 - hL^2); with the cell's own
+// face thicknesses h- (right) and h+ (left) the cell update
+//   -(F1_r - F1_l)/dx + g hbar (d_r - d_l)/dx
+// equals -(A1_r - A1_l + G1_r + G1_l + g hbar (h- - h+ - d_r + d_l))/dx, and
+// h- - h+ - d_r + d_l is the eta slope: the lake at rest is exact in any
+// precision.
 template <typename T>
-__device__ __forceinline__ void rusanov(T g, T hL, T uL, T wL, T hR, T uR, T wR,
-                                        T& F0, T& F1, T& F2)
+__device__ __forceinline__ void rusanov(T g, T df, T eL, T uL, T wL, T eR, T uR, T wR,
+                                        T& F0, T& A1, T& G1, T& F2)
 {
+    const T hL = eL + df, hR = eR + df;
     const T qL = hL * uL, qR = hR * uR;
     const T aL = tabs(uL) + tsqrt(g * hL), aR = tabs(uR) + tsqrt(g * hR);
     const T s = aL > aR ? aL : aR;
-    const T fL = qL * uL + T(0.5) * g * hL * hL;
-    const T fR = qR * uR + T(0.5) * g * hR * hR;
-    F0 = T(0.5) * (qL + qR) - T(0.5) * s * (hR - hL);
-    F1 = T(0.5) * (fL + fR) - T(0.5) * s * (qR - qL);
+    const T de = eR - eL;
+    F0 = T(0.5) * (qL + qR) - T(0.5) * s * de;
+    A1 = T(0.5) * (qL * uL + qR * uR) - T(0.5) * s * (qR - qL);
+    G1 = T(0.25) * g * (hR + hL) * de;
     F2 = T(0.5) * (qL * wL + qR * wR) - T(0.5) * s * (hR * wR - hL * wL);
 }
 
 template <typename T>
 struct PredArgs {
     Geo G;
-    const T* h; const T* hu; const T* hw;     // Q^n
-    T* ht; T* hut; T* hwt;                    // Q~^{n+1}
+    const T* z; const T* hu; const T* hw;     // Q^n (zeta = h - d0)
+    T* zt; T* hut; T* hwt;                    // Q~^{n+1}
     const T* d0;
     const Slide* slide; const Kin* kin;
     uint32_t* marks;                          // nb * wpitch words
-    double* mass_part;                        // nb * ntiles
+    double* mass_part;                        // nb * ntiles: sum of zeta~
     double dt;
     double knh;
     int crit;
@@ -102,18 +112,18 @@ template <typename T>
 __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
 {
     constexpr int TILE = kPredTile, H = kPredHalo, NL = TILE + 2 * H;
-    __shared__ T sh[NL], shu[NL], shw[NL];      // Q^n, later Q~
+    __shared__ T sz[NL], shu[NL], shw[NL];      // Q^n, later Q~
+    __shared__ T sd0[NL], smn[NL], smn1[NL];    // static depth, mound at t^n, t^{n+1}
     __shared__ T se[NL], su[NL], sw[NL];        // stage primitives eta, u, w
-    __shared__ T sdn[NL], sdn1[NL];             // depth at t^n, t^{n+1}
     __shared__ T sle[NL], slu[NL], slw[NL];     // limited slopes
-    __shared__ T F0[NL], F1[NL], F2[NL];        // face l: between local cells l-1 and l
+    __shared__ T F0[NL], A1[NL], G1[NL], F2[NL];  // face l: between local cells l-1 and l
     __shared__ T k1h[NL], k1u[NL], k1w[NL];     // stage-1 rates
     __shared__ double red[32];
 
     const Geo& G = a.G;
     const int b = blockIdx.y, i0 = blockIdx.x * TILE, tid = threadIdx.x;
     const size_t mo = (size_t)b * G.pitch;
-    const T* __restrict__ Hn = a.h + mo;
+    const T* __restrict__ Zn = a.z + mo;
     const T* __restrict__ HUn = a.hu + mo;
     const T* __restrict__ HWn = a.hw + mo;
     const T* __restrict__ D0 = a.d0 + mo;
@@ -121,22 +131,24 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
     const Kin kn = a.kin[b];
     const T g = T(G.g), dx = T(G.dx), dt = T(a.dt), half_dt = T(0.5) * T(a.dt);
 
-    // A: load Q^n and the bottom at both times.  Cells outside [-6, nx+5]
-    // feed only outputs outside [-1, nx] and get a benign still state.
+    // A: load Q^n, d0 and the mound at both times.  Cells outside
+    // [-6, nx+5] feed only outputs outside [-1, nx]; they get still water.
     for (int l = tid; l < NL; l += TILE) {
         const int j = i0 - H + l;
-        T hv = T(1), huv = T(0), hwv = T(0), dn = T(1), dn1 = T(1);
+        T zv = T(0), huv = T(0), hwv = T(0), d0v = T(1), mn = T(0), mn1 = T(0);
         if (j >= -6 && j <= G.nx + 5) {
             int sg;
             const int c = resolve(j, G.nx, G.bc, &sg);
-            hv = Hn[c];
+            zv = Zn[c];
             huv = sg > 0 ? HUn[c] : -HUn[c];
             hwv = HWn[c];
-            dn = depth_at(D0, c, G.x0, G.dx, sl, kn.s_n);
-            dn1 = depth_at(D0, c, G.x0, G.dx, sl, kn.s_n1);
+            d0v = D0[c];
+            mn = mound_at<T>(c, G.x0, G.dx, sl, kn.s_n);
+            mn1 = mound_at<T>(c, G.x0, G.dx, sl, kn.s_n1);
         }
-        sh[l] = hv; shu[l] = huv; shw[l] = hwv; sdn[l] = dn; sdn1[l] = dn1;
-        se[l] = hv - dn; su[l] = huv / hv; sw[l] = hwv / hv;
+        const T hv = zv + d0v;
+        sz[l] = zv; shu[l] = huv; shw[l] = hwv; sd0[l] = d0v; smn[l] = mn; smn1[l] = mn1;
+        se[l] = zv + mn; su[l] = huv / hv; sw[l] = hwv / hv;
     }
     __syncthreads();
 
@@ -150,29 +162,26 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
 
     // C: stage-1 face fluxes on faces [2, NL-1); depth continuous at faces
     for (int f = tid + 2; f < NL - 1; f += TILE) {
-        const T df = T(0.5) * (sdn[f - 1] + sdn[f]);
-        const T hL = se[f - 1] + T(0.5) * sle[f - 1] + df;
-        const T uL = su[f - 1] + T(0.5) * slu[f - 1];
-        const T wL = sw[f - 1] + T(0.5) * slw[f - 1];
-        const T hR = se[f] - T(0.5) * sle[f] + df;
-        const T uR = su[f] - T(0.5) * slu[f];
-        const T wR = sw[f] - T(0.5) * slw[f];
-        rusanov(g, hL, uL, wL, hR, uR, wR, F0[f], F1[f], F2[f]);
+        const T df = T(0.5) * ((sd0[f - 1] - smn[f - 1]) + (sd0[f] - smn[f]));
+        rusanov(g, df, se[f - 1] + T(0.5) * sle[f - 1], su[f - 1] + T(0.5) * slu[f - 1],
+                sw[f - 1] + T(0.5) * slw[f - 1], se[f] - T(0.5) * sle[f], su[f] - T(0.5) * slu[f],
+                sw[f] - T(0.5) * slw[f], F0[f], A1[f], G1[f], F2[f]);
     }
     __syncthreads();
 
     // D: stage-1 rates and Q* on cells [2, NL-2); Q* stored as primitives
     //    against the bottom at t^{n+1}
     for (int l = tid + 2; l < NL - 2; l += TILE) {
-        const T dfl = T(0.5) * (sdn[l - 1] + sdn[l]), dfr = T(0.5) * (sdn[l] + sdn[l + 1]);
-        const T hpl = se[l] - T(0.5) * sle[l] + dfl, hmr = se[l] + T(0.5) * sle[l] + dfr;
-        const T S = g * T(0.5) * (hpl + hmr) * (dfr - dfl) / dx;
+        const T dm = sd0[l - 1] - smn[l - 1], dc = sd0[l] - smn[l], dp = sd0[l + 1] - smn[l + 1];
+        const T dfl = T(0.5) * (dm + dc), dfr = T(0.5) * (dc + dp);
+        const T hbar = T(0.5) * ((se[l] - T(0.5) * sle[l] + dfl) + (se[l] + T(0.5) * sle[l] + dfr));
         const T r0 = -(F0[l + 1] - F0[l]) / dx;
-        const T r1 = -(F1[l + 1] - F1[l]) / dx + S;
+        const T r1 = -((A1[l + 1] - A1[l]) + (G1[l + 1] + G1[l]) + g * hbar * sle[l]) / dx;
         const T r2 = -(F2[l + 1] - F2[l]) / dx;
         k1h[l] = r0; k1u[l] = r1; k1w[l] = r2;
-        const T hs = sh[l] + dt * r0, hus = shu[l] + dt * r1, hws = shw[l] + dt * r2;
-        se[l] = hs - sdn1[l]; su[l] = hus / hs; sw[l] = hws / hs;
+        const T zs = sz[l] + dt * r0, hus = shu[l] + dt * r1, hws = shw[l] + dt * r2;
+        const T hs = zs + sd0[l];
+        se[l] = zs + smn1[l]; su[l] = hus / hs; sw[l] = hws / hs;
     }
     __syncthreads();
 
@@ -186,32 +195,28 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
 
     // F: stage-2 fluxes on faces [4, NL-3)
     for (int f = tid + 4; f < NL - 3; f += TILE) {
-        const T df = T(0.5) * (sdn1[f - 1] + sdn1[f]);
-        const T hL = se[f - 1] + T(0.5) * sle[f - 1] + df;
-        const T uL = su[f - 1] + T(0.5) * slu[f - 1];
-        const T wL = sw[f - 1] + T(0.5) * slw[f - 1];
-        const T hR = se[f] - T(0.5) * sle[f] + df;
-        const T uR = su[f] - T(0.5) * slu[f];
-        const T wR = sw[f] - T(0.5) * slw[f];
-        rusanov(g, hL, uL, wL, hR, uR, wR, F0[f], F1[f], F2[f]);
+        const T df = T(0.5) * ((sd0[f - 1] - smn1[f - 1]) + (sd0[f] - smn1[f]));
+        rusanov(g, df, se[f - 1] + T(0.5) * sle[f - 1], su[f - 1] + T(0.5) * slu[f - 1],
+                sw[f - 1] + T(0.5) * slw[f - 1], se[f] - T(0.5) * sle[f], su[f] - T(0.5) * slu[f],
+                sw[f] - T(0.5) * slw[f], F0[f], A1[f], G1[f], F2[f]);
     }
     __syncthreads();
 
     // G: stage-2 rates and Q~ on [4, NL-4) (the tile and one cell each side)
     for (int l = tid + 4; l < NL - 4; l += TILE) {
-        const T dfl = T(0.5) * (sdn1[l - 1] + sdn1[l]), dfr = T(0.5) * (sdn1[l] + sdn1[l + 1]);
-        const T hpl = se[l] - T(0.5) * sle[l] + dfl, hmr = se[l] + T(0.5) * sle[l] + dfr;
-        const T S = g * T(0.5) * (hpl + hmr) * (dfr - dfl) / dx;
+        const T dm = sd0[l - 1] - smn1[l - 1], dc = sd0[l] - smn1[l], dp = sd0[l + 1] - smn1[l + 1];
+        const T dfl = T(0.5) * (dm + dc), dfr = T(0.5) * (dc + dp);
+        const T hbar = T(0.5) * ((se[l] - T(0.5) * sle[l] + dfl) + (se[l] + T(0.5) * sle[l] + dfr));
         const T r0 = -(F0[l + 1] - F0[l]) / dx;
-        const T r1 = -(F1[l + 1] - F1[l]) / dx + S;
+        const T r1 = -((A1[l + 1] - A1[l]) + (G1[l + 1] + G1[l]) + g * hbar * sle[l]) / dx;
         const T r2 = -(F2[l + 1] - F2[l]) / dx;
-        const T hn = sh[l] + half_dt * (k1h[l] + r0);
+        const T zn = sz[l] + half_dt * (k1h[l] + r0);
         const T hun = shu[l] + half_dt * (k1u[l] + r1);
         const T hwn = shw[l] + half_dt * (k1w[l] + r2);
-        sh[l] = hn; shu[l] = hun; shw[l] = hwn;
+        sz[l] = zn; shu[l] = hun; shw[l] = hwn;
         const int j = i0 - H + l;
         if (j >= i0 && j < i0 + TILE && j < G.nx) {
-            a.ht[mo + j] = hn; a.hut[mo + j] = hun; a.hwt[mo + j] = hwn;
+            a.zt[mo + j] = zn; a.hut[mo + j] = hun; a.hwt[mo + j] = hwn;
         }
     }
     __syncthreads();
@@ -223,19 +228,22 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
         bool mark = false;
         double mass = 0.0;
         if (inside) {
-            mass = (double)sh[l];
+            mass = (double)sz[l];
             if (a.all_global) {
                 mark = true;
             } else if (a.crit >= NH_CRIT_ETA_D) {
                 const T inv2dx = T(1) / (T(2) * dx);
+                // eta~ = zeta~ + m, h~ = zeta~ + d0 at l-1, l, l+1
+                const T em = sz[l - 1] + smn1[l - 1], ec = sz[l] + smn1[l], ep = sz[l + 1] + smn1[l + 1];
+                const T hm = sz[l - 1] + sd0[l - 1], hc = sz[l] + sd0[l], hp = sz[l + 1] + sd0[l + 1];
                 T c;
                 switch (a.crit) {
-                case NH_CRIT_ETA_D: c = tabs((sh[l] - sdn1[l]) / sdn1[l]); break;
-                case NH_CRIT_ETA_X: c = tabs(((sh[l + 1] - sdn1[l + 1]) - (sh[l - 1] - sdn1[l - 1])) * inv2dx); break;
-                case NH_CRIT_U:     c = tabs(shu[l] / sh[l]); break;
-                case NH_CRIT_U_X:   c = tabs((shu[l + 1] / sh[l + 1] - shu[l - 1] / sh[l - 1]) * inv2dx); break;
-                case NH_CRIT_W:     c = tabs(shw[l] / sh[l]); break;
-                default:            c = tabs((shw[l + 1] / sh[l + 1] - shw[l - 1] / sh[l - 1]) * inv2dx); break;
+                case NH_CRIT_ETA_D: c = tabs(ec / (sd0[l] - smn1[l])); break;
+                case NH_CRIT_ETA_X: c = tabs((ep - em) * inv2dx); break;
+                case NH_CRIT_U:     c = tabs(shu[l] / hc); break;
+                case NH_CRIT_U_X:   c = tabs((shu[l + 1] / hp - shu[l - 1] / hm) * inv2dx); break;
+                case NH_CRIT_W:     c = tabs(shw[l] / hc); break;
+                default:            c = tabs((shw[l + 1] / hp - shw[l - 1] / hm) * inv2dx); break;
                 }
                 mark = (double)c > a.knh;
             }
@@ -275,7 +283,9 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(CompactArgs a)
     const uint32_t* M = a.marks + (size_t)b * a.wpitch;
     for (int w = tid; w < nw; w += blockDim.x) s_m[w] = M[w];
     if (tid == 0) s_base = 0;
-    if (b == 0 && tid == 0) { a.ctl->not_done = 0; a.ctl->n_cg = 0; a.ctl->n_bicg = 0; }
+    if (b == 0 && tid == 0) {
+        a.ctl->not_done = 0; a.ctl->n_cg = 0; a.ctl->n_bicg = 0; a.ctl->n_fallback = 0;
+    }
     __syncthreads();
     const int e = a.enlarge;
     int* L = a.list + (size_t)b * a.pitch;
@@ -343,6 +353,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(CompactArgs a)
         s.rel_res = 0.0; s.min_gamma = 0.0; s.snorm = 0.0;
         s.status = NH_OK; s.iters = 0; s.done = (n == 0); s.kind = -1; s.zero_sol = 0;
         s.s_conv = 0; s.n_active = n; s.nchunks = (n + kChunk - 1) / kChunk;
+        s.auto_kind = 0; s.pad = 0;
         a.ms[b] = s;
     }
 }
@@ -384,51 +395,52 @@ __device__ __forceinline__ double member_min(const double* part, int n, double* 
 
 // --------------------------------------------------------------- assembly
 
-template <typename T>
+template <typename TS>
 struct AsmArgs {
     Geo G;
-    const T* ht; const T* hut; const T* hwt;
-    const T* d0;
+    const TS* zt; const TS* hut; const TS* hwt;   // Q~ (zeta = h - d0)
+    const double* d0;                           // static depth, FP64
     const Slide* slide; const Kin* kin;
     const int* list; const uint32_t* act;
     MState* ms;
-    T* diag; T* offl; T* offr; T* R;
+    double* diag; double* offl; double* offr; double* R;      // FP64 operator
+    float* diag32; float* offl32; float* offr32;              // FP32 copies (mixed)
     int* nbl; int* nbr;
-    T* c6; T* cx; T* phi; T* ddx;            // correction coefficients
-    double* part;                            // [2][nb * maxch]
+    TS* c6; TS* cx; TS* phi; TS* ddx;           // correction coefficients
+    double* part;                               // [2][nb * maxch]
     int* cnt;
     double dt;
-    int solver;                              // NH_SOLVER_*
+    int solver;                                 // NH_SOLVER_*
 };
 
-template <typename T>
 struct CellQ {
-    T h, K, beta, U0, V, phi, d_x, D, d_t;
+    double h, K, beta, U0, V, phi, d_x, D, d_t;
 };
 
-// Per-cell quantities of the elliptic equation at an in-domain cell c.
-template <typename T>
-__device__ __forceinline__ CellQ<T> cell_q(const AsmArgs<T>& a, const T* __restrict__ ht,
-                                           const T* __restrict__ hut, const T* __restrict__ D0,
-                                           int c, const Slide& sl, const Kin& kn)
+// Per-cell quantities of the elliptic equation at an in-domain cell c, in FP64
+// whatever the state precision.
+template <typename TS>
+__device__ __forceinline__ CellQ cell_q(const AsmArgs<TS>& a, const TS* __restrict__ zt,
+                                        const TS* __restrict__ hut, const double* __restrict__ D0,
+                                        int c, const Slide& sl, const Kin& kn)
 {
     const Geo& G = a.G;
-    const Bottom<T> B = bottom_full(D0, c, G.nx, G.bc, G.x0, G.dx, sl, kn);
+    const Bottom<double> B = bottom_full(D0, c, G.nx, G.bc, G.x0, G.dx, sl, kn);
     int sg;
     const int cm = resolve(c - 1, G.nx, G.bc, &sg), cp = resolve(c + 1, G.nx, G.bc, &sg);
-    const T etam = ht[cm] - depth_at(D0, cm, G.x0, G.dx, sl, kn.s_n1);
-    const T etap = ht[cp] - depth_at(D0, cp, G.x0, G.dx, sl, kn.s_n1);
-    const T eta_x = (etap - etam) / (T(2) * T(G.dx));
-    CellQ<T> q;
-    q.h = ht[c];
-    const T u = hut[c] / q.h;
+    const double etam = (double)zt[cm] + mound_at<double>(cm, G.x0, G.dx, sl, kn.s_n1);
+    const double etap = (double)zt[cp] + mound_at<double>(cp, G.x0, G.dx, sl, kn.s_n1);
+    const double eta_x = (etap - etam) / (2.0 * G.dx);
+    CellQ q;
+    q.h = (double)zt[c] + D0[c];
+    const double u = (double)hut[c] / q.h;
     q.d_x = B.d_x;
     q.d_t = B.d_t;
-    q.D = T(4) + B.d_x * B.d_x;
-    q.phi = T(a.dt) * q.h / q.D * (T(G.g) * B.d_x * eta_x - B.d_tt - T(2) * u * B.d_xt - u * u * B.d_xx);
-    q.K = T(4) / (q.h * q.D);
-    q.beta = T(6) * B.d_x / (q.h * q.h * q.D);
-    q.U0 = hut[c] + q.phi * B.d_x;
+    q.D = 4.0 + B.d_x * B.d_x;
+    q.phi = a.dt * q.h / q.D * (G.g * B.d_x * eta_x - B.d_tt - 2.0 * u * B.d_xt - u * u * B.d_xx);
+    q.K = 4.0 / (q.h * q.D);
+    q.beta = 6.0 * B.d_x / (q.h * q.h * q.D);
+    q.U0 = (double)hut[c] + q.phi * B.d_x;
     q.V = q.U0 / q.h;
     return q;
 }
@@ -438,8 +450,8 @@ __device__ __forceinline__ bool bit_at(const uint32_t* w, int i)
     return (w[i >> 5] >> (i & 31)) & 1u;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<T> a)
+template <typename TS>
+__global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
 {
     __shared__ double red[64];
     const Geo& G = a.G;
@@ -450,8 +462,8 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<T> a)
         const int nch = (n + kChunk - 1) / kChunk;
         if (j >= nch) continue;
         const size_t mo = (size_t)b * G.pitch;
-        const T* ht = a.ht + mo; const T* hut = a.hut + mo; const T* hwt = a.hwt + mo;
-        const T* D0 = a.d0 + mo;
+        const TS* zt = a.zt + mo; const TS* hut = a.hut + mo; const TS* hwt = a.hwt + mo;
+        const double* D0 = a.d0 + mo;
         const uint32_t* act = a.act + (size_t)b * G.wpitch;
         const Slide sl = a.slide[b];
         const Kin kn = a.kin[b];
@@ -461,17 +473,17 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<T> a)
             const int i = a.list[mo + k];
             int sgm, sgp;
             const int cm = resolve(i - 1, G.nx, G.bc, &sgm), cp = resolve(i + 1, G.nx, G.bc, &sgp);
-            const CellQ<T> qi = cell_q(a, ht, hut, D0, i, sl, kn);
-            const CellQ<T> qm = cell_q(a, ht, hut, D0, cm, sl, kn);
-            const CellQ<T> qp = cell_q(a, ht, hut, D0, cp, sl, kn);
-            const T dxT = T(G.dx), idx2 = T(1) / (dxT * dxT);
-            const T Kl = T(0.5) * (qm.K + qi.K), Kr = T(0.5) * (qi.K + qp.K);
-            const T bm = sgm > 0 ? qm.beta : -qm.beta, bp = sgp > 0 ? qp.beta : -qp.beta;
-            const T Vm = sgm > 0 ? qm.V : -qm.V, Vp = sgp > 0 ? qp.V : -qp.V;
-            const T h = qi.h, h2 = h * h;
-            const T gam = (bp - bm) / (T(2) * dxT) + T(12) * (T(1) + qi.d_x * qi.d_x) / (h2 * h * qi.D);
-            const T Rk = -((Vp - Vm) / (T(2) * dxT) + T(2) * qi.d_x * qi.U0 / h2 + T(2) * hwt[i] / h2
-                           + T(2) * qi.phi / h2 + T(2) * qi.d_t / h);
+            const CellQ qi = cell_q(a, zt, hut, D0, i, sl, kn);
+            const CellQ qm = cell_q(a, zt, hut, D0, cm, sl, kn);
+            const CellQ qp = cell_q(a, zt, hut, D0, cp, sl, kn);
+            const double idx2 = 1.0 / (G.dx * G.dx);
+            const double Kl = 0.5 * (qm.K + qi.K), Kr = 0.5 * (qi.K + qp.K);
+            const double bm = sgm > 0 ? qm.beta : -qm.beta, bp = sgp > 0 ? qp.beta : -qp.beta;
+            const double Vm = sgm > 0 ? qm.V : -qm.V, Vp = sgp > 0 ? qp.V : -qp.V;
+            const double h = qi.h, h2 = h * h;
+            const double gam = (bp - bm) / (2.0 * G.dx) + 12.0 * (1.0 + qi.d_x * qi.d_x) / (h2 * h * qi.D);
+            const double Rk = -((Vp - Vm) / (2.0 * G.dx) + 2.0 * qi.d_x * qi.U0 / h2 + 2.0 * (double)hwt[i] / h2
+                                + 2.0 * qi.phi / h2 + 2.0 * qi.d_t / h);
             // neighbours inside the active set (zero Dirichlet data outside)
             bool hasl, hasr;
             int kl = -1, kr = -1;
@@ -486,18 +498,26 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<T> a)
                 if (hasl) kl = k - 1;
                 if (hasr) kr = k + 1;
             }
-            a.diag[mo + k] = (Kl + Kr) * idx2 + gam;
-            a.offl[mo + k] = hasl ? -Kl * idx2 : T(0);
-            a.offr[mo + k] = hasr ? -Kr * idx2 : T(0);
+            const double dg = (Kl + Kr) * idx2 + gam;
+            const double ol = hasl ? -Kl * idx2 : 0.0;
+            const double orr = hasr ? -Kr * idx2 : 0.0;
+            a.diag[mo + k] = dg;
+            a.offl[mo + k] = ol;
+            a.offr[mo + k] = orr;
             a.R[mo + k] = Rk;
+            if (a.diag32) {
+                a.diag32[mo + k] = (float)dg;
+                a.offl32[mo + k] = (float)ol;
+                a.offr32[mo + k] = (float)orr;
+            }
             a.nbl[mo + k] = kl;
             a.nbr[mo + k] = kr;
-            a.c6[mo + k] = T(6) / (h * qi.D);
-            a.cx[mo + k] = qi.d_x / qi.D;
-            a.phi[mo + k] = qi.phi;
-            a.ddx[mo + k] = qi.d_x;
-            r2 = (double)Rk * (double)Rk;
-            gmin = (double)gam;
+            a.c6[mo + k] = TS(6.0 / (h * qi.D));
+            a.cx[mo + k] = TS(qi.d_x / qi.D);
+            a.phi[mo + k] = TS(qi.phi);
+            a.ddx[mo + k] = TS(qi.d_x);
+            r2 = Rk * Rk;
+            gmin = gam;
         }
         double v[1] = {r2};
         block_sum<1>(v, red);
@@ -513,9 +533,11 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<T> a)
                 s.bnorm2 = bn2;
                 s.bnorm = sqrt(bn2);
                 s.min_gamma = gmn;
-                int kind = a.solver;
-                if (kind == NH_SOLVER_AUTO) kind = (gmn > 0.0) ? NH_SOLVER_CG : NH_SOLVER_BICGSTAB;
-                s.kind = kind;
+                // AUTO: the operator is symmetric, so CG; gamma > 0 on every
+                // active cell guarantees positive definiteness, otherwise CG's
+                // own curvature checks decide and BiCGStab takes over on failure
+                s.auto_kind = (a.solver == NH_SOLVER_AUTO);
+                s.kind = (a.solver == NH_SOLVER_BICGSTAB) ? NH_SOLVER_BICGSTAB : NH_SOLVER_CG;
             }
         }
     }
@@ -533,6 +555,8 @@ struct SolveArgs {
     const double* psi_prev;    // dense, previous step's pressure unknown
     double guess_scale;        // dt_new / dt_old, or 0 for a zero guess
     T* x; T* r; T* p0; T* p1; T* q; T* rh; T* v0; T* v1; T* s; T* t;
+    T* r1; T* z;               // PCG: second residual buffer, preconditioned residual
+    int maxpb;                 // preconditioner blocks per member (upper bound)
     MState* ms; Ctl* ctl;
     double* part;              // [3][nb * maxch]
     int* cnt;
@@ -569,6 +593,7 @@ __global__ void __launch_bounds__(kChunk) k_solve_init(SolveArgs<T> a)
 {
     __shared__ double red[64];
     NH_FOR_ITEMS(a)
+        if (a.ms[b].done) continue;
         double rr = 0.0;
         if (in) {
             const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
@@ -626,6 +651,22 @@ __device__ __forceinline__ void finish_member(MState& s, Ctl* ctl, int status, i
     atomicSub(&ctl->not_done, 1);
 }
 
+// CG curvature or preconditioner breakdown: AUTO members hand over to
+// BiCGStab (restarted from the warm start); forced CG reports NONFINITE.
+template <typename T>
+__device__ __forceinline__ void cg_breakdown(MState& s, Ctl* ctl, int it)
+{
+    if (s.auto_kind && s.kind == NH_SOLVER_CG) {
+        s.status = kStatusFallback;
+        s.iters = it;
+        s.done = 1;
+        atomicSub(&ctl->not_done, 1);
+        atomicAdd(&ctl->n_fallback, 1);
+    } else {
+        finish_member<T>(s, ctl, NH_ERR_NONFINITE, it, NAN);
+    }
+}
+
 // CG, first half of iteration it: p = r + beta p_old (neighbours on the fly),
 // q = A p, partial <p, q>; last CTA of the member: alpha = rr / <p, q>.
 template <typename T>
@@ -656,7 +697,7 @@ __global__ void __launch_bounds__(kChunk) k_cg_a(SolveArgs<T> a)
             const double s_pq = member_sum(a.part + (size_t)b * a.maxch, nch, red);
             if (threadIdx.x == 0) {
                 MState& s = a.ms[b];
-                if (!isfinite(s_pq) || s_pq == 0.0) finish_member<T>(s, a.ctl, NH_ERR_NONFINITE, it, NAN);
+                if (!isfinite(s_pq) || !(s_pq > 0.0)) cg_breakdown<T>(s, a.ctl, it);
                 else s.alpha = s.rr / s_pq;
             }
         }
@@ -839,6 +880,325 @@ __global__ void __launch_bounds__(kChunk) k_bi_3(SolveArgs<T> a)
     NH_END_ITEMS
 }
 
+
+// ------------------------------------------- preconditioned CG (line / PCR)
+
+// Line preconditioner z = M^{-1} r_new.  M is the tridiagonal operator
+// restricted to blocks of kPcrRows consecutive active cells (couplings across a
+// block edge are dropped; a contiguous active segment inside one block is
+// solved exactly), factorised by parallel cyclic reduction in shared memory in
+// precision TP.  Partials <z, r_new> and <z, r_old> feed the flexible
+// (Polak-Ribiere) beta = (<z, r_new> - <z, r_old>) / <z_old, r_old>, which
+// tolerates the rounding of a low-precision preconditioner.  it == 0 is the
+// set-up pass after k_solve_init (rz only).
+enum { PCR_PCG = 0, PCR_BI_P = 1, PCR_BI_S = 2 };
+
+// Right-hand side of the preconditioner solve for row k and the vector it is
+// stored in (BiCGStab forms p and s here, element-wise, before solving).
+template <typename T>
+__device__ __forceinline__ T pcr_rhs(const SolveArgs<T>& a, int mode, const T* rnew, size_t idx,
+                                     T beta, T omega, T alpha)
+{
+    if (mode == PCR_PCG) return rnew[idx];
+    if (mode == PCR_BI_P) {
+        const T pk = a.r[idx] + beta * (a.p0[idx] - omega * a.v0[idx]);
+        a.p0[idx] = pk;
+        return pk;
+    }
+    const T sk = a.r[idx] - alpha * a.v0[idx];
+    a.s[idx] = sk;
+    return sk;
+}
+
+template <typename T, typename TP>
+__global__ void __launch_bounds__(kPcrThreads) k_pcr(SolveArgs<T> a, int mode)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TP* sa = reinterpret_cast<TP*>(smem_raw);
+    TP* sb = sa + kPcrRows;
+    TP* sc = sb + kPcrRows;
+    TP* sd = sc + kPcrRows;
+    __shared__ double red[64];
+    constexpr int RPT = kPcrRows / kPcrThreads;
+    const int it = a.it;
+    const T* rnew = (it & 1) ? a.r1 : a.r;
+    const T* rold = (it & 1) ? a.r : a.r1;
+    const size_t stride = (size_t)a.nb * a.maxpb;
+    for (int wi = blockIdx.x; wi < a.nb * a.maxpb; wi += gridDim.x) {
+        const int b = wi / a.maxpb, jb = wi - b * a.maxpb;
+        const int want = (mode == PCR_PCG) ? NH_SOLVER_CG : NH_SOLVER_BICGSTAB;
+        if (a.ms[b].done || a.ms[b].kind != want) continue;
+        const int n = a.ms[b].n_active;
+        const int npb = (n + kPcrRows - 1) / kPcrRows;
+        if (jb >= npb) continue;
+        const size_t mo = (size_t)b * a.pitch;
+        const int k0 = jb * kPcrRows;
+        const int rows = min(kPcrRows, n - k0);
+        const T beta = T(a.ms[b].beta), omega = T(a.ms[b].omega), alpha = T(a.ms[b].alpha);
+        double ss = 0.0;
+        for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
+            const int k = k0 + i;
+            const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+            sa[i] = (i > 0 && kl == k - 1) ? TP(a.offl[mo + k]) : TP(0);
+            sc[i] = (i < rows - 1 && kr == k + 1) ? TP(a.offr[mo + k]) : TP(0);
+            sb[i] = TP(a.diag[mo + k]);
+            const T rhs = pcr_rhs(a, mode, rnew, mo + k, beta, omega, alpha);
+            if (mode == PCR_BI_S) ss += (double)rhs * (double)rhs;
+            sd[i] = TP(rhs);
+        }
+        __syncthreads();
+        for (int s = 1; s < rows; s <<= 1) {
+            TP na[RPT], nb2[RPT], nc[RPT], nd[RPT];
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                const int i = threadIdx.x + m * kPcrThreads;
+                if (i < rows) {
+                    const TP ai = sa[i], ci = sc[i];
+                    TP a2 = TP(0), c2 = TP(0), b2 = sb[i], d2 = sd[i];
+                    if (i - s >= 0) {
+                        const TP al = -ai / sb[i - s];
+                        a2 = al * sa[i - s]; b2 += al * sc[i - s]; d2 += al * sd[i - s];
+                    }
+                    if (i + s < rows) {
+                        const TP ga = -ci / sb[i + s];
+                        c2 = ga * sc[i + s]; b2 += ga * sa[i + s]; d2 += ga * sd[i + s];
+                    }
+                    na[m] = a2; nb2[m] = b2; nc[m] = c2; nd[m] = d2;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                const int i = threadIdx.x + m * kPcrThreads;
+                if (i < rows) { sa[i] = na[m]; sb[i] = nb2[m]; sc[i] = nc[m]; sd[i] = nd[m]; }
+            }
+            __syncthreads();
+        }
+        double acc[2] = {0.0, 0.0};
+        // PCG: z = M^{-1} r_new;  BiCGStab: p-hat (into p1) or s-hat (into z)
+        T* out = (mode == PCR_BI_P) ? a.p1 : a.z;
+        for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
+            const int k = k0 + i;
+            const T zk = T(sd[i] / sb[i]);
+            out[mo + k] = zk;
+            if (mode == PCR_PCG) {
+                acc[0] += (double)zk * (double)rnew[mo + k];
+                if (it > 0) acc[1] += (double)zk * (double)rold[mo + k];
+            }
+        }
+        if (mode == PCR_BI_P) continue;   // no reduction needed for p-hat
+        if (mode == PCR_BI_S) acc[0] = ss;
+        block_sum<2>(acc, red);
+        if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
+        if (mode == PCR_BI_S) {
+            if (arrive_last(a.cnt, b, npb)) {
+                const double s_ss = member_sum(a.part + (size_t)b * a.maxpb, npb, red);
+                if (threadIdx.x == 0) {
+                    MState& st = a.ms[b];
+                    st.snorm = sqrt(s_ss);
+                    if (!isfinite(s_ss)) finish_member<T>(st, a.ctl, NH_ERR_NONFINITE, it, NAN);
+                    else if (st.snorm <= a.rtol * st.bnorm) st.s_conv = 1;
+                }
+            }
+            continue;
+        }
+        if (arrive_last(a.cnt, b, npb)) {
+            const size_t mb = (size_t)b * a.maxpb;
+            const double zr = member_sum(a.part + mb, npb, red);
+            const double zro = member_sum(a.part + stride + mb, npb, red);
+            if (threadIdx.x == 0) {
+                MState& st = a.ms[b];
+                if (!isfinite(zr) || !(zr > 0.0)) cg_breakdown<T>(st, a.ctl, it);
+                else if (it == 0) st.rz = zr;
+                else { st.beta = (zr - zro) / st.rz; st.rz = zr; }
+            }
+        }
+    }
+}
+
+// PCG, first kernel of iteration it: p = z + beta p_old (neighbours on the
+// fly), q = A p, partial <p, q>; last CTA: alpha = <r, z> / <p, q>.
+template <typename T>
+__global__ void __launch_bounds__(kChunk) k_pcg_a(SolveArgs<T> a)
+{
+    __shared__ double red[64];
+    const int it = a.it;
+    const T* pold = (it & 1) ? a.p0 : a.p1;
+    T* pnew = (it & 1) ? a.p1 : a.p0;
+    NH_FOR_ITEMS(a)
+        if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_CG) continue;
+        const T beta = (it == 1) ? T(0) : T(a.ms[b].beta);
+        double pq = 0.0;
+        if (in) {
+            const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+            const T pk = a.z[mo + k] + beta * pold[mo + k];
+            const T pl = kl >= 0 ? a.z[mo + kl] + beta * pold[mo + kl] : T(0);
+            const T pr = kr >= 0 ? a.z[mo + kr] + beta * pold[mo + kr] : T(0);
+            const T qk = apply_row(a, mo, k, pk, pl, pr);
+            pnew[mo + k] = pk;
+            a.q[mo + k] = qk;
+            pq = (double)pk * (double)qk;
+        }
+        double v[1] = {pq};
+        block_sum<1>(v, red);
+        if (threadIdx.x == 0) a.part[wi] = v[0];
+        if (arrive_last(a.cnt, b, nch)) {
+            const double s_pq = member_sum(a.part + (size_t)b * a.maxch, nch, red);
+            if (threadIdx.x == 0) {
+                MState& s = a.ms[b];
+                if (!isfinite(s_pq) || !(s_pq > 0.0)) cg_breakdown<T>(s, a.ctl, it);
+                else s.alpha = s.rz / s_pq;
+            }
+        }
+    NH_END_ITEMS
+}
+
+// PCG, second kernel: x += alpha p, r_new = r_old - alpha q (other buffer),
+// partial <r_new, r_new>; last CTA: convergence test on ||r_new|| / ||R||.
+template <typename T>
+__global__ void __launch_bounds__(kChunk) k_pcg_b(SolveArgs<T> a)
+{
+    __shared__ double red[64];
+    const int it = a.it;
+    const T* p = (it & 1) ? a.p1 : a.p0;
+    const T* rold = (it & 1) ? a.r : a.r1;
+    T* rnew = (it & 1) ? a.r1 : a.r;
+    NH_FOR_ITEMS(a)
+        if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_CG) continue;
+        const T alpha = T(a.ms[b].alpha);
+        double rr = 0.0;
+        if (in) {
+            a.x[mo + k] = a.x[mo + k] + alpha * p[mo + k];
+            const T rk = rold[mo + k] - alpha * a.q[mo + k];
+            rnew[mo + k] = rk;
+            rr = (double)rk * (double)rk;
+        }
+        double v[1] = {rr};
+        block_sum<1>(v, red);
+        if (threadIdx.x == 0) a.part[wi] = v[0];
+        if (arrive_last(a.cnt, b, nch)) {
+            const double s_rr = member_sum(a.part + (size_t)b * a.maxch, nch, red);
+            if (threadIdx.x == 0) {
+                MState& s = a.ms[b];
+                const double rel = sqrt(s_rr) / s.bnorm;
+                if (!isfinite(s_rr)) finish_member<T>(s, a.ctl, NH_ERR_NONFINITE, it, NAN);
+                else if (sqrt(s_rr) <= a.rtol * s.bnorm) finish_member<T>(s, a.ctl, NH_OK, it, rel);
+                else if (it >= a.max_iter) finish_member<T>(s, a.ctl, NH_ERR_NOT_CONVERGED, it, rel);
+                else s.rr = s_rr;
+            }
+        }
+    NH_END_ITEMS
+}
+
+
+// Preconditioned (right) BiCGStab.  Per iteration: k_pcr(PCR_BI_P) forms
+// p = r + beta (p - omega v) and p-hat = M^{-1} p; k_pbi_mv(0) v = A p-hat,
+// alpha = rho / <rh, v>; k_pcr(PCR_BI_S) forms s = r - alpha v, s-hat =
+// M^{-1} s and tests ||s||; k_pbi_mv(1) t = A s-hat, omega = <t,s>/<t,t>;
+// k_pbi_upd x += alpha p-hat + omega s-hat, r = s - omega t, tests ||r||.
+template <typename T>
+__global__ void __launch_bounds__(kChunk) k_pbi_mv(SolveArgs<T> a, int which)
+{
+    __shared__ double red[64];
+    const int it = a.it;
+    const T* xin = which == 0 ? a.p1 : a.z;        // p-hat or s-hat
+    T* yout = which == 0 ? a.v0 : a.t;             // v or t
+    const size_t stride = (size_t)a.nb * a.maxch;
+    NH_FOR_ITEMS(a)
+        if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_BICGSTAB) continue;
+        if (which == 1 && a.ms[b].s_conv) continue;
+        double acc[2] = {0.0, 0.0};
+        if (in) {
+            const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+            const T xk = xin[mo + k];
+            const T xl = kl >= 0 ? xin[mo + kl] : T(0);
+            const T xr = kr >= 0 ? xin[mo + kr] : T(0);
+            const T yk = apply_row(a, mo, k, xk, xl, xr);
+            yout[mo + k] = yk;
+            if (which == 0) {
+                acc[0] = (double)a.rh[mo + k] * (double)yk;
+            } else {
+                const double sk = (double)a.s[mo + k];
+                acc[0] = (double)yk * sk;
+                acc[1] = (double)yk * (double)yk;
+            }
+        }
+        block_sum<2>(acc, red);
+        if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
+        if (arrive_last(a.cnt, b, nch)) {
+            const size_t mb = (size_t)b * a.maxch;
+            const double s0 = member_sum(a.part + mb, nch, red);
+            const double s1 = which == 1 ? member_sum(a.part + stride + mb, nch, red) : 0.0;
+            if (threadIdx.x == 0) {
+                MState& s = a.ms[b];
+                if (which == 0) {
+                    if (!isfinite(s0) || s0 == 0.0) finish_member<T>(s, a.ctl, NH_ERR_NONFINITE, it, NAN);
+                    else s.alpha = s.rr / s0;
+                } else {
+                    if (!isfinite(s1) || s1 == 0.0) finish_member<T>(s, a.ctl, NH_ERR_NONFINITE, it, NAN);
+                    else s.omega = s0 / s1;
+                }
+            }
+        }
+    NH_END_ITEMS
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kChunk) k_pbi_upd(SolveArgs<T> a)
+{
+    __shared__ double red[64];
+    const int it = a.it;
+    const size_t stride = (size_t)a.nb * a.maxch;
+    NH_FOR_ITEMS(a)
+        if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_BICGSTAB) continue;
+        const T alpha = T(a.ms[b].alpha), omega = T(a.ms[b].omega);
+        const bool sconv = a.ms[b].s_conv != 0;
+        double acc[2] = {0.0, 0.0};
+        if (in) {
+            if (sconv) {
+                a.x[mo + k] = a.x[mo + k] + alpha * a.p1[mo + k];
+            } else {
+                a.x[mo + k] = a.x[mo + k] + alpha * a.p1[mo + k] + omega * a.z[mo + k];
+                const T rk = a.s[mo + k] - omega * a.t[mo + k];
+                a.r[mo + k] = rk;
+                acc[0] = (double)rk * (double)rk;
+                acc[1] = (double)a.rh[mo + k] * (double)rk;
+            }
+        }
+        block_sum<2>(acc, red);
+        if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
+        if (arrive_last(a.cnt, b, nch)) {
+            const size_t mb = (size_t)b * a.maxch;
+            const double rr = member_sum(a.part + mb, nch, red);
+            const double rhr = member_sum(a.part + stride + mb, nch, red);
+            if (threadIdx.x == 0) {
+                MState& s = a.ms[b];
+                if (sconv) {
+                    finish_member<T>(s, a.ctl, NH_OK, it, s.snorm / s.bnorm);
+                } else {
+                    const double rn = sqrt(rr);
+                    if (!isfinite(rr)) finish_member<T>(s, a.ctl, NH_ERR_NONFINITE, it, NAN);
+                    else if (rn <= a.rtol * s.bnorm) finish_member<T>(s, a.ctl, NH_OK, it, rn / s.bnorm);
+                    else if (it >= a.max_iter) finish_member<T>(s, a.ctl, NH_ERR_NOT_CONVERGED, it, rn / s.bnorm);
+                    else { s.beta = (rhr / s.rr) * (s.alpha / s.omega); s.rr = rhr; }
+                }
+            }
+        }
+    NH_END_ITEMS
+}
+
+// Members whose CG broke down restart as BiCGStab members.
+__global__ void k_fallback_reset(MState* ms, int nb)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    MState& s = ms[b];
+    if (s.status == kStatusFallback) {
+        s.status = NH_OK; s.done = 0; s.kind = NH_SOLVER_BICGSTAB; s.s_conv = 0;
+        s.alpha = 1.0; s.beta = 0.0; s.omega = 1.0;
+    }
+}
+
 // ------------------------------------------------------------- correction
 
 struct ClearArgs {
@@ -864,7 +1224,7 @@ struct CorrArgs {
     int nb, pitch, maxch;
     double dx;
     const int* list; const int* nbl; const int* nbr;
-    const T* x;
+    const double* x;       // psi on active cells (FP64)
     const T* c6; const T* cx; const T* phi; const T* ddx;
     const MState* ms;
     T* hu; T* hw;          // Q~ buffers, corrected in place into Q^{n+1}
@@ -885,15 +1245,171 @@ __global__ void __launch_bounds__(kChunk) k_correct(CorrArgs<T> a)
         if (k >= n) continue;
         const bool zero = s.zero_sol != 0;
         const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
-        const T ps = zero ? T(0) : a.x[mo + k];
-        const T pl = (zero || kl < 0) ? T(0) : a.x[mo + kl];
-        const T pr = (zero || kr < 0) ? T(0) : a.x[mo + kr];
-        const T ps_x = (pr - pl) / (T(2) * T(a.dx));
-        const T P = a.c6[mo + k] * ps + a.cx[mo + k] * ps_x + a.phi[mo + k];
+        const double ps = zero ? 0.0 : a.x[mo + k];
+        const double pl = (zero || kl < 0) ? 0.0 : a.x[mo + kl];
+        const double pr = (zero || kr < 0) ? 0.0 : a.x[mo + kr];
+        const T ps_x = T((pr - pl) / (2.0 * a.dx));
+        const T P = a.c6[mo + k] * T(ps) + a.cx[mo + k] * ps_x + a.phi[mo + k];
         const int i = a.list[mo + k];
         a.hu[mo + i] = a.hu[mo + i] - ps_x + a.ddx[mo + k] * P;
         a.hw[mo + i] = a.hw[mo + i] + P;
-        a.psi[mo + i] = (double)ps;
+        a.psi[mo + i] = ps;
+    }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n)
+{
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        b[q] = (float)a[q];
+}
+
+// zeta = h - d0 from an FP64 host-layout staging array (pitched), and back.
+template <typename T>
+__global__ void k_state_in(const double* __restrict__ h, const double* __restrict__ hu,
+                           const double* __restrict__ hw, const double* __restrict__ d0,
+                           T* z, T* tu, T* tw, int nb, int nx, int pitch)
+{
+    const size_t total = (size_t)nb * nx;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = q / nx, i = q - b * nx, o = b * pitch + i;
+        z[o] = T(h[q] - d0[o]);
+        tu[o] = T(hu[q]);
+        tw[o] = T(hw[q]);
+    }
+}
+
+template <typename T>
+__global__ void k_state_out(const T* __restrict__ z, const T* __restrict__ tu, const T* __restrict__ tw,
+                            const double* __restrict__ d0, const double* __restrict__ psi,
+                            double* h, double* hu, double* hw, double* p, double rho_over_dt,
+                            int nb, int nx, int pitch)
+{
+    const size_t total = (size_t)nb * nx;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = q / nx, i = q - b * nx, o = b * pitch + i;
+        const double hh = (double)z[o] + d0[o];
+        h[q] = hh;
+        hu[q] = (double)tu[o];
+        hw[q] = (double)tw[o];
+        p[q] = rho_over_dt * psi[o] / hh;
+    }
+}
+
+// ------------------------------------------------ mixed precision: refinement
+
+// Outer (FP64) iterate of the mixed path.  k_ir_resid computes
+// r64 = R - A x64 in FP64 on the active cells (x64 gathered from the previous
+// pressure at pass 0), tests ||r64|| <= rtol ||R||, and hands r64 rounded to
+// FP32 to the inner FP32 Krylov solve as its right-hand side.
+struct IRState {
+    double bnorm64;
+    double rel;
+    int done;
+    int passes;
+    int status;
+    int iters;          // inner Krylov iterations summed over passes
+};
+
+struct IRArgs {
+    int nb, pitch, maxch;
+    const int* list; const int* nbl; const int* nbr;
+    const double* diag; const double* offl; const double* offr; const double* R;
+    const double* psi_prev; double guess_scale;
+    double* x64;
+    const float* e32;       // inner solution
+    float* rhs32;           // inner right-hand side
+    MState* ms; IRState* ir; Ctl* ctl;
+    double* part; int* cnt;
+    double rtol;
+    int pass;               // 0: x64 = warm start; >0: after k_ir_update
+    int ir_max;
+};
+
+__global__ void __launch_bounds__(kChunk) k_ir_resid(IRArgs a)
+{
+    __shared__ double red[64];
+    const size_t stride = (size_t)a.nb * a.maxch;
+    for (int wi = blockIdx.x; wi < a.nb * a.maxch; wi += gridDim.x) {
+        const int b = wi / a.maxch, j = wi - b * a.maxch;
+        const int nch = a.ms[b].nchunks;
+        if (j >= nch) continue;
+        if (a.pass > 0 && a.ir[b].done) continue;
+        const int n = a.ms[b].n_active;
+        const size_t mo = (size_t)b * a.pitch;
+        const int k = j * kChunk + threadIdx.x;
+        double acc[2] = {0.0, 0.0};
+        if (k < n) {
+            const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+            double xk = 0.0, xl = 0.0, xr = 0.0;
+            if (a.pass == 0) {
+                const double sc = a.guess_scale;
+                if (sc != 0.0) {
+                    xk = a.psi_prev[mo + a.list[mo + k]] * sc;
+                    if (kl >= 0) xl = a.psi_prev[mo + a.list[mo + kl]] * sc;
+                    if (kr >= 0) xr = a.psi_prev[mo + a.list[mo + kr]] * sc;
+                }
+                a.x64[mo + k] = xk;
+            } else {
+                xk = a.x64[mo + k];
+                if (kl >= 0) xl = a.x64[mo + kl];
+                if (kr >= 0) xr = a.x64[mo + kr];
+            }
+            const double rk = a.R[mo + k] - (a.diag[mo + k] * xk + a.offl[mo + k] * xl + a.offr[mo + k] * xr);
+            const float rf = (float)rk;
+            a.rhs32[mo + k] = rf;
+            acc[0] = rk * rk;
+            acc[1] = (double)rf * (double)rf;
+        }
+        block_sum<2>(acc, red);
+        if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
+        if (arrive_last(a.cnt, b, nch)) {
+            const size_t mb = (size_t)b * a.maxch;
+            const double rr = member_sum(a.part + mb, nch, red);
+            const double rr32 = member_sum(a.part + stride + mb, nch, red);
+            if (threadIdx.x == 0) {
+                IRState& q = a.ir[b];
+                MState& s = a.ms[b];
+                if (a.pass == 0) {
+                    q.bnorm64 = s.bnorm; q.done = 0; q.passes = 0; q.status = NH_OK; q.iters = 0;
+                } else {
+                    q.iters += s.iters;
+                    if (s.status == NH_ERR_NONFINITE) q.status = NH_ERR_NONFINITE;
+                }
+                q.passes = a.pass;
+                const double rel = q.bnorm64 > 0.0 ? sqrt(rr) / q.bnorm64 : 0.0;
+                q.rel = rel;
+                bool fin = true;
+                if (q.bnorm64 == 0.0) { s.zero_sol = 1; q.rel = 0.0; }
+                else if (q.status != NH_OK) { }
+                else if (!isfinite(rr)) q.status = NH_ERR_NONFINITE;
+                else if (sqrt(rr) <= a.rtol * q.bnorm64) { }
+                else if (a.pass >= a.ir_max) q.status = NH_ERR_NOT_CONVERGED;
+                else fin = false;
+                if (fin) {
+                    q.done = 1;
+                    s.done = 1; s.status = q.status; s.rel_res = q.rel; s.iters = q.iters;
+                } else {
+                    // set up the next inner FP32 solve: right-hand side rhs32
+                    s.bnorm2 = rr32; s.bnorm = sqrt(rr32); s.done = 0; s.iters = 0;
+                    s.status = NH_OK; s.s_conv = 0; s.rel_res = 0.0;
+                    atomicAdd(&a.ctl->ir_pending, 1);
+                }
+            }
+        }
+    }
+}
+
+// x64 += e32 on the active cells of members that ran an inner solve in this
+// pass (those not yet done after the previous residual).
+__global__ void k_ir_update(IRArgs a)
+{
+    const size_t total = (size_t)a.nb * a.pitch;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(q / a.pitch), k = (int)(q - (size_t)b * a.pitch);
+        if (!a.ir[b].done && k < a.ms[b].n_active) a.x64[q] += (double)a.e32[q];
     }
 }
 

@@ -27,12 +27,16 @@ NH_LIM_NONE, NH_LIM_CENTRAL, NH_LIM_MINMOD, NH_LIM_MC = range(4)
  NH_CRIT_W, NH_CRIT_W_X) = range(8)
 NH_SOLVER_AUTO, NH_SOLVER_CG, NH_SOLVER_BICGSTAB = range(3)
 NH_GUESS_ZERO, NH_GUESS_PREV = 0, 1
+NH_PRECOND_NONE, NH_PRECOND_LINE = 0, 1
 NH_SLIDE_NONE, NH_SLIDE_GAUSS_LNCOSH = 0, 1
 
 # every exported symbol of the ABI (checked by the CPU test suite)
 EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion",
-           "nh_set_solver", "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run",
-           "nh_destroy", "nh_status_string")
+           "nh_set_solver", "nh_set_preconditioner", "nh_set_state", "nh_put_state", "nh_get_state",
+           "nh_get_mask", "nh_step", "nh_run", "nh_set_profiling", "nh_get_profile", "nh_destroy",
+           "nh_status_string")
+KERNEL_CLASSES = ("kinematics", "predict", "compact", "assemble", "solve_init", "precond", "pcg_a",
+                  "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct")
 
 
 class nh_grid_desc(C.Structure):
@@ -96,8 +100,12 @@ def load():
         L.nh_set_criterion.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int]
         L.nh_set_solver.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
                                     C.c_double]
+        L.nh_set_preconditioner.argtypes = [C.c_void_p, C.c_int]
         L.nh_set_state.argtypes = [C.c_void_p, _D, _D, _D, C.c_double]
         L.nh_get_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
+        L.nh_put_state.argtypes = [C.c_void_p, _D, _D, _D]
+        L.nh_set_profiling.argtypes = [C.c_void_p, C.c_int]
+        L.nh_get_profile.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
         L.nh_get_mask.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), C.POINTER(C.c_int), _D]
         L.nh_step.argtypes = [C.c_void_p, C.c_double, C.POINTER(nh_step_info)]
         L.nh_run.argtypes = [C.c_void_p, C.c_double, C.c_longlong, C.POINTER(nh_run_info)]
@@ -106,6 +114,7 @@ def load():
         L.nh_status_string.argtypes = [C.c_int]
         L.nh_status_string.restype = C.c_char_p
         for f in ("nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
+                  "nh_set_preconditioner", "nh_put_state", "nh_set_profiling", "nh_get_profile",
                   "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run"):
             getattr(L, f).restype = C.c_int
         _LIB = L
@@ -184,9 +193,12 @@ class Grid:
                                        int(bool(first_step_global))), "nh_set_criterion")
 
     def set_solver(self, kind=NH_SOLVER_AUTO, rtol=1e-12, max_iter=20000, guess=NH_GUESS_PREV,
-                   ir_max=8, inner_rtol=1e-5):
+                   ir_max=30, inner_rtol=1e-5):
         _check(self.L.nh_set_solver(self.h, int(kind), float(rtol), int(max_iter), int(guess),
                                     int(ir_max), float(inner_rtol)), "nh_set_solver")
+
+    def set_preconditioner(self, kind=NH_PRECOND_LINE):
+        _check(self.L.nh_set_preconditioner(self.h, int(kind)), "nh_set_preconditioner")
 
     # -- state
     def set_state(self, h, hu, hw, t=0.0):
@@ -198,6 +210,21 @@ class Grid:
         """Same as set_state from raw host addresses (e.g. pinned tensors)."""
         _check(self.L.nh_set_state(self.h, C.cast(C.c_void_p(h_ptr), _D), C.cast(C.c_void_p(hu_ptr), _D),
                                    C.cast(C.c_void_p(hw_ptr), _D), float(t)), "nh_set_state")
+
+    def put_state_ptr(self, h_ptr, hu_ptr, hw_ptr):
+        """Replace the state from raw host addresses, keeping time and warm start."""
+        cast = lambda p: C.cast(C.c_void_p(p), _D)
+        _check(self.L.nh_put_state(self.h, cast(h_ptr), cast(hu_ptr), cast(hw_ptr)), "nh_put_state")
+
+    def set_profiling(self, enable=True):
+        _check(self.L.nh_set_profiling(self.h, int(bool(enable))), "nh_set_profiling")
+
+    def get_profile(self):
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+        _check(self.L.nh_get_profile(self.h, _dptr(ms), n.ctypes.data_as(C.POINTER(C.c_longlong))),
+               "nh_get_profile")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def get_state(self):
         n = self.nx * self.nb

@@ -37,7 +37,7 @@ _CRIT = {O.CRIT_GLOBAL: N.NH_CRIT_GLOBAL, O.CRIT_HYDROSTATIC: N.NH_CRIT_HYDROSTA
 
 def make_gpu(wl, crit, knh=1e-3, enlarge=1, first=0, solver=O.SOLVER_AUTO, rtol=1e-12,
              max_iter=20000, guess=O.GUESS_PREV, bc=O.BC_WALL, limiter=O.LIM_CENTRAL,
-             precision=N.NH_FP64, members=None):
+             precision=N.NH_FP64, members=None, precond=N.NH_PRECOND_LINE):
     import copy
     if members is not None:
         wl = copy.copy(wl)
@@ -47,22 +47,25 @@ def make_gpu(wl, crit, knh=1e-3, enlarge=1, first=0, solver=O.SOLVER_AUTO, rtol=
     G.set_solver({O.SOLVER_AUTO: N.NH_SOLVER_AUTO, O.SOLVER_CG: N.NH_SOLVER_CG,
                   O.SOLVER_BICGSTAB: N.NH_SOLVER_BICGSTAB}[solver], rtol, max_iter,
                  N.NH_GUESS_PREV if guess == O.GUESS_PREV else N.NH_GUESS_ZERO)
+    G.set_preconditioner(precond)
     return G
 
 
 def compare(wl, G, ref, tol_eta=1e-9, what=""):
-    """max |d eta| <= tol_eta * a and the same bound on hu, hw relative to their scale."""
+    """max |d eta| <= tol_eta * a and max |d hu|, |d hw| <= tol_eta * a * sqrt(g h_max)
+    (a = the workload's amplitude; a sqrt(g h) is the momentum scale of a wave
+    of that amplitude).  Returns the worst |d eta| / a."""
     h, hu, hw, p = G.get_state()
     worst = 0.0
     for b, (s, infos, mask) in enumerate(ref):
         a = wl.amplitude
-        d_eta = np.max(np.abs(h[b] - s.h))
-        scale_u = max(np.max(np.abs(s.hu)), 1e-30)
-        scale_w = max(np.max(np.abs(s.hw)), 1e-30)
-        d_hu = np.max(np.abs(hu[b] - s.hu)) / scale_u
-        d_hw = np.max(np.abs(hw[b] - s.hw)) / scale_w
+        m = wl.members[b]
+        qscale = a * np.sqrt(9.81 * float(np.max(m.d0)))
+        d_eta = float(np.max(np.abs(h[b] - s.h)))
+        d_hu = float(np.max(np.abs(hu[b] - s.hu)))
+        d_hw = float(np.max(np.abs(hw[b] - s.hw)))
         worst = max(worst, d_eta / a)
         assert d_eta <= tol_eta * a, (what, b, "eta", d_eta / a)
-        assert d_hu <= 10 * tol_eta, (what, b, "hu", d_hu)
-        assert d_hw <= 10 * tol_eta, (what, b, "hw", d_hw)
+        assert d_hu <= tol_eta * qscale, (what, b, "hu", d_hu / qscale)
+        assert d_hw <= tol_eta * qscale, (what, b, "hw", d_hw / qscale)
     return worst
