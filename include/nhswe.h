@@ -214,6 +214,38 @@ nh_status nh_set_profiling(nh_grid* g, int enable);
    since the last nh_set_profiling call.  Errors: NH_ERR_ARG. */
 nh_status nh_get_profile(nh_grid* g, double* ms, long long* launches);
 
+/* ---- Predictor step without any allocation (the paper has no counterpart:
+   this entry point exists for callers that cannot allocate device memory) ----
+
+   Some callers cannot call cudaMalloc or hand the library a workspace: a host
+   framework that plans all device memory before it starts, a real-time loop
+   that must not block in an allocator, or code that cannot keep a workspace
+   alive between calls.  nh_predict_static runs the hydrostatic predictor of
+   Sec. 3.1 (Heun, Eqs. 8-9; the same kernel nh_step uses) on the caller's
+   device buffers for one member and keeps its scratch in a fixed device array
+   inside the library, so it allocates nothing.
+
+   h, hu, hw, d0: device, FP64, nx values each: thickness h > 0 (m), hu, hw
+   (m^2/s) at time t, static depth d0 (m).  h_out, hu_out, hw_out: device,
+   FP64, nx values: the predicted state at t + dt (no non-hydrostatic
+   correction); each output must not alias its input.  slide: host pointer to
+   the member's bottom motion, or NULL for a static bottom.  mass: host
+   pointer receiving sum(h_out) dx, or NULL; when non-NULL the call
+   synchronises `stream`.  Geometry arguments as in nh_grid_desc (one member).
+   Limits: 8 <= nx <= NH_STATIC_MAX_CELLS, else NH_ERR_ARG.
+   The scratch array (about 2.2 MB) is held by every GPU that loads the
+   library until the process exits.  The first call on a device looks up the
+   array's device address (cudaGetSymbolAddress) with that device current;
+   make that first call before any stream capture.  All calls share the
+   array, so calls that overlap on the GPU race; issue them on one stream.
+   Errors: NH_ERR_ARG, NH_ERR_CUDA. */
+#define NH_STATIC_MAX_CELLS 262144
+nh_status nh_predict_static(const double* h, const double* hu, const double* hw,
+                            const double* d0, double* h_out, double* hu_out, double* hw_out,
+                            int nx, double dx, double x0, int bc, int limiter, double g,
+                            const nh_slide_desc* slide, double t, double dt, double* mass,
+                            void* stream);
+
 /* Release the handle (the workspace stays the caller's). */
 void nh_destroy(nh_grid* g);
 

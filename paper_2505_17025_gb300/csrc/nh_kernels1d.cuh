@@ -24,7 +24,7 @@ struct Geo {
 
 // ------------------------------------------------------------------ slide
 
-__global__ void k_kinematics(const Slide* __restrict__ sl, Kin* __restrict__ kin, int nb,
+static __global__ void k_kinematics(const Slide* __restrict__ sl, Kin* __restrict__ kin, int nb,
                              double t_n, double t_n1)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -272,7 +272,7 @@ struct CompactArgs {
 // `enlarge` cells with word shifts (wrapped explicitly at periodic ends),
 // then compacted in cell order: popcount per word, block-wide exclusive scan,
 // each thread writes the positions of its set bits.
-__global__ void __launch_bounds__(kCompactThreads) k_compact(CompactArgs a)
+static __global__ void __launch_bounds__(kCompactThreads) k_compact(CompactArgs a)
 {
     extern __shared__ uint32_t s_m[];
     __shared__ int s_wsum[32];
@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(kChunk) k_pbi_upd(SolveArgs<T> a)
 }
 
 // Members whose CG broke down restart as BiCGStab members.
-__global__ void k_fallback_reset(MState* ms, int nb)
+static __global__ void k_fallback_reset(MState* ms, int nb)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -1209,7 +1209,7 @@ struct ClearArgs {
 };
 
 // Zero the dense pressure unknown on the previous step's active cells.
-__global__ void k_clear_prev(ClearArgs a)
+static __global__ void k_clear_prev(ClearArgs a)
 {
     const size_t total = (size_t)a.nb * a.pitch;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -1257,7 +1257,7 @@ __global__ void __launch_bounds__(kChunk) k_correct(CorrArgs<T> a)
     }
 }
 
-__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n)
+static __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n)
 {
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
         b[q] = (float)a[q];
@@ -1327,7 +1327,7 @@ struct IRArgs {
     int ir_max;
 };
 
-__global__ void __launch_bounds__(kChunk) k_ir_resid(IRArgs a)
+static __global__ void __launch_bounds__(kChunk) k_ir_resid(IRArgs a)
 {
     __shared__ double red[64];
     const size_t stride = (size_t)a.nb * a.maxch;
@@ -1403,7 +1403,7 @@ __global__ void __launch_bounds__(kChunk) k_ir_resid(IRArgs a)
 
 // x64 += e32 on the active cells of members that ran an inner solve in this
 // pass (those not yet done after the previous residual).
-__global__ void k_ir_update(IRArgs a)
+static __global__ void k_ir_update(IRArgs a)
 {
     const size_t total = (size_t)a.nb * a.pitch;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -1427,7 +1427,7 @@ struct Summary {
     double mass;
 };
 
-__global__ void k_summary(const MState* ms, int nb, const double* mass_part, int nparts, double dx,
+static __global__ void k_summary(const MState* ms, int nb, const double* mass_part, int nparts, double dx,
                           Summary* out)
 {
     __shared__ double red[64];

@@ -34,7 +34,8 @@ NH_SLIDE_NONE, NH_SLIDE_GAUSS_LNCOSH = 0, 1
 EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion",
            "nh_set_solver", "nh_set_preconditioner", "nh_set_state", "nh_put_state", "nh_get_state",
            "nh_get_mask", "nh_step", "nh_run", "nh_set_profiling", "nh_get_profile", "nh_destroy",
-           "nh_status_string")
+           "nh_status_string", "nh_predict_static")
+NH_STATIC_MAX_CELLS = 262144
 KERNEL_CLASSES = ("kinematics", "predict", "compact", "assemble", "solve_init", "precond", "pcg_a",
                   "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct")
 
@@ -111,6 +112,11 @@ def load():
         L.nh_run.argtypes = [C.c_void_p, C.c_double, C.c_longlong, C.POINTER(nh_run_info)]
         L.nh_destroy.argtypes = [C.c_void_p]
         L.nh_destroy.restype = None
+        L.nh_predict_static.argtypes = [C.c_void_p] * 7 + [C.c_int, C.c_double, C.c_double, C.c_int,
+                                                           C.c_int, C.c_double,
+                                                           C.POINTER(nh_slide_desc), C.c_double,
+                                                           C.c_double, _D, C.c_void_p]
+        L.nh_predict_static.restype = C.c_int
         L.nh_status_string.argtypes = [C.c_int]
         L.nh_status_string.restype = C.c_char_p
         for f in ("nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
