@@ -42,9 +42,9 @@ BYTES_PER_UNIT_FP64 = {
     "compact": 4.25,      # read mark bits, write dilated bits (2/8) and the int32 list entry
     "assemble": 116.0,    # read zeta~, hu~, hw~, d0, list (36); write 8 coefficients + 2 neighbours (80)
     "solve_init": 84.0,   # read R, 3 coeffs, 2 nbrs, list (44); write x, r, rh, 4 zeroed vectors (..)
-    "precond": 56.0,      # read 3 coeffs, 2 nbrs, r_new, r_old (48); write z (8)
+    "precond": 88.0,      # fused PCG update + PCR: read 3 coeffs, 2 nbrs, x, p, r_old, q (64); write x, r_new, z (24)
     "pcg_a": 64.0,        # read z, p_old, 3 coeffs, 2 nbrs (48); write p, q (16)
-    "pcg_b": 48.0,        # read x, p, r_old, q (32); write x, r_new (16)
+    "pcg_loop": 152.0,    # per PCG iteration: phase A (pcg_a, 64) + phase B (update + PCR, 88)
     "cg_a": 64.0,
     "cg_b": 48.0,
     "correct": 92.0,      # read list, nbrs, x, 4 coeffs, hu, hw (68); write hu, hw, psi (24)
@@ -55,9 +55,9 @@ BYTES_PER_UNIT_MIXED = {
     "compact": 4.25,
     "assemble": 120.0,    # read 3 fields, d0 (FP64), list (24); FP64 op + rhs (32), FP32 op (12), 4 coeffs (16), nbrs (8)
     "solve_init": 44.0,   # k_ir_resid: read R, 3 FP64 coeffs, nbrs, x64 (48, cached neighbours); write rhs32
-    "precond": 32.0,      # read 3 FP32 coeffs, 2 nbrs, r_new, r_old (28); write z (4)
-    "pcg_a": 32.0,
-    "pcg_b": 24.0,
+    "precond": 48.0,      # read 3 FP32 coeffs, 2 nbrs, x, p, r_old, q (36); write x, r_new, z (12)
+    "pcg_a": 36.0,
+    "pcg_loop": 84.0,     # per inner PCG iteration: 36 + 48
     "correct": 50.0,
 }
 def _load_peaks():
@@ -230,6 +230,9 @@ def run_ours(args):
     if dn > 0 and name in table:
         units = cells if name == "predict" else act_mean
         bytes_per_launch = table[name] * units
+        if name == "pcg_loop":
+            # one launch runs every iteration of a solve
+            bytes_per_launch *= iters_mean * args.steps / dn
         achieved = bytes_per_launch / (dms * 1e-3 / dn) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": f"k_{name}",

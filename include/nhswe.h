@@ -201,7 +201,9 @@ nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info);
 enum { NH_K_KINEMATICS = 0, NH_K_PREDICT = 1, NH_K_COMPACT = 2, NH_K_ASSEMBLE = 3,
        NH_K_SOLVE_INIT = 4, NH_K_PRECOND = 5, NH_K_PCG_A = 6, NH_K_PCG_B = 7,
        NH_K_CG_A = 8, NH_K_CG_B = 9, NH_K_BI_1 = 10, NH_K_BI_2 = 11, NH_K_BI_3 = 12,
-       NH_K_SUMMARY = 13, NH_K_CLEAR = 14, NH_K_CORRECT = 15, NH_K_COUNT = 16 };
+       NH_K_SUMMARY = 13, NH_K_CLEAR = 14, NH_K_CORRECT = 15,
+       NH_K_PCG_LOOP = 16,   /* all PCG iterations of a solve in one cooperative launch */
+       NH_K_COUNT = 17 };
 
 /* enable != 0: bracket every kernel launch with CUDA events on the handle's
    stream and accumulate per-class device time (read back at the step's own

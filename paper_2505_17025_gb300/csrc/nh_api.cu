@@ -20,6 +20,8 @@ struct nh_grid {
     nh_grid_desc d;
     cudaStream_t stream;
     int nx, nb, pitch, wpitch, ntiles, maxch, sm_count, items_grid, pcr_grid;
+    int coop_grid[2];            // persistent PCG CTAs (FP64 / FP32 vectors), 0 = unavailable
+    long long barrier_budget;    // clock cycles a grid barrier may spin
     size_t es;                   // element size of state / Krylov vectors
     bool mixed;
     double mass0;                // sum of d0 dx over all members (FP64)
@@ -45,6 +47,7 @@ struct nh_grid {
     Slide* slide; Kin* kin;
     uint32_t* marks; uint32_t* act;
     int* list[2]; int* nact[2];
+    int2* items; int2* pitems;                 // work lists of the step
     double *diag, *offl, *offr, *R;            // FP64 operator and right-hand side
     float *diag32, *offl32, *offr32, *rhs32;   // mixed: FP32 operator and inner rhs
     void *c6, *cx, *phi, *ddx;                 // correction coefficients (type T)
@@ -123,6 +126,8 @@ size_t carve(const nh_grid_desc& d, nh_grid* g, char* base)
         G->list[k] = (int*)c.take(sizeof(int) * N);
         G->nact[k] = (int*)c.take(sizeof(int) * nb);
     }
+    G->items = (int2*)c.take(sizeof(int2) * (size_t)nb * maxch);
+    G->pitems = (int2*)c.take(sizeof(int2) * (size_t)nb * maxpb);
     G->diag = (double*)c.take(N * 8); G->offl = (double*)c.take(N * 8);
     G->offr = (double*)c.take(N * 8); G->R = (double*)c.take(N * 8);
     if (mixed) {
@@ -235,6 +240,7 @@ SolveArgs<T> solve_args(nh_grid* g, int lcur, const T* diag, const T* offl, cons
     a.q = (T*)g->q; a.rh = (T*)g->rh; a.v0 = (T*)g->v0; a.v1 = (T*)g->v1;
     a.s = (T*)g->s; a.t = (T*)g->t;
     a.r1 = (T*)g->r1; a.z = (T*)g->z; a.maxpb = g->maxpb;
+    a.items = g->items; a.pitems = g->pitems;
     a.ms = g->ms; a.ctl = g->ctl; a.part = g->part; a.cnt = g->cnt;
     a.rtol = rtol; a.max_iter = g->max_iter; a.it = 0;
     return a;
@@ -267,6 +273,7 @@ nh_status krylov_pass(nh_grid* g, SolveArgs<T>& sa)
 {
     cudaStream_t st = g->stream;
     CK(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
+    CK(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
     LAUNCH(NH_K_SOLVE_INIT, k_solve_init<T><<<g->items_grid, kChunk, 0, st>>>(sa));
     Ctl hctl;
     CK(cudaMemcpyAsync(&hctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -278,12 +285,27 @@ nh_status krylov_pass(nh_grid* g, SolveArgs<T>& sa)
         LAUNCH(NH_K_PRECOND, k_pcr<T, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG));
     }
     if (hctl.not_done <= 0) return NH_OK;
+    const int cg = g->coop_grid[sizeof(T) == 8 ? 0 : 1];
+    if (pcg && hctl.n_cg > 0 && hctl.n_bicg == 0 && cg > 0) {
+        // every PCG iteration in one cooperative launch, no host round trip
+        CK(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));   // timeout, bar_count, bar_gen
+        long long budget = g->barrier_budget;
+        void* args[] = {(void*)&sa, (void*)&budget};
+        prof_pre(g, NH_K_PCG_LOOP);
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, float>, dim3(cg),
+                                                    dim3(kPcrThreads), args, pcr_smem, st);
+        prof_post(g);
+        if (e != cudaSuccess) return NH_ERR_CUDA;
+        int to = 0;
+        CK(cudaMemcpyAsync(&to, &g->ctl->timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SYNC();
+        return to ? NH_ERR_TIMEOUT : NH_OK;
+    }
     for (int it = 1; it <= g->max_iter; ++it) {
         sa.it = it;
         if (hctl.n_cg > 0 && pcg) {
             LAUNCH(NH_K_PCG_A, k_pcg_a<T><<<g->items_grid, kChunk, 0, st>>>(sa));
-            LAUNCH(NH_K_PCG_B, k_pcg_b<T><<<g->items_grid, kChunk, 0, st>>>(sa));
-            LAUNCH(NH_K_PRECOND, k_pcr<T, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG));
+            LAUNCH(NH_K_PRECOND, k_pcr<T, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG_STEP));
         } else if (hctl.n_cg > 0) {
             LAUNCH(NH_K_CG_A, k_cg_a<T><<<g->items_grid, kChunk, 0, st>>>(sa));
             LAUNCH(NH_K_CG_B, k_cg_b<T><<<g->items_grid, kChunk, 0, st>>>(sa));
@@ -320,7 +342,7 @@ nh_status refine(nh_grid* g, int lnew, double guess_scale)
     ia.psi_prev = g->psi; ia.guess_scale = guess_scale;
     ia.x64 = g->x64; ia.e32 = (const float*)g->x; ia.rhs32 = g->rhs32;
     ia.ms = g->ms; ia.ir = g->ir; ia.ctl = g->ctl; ia.part = g->part; ia.cnt = g->cnt;
-    ia.rtol = g->rtol; ia.ir_max = g->ir_max;
+    ia.rtol = g->rtol; ia.ir_max = g->ir_max; ia.items = g->items;
     SolveArgs<float> sa = solve_args<float>(g, lnew, g->diag32, g->offl32, g->offr32, g->rhs32,
                                             g->inner_rtol);
     const size_t total = (size_t)g->nb * g->pitch;
@@ -373,6 +395,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     ca.ms = g->ms; ca.ctl = g->ctl;
     const size_t csm = sizeof(uint32_t) * (size_t)((g->nx + 31) / 32);
     LAUNCH(NH_K_COMPACT, k_compact<<<g->nb, kCompactThreads, csm, st>>>(ca));
+    LAUNCH(NH_K_COMPACT, k_items<<<1, 1024, 0, st>>>(g->ms, g->nb, g->items, g->pitems, g->ctl));
 
     AsmArgs<T> aa;
     aa.G = G;
@@ -384,6 +407,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     aa.nbl = g->nbl; aa.nbr = g->nbr;
     aa.c6 = (T*)g->c6; aa.cx = (T*)g->cx; aa.phi = (T*)g->phi; aa.ddx = (T*)g->ddx;
     aa.part = g->part; aa.cnt = g->cnt; aa.dt = dt; aa.solver = g->solver;
+    aa.items = g->items; aa.ctl = g->ctl;
     LAUNCH(NH_K_ASSEMBLE, k_assemble<T><<<g->items_grid, kChunk, 0, st>>>(aa));
 
     const double* xfinal;
@@ -425,6 +449,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
         co.c6 = (const T*)g->c6; co.cx = (const T*)g->cx; co.phi = (const T*)g->phi;
         co.ddx = (const T*)g->ddx; co.ms = g->ms;
         co.hu = (T*)g->shu[nxt]; co.hw = (T*)g->shw[nxt]; co.psi = g->psi;
+        co.items = g->items; co.ctl = g->ctl;
         LAUNCH(NH_K_CORRECT, k_correct<T><<<g->items_grid, kChunk, 0, st>>>(co));
         CK(cudaGetLastError());
         g->cur = nxt;
@@ -565,6 +590,27 @@ nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host, void* 
             cudaFuncSetAttribute(k_pcr<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
+        }
+        if (cudaFuncSetAttribute(k_pcg_persistent<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess ||
+            cudaFuncSetAttribute(k_pcg_persistent<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess) {
+            rc = NH_ERR_CUDA; break;
+        }
+        {
+            int coop = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+            const size_t sm_bytes = 4 * sizeof(float) * kPcrRows;
+            g->coop_grid[0] = g->coop_grid[1] = 0;
+            if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<double, float>,
+                                                                      kPcrThreads, sm_bytes) == cudaSuccess)
+                g->coop_grid[0] = per_sm * sms;
+            if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<float, float>,
+                                                                      kPcrThreads, sm_bytes) == cudaSuccess)
+                g->coop_grid[1] = per_sm * sms;
+            int clk_khz = 0;
+            cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+            g->barrier_budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL;   // about one second
         }
         if (cudaFuncSetAttribute(k_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(uint32_t) * ((g->nx + 31) / 32))) != cudaSuccess) {

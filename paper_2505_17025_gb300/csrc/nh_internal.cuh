@@ -66,7 +66,9 @@ struct MState {
     int n_active;
     int nchunks;
     int auto_kind;     // AUTO: CG first, BiCGStab if CG detects indefiniteness
-    int pad;
+    int npb;           // preconditioner blocks
+    int ioff;          // first work item (kChunk cells) of this member in the item list
+    int poff;          // first preconditioner block of this member in the block list
 };
 
 // MState.status value (never returned): CG broke down on an AUTO member,
@@ -79,7 +81,13 @@ struct Ctl {
     int n_cg, n_bicg;  // members per solver kind after set-up
     int ir_pending;    // mixed path: members needing another refinement pass
     int n_fallback;    // AUTO members whose CG broke down in this solve
-    int pad[3];
+    int n_items;       // work items (member, chunk of kChunk active cells) this step
+    int n_pitems;      // preconditioner blocks (member, kPcrRows active cells) this step
+    int timeout;       // a bounded grid barrier gave up (persistent solve)
+    unsigned bar_count;         // grid barrier: arrivals
+    unsigned bar_gen;           // grid barrier: generation
+    int go[2];                  // persistent solve: continue flag per iteration parity
+    int pad2;
 };
 
 __device__ __forceinline__ int resolve(int j, int n, int bc, int* sgn)
@@ -106,7 +114,7 @@ __device__ __forceinline__ T mound_at(int c, double x0, double dx, const Slide& 
 {
     if (sl.shape != NH_SLIDE_GAUSS_LNCOSH) return T(0);
     const double xc = x0 + (c + 0.5) * dx;
-    const T xi = T((xc - sl.xc0 - s) / sl.L);
+    const T xi = T((xc - sl.xc0 - s) * (1.0 / sl.L));
     return T(sl.A) * texp(-xi * xi);
 }
 

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
     const Slide sl = a.slide[b];
     const Kin kn = a.kin[b];
     const T g = T(G.g), dx = T(G.dx), dt = T(a.dt), half_dt = T(0.5) * T(a.dt);
+    const T idx = T(1.0 / G.dx);
 
     // A: load Q^n, d0 and the mound at both times.  Cells outside
     // [-6, nx+5] feed only outputs outside [-1, nx]; they get still water.
@@ -146,9 +147,9 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
             mn = mound_at<T>(c, G.x0, G.dx, sl, kn.s_n);
             mn1 = mound_at<T>(c, G.x0, G.dx, sl, kn.s_n1);
         }
-        const T hv = zv + d0v;
+        const T rh = T(1) / (zv + d0v);
         sz[l] = zv; shu[l] = huv; shw[l] = hwv; sd0[l] = d0v; smn[l] = mn; smn1[l] = mn1;
-        se[l] = zv + mn; su[l] = huv / hv; sw[l] = hwv / hv;
+        se[l] = zv + mn; su[l] = huv * rh; sw[l] = hwv * rh;
     }
     __syncthreads();
 
@@ -175,13 +176,13 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
         const T dm = sd0[l - 1] - smn[l - 1], dc = sd0[l] - smn[l], dp = sd0[l + 1] - smn[l + 1];
         const T dfl = T(0.5) * (dm + dc), dfr = T(0.5) * (dc + dp);
         const T hbar = T(0.5) * ((se[l] - T(0.5) * sle[l] + dfl) + (se[l] + T(0.5) * sle[l] + dfr));
-        const T r0 = -(F0[l + 1] - F0[l]) / dx;
-        const T r1 = -((A1[l + 1] - A1[l]) + (G1[l + 1] + G1[l]) + g * hbar * sle[l]) / dx;
-        const T r2 = -(F2[l + 1] - F2[l]) / dx;
+        const T r0 = -(F0[l + 1] - F0[l]) * idx;
+        const T r1 = -((A1[l + 1] - A1[l]) + (G1[l + 1] + G1[l]) + g * hbar * sle[l]) * idx;
+        const T r2 = -(F2[l + 1] - F2[l]) * idx;
         k1h[l] = r0; k1u[l] = r1; k1w[l] = r2;
         const T zs = sz[l] + dt * r0, hus = shu[l] + dt * r1, hws = shw[l] + dt * r2;
-        const T hs = zs + sd0[l];
-        se[l] = zs + smn1[l]; su[l] = hus / hs; sw[l] = hws / hs;
+        const T rhs = T(1) / (zs + sd0[l]);
+        se[l] = zs + smn1[l]; su[l] = hus * rhs; sw[l] = hws * rhs;
     }
     __syncthreads();
 
@@ -207,9 +208,9 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
         const T dm = sd0[l - 1] - smn1[l - 1], dc = sd0[l] - smn1[l], dp = sd0[l + 1] - smn1[l + 1];
         const T dfl = T(0.5) * (dm + dc), dfr = T(0.5) * (dc + dp);
         const T hbar = T(0.5) * ((se[l] - T(0.5) * sle[l] + dfl) + (se[l] + T(0.5) * sle[l] + dfr));
-        const T r0 = -(F0[l + 1] - F0[l]) / dx;
-        const T r1 = -((A1[l + 1] - A1[l]) + (G1[l + 1] + G1[l]) + g * hbar * sle[l]) / dx;
-        const T r2 = -(F2[l + 1] - F2[l]) / dx;
+        const T r0 = -(F0[l + 1] - F0[l]) * idx;
+        const T r1 = -((A1[l + 1] - A1[l]) + (G1[l + 1] + G1[l]) + g * hbar * sle[l]) * idx;
+        const T r2 = -(F2[l + 1] - F2[l]) * idx;
         const T zn = sz[l] + half_dt * (k1h[l] + r0);
         const T hun = shu[l] + half_dt * (k1u[l] + r1);
         const T hwn = shw[l] + half_dt * (k1w[l] + r2);
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
             if (a.all_global) {
                 mark = true;
             } else if (a.crit >= NH_CRIT_ETA_D) {
-                const T inv2dx = T(1) / (T(2) * dx);
+                const T inv2dx = T(0.5) * idx;
                 // eta~ = zeta~ + m, h~ = zeta~ + d0 at l-1, l, l+1
                 const T em = sz[l - 1] + smn1[l - 1], ec = sz[l] + smn1[l], ep = sz[l + 1] + smn1[l + 1];
                 const T hm = sz[l - 1] + sd0[l - 1], hc = sz[l] + sd0[l], hp = sz[l + 1] + sd0[l + 1];
@@ -353,7 +354,7 @@ static __global__ void __launch_bounds__(kCompactThreads) k_compact(CompactArgs 
         s.rel_res = 0.0; s.min_gamma = 0.0; s.snorm = 0.0;
         s.status = NH_OK; s.iters = 0; s.done = (n == 0); s.kind = -1; s.zero_sol = 0;
         s.s_conv = 0; s.n_active = n; s.nchunks = (n + kChunk - 1) / kChunk;
-        s.auto_kind = 0; s.pad = 0;
+        s.auto_kind = 0; s.npb = (n + kPcrRows - 1) / kPcrRows; s.ioff = 0; s.poff = 0;
         a.ms[b] = s;
     }
 }
@@ -376,6 +377,52 @@ __device__ __forceinline__ bool arrive_last(int* cnt, int b, int total)
     __syncthreads();
     if (s_last) __threadfence();
     return s_last != 0;
+}
+
+// Work lists of the step: item w = (member, chunk of kChunk active cells),
+// pitem w = (member, block of kPcrRows active cells), member-major, so each
+// member's items are contiguous from ms[b].ioff / ms[b].poff.  One CTA.
+static __global__ void __launch_bounds__(1024) k_items(MState* ms, int nb, int2* items, int2* pitems, Ctl* ctl)
+{
+    __shared__ int s_w[2][32];
+    __shared__ int s_base[2];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
+    if (tid == 0) { s_base[0] = 0; s_base[1] = 0; }
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int b = b0 + tid;
+        const int c0 = b < nb ? ms[b].nchunks : 0, c1 = b < nb ? ms[b].npb : 0;
+        int i0 = c0, i1 = c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y0 = __shfl_up_sync(0xffffffffu, i0, o), y1 = __shfl_up_sync(0xffffffffu, i1, o);
+            if (lane >= o) { i0 += y0; i1 += y1; }
+        }
+        if (lane == 31) { s_w[0][wid] = i0; s_w[1][wid] = i1; }
+        __syncthreads();
+        if (wid == 0) {
+            int v0 = lane < nwarp ? s_w[0][lane] : 0, v1 = lane < nwarp ? s_w[1][lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y0 = __shfl_up_sync(0xffffffffu, v0, o), y1 = __shfl_up_sync(0xffffffffu, v1, o);
+                if (lane >= o) { v0 += y0; v1 += y1; }
+            }
+            s_w[0][lane] = v0; s_w[1][lane] = v1;
+        }
+        __syncthreads();
+        const int o0 = s_base[0] + i0 - c0 + (wid > 0 ? s_w[0][wid - 1] : 0);
+        const int o1 = s_base[1] + i1 - c1 + (wid > 0 ? s_w[1][wid - 1] : 0);
+        if (b < nb) {
+            ms[b].ioff = o0;
+            ms[b].poff = o1;
+            for (int j = 0; j < c0; ++j) items[o0 + j] = make_int2(b, j);
+            for (int j = 0; j < c1; ++j) pitems[o1 + j] = make_int2(b, j);
+        }
+        __syncthreads();
+        if (tid == 0) { s_base[0] += s_w[0][nwarp - 1]; s_base[1] += s_w[1][nwarp - 1]; }
+        __syncthreads();
+    }
+    if (tid == 0) { ctl->n_items = s_base[0]; ctl->n_pitems = s_base[1]; }
 }
 
 // Deterministic block-wide sum of part[0..n) (thread 0 gets it).
@@ -409,6 +456,7 @@ struct AsmArgs {
     TS* c6; TS* cx; TS* phi; TS* ddx;           // correction coefficients
     double* part;                               // [2][nb * maxch]
     int* cnt;
+    const int2* items; const Ctl* ctl;
     double dt;
     int solver;                                 // NH_SOLVER_*
 };
@@ -456,11 +504,13 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
     __shared__ double red[64];
     const Geo& G = a.G;
     const int tid = threadIdx.x;
-    for (int wi = blockIdx.x; wi < G.nb * G.maxch; wi += gridDim.x) {
-        const int b = wi / G.maxch, j = wi - b * G.maxch;
+    const int n_items = a.ctl->n_items;
+    for (int wi = blockIdx.x; wi < n_items; wi += gridDim.x) {
+        const int2 itm = a.items[wi];
+        const int b = itm.x, j = itm.y;
         const int n = a.ms[b].n_active;
-        const int nch = (n + kChunk - 1) / kChunk;
-        if (j >= nch) continue;
+        const int nch = a.ms[b].nchunks;
+        const int ioff = a.ms[b].ioff;
         const size_t mo = (size_t)b * G.pitch;
         const TS* zt = a.zt + mo; const TS* hut = a.hut + mo; const TS* hwt = a.hwt + mo;
         const double* D0 = a.d0 + mo;
@@ -526,8 +576,8 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
         double* P1 = a.part + (size_t)G.nb * G.maxch;
         if (tid == 0) { P0[wi] = v[0]; P1[wi] = gm; }
         if (arrive_last(a.cnt, b, nch)) {
-            const double bn2 = member_sum(P0 + (size_t)b * G.maxch, nch, red);
-            const double gmn = member_min(P1 + (size_t)b * G.maxch, nch, red);
+            const double bn2 = member_sum(P0 + ioff, nch, red);
+            const double gmn = member_min(P1 + ioff, nch, red);
             if (tid == 0) {
                 MState& s = a.ms[b];
                 s.bnorm2 = bn2;
@@ -557,6 +607,7 @@ struct SolveArgs {
     T* x; T* r; T* p0; T* p1; T* q; T* rh; T* v0; T* v1; T* s; T* t;
     T* r1; T* z;               // PCG: second residual buffer, preconditioned residual
     int maxpb;                 // preconditioner blocks per member (upper bound)
+    const int2* items; const int2* pitems;
     MState* ms; Ctl* ctl;
     double* part;              // [3][nb * maxch]
     int* cnt;
@@ -576,11 +627,13 @@ __device__ __forceinline__ T apply_row(const SolveArgs<T>& a, size_t mo, int k, 
 
 // Shared prologue of the solve kernels: loop over (member, chunk) work items.
 #define NH_FOR_ITEMS(A)                                                         \
-    for (int wi = blockIdx.x; wi < (A).nb * (A).maxch; wi += gridDim.x) {        \
-        const int b = wi / (A).maxch, j = wi - b * (A).maxch;                   \
+    const int n_items_ = (A).ctl->n_items;                                      \
+    for (int wi = blockIdx.x; wi < n_items_; wi += gridDim.x) {                 \
+        const int2 itm_ = (A).items[wi];                                        \
+        const int b = itm_.x, j = itm_.y;                                       \
         const int nch = (A).ms[b].nchunks;                                      \
-        if (j >= nch) continue;                                                 \
         const int n = (A).ms[b].n_active;                                       \
+        const int ioff = (A).ms[b].ioff;                                        \
         const size_t mo = (size_t)b * (A).pitch;                                \
         const int k = j * kChunk + threadIdx.x;                                 \
         const bool in = k < n;
@@ -619,7 +672,7 @@ __global__ void __launch_bounds__(kChunk) k_solve_init(SolveArgs<T> a)
         double* P0 = a.part;
         if (threadIdx.x == 0) P0[wi] = v[0];
         if (arrive_last(a.cnt, b, nch)) {
-            const double s_rr = member_sum(P0 + (size_t)b * a.maxch, nch, red);
+            const double s_rr = member_sum(P0 + ioff, nch, red);
             if (threadIdx.x == 0) {
                 MState& s = a.ms[b];
                 s.rr = s_rr;
@@ -694,7 +747,7 @@ __global__ void __launch_bounds__(kChunk) k_cg_a(SolveArgs<T> a)
         block_sum<1>(v, red);
         if (threadIdx.x == 0) a.part[wi] = v[0];
         if (arrive_last(a.cnt, b, nch)) {
-            const double s_pq = member_sum(a.part + (size_t)b * a.maxch, nch, red);
+            const double s_pq = member_sum(a.part + ioff, nch, red);
             if (threadIdx.x == 0) {
                 MState& s = a.ms[b];
                 if (!isfinite(s_pq) || !(s_pq > 0.0)) cg_breakdown<T>(s, a.ctl, it);
@@ -727,7 +780,7 @@ __global__ void __launch_bounds__(kChunk) k_cg_b(SolveArgs<T> a)
         block_sum<1>(v, red);
         if (threadIdx.x == 0) a.part[wi] = v[0];
         if (arrive_last(a.cnt, b, nch)) {
-            const double s_rr = member_sum(a.part + (size_t)b * a.maxch, nch, red);
+            const double s_rr = member_sum(a.part + ioff, nch, red);
             if (threadIdx.x == 0) {
                 MState& s = a.ms[b];
                 const double rel = sqrt(s_rr) / s.bnorm;
@@ -769,7 +822,7 @@ __global__ void __launch_bounds__(kChunk) k_bi_1(SolveArgs<T> a)
         block_sum<1>(v, red);
         if (threadIdx.x == 0) a.part[wi] = v[0];
         if (arrive_last(a.cnt, b, nch)) {
-            const double s_rv = member_sum(a.part + (size_t)b * a.maxch, nch, red);
+            const double s_rv = member_sum(a.part + ioff, nch, red);
             if (threadIdx.x == 0) {
                 MState& s = a.ms[b];
                 if (!isfinite(s_rv) || s_rv == 0.0) finish_member<T>(s, a.ctl, NH_ERR_NONFINITE, it, NAN);
@@ -811,7 +864,7 @@ __global__ void __launch_bounds__(kChunk) k_bi_2(SolveArgs<T> a)
             a.part[2 * stride + wi] = acc[2];
         }
         if (arrive_last(a.cnt, b, nch)) {
-            const size_t mb = (size_t)b * a.maxch;
+            const size_t mb = ioff;
             const double ts = member_sum(a.part + mb, nch, red);
             const double tt = member_sum(a.part + stride + mb, nch, red);
             const double ss = member_sum(a.part + 2 * stride + mb, nch, red);
@@ -861,7 +914,7 @@ __global__ void __launch_bounds__(kChunk) k_bi_3(SolveArgs<T> a)
         block_sum<2>(acc, red);
         if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
         if (arrive_last(a.cnt, b, nch)) {
-            const size_t mb = (size_t)b * a.maxch;
+            const size_t mb = ioff;
             const double rr = member_sum(a.part + mb, nch, red);
             const double rhr = member_sum(a.part + stride + mb, nch, red);
             if (threadIdx.x == 0) {
@@ -891,15 +944,25 @@ __global__ void __launch_bounds__(kChunk) k_bi_3(SolveArgs<T> a)
 // (Polak-Ribiere) beta = (<z, r_new> - <z, r_old>) / <z_old, r_old>, which
 // tolerates the rounding of a low-precision preconditioner.  it == 0 is the
 // set-up pass after k_solve_init (rz only).
-enum { PCR_PCG = 0, PCR_BI_P = 1, PCR_BI_S = 2 };
+enum { PCR_PCG = 0, PCR_BI_P = 1, PCR_BI_S = 2, PCR_PCG_STEP = 3 };
 
-// Right-hand side of the preconditioner solve for row k and the vector it is
-// stored in (BiCGStab forms p and s here, element-wise, before solving).
+// Right-hand side of the preconditioner solve for row k, formed element-wise
+// and stored: PCG set-up reads r; the fused PCG step first updates
+// x += alpha p and r_new = r_old - alpha q; BiCGStab forms p and s.
 template <typename T>
-__device__ __forceinline__ T pcr_rhs(const SolveArgs<T>& a, int mode, const T* rnew, size_t idx,
+__device__ __forceinline__ T pcr_rhs(const SolveArgs<T>& a, int mode, int it, size_t idx,
                                      T beta, T omega, T alpha)
 {
-    if (mode == PCR_PCG) return rnew[idx];
+    if (mode == PCR_PCG) return a.r[idx];
+    if (mode == PCR_PCG_STEP) {
+        const T* p = (it & 1) ? a.p1 : a.p0;
+        const T* rold = (it & 1) ? a.r : a.r1;
+        T* rnew = (it & 1) ? a.r1 : a.r;
+        a.x[idx] = a.x[idx] + alpha * p[idx];
+        const T rk = rold[idx] - alpha * a.q[idx];
+        rnew[idx] = rk;
+        return rk;
+    }
     if (mode == PCR_BI_P) {
         const T pk = a.r[idx] + beta * (a.p0[idx] - omega * a.v0[idx]);
         a.p0[idx] = pk;
@@ -910,6 +973,19 @@ __device__ __forceinline__ T pcr_rhs(const SolveArgs<T>& a, int mode, const T* r
     return sk;
 }
 
+// Line preconditioner z = M^{-1} rhs.  M is the tridiagonal operator
+// restricted to blocks of kPcrRows consecutive active cells (couplings across a
+// block edge are dropped; a contiguous active segment inside one block is
+// solved exactly), factorised by parallel cyclic reduction in shared memory in
+// precision TP.
+//  PCR_PCG      (it = 0) after k_solve_init: z = M^{-1} r, rz = <z, r>.
+//  PCR_PCG_STEP (it >= 1) fused second half of PCG iteration it: x += alpha p,
+//               r_new = r_old - alpha q, convergence test on ||r_new||, then
+//               z = M^{-1} r_new and the flexible (Polak-Ribiere)
+//               beta = (<z, r_new> - <z, r_old>) / <z_old, r_old>, which
+//               tolerates the rounding of a low-precision preconditioner.
+//  PCR_BI_P / PCR_BI_S  BiCGStab's p-hat = M^{-1} p (into p1), s-hat = M^{-1} s
+//               (into z) with the ||s|| test.
 template <typename T, typename TP>
 __global__ void __launch_bounds__(kPcrThreads) k_pcr(SolveArgs<T> a, int mode)
 {
@@ -918,19 +994,21 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcr(SolveArgs<T> a, int mode)
     TP* sb = sa + kPcrRows;
     TP* sc = sb + kPcrRows;
     TP* sd = sc + kPcrRows;
-    __shared__ double red[64];
+    __shared__ double red[96];
     constexpr int RPT = kPcrRows / kPcrThreads;
     const int it = a.it;
-    const T* rnew = (it & 1) ? a.r1 : a.r;
+    const T* rnew = (mode == PCR_PCG) ? a.r : ((it & 1) ? a.r1 : a.r);
     const T* rold = (it & 1) ? a.r : a.r1;
-    const size_t stride = (size_t)a.nb * a.maxpb;
-    for (int wi = blockIdx.x; wi < a.nb * a.maxpb; wi += gridDim.x) {
-        const int b = wi / a.maxpb, jb = wi - b * a.maxpb;
-        const int want = (mode == PCR_PCG) ? NH_SOLVER_CG : NH_SOLVER_BICGSTAB;
+    const size_t stride = (size_t)a.nb * a.maxch;
+    const int want = (mode == PCR_PCG || mode == PCR_PCG_STEP) ? NH_SOLVER_CG : NH_SOLVER_BICGSTAB;
+    const int n_pitems = a.ctl->n_pitems;
+    for (int wi = blockIdx.x; wi < n_pitems; wi += gridDim.x) {
+        const int2 itm = a.pitems[wi];
+        const int b = itm.x, jb = itm.y;
         if (a.ms[b].done || a.ms[b].kind != want) continue;
         const int n = a.ms[b].n_active;
-        const int npb = (n + kPcrRows - 1) / kPcrRows;
-        if (jb >= npb) continue;
+        const int npb = a.ms[b].npb;
+        const int poff = a.ms[b].poff;
         const size_t mo = (size_t)b * a.pitch;
         const int k0 = jb * kPcrRows;
         const int rows = min(kPcrRows, n - k0);
@@ -942,8 +1020,8 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcr(SolveArgs<T> a, int mode)
             sa[i] = (i > 0 && kl == k - 1) ? TP(a.offl[mo + k]) : TP(0);
             sc[i] = (i < rows - 1 && kr == k + 1) ? TP(a.offr[mo + k]) : TP(0);
             sb[i] = TP(a.diag[mo + k]);
-            const T rhs = pcr_rhs(a, mode, rnew, mo + k, beta, omega, alpha);
-            if (mode == PCR_BI_S) ss += (double)rhs * (double)rhs;
+            const T rhs = pcr_rhs(a, mode, it, mo + k, beta, omega, alpha);
+            if (mode == PCR_BI_S || mode == PCR_PCG_STEP) ss += (double)rhs * (double)rhs;
             sd[i] = TP(rhs);
         }
         __syncthreads();
@@ -974,50 +1052,57 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcr(SolveArgs<T> a, int mode)
             }
             __syncthreads();
         }
-        double acc[2] = {0.0, 0.0};
-        // PCG: z = M^{-1} r_new;  BiCGStab: p-hat (into p1) or s-hat (into z)
+        double acc[3] = {0.0, 0.0, ss};
         T* out = (mode == PCR_BI_P) ? a.p1 : a.z;
         for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
             const int k = k0 + i;
             const T zk = T(sd[i] / sb[i]);
             out[mo + k] = zk;
-            if (mode == PCR_PCG) {
+            if (mode == PCR_PCG || mode == PCR_PCG_STEP) {
                 acc[0] += (double)zk * (double)rnew[mo + k];
-                if (it > 0) acc[1] += (double)zk * (double)rold[mo + k];
+                if (mode == PCR_PCG_STEP) acc[1] += (double)zk * (double)rold[mo + k];
             }
         }
-        if (mode == PCR_BI_P) continue;   // no reduction needed for p-hat
-        if (mode == PCR_BI_S) acc[0] = ss;
-        block_sum<2>(acc, red);
-        if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
+        if (mode == PCR_BI_P) { __syncthreads(); continue; }   // no reduction for p-hat
+        block_sum<3>(acc, red);
+        if (threadIdx.x == 0) {
+            a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; a.part[2 * stride + wi] = acc[2];
+        }
+        if (!arrive_last(a.cnt, b, npb)) continue;
         if (mode == PCR_BI_S) {
-            if (arrive_last(a.cnt, b, npb)) {
-                const double s_ss = member_sum(a.part + (size_t)b * a.maxpb, npb, red);
-                if (threadIdx.x == 0) {
-                    MState& st = a.ms[b];
-                    st.snorm = sqrt(s_ss);
-                    if (!isfinite(s_ss)) finish_member<T>(st, a.ctl, NH_ERR_NONFINITE, it, NAN);
-                    else if (st.snorm <= a.rtol * st.bnorm) st.s_conv = 1;
-                }
+            const double s_ss = member_sum(a.part + 2 * stride + poff, npb, red);
+            if (threadIdx.x == 0) {
+                MState& st = a.ms[b];
+                st.snorm = sqrt(s_ss);
+                if (!isfinite(s_ss)) finish_member<T>(st, a.ctl, NH_ERR_NONFINITE, it, NAN);
+                else if (st.snorm <= a.rtol * st.bnorm) st.s_conv = 1;
             }
             continue;
         }
-        if (arrive_last(a.cnt, b, npb)) {
-            const size_t mb = (size_t)b * a.maxpb;
-            const double zr = member_sum(a.part + mb, npb, red);
-            const double zro = member_sum(a.part + stride + mb, npb, red);
-            if (threadIdx.x == 0) {
-                MState& st = a.ms[b];
+        const double zr = member_sum(a.part + poff, npb, red);
+        const double zro = member_sum(a.part + stride + poff, npb, red);
+        const double rr = member_sum(a.part + 2 * stride + poff, npb, red);
+        if (threadIdx.x == 0) {
+            MState& st = a.ms[b];
+            if (mode == PCR_PCG) {
                 if (!isfinite(zr) || !(zr > 0.0)) cg_breakdown<T>(st, a.ctl, it);
-                else if (it == 0) st.rz = zr;
-                else { st.beta = (zr - zro) / st.rz; st.rz = zr; }
+                else st.rz = zr;
+            } else {
+                const double rel = sqrt(rr) / st.bnorm;
+                if (!isfinite(rr)) finish_member<T>(st, a.ctl, NH_ERR_NONFINITE, it, NAN);
+                else if (sqrt(rr) <= a.rtol * st.bnorm) finish_member<T>(st, a.ctl, NH_OK, it, rel);
+                else if (it >= a.max_iter) finish_member<T>(st, a.ctl, NH_ERR_NOT_CONVERGED, it, rel);
+                else if (!isfinite(zr) || !(zr > 0.0)) cg_breakdown<T>(st, a.ctl, it);
+                else { st.beta = (zr - zro) / st.rz; st.rz = zr; st.rr = rr; }
             }
         }
     }
 }
 
 // PCG, first kernel of iteration it: p = z + beta p_old (neighbours on the
-// fly), q = A p, partial <p, q>; last CTA: alpha = <r, z> / <p, q>.
+// fly), q = A p, partial <p, q>; last CTA: alpha = <r, z> / <p, q>.  The
+// neighbours of active cell k are k -/+ 1 except across a periodic wrap, so
+// z and p_old are loaded at k -/+ 1 without waiting for the neighbour index.
 template <typename T>
 __global__ void __launch_bounds__(kChunk) k_pcg_a(SolveArgs<T> a)
 {
@@ -1030,10 +1115,16 @@ __global__ void __launch_bounds__(kChunk) k_pcg_a(SolveArgs<T> a)
         const T beta = (it == 1) ? T(0) : T(a.ms[b].beta);
         double pq = 0.0;
         if (in) {
+            const int km = k > 0 ? k - 1 : k, kp = k + 1 < n ? k + 1 : k;
+            const T zk = a.z[mo + k], zm = a.z[mo + km], zp = a.z[mo + kp];
+            const T ok = pold[mo + k], om = pold[mo + km], op = pold[mo + kp];
             const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
-            const T pk = a.z[mo + k] + beta * pold[mo + k];
-            const T pl = kl >= 0 ? a.z[mo + kl] + beta * pold[mo + kl] : T(0);
-            const T pr = kr >= 0 ? a.z[mo + kr] + beta * pold[mo + kr] : T(0);
+            const T pk = zk + beta * ok;
+            T pl = T(0), pr = T(0);
+            if (kl == k - 1) pl = zm + beta * om;
+            else if (kl >= 0) pl = a.z[mo + kl] + beta * pold[mo + kl];
+            if (kr == k + 1) pr = zp + beta * op;
+            else if (kr >= 0) pr = a.z[mo + kr] + beta * pold[mo + kr];
             const T qk = apply_row(a, mo, k, pk, pl, pr);
             pnew[mo + k] = pk;
             a.q[mo + k] = qk;
@@ -1043,7 +1134,7 @@ __global__ void __launch_bounds__(kChunk) k_pcg_a(SolveArgs<T> a)
         block_sum<1>(v, red);
         if (threadIdx.x == 0) a.part[wi] = v[0];
         if (arrive_last(a.cnt, b, nch)) {
-            const double s_pq = member_sum(a.part + (size_t)b * a.maxch, nch, red);
+            const double s_pq = member_sum(a.part + ioff, nch, red);
             if (threadIdx.x == 0) {
                 MState& s = a.ms[b];
                 if (!isfinite(s_pq) || !(s_pq > 0.0)) cg_breakdown<T>(s, a.ctl, it);
@@ -1053,43 +1144,195 @@ __global__ void __launch_bounds__(kChunk) k_pcg_a(SolveArgs<T> a)
     NH_END_ITEMS
 }
 
-// PCG, second kernel: x += alpha p, r_new = r_old - alpha q (other buffer),
-// partial <r_new, r_new>; last CTA: convergence test on ||r_new|| / ||R||.
-template <typename T>
-__global__ void __launch_bounds__(kChunk) k_pcg_b(SolveArgs<T> a)
+
+
+// ------------------------------------------- persistent PCG (one launch)
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// spin is bounded by `budget` clock cycles: on expiry the CTA records a
+// timeout and returns false instead of waiting for ever.  The last CTA to
+// arrive runs `last` (a decision every CTA reads after the barrier) before
+// releasing the others.
+template <typename F>
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long long budget, F last)
 {
-    __shared__ double red[64];
-    const int it = a.it;
-    const T* p = (it & 1) ? a.p1 : a.p0;
-    const T* rold = (it & 1) ? a.r : a.r1;
-    T* rnew = (it & 1) ? a.r1 : a.r;
-    NH_FOR_ITEMS(a)
-        if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_CG) continue;
-        const T alpha = T(a.ms[b].alpha);
-        double rr = 0.0;
-        if (in) {
-            a.x[mo + k] = a.x[mo + k] + alpha * p[mo + k];
-            const T rk = rold[mo + k] - alpha * a.q[mo + k];
-            rnew[mo + k] = rk;
-            rr = (double)rk * (double)rk;
-        }
-        double v[1] = {rr};
-        block_sum<1>(v, red);
-        if (threadIdx.x == 0) a.part[wi] = v[0];
-        if (arrive_last(a.cnt, b, nch)) {
-            const double s_rr = member_sum(a.part + (size_t)b * a.maxch, nch, red);
-            if (threadIdx.x == 0) {
-                MState& s = a.ms[b];
-                const double rel = sqrt(s_rr) / s.bnorm;
-                if (!isfinite(s_rr)) finish_member<T>(s, a.ctl, NH_ERR_NONFINITE, it, NAN);
-                else if (sqrt(s_rr) <= a.rtol * s.bnorm) finish_member<T>(s, a.ctl, NH_OK, it, rel);
-                else if (it >= a.max_iter) finish_member<T>(s, a.ctl, NH_ERR_NOT_CONVERGED, it, rel);
-                else s.rr = s_rr;
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &ctl->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == nblocks) {
+            last();
+            ctl->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > budget) { ok = 0; atomicExch(&ctl->timeout, 1); break; }
+                __nanosleep(64);
             }
         }
-    NH_END_ITEMS
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
+// All PCG iterations of one solve in one cooperative launch: per iteration
+// phase A (p = z + beta p_old, q = A p, <p, q> -> alpha) and phase B (x, r
+// update, ||r||, line preconditioner, beta), separated by grid barriers.  Work
+// is split by preconditioner blocks (kPcrRows active cells, kPcrThreads
+// threads).  Members finish independently; the loop ends when no member is
+// left, after max_iter, or when a barrier times out (ctl->timeout).
+template <typename T, typename TP>
+__global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, long long budget)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TP* sa = reinterpret_cast<TP*>(smem_raw);
+    TP* sb = sa + kPcrRows;
+    TP* sc = sb + kPcrRows;
+    TP* sd = sc + kPcrRows;
+    __shared__ double red[96];
+    constexpr int RPT = kPcrRows / kPcrThreads;
+    const size_t stride = (size_t)a.nb * a.maxch;
+    const int n_pitems = a.ctl->n_pitems;
+    Ctl* ctl = a.ctl;
+    const unsigned nblk = gridDim.x;
+    for (int it = 1; it <= a.max_iter; ++it) {
+        const T* pold = (it & 1) ? a.p0 : a.p1;
+        T* pnew = (it & 1) ? a.p1 : a.p0;
+        const T* rold = (it & 1) ? a.r : a.r1;
+        T* rnew = (it & 1) ? a.r1 : a.r;
+        // ---- phase A
+        for (int wi = blockIdx.x; wi < n_pitems; wi += gridDim.x) {
+            const int2 itm = a.pitems[wi];
+            const int b = itm.x, jb = itm.y;
+            if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_CG) continue;
+            const int n = a.ms[b].n_active, npb = a.ms[b].npb, poff = a.ms[b].poff;
+            const size_t mo = (size_t)b * a.pitch;
+            const int k0 = jb * kPcrRows, rows = min(kPcrRows, n - k0);
+            const T beta = (it == 1) ? T(0) : T(a.ms[b].beta);
+            double pq = 0.0;
+            for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
+                const int k = k0 + i;
+                const int km = k > 0 ? k - 1 : k, kp = k + 1 < n ? k + 1 : k;
+                const T zk = a.z[mo + k], zm = a.z[mo + km], zp = a.z[mo + kp];
+                const T ok = pold[mo + k], om = pold[mo + km], op = pold[mo + kp];
+                const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+                const T pk = zk + beta * ok;
+                T pl = T(0), pr = T(0);
+                if (kl == k - 1) pl = zm + beta * om;
+                else if (kl >= 0) pl = a.z[mo + kl] + beta * pold[mo + kl];
+                if (kr == k + 1) pr = zp + beta * op;
+                else if (kr >= 0) pr = a.z[mo + kr] + beta * pold[mo + kr];
+                const T qk = apply_row(a, mo, k, pk, pl, pr);
+                pnew[mo + k] = pk;
+                a.q[mo + k] = qk;
+                pq += (double)pk * (double)qk;
+            }
+            double v[1] = {pq};
+            block_sum<1>(v, red);
+            if (threadIdx.x == 0) a.part[wi] = v[0];
+            if (arrive_last(a.cnt, b, npb)) {
+                const double s_pq = member_sum(a.part + poff, npb, red);
+                if (threadIdx.x == 0) {
+                    MState& s = a.ms[b];
+                    if (!isfinite(s_pq) || !(s_pq > 0.0)) cg_breakdown<T>(s, ctl, it);
+                    else s.alpha = s.rz / s_pq;
+                }
+            }
+        }
+        if (!grid_barrier(ctl, nblk, budget, [] {})) return;
+        // ---- phase B
+        for (int wi = blockIdx.x; wi < n_pitems; wi += gridDim.x) {
+            const int2 itm = a.pitems[wi];
+            const int b = itm.x, jb = itm.y;
+            if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_CG) continue;
+            const int n = a.ms[b].n_active, npb = a.ms[b].npb, poff = a.ms[b].poff;
+            const size_t mo = (size_t)b * a.pitch;
+            const int k0 = jb * kPcrRows, rows = min(kPcrRows, n - k0);
+            const T alpha = T(a.ms[b].alpha);
+            double ss = 0.0;
+            for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
+                const int k = k0 + i;
+                const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+                sa[i] = (i > 0 && kl == k - 1) ? TP(a.offl[mo + k]) : TP(0);
+                sc[i] = (i < rows - 1 && kr == k + 1) ? TP(a.offr[mo + k]) : TP(0);
+                sb[i] = TP(a.diag[mo + k]);
+                a.x[mo + k] = a.x[mo + k] + alpha * pnew[mo + k];
+                const T rk = rold[mo + k] - alpha * a.q[mo + k];
+                rnew[mo + k] = rk;
+                ss += (double)rk * (double)rk;
+                sd[i] = TP(rk);
+            }
+            __syncthreads();
+            for (int s = 1; s < rows; s <<= 1) {
+                TP na[RPT], nb2[RPT], nc[RPT], nd[RPT];
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    const int i = threadIdx.x + m * kPcrThreads;
+                    if (i < rows) {
+                        const TP ai = sa[i], ci = sc[i];
+                        TP a2 = TP(0), c2 = TP(0), b2 = sb[i], d2 = sd[i];
+                        if (i - s >= 0) {
+                            const TP al = -ai / sb[i - s];
+                            a2 = al * sa[i - s]; b2 += al * sc[i - s]; d2 += al * sd[i - s];
+                        }
+                        if (i + s < rows) {
+                            const TP ga = -ci / sb[i + s];
+                            c2 = ga * sc[i + s]; b2 += ga * sa[i + s]; d2 += ga * sd[i + s];
+                        }
+                        na[m] = a2; nb2[m] = b2; nc[m] = c2; nd[m] = d2;
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    const int i = threadIdx.x + m * kPcrThreads;
+                    if (i < rows) { sa[i] = na[m]; sb[i] = nb2[m]; sc[i] = nc[m]; sd[i] = nd[m]; }
+                }
+                __syncthreads();
+            }
+            double acc[3] = {0.0, 0.0, ss};
+            for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
+                const int k = k0 + i;
+                const T zk = T(sd[i] / sb[i]);
+                a.z[mo + k] = zk;
+                acc[0] += (double)zk * (double)rnew[mo + k];
+                acc[1] += (double)zk * (double)rold[mo + k];
+            }
+            block_sum<3>(acc, red);
+            if (threadIdx.x == 0) {
+                a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; a.part[2 * stride + wi] = acc[2];
+            }
+            if (arrive_last(a.cnt, b, npb)) {
+                const double zr = member_sum(a.part + poff, npb, red);
+                const double zro = member_sum(a.part + stride + poff, npb, red);
+                const double rr = member_sum(a.part + 2 * stride + poff, npb, red);
+                if (threadIdx.x == 0) {
+                    MState& st = a.ms[b];
+                    const double rel = sqrt(rr) / st.bnorm;
+                    if (!isfinite(rr)) finish_member<T>(st, ctl, NH_ERR_NONFINITE, it, NAN);
+                    else if (sqrt(rr) <= a.rtol * st.bnorm) finish_member<T>(st, ctl, NH_OK, it, rel);
+                    else if (it >= a.max_iter) finish_member<T>(st, ctl, NH_ERR_NOT_CONVERGED, it, rel);
+                    else if (!isfinite(zr) || !(zr > 0.0)) cg_breakdown<T>(st, ctl, it);
+                    else { st.beta = (zr - zro) / st.rz; st.rz = zr; st.rr = rr; }
+                }
+            }
+        }
+        const int par = it & 1;
+        if (!grid_barrier(ctl, nblk, budget, [ctl, par] {
+                ctl->go[par] = (*(volatile int*)&ctl->not_done) > 0;
+            }))
+            return;
+        if (*(volatile int*)&ctl->go[par] == 0) return;
+    }
+}
 
 // Preconditioned (right) BiCGStab.  Per iteration: k_pcr(PCR_BI_P) forms
 // p = r + beta (p - omega v) and p-hat = M^{-1} p; k_pbi_mv(0) v = A p-hat,
@@ -1126,7 +1369,7 @@ __global__ void __launch_bounds__(kChunk) k_pbi_mv(SolveArgs<T> a, int which)
         block_sum<2>(acc, red);
         if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
         if (arrive_last(a.cnt, b, nch)) {
-            const size_t mb = (size_t)b * a.maxch;
+            const size_t mb = ioff;
             const double s0 = member_sum(a.part + mb, nch, red);
             const double s1 = which == 1 ? member_sum(a.part + stride + mb, nch, red) : 0.0;
             if (threadIdx.x == 0) {
@@ -1168,7 +1411,7 @@ __global__ void __launch_bounds__(kChunk) k_pbi_upd(SolveArgs<T> a)
         block_sum<2>(acc, red);
         if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
         if (arrive_last(a.cnt, b, nch)) {
-            const size_t mb = (size_t)b * a.maxch;
+            const size_t mb = ioff;
             const double rr = member_sum(a.part + mb, nch, red);
             const double rhr = member_sum(a.part + stride + mb, nch, red);
             if (threadIdx.x == 0) {
@@ -1229,16 +1472,18 @@ struct CorrArgs {
     const MState* ms;
     T* hu; T* hw;          // Q~ buffers, corrected in place into Q^{n+1}
     double* psi;           // dense pressure unknown (for the next warm start)
+    const int2* items; const Ctl* ctl;
 };
 
 // Eqs. 10-11 on the active cells (h is not corrected, Sec. 3.2).
 template <typename T>
 __global__ void __launch_bounds__(kChunk) k_correct(CorrArgs<T> a)
 {
-    for (int wi = blockIdx.x; wi < a.nb * a.maxch; wi += gridDim.x) {
-        const int b = wi / a.maxch, j = wi - b * a.maxch;
+    const int n_items = a.ctl->n_items;
+    for (int wi = blockIdx.x; wi < n_items; wi += gridDim.x) {
+        const int2 itm = a.items[wi];
+        const int b = itm.x, j = itm.y;
         const MState& s = a.ms[b];
-        if (j >= s.nchunks) continue;
         const int n = s.n_active;
         const size_t mo = (size_t)b * a.pitch;
         const int k = j * kChunk + threadIdx.x;
@@ -1325,16 +1570,19 @@ struct IRArgs {
     double rtol;
     int pass;               // 0: x64 = warm start; >0: after k_ir_update
     int ir_max;
+    const int2* items;
 };
 
 static __global__ void __launch_bounds__(kChunk) k_ir_resid(IRArgs a)
 {
     __shared__ double red[64];
     const size_t stride = (size_t)a.nb * a.maxch;
-    for (int wi = blockIdx.x; wi < a.nb * a.maxch; wi += gridDim.x) {
-        const int b = wi / a.maxch, j = wi - b * a.maxch;
+    const int n_items = a.ctl->n_items;
+    for (int wi = blockIdx.x; wi < n_items; wi += gridDim.x) {
+        const int2 itm = a.items[wi];
+        const int b = itm.x, j = itm.y;
         const int nch = a.ms[b].nchunks;
-        if (j >= nch) continue;
+        const int ioff = a.ms[b].ioff;
         if (a.pass > 0 && a.ir[b].done) continue;
         const int n = a.ms[b].n_active;
         const size_t mo = (size_t)b * a.pitch;
@@ -1365,7 +1613,7 @@ static __global__ void __launch_bounds__(kChunk) k_ir_resid(IRArgs a)
         block_sum<2>(acc, red);
         if (threadIdx.x == 0) { a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; }
         if (arrive_last(a.cnt, b, nch)) {
-            const size_t mb = (size_t)b * a.maxch;
+            const size_t mb = ioff;
             const double rr = member_sum(a.part + mb, nch, red);
             const double rr32 = member_sum(a.part + stride + mb, nch, red);
             if (threadIdx.x == 0) {

@@ -37,7 +37,8 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh_status_string", "nh_predict_static")
 NH_STATIC_MAX_CELLS = 262144
 KERNEL_CLASSES = ("kinematics", "predict", "compact", "assemble", "solve_init", "precond", "pcg_a",
-                  "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct")
+                  "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct",
+                  "pcg_loop")
 
 
 class nh_grid_desc(C.Structure):
