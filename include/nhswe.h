@@ -138,6 +138,17 @@ size_t nh_workspace_bytes(const nh_grid_desc* desc);
 nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host,
                          void* ws, size_t ws_bytes, void* stream, nh_grid** out);
 
+/* Ensemble of members with different cell counts (uneven grids) in one
+   handle: nx_per_member[b] cells for member b (8 <= nx <= 2^20); desc->nx is
+   ignored.  Host arrays of every entry point are then the members
+   concatenated: member b occupies [sum_{b'<b} nx_{b'}, sum_{b'<=b} nx_{b'}).
+   d0_host likewise.  Every kernel of a step still processes all members in
+   one launch; device storage per member is sized for the largest member.
+   Errors as nh_create_grid. */
+size_t nh_workspace_bytes_ensemble(const nh_grid_desc* desc, const int* nx_per_member);
+nh_status nh_create_ensemble(const nh_grid_desc* desc, const int* nx_per_member, const double* d0_host,
+                             void* ws, size_t ws_bytes, void* stream, nh_grid** out);
+
 /* Bottom motion per member (Sec. 4.2-4.3 describe the paper's own moving
    bottoms; this library moves a Gaussian mound, see nh_slide_desc).
    slides: nbatch entries, or NULL for a static bottom.  Errors: NH_ERR_ARG. */
@@ -196,6 +207,16 @@ nh_status nh_step(nh_grid* g, double dt, nh_step_info* info);
 /* n_steps steps of size dt; stops at the first failing step (whose status is
    returned; info->last describes it).  info may be NULL. */
 nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info);
+
+/* use_graphs != 0 (the default): nh_run captures one FP64 step per
+   state-buffer parity as a CUDA graph (on a private capture stream, replayed
+   on the handle's stream) and replays it n_steps times with a single
+   synchronisation at the end; time and step acceptance live on the device.
+   Used when the handle is FP64 with NH_PRECOND_LINE and solver AUTO or CG,
+   profiling is off and dt is unchanged.  A step that fails inside a replay
+   stops the replay with the last accepted state intact and is redone by the
+   step-by-step path.  use_graphs == 0: always step by step. */
+nh_status nh_set_run_mode(nh_grid* g, int use_graphs);
 
 /* Kernel classes timed by the profiler (index into nh_get_profile arrays). */
 enum { NH_K_KINEMATICS = 0, NH_K_PREDICT = 1, NH_K_COMPACT = 2, NH_K_ASSEMBLE = 3,

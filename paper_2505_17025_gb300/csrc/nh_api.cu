@@ -24,6 +24,20 @@ struct nh_grid {
     long long barrier_budget;    // clock cycles a grid barrier may spin
     size_t es;                   // element size of state / Krylov vectors
     bool mixed;
+    bool uneven;                 // members have different cell counts
+    std::vector<int> nxh;        // cells per member
+    std::vector<long long> offh; // host layout: member b at [offh[b], offh[b+1])
+    long long ncells;            // sum of nxh
+    int* nxd;                    // device copy of nxh
+    long long* offd;             // device copy of offh
+    void* ws_base;               // the caller's workspace
+    TimeCtl* tc;                 // device time control of captured runs
+    cudaStream_t cap_stream;     // private stream used only to capture graphs
+    cudaGraphExec_t graph[2];    // one captured step per state-buffer parity
+    bool graph_valid;
+    double graph_key[10];        // settings the graphs were captured with
+    int graph_runs;              // nh_run calls served by graphs (diagnostics)
+    bool use_graphs;             // nh_run may replay captured graphs
     double mass0;                // sum of d0 dx over all members (FP64)
     // configuration
     int crit, enlarge, first_global;
@@ -97,8 +111,9 @@ bool desc_ok(const nh_grid_desc* d)
     return true;
 }
 
-// Lay out every buffer; with base == nullptr only the size is computed.
-size_t carve(const nh_grid_desc& d, nh_grid* g, char* base)
+// Lay out every buffer; with base == nullptr only the size is computed.  d.nx
+// is the largest member's cell count; ncells the sum over members.
+size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
 {
     const int nx = d.nx, nb = d.nbatch;
     const bool mixed = d.precision == NH_MIXED;
@@ -117,7 +132,9 @@ size_t carve(const nh_grid_desc& d, nh_grid* g, char* base)
     }
     G->d0 = c.take(N * es);
     G->d0d = (double*)c.take(N * 8);
-    G->stage = (double*)c.take(3 * (size_t)nb * nx * 8);
+    G->stage = (double*)c.take(3 * (size_t)ncells * 8);
+    G->nxd = (int*)c.take(sizeof(int) * nb);
+    G->offd = (long long*)c.take(sizeof(long long) * (nb + 1));
     G->slide = (Slide*)c.take(sizeof(Slide) * nb);
     G->kin = (Kin*)c.take(sizeof(Kin) * nb);
     G->marks = (uint32_t*)c.take(sizeof(uint32_t) * (size_t)nb * wpitch);
@@ -153,6 +170,7 @@ size_t carve(const nh_grid_desc& d, nh_grid* g, char* base)
     G->cnt = (int*)c.take(sizeof(int) * nb);
     G->mass_part = (double*)c.take(sizeof(double) * (size_t)nb * ntiles);
     G->summary = (Summary*)c.take(sizeof(Summary));
+    G->tc = (TimeCtl*)c.take(sizeof(TimeCtl));
     if (g) {
         g->nx = nx; g->nb = nb; g->pitch = pitch; g->wpitch = wpitch; g->ntiles = ntiles;
         g->maxch = maxch; g->es = es; g->maxpb = maxpb; g->mixed = mixed;
@@ -220,6 +238,7 @@ Geo geo(const nh_grid* g)
     G.nx = g->nx; G.nb = g->nb; G.pitch = g->pitch; G.wpitch = g->wpitch; G.bc = g->d.bc;
     G.lim = g->d.limiter; G.ntiles = g->ntiles; G.maxch = g->maxch;
     G.dx = g->d.dx; G.x0 = g->d.x0; G.g = g->d.g;
+    G.nxv = g->uneven ? g->nxd : nullptr;
     return G;
 }
 
@@ -241,6 +260,7 @@ SolveArgs<T> solve_args(nh_grid* g, int lcur, const T* diag, const T* offl, cons
     a.s = (T*)g->s; a.t = (T*)g->t;
     a.r1 = (T*)g->r1; a.z = (T*)g->z; a.maxpb = g->maxpb;
     a.items = g->items; a.pitems = g->pitems;
+    a.tc = nullptr;
     a.ms = g->ms; a.ctl = g->ctl; a.part = g->part; a.cnt = g->cnt;
     a.rtol = rtol; a.max_iter = g->max_iter; a.it = 0;
     return a;
@@ -387,12 +407,13 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     pa.d0 = (const T*)g->d0; pa.slide = g->slide; pa.kin = g->kin;
     pa.marks = g->marks; pa.mass_part = g->mass_part; pa.dt = dt; pa.knh = g->knh; pa.crit = g->crit;
     pa.all_global = (g->crit == NH_CRIT_GLOBAL) || (g->first_global && g->steps == 0);
+    pa.tc = nullptr;
     LAUNCH(NH_K_PREDICT, k_predict<T><<<dim3(g->ntiles, g->nb), kPredTile, 0, st>>>(pa));
 
     CompactArgs ca;
     ca.nx = g->nx; ca.pitch = g->pitch; ca.wpitch = g->wpitch; ca.bc = g->d.bc; ca.enlarge = g->enlarge;
     ca.marks = g->marks; ca.act = g->act; ca.list = g->list[lnew]; ca.nact = g->nact[lnew];
-    ca.ms = g->ms; ca.ctl = g->ctl;
+    ca.ms = g->ms; ca.ctl = g->ctl; ca.nxv = g->uneven ? g->nxd : nullptr; ca.tc = nullptr;
     const size_t csm = sizeof(uint32_t) * (size_t)((g->nx + 31) / 32);
     LAUNCH(NH_K_COMPACT, k_compact<<<g->nb, kCompactThreads, csm, st>>>(ca));
     LAUNCH(NH_K_COMPACT, k_items<<<1, 1024, 0, st>>>(g->ms, g->nb, g->items, g->pitems, g->ctl));
@@ -423,7 +444,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
         xfinal = (const double*)g->x;
     }
 
-    LAUNCH(NH_K_SUMMARY, k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->ntiles, g->d.dx, g->summary));
+    LAUNCH(NH_K_SUMMARY, k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->ntiles, g->d.dx, g->summary, nullptr));
     Summary S;
     CK(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
     SYNC();
@@ -439,7 +460,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     if (status == NH_OK) {
         ClearArgs cl;
         cl.nb = g->nb; cl.pitch = g->pitch; cl.maxlist = g->pitch;
-        cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi;
+        cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = nullptr;
         const size_t total = (size_t)g->nb * g->pitch;
         int cgrid = (int)std::min<size_t>((total + 255) / 256, (size_t)g->sm_count * 8);
         LAUNCH(NH_K_CLEAR, k_clear_prev<<<cgrid, 256, 0, st>>>(cl));
@@ -449,7 +470,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
         co.c6 = (const T*)g->c6; co.cx = (const T*)g->cx; co.phi = (const T*)g->phi;
         co.ddx = (const T*)g->ddx; co.ms = g->ms;
         co.hu = (T*)g->shu[nxt]; co.hw = (T*)g->shw[nxt]; co.psi = g->psi;
-        co.items = g->items; co.ctl = g->ctl;
+        co.items = g->items; co.ctl = g->ctl; co.tc = nullptr;
         LAUNCH(NH_K_CORRECT, k_correct<T><<<g->items_grid, kChunk, 0, st>>>(co));
         CK(cudaGetLastError());
         g->cur = nxt;
@@ -474,6 +495,168 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     return status;
 }
 
+// ---------------------------------------------------------- captured runs
+
+// Enqueue one FP64 step on `st` with fixed buffer roles (no host round trip):
+// the device time control block supplies t, the commit kernel accepts the step
+// or aborts the run.  Used only while capturing a graph.
+nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, double dt)
+{
+    const int nxt = cur ^ 1, lnew = lprev ^ 1;
+    const Geo G = geo(g);
+    k_kinematics_dev<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slide, g->kin, g->nb, g->tc);
+    PredArgs<double> pa;
+    pa.G = G;
+    pa.z = (const double*)g->sz[cur]; pa.hu = (const double*)g->shu[cur]; pa.hw = (const double*)g->shw[cur];
+    pa.zt = (double*)g->sz[nxt]; pa.hut = (double*)g->shu[nxt]; pa.hwt = (double*)g->shw[nxt];
+    pa.d0 = (const double*)g->d0; pa.slide = g->slide; pa.kin = g->kin;
+    pa.marks = g->marks; pa.mass_part = g->mass_part; pa.dt = dt; pa.knh = g->knh; pa.crit = g->crit;
+    pa.all_global = (g->crit == NH_CRIT_GLOBAL);
+    pa.tc = g->tc;
+    k_predict<double><<<dim3(g->ntiles, g->nb), kPredTile, 0, st>>>(pa);
+    CompactArgs ca;
+    ca.nx = g->nx; ca.pitch = g->pitch; ca.wpitch = g->wpitch; ca.bc = g->d.bc; ca.enlarge = g->enlarge;
+    ca.marks = g->marks; ca.act = g->act; ca.list = g->list[lnew]; ca.nact = g->nact[lnew];
+    ca.ms = g->ms; ca.ctl = g->ctl; ca.nxv = g->uneven ? g->nxd : nullptr; ca.tc = g->tc;
+    k_compact<<<g->nb, kCompactThreads, sizeof(uint32_t) * (size_t)((g->nx + 31) / 32), st>>>(ca);
+    k_items<<<1, 1024, 0, st>>>(g->ms, g->nb, g->items, g->pitems, g->ctl);
+    AsmArgs<double> aa;
+    aa.G = G;
+    aa.zt = (const double*)g->sz[nxt]; aa.hut = (const double*)g->shu[nxt]; aa.hwt = (const double*)g->shw[nxt];
+    aa.d0 = g->d0d; aa.slide = g->slide; aa.kin = g->kin;
+    aa.list = g->list[lnew]; aa.act = g->act; aa.ms = g->ms;
+    aa.diag = g->diag; aa.offl = g->offl; aa.offr = g->offr; aa.R = g->R;
+    aa.diag32 = nullptr; aa.offl32 = nullptr; aa.offr32 = nullptr;
+    aa.nbl = g->nbl; aa.nbr = g->nbr;
+    aa.c6 = (double*)g->c6; aa.cx = (double*)g->cx; aa.phi = (double*)g->phi; aa.ddx = (double*)g->ddx;
+    aa.part = g->part; aa.cnt = g->cnt; aa.dt = dt; aa.solver = g->solver;
+    aa.items = g->items; aa.ctl = g->ctl;
+    k_assemble<double><<<g->items_grid, kChunk, 0, st>>>(aa);
+    SolveArgs<double> sa = solve_args<double>(g, lnew, g->diag, g->offl, g->offr, g->R, g->rtol);
+    sa.guess_scale = (g->guess == NH_GUESS_PREV) ? 1.0 : 0.0;
+    sa.tc = g->tc;
+    CK(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
+    CK(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
+    k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa);
+    const size_t pcr_smem = 4 * sizeof(float) * (size_t)kPcrRows;
+    sa.it = 0;
+    k_pcr<double, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG);
+    CK(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(g->coop_grid[0]);
+        cfg.blockDim = dim3(kPcrThreads);
+        cfg.dynamicSmemBytes = pcr_smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        long long budget = g->barrier_budget;
+        CK(cudaLaunchKernelEx(&cfg, k_pcg_persistent<double, float>, sa, budget));
+    }
+    k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->ntiles, g->d.dx, g->summary, g->tc);
+    k_commit<<<1, 32, 0, st>>>(g->summary, g->tc);
+    ClearArgs cl;
+    cl.nb = g->nb; cl.pitch = g->pitch; cl.maxlist = g->pitch;
+    cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = g->tc;
+    const size_t total = (size_t)g->nb * g->pitch;
+    k_clear_prev<<<(int)std::min<size_t>((total + 255) / 256, (size_t)g->sm_count * 8), 256, 0, st>>>(cl);
+    CorrArgs<double> co;
+    co.nb = g->nb; co.pitch = g->pitch; co.maxch = g->maxch; co.dx = g->d.dx;
+    co.list = g->list[lnew]; co.nbl = g->nbl; co.nbr = g->nbr; co.x = (const double*)g->x;
+    co.c6 = (const double*)g->c6; co.cx = (const double*)g->cx; co.phi = (const double*)g->phi;
+    co.ddx = (const double*)g->ddx; co.ms = g->ms;
+    co.hu = (double*)g->shu[nxt]; co.hw = (double*)g->shw[nxt]; co.psi = g->psi;
+    co.items = g->items; co.ctl = g->ctl; co.tc = g->tc;
+    k_correct<double><<<g->items_grid, kChunk, 0, st>>>(co);
+    CK(cudaGetLastError());
+    return NH_OK;
+}
+
+bool graph_eligible(const nh_grid* g, double dt)
+{
+    return !g->mixed && g->precond == NH_PRECOND_LINE && g->solver != NH_SOLVER_BICGSTAB &&
+           g->coop_grid[0] > 0 && !g->prof_on && !(g->first_global && g->steps == 0) &&
+           (g->last_dt == 0.0 || g->last_dt == dt) && g->cap_stream != nullptr;
+}
+
+void graph_destroy(nh_grid* g)
+{
+    for (int p = 0; p < 2; ++p)
+        if (g->graph[p]) { cudaGraphExecDestroy(g->graph[p]); g->graph[p] = nullptr; }
+    g->graph_valid = false;
+}
+
+nh_status graph_prepare(nh_grid* g, double dt)
+{
+    const double key[10] = {dt, (double)g->crit, g->knh, (double)g->enlarge, (double)g->solver, g->rtol,
+                            (double)g->max_iter, (double)g->guess, (double)(g->cur ^ g->lcur), 0.0};
+    if (g->graph_valid && std::memcmp(key, g->graph_key, sizeof(key)) == 0) return NH_OK;
+    graph_destroy(g);
+    for (int p = 0; p < 2; ++p) {
+        const int cur = p, lprev = p ^ g->cur ^ g->lcur;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+        nh_status rc = enqueue_graph_step(g, g->cap_stream, cur, lprev, dt);
+        cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+        if (rc != NH_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            graph_destroy(g);
+            return rc != NH_OK ? rc : NH_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&g->graph[p], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { g->graph[p] = nullptr; graph_destroy(g); return NH_ERR_CUDA; }
+    }
+    std::memcpy(g->graph_key, key, sizeof(key));
+    g->graph_valid = true;
+    return NH_OK;
+}
+
+// n_steps steps by replaying the captured one-step graphs on the caller's
+// stream; one synchronisation at the end.
+nh_status graph_run(nh_grid* g, double dt, long long n_steps, nh_run_info* R)
+{
+    nh_status rc = graph_prepare(g, dt);
+    if (rc != NH_OK) return rc;
+    cudaStream_t st = g->stream;
+    TimeCtl tc;
+    std::memset(&tc, 0, sizeof(tc));
+    tc.t_base = g->t_base; tc.dt = dt; tc.n = g->n_since; tc.done = 0; tc.abort = 0;
+    tc.prev_ok = (g->last_dt == dt) ? 1 : 0;
+    CK(cudaMemcpyAsync(g->tc, &tc, sizeof(tc), cudaMemcpyHostToDevice, st));
+    for (long long k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(g->graph[(g->cur + k) & 1], st));
+    Summary S;
+    CK(cudaMemcpyAsync(&tc, g->tc, sizeof(tc), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const long long done = tc.done;
+    if (done & 1) { g->cur ^= 1; g->lcur ^= 1; }
+    g->steps += done;
+    g->n_since += done;
+    if (done > 0) g->last_dt = dt;
+    g->graph_runs += 1;
+    R->steps = done;
+    R->iters_total = tc.iters_total;
+    R->active_total = tc.active_total;
+    nh_step_info& I = R->last;
+    I.step = g->steps;
+    I.t = g->t_base + (double)g->n_since * dt;
+    I.n_active = S.n_active; I.n_active_max = S.n_active_max; I.iters = S.iters; I.ir_passes = 0;
+    I.solver = S.n_active == 0 ? -1 : (S.any_bicg ? NH_SOLVER_BICGSTAB : NH_SOLVER_CG);
+    I.status = tc.abort ? tc.fail_status : NH_OK;
+    I.rel_res = S.rel_res; I.min_gamma = S.min_gamma; I.mass = S.mass + g->mass0;
+    if (tc.abort) {
+        // the failing step: AUTO members whose CG broke down are retried by the
+        // step-by-step path (BiCGStab fallback) before the run is reported failed
+        return (nh_status)(tc.fail_status == kStatusFallback ? NH_ERR_NONFINITE : tc.fail_status);
+    }
+    return NH_OK;
+}
+
 nh_status do_step(nh_grid* g, double dt, nh_step_info* info)
 {
     if (!g->has_state) return NH_ERR_STATE;
@@ -485,14 +668,14 @@ template <typename T>
 nh_status upload_state(nh_grid* g, const double* h, const double* hu, const double* hw)
 {
     cudaStream_t st = g->stream;
-    const size_t n = (size_t)g->nb * g->nx;
+    const size_t n = (size_t)g->ncells;
     CK(cudaMemcpyAsync(g->stage, h, n * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(g->stage + n, hu, n * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(g->stage + 2 * n, hw, n * 8, cudaMemcpyHostToDevice, st));
     const int c = g->cur;
-    const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sm_count * 8);
-    k_state_in<T><<<grid, 256, 0, st>>>(g->stage, g->stage + n, g->stage + 2 * n, g->d0d,
-                                       (T*)g->sz[c], (T*)g->shu[c], (T*)g->shw[c], g->nb, g->nx, g->pitch);
+    const dim3 grid((unsigned)std::min<size_t>((g->nx + 255) / 256, 64), (unsigned)g->nb);
+    k_state_in<T><<<grid, 256, 0, st>>>(g->stage, g->stage + n, g->stage + 2 * n, g->d0d, (T*)g->sz[c],
+                                       (T*)g->shu[c], (T*)g->shw[c], g->nb, g->pitch, g->offd);
     CK(cudaGetLastError());
     return NH_OK;
 }
@@ -501,15 +684,15 @@ template <typename T>
 nh_status download_state(nh_grid* g, double* h, double* hu, double* hw, double* p)
 {
     cudaStream_t st = g->stream;
-    const size_t n = (size_t)g->nb * g->nx;
+    const size_t n = (size_t)g->ncells;
     const int c = g->cur;
-    const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sm_count * 8);
     const double sc = g->last_dt > 0.0 ? g->d.rho / g->last_dt : 0.0;
     // p is formed in an FP64-sized solver vector: those are scratch between steps
     double* p_dev = g->es == 8 ? (double*)g->r1 : g->x64;
+    const dim3 grid((unsigned)std::min<size_t>((g->nx + 255) / 256, 64), (unsigned)g->nb);
     k_state_out<T><<<grid, 256, 0, st>>>((const T*)g->sz[c], (const T*)g->shu[c], (const T*)g->shw[c],
                                         g->d0d, g->psi, g->stage, g->stage + n, g->stage + 2 * n, p_dev,
-                                        sc, g->nb, g->nx, g->pitch);
+                                        sc, g->nb, g->pitch, g->offd);
     CK(cudaGetLastError());
     if (h) CK(cudaMemcpyAsync(h, g->stage, n * 8, cudaMemcpyDeviceToHost, st));
     if (hu) CK(cudaMemcpyAsync(hu, g->stage + n, n * 8, cudaMemcpyDeviceToHost, st));
@@ -519,26 +702,29 @@ nh_status download_state(nh_grid* g, double* h, double* hu, double* hw, double* 
     return NH_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-size_t nh_workspace_bytes(const nh_grid_desc* desc)
-{
-    if (!desc_ok(desc)) return 0;
-    return carve(*desc, nullptr, nullptr);
-}
-
-nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host, void* ws, size_t ws_bytes,
-                         void* stream, nh_grid** out)
+// Shared body of nh_create_grid / nh_create_ensemble.  nxv: cells per member.
+nh_status create_impl(const nh_grid_desc* desc_in, const int* nxv, const double* d0_host, void* ws,
+                      size_t ws_bytes, void* stream, nh_grid** out)
 {
     if (!out) return NH_ERR_ARG;
     *out = nullptr;
-    if (!desc_ok(desc) || !d0_host || !ws) return NH_ERR_ARG;
+    if (!desc_in || !nxv || !d0_host || !ws) return NH_ERR_ARG;
+    nh_grid_desc desc = *desc_in;
+    long long ncells = 0;
+    int nxmax = 0;
+    bool uneven = false;
+    for (int b = 0; b < desc.nbatch; ++b) {
+        if (nxv[b] < 8 || nxv[b] > (1 << 20)) return NH_ERR_ARG;
+        ncells += nxv[b];
+        nxmax = std::max(nxmax, nxv[b]);
+        if (nxv[b] != nxv[0]) uneven = true;
+    }
+    desc.nx = nxmax;
+    if (!desc_ok(&desc)) return NH_ERR_ARG;
     if (((uintptr_t)ws % kAlign) != 0) return NH_ERR_ARG;
-    const size_t need = carve(*desc, nullptr, nullptr);
+    const size_t need = carve(desc, ncells, nullptr, nullptr);
     if (ws_bytes < need) return NH_ERR_ARG;
-    for (size_t q = 0; q < (size_t)desc->nx * desc->nbatch; ++q)
+    for (long long q = 0; q < ncells; ++q)
         if (!(d0_host[q] > 0.0) || !std::isfinite(d0_host[q])) return NH_ERR_ARG;
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -546,9 +732,80 @@ nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host, void* 
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     nh_grid* g = new (std::nothrow) nh_grid();
     if (!g) return NH_ERR_ARG;
-    g->d = *desc;
+    g->d = desc;
     g->stream = (cudaStream_t)stream;
-    carve(*desc, g, (char*)ws);
+    carve(desc, ncells, g, (char*)ws);
+    g->ws_base = ws;
+    g->uneven = uneven;
+    g->ncells = ncells;
+    g->nxh.assign(nxv, nxv + desc.nbatch);
+    g->offh.assign(desc.nbatch + 1, 0);
+    for (int b = 0; b < desc.nbatch; ++b) g->offh[b + 1] = g->offh[b] + nxv[b];
+    *out = g;
+    return NH_OK;
+}
+
+}  // namespace
+
+extern "C" {}  // namespace
+
+extern "C" {
+
+size_t nh_workspace_bytes(const nh_grid_desc* desc)
+{
+    if (!desc_ok(desc)) return 0;
+    return carve(*desc, (long long)desc->nx * desc->nbatch, nullptr, nullptr);
+}
+
+size_t nh_workspace_bytes_ensemble(const nh_grid_desc* desc, const int* nx_per_member)
+{
+    if (!desc || !nx_per_member || desc->nbatch < 1) return 0;
+    nh_grid_desc d = *desc;
+    long long ncells = 0;
+    int nxmax = 0;
+    for (int b = 0; b < d.nbatch; ++b) {
+        if (nx_per_member[b] < 8 || nx_per_member[b] > (1 << 20)) return 0;
+        ncells += nx_per_member[b];
+        nxmax = std::max(nxmax, nx_per_member[b]);
+    }
+    d.nx = nxmax;
+    if (!desc_ok(&d)) return 0;
+    return carve(d, ncells, nullptr, nullptr);
+}
+
+static nh_status finish_create(nh_grid* g, const double* d0_host, int dev, int sms);
+
+nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host, void* ws, size_t ws_bytes,
+                         void* stream, nh_grid** out)
+{
+    if (!out) return NH_ERR_ARG;
+    *out = nullptr;
+    if (!desc_ok(desc)) return NH_ERR_ARG;
+    std::vector<int> nxv(desc->nbatch, desc->nx);
+    return nh_create_ensemble(desc, nxv.data(), d0_host, ws, ws_bytes, stream, out);
+}
+
+nh_status nh_create_ensemble(const nh_grid_desc* desc, const int* nx_per_member, const double* d0_host,
+                             void* ws, size_t ws_bytes, void* stream, nh_grid** out)
+{
+    nh_status rc0 = create_impl(desc, nx_per_member, d0_host, ws, ws_bytes, stream, out);
+    if (rc0 != NH_OK) return rc0;
+    nh_grid* g = *out;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { delete g; return NH_ERR_CUDA; }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { delete g; return NH_ERR_CUDA; }
+    nh_status rc = finish_create(g, d0_host, dev, sms);
+    if (rc != NH_OK) { delete g; return rc; }
+    *out = g;
+    return NH_OK;
+}
+
+static nh_status finish_create(nh_grid* g, const double* d0_host, int dev, int sms)
+{
+    void* ws = g->ws_base;
+    const size_t need = carve(g->d, g->ncells, nullptr, nullptr);
     g->sm_count = sms;
     g->items_grid = (int)std::min<long long>((long long)g->nb * g->maxch, (long long)sms * 8);
     if (g->items_grid < 1) g->items_grid = 1;
@@ -561,15 +818,23 @@ nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host, void* 
     g->cur = 0; g->lcur = 0;
     g->prof_on = false; g->prof_used = 0;
     for (int k = 0; k < NH_K_COUNT; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
+    g->graph[0] = g->graph[1] = nullptr; g->graph_valid = false; g->graph_runs = 0; g->use_graphs = true;
+    if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) g->cap_stream = nullptr;
     cudaStream_t st = g->stream;
-    const size_t hp = (size_t)g->nx * sizeof(double), dp = (size_t)g->pitch * sizeof(double);
     nh_status rc = NH_OK;
     do {
         if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess) { rc = NH_ERR_CUDA; break; }
-        if (cudaMemcpy2DAsync(g->d0d, dp, d0_host, hp, hp, g->nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        const size_t N = (size_t)g->nb * g->pitch;
+        // member counts and offsets, then d0 scattered from the concatenated host layout
+        if (cudaMemcpyAsync(g->nxd, g->nxh.data(), sizeof(int) * g->nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(g->offd, g->offh.data(), sizeof(long long) * (g->nb + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(g->stage, d0_host, sizeof(double) * g->ncells, cudaMemcpyHostToDevice, st) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
         }
-        const size_t N = (size_t)g->nb * g->pitch;
+        k_fill<<<(int)std::min<size_t>((N + 255) / 256, (size_t)sms * 8), 256, 0, st>>>(g->d0d, 1.0, N);
+        k_scatter<<<dim3((unsigned)std::min((g->nx + 255) / 256, 64), (unsigned)g->nb), 256, 0, st>>>(
+            g->stage, g->d0d, g->pitch, g->offd);
+        if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; break; }
         if (g->mixed) {
             k_to_float<<<(int)std::min<size_t>((N + 255) / 256, (size_t)sms * 8), 256, 0, st>>>(g->d0d, (float*)g->d0, N);
             if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; break; }
@@ -577,7 +842,7 @@ nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host, void* 
             rc = NH_ERR_CUDA; break;
         }
         double m0 = 0.0;
-        for (size_t q = 0; q < (size_t)g->nx * g->nb; ++q) m0 += d0_host[q];
+        for (long long q = 0; q < g->ncells; ++q) m0 += d0_host[q];
         g->mass0 = m0 * g->d.dx;
         std::vector<Slide> sl(g->nb);
         for (auto& s : sl) { s.A = 0; s.L = 1; s.xc0 = 0; s.s0 = 0; s.t0 = 1; s.shape = NH_SLIDE_NONE; s.pad = 0; }
@@ -617,9 +882,7 @@ nh_status nh_create_grid(const nh_grid_desc* desc, const double* d0_host, void* 
             rc = NH_ERR_CUDA; break;
         }
     } while (0);
-    if (rc != NH_OK) { delete g; return rc; }
-    *out = g;
-    return NH_OK;
+    return rc;
 }
 
 nh_status nh_set_bottom_motion(nh_grid* g, const nh_slide_desc* slides)
@@ -677,7 +940,7 @@ nh_status nh_set_preconditioner(nh_grid* g, int kind)
 nh_status nh_set_state(nh_grid* g, const double* h, const double* hu, const double* hw, double t)
 {
     if (!g || !h || !hu || !hw || !std::isfinite(t)) return NH_ERR_ARG;
-    for (size_t q = 0; q < (size_t)g->nx * g->nb; ++q)
+    for (long long q = 0; q < g->ncells; ++q)
         if (!(h[q] > 0.0) || !std::isfinite(h[q]) || !std::isfinite(hu[q]) || !std::isfinite(hw[q]))
             return NH_ERR_ARG;
     cudaStream_t st = g->stream;
@@ -699,6 +962,13 @@ nh_status nh_put_state(nh_grid* g, const double* h, const double* hu, const doub
     if (!g || !h || !hu || !hw) return NH_ERR_ARG;
     if (!g->has_state) return NH_ERR_STATE;
     return g->mixed ? upload_state<float>(g, h, hu, hw) : upload_state<double>(g, h, hu, hw);
+}
+
+nh_status nh_set_run_mode(nh_grid* g, int use_graphs)
+{
+    if (!g) return NH_ERR_ARG;
+    g->use_graphs = use_graphs != 0;
+    return NH_OK;
 }
 
 nh_status nh_set_profiling(nh_grid* g, int enable)
@@ -740,8 +1010,8 @@ nh_status nh_get_mask(nh_grid* g, unsigned char* mask, int* iters, double* rel_r
         CK(cudaMemcpyAsync(w.data(), g->act, sizeof(uint32_t) * w.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (int b = 0; b < g->nb; ++b)
-            for (int i = 0; i < g->nx; ++i)
-                mask[(size_t)b * g->nx + i] = (w[(size_t)b * g->wpitch + (i >> 5)] >> (i & 31)) & 1u;
+            for (int i = 0; i < g->nxh[b]; ++i)
+                mask[g->offh[b] + i] = (w[(size_t)b * g->wpitch + (i >> 5)] >> (i & 31)) & 1u;
     }
     if (iters || rel_res) {
         std::vector<MState> ms(g->nb);
@@ -764,9 +1034,23 @@ nh_status nh_step(nh_grid* g, double dt, nh_step_info* info)
 nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info)
 {
     if (!g || n_steps < 0) return NH_ERR_ARG;
+    if (!g->has_state) return NH_ERR_STATE;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return NH_ERR_ARG;
     nh_run_info R;
     std::memset(&R, 0, sizeof(R));
     nh_status rc = NH_OK;
+    if (g->use_graphs && n_steps > 0 && graph_eligible(g, dt)) {
+        rc = graph_run(g, dt, n_steps, &R);
+        if (rc == NH_OK || R.steps == n_steps) {
+            if (info) *info = R;
+            return rc;
+        }
+        // a step failed inside the captured run: redo it step by step (this
+        // also gives AUTO members their BiCGStab fallback) and continue there
+        n_steps -= R.steps;
+        std::memset(&R, 0, sizeof(R));
+        rc = NH_OK;
+    }
     for (long long k = 0; k < n_steps; ++k) {
         nh_step_info si;
         rc = do_step(g, dt, &si);
@@ -785,6 +1069,8 @@ void nh_destroy(nh_grid* g)
     if (!g) return;
     cudaStreamSynchronize(g->stream);
     for (cudaEvent_t e : g->prof_pool) cudaEventDestroy(e);
+    graph_destroy(g);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
 }
 

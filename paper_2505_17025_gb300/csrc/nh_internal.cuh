@@ -75,6 +75,22 @@ struct MState {
 // which is then solved again by BiCGStab.
 constexpr int kStatusFallback = 100;
 
+// Device-side time stepping of a captured run: t^n = t_base + n dt.  A failed
+// step sets `abort` (and `fail_step`); the kernels that write the state or the
+// pressure then stand down, so the last committed state stays intact.
+struct TimeCtl {
+    double t_base;
+    double dt;
+    long long n;          // steps since t_base
+    long long done;       // steps committed in this run
+    long long iters_total;   // Krylov iterations summed over committed steps
+    long long active_total;  // active cells summed over committed steps
+    int abort;
+    int fail_status;
+    int prev_ok;          // psi holds the previous step's solution for this dt
+    int pad;
+};
+
 // Counters shared by all members (device).
 struct Ctl {
     int not_done;      // members still iterating

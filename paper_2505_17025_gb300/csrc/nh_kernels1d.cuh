@@ -20,7 +20,10 @@ namespace nh {
 struct Geo {
     int nx, nb, pitch, wpitch, bc, lim, ntiles, maxch;
     double dx, x0, g;
+    const int* nxv;      // per-member cell counts (uneven ensembles), or null: all nx
 };
+
+__device__ __forceinline__ int member_nx(const Geo& G, int b) { return G.nxv ? G.nxv[b] : G.nx; }
 
 // ------------------------------------------------------------------ slide
 
@@ -33,6 +36,27 @@ static __global__ void k_kinematics(const Slide* __restrict__ sl, Kin* __restric
     Kin k{0.0, 0.0, 0.0, 0.0};
     if (s.shape == NH_SLIDE_GAUSS_LNCOSH) {
         // s(t) = s0 ln cosh(t/t0);  s' = (s0/t0) tanh(t/t0);  s'' = (s0/t0^2) / cosh^2(t/t0)
+        double zn = t_n / s.t0, z1 = t_n1 / s.t0;
+        k.s_n = s.s0 * log(cosh(zn));
+        k.s_n1 = s.s0 * log(cosh(z1));
+        k.sd_n1 = (s.s0 / s.t0) * tanh(z1);
+        double c1 = cosh(z1);
+        k.sdd_n1 = (s.s0 / (s.t0 * s.t0)) / (c1 * c1);
+    }
+    kin[b] = k;
+}
+
+// Same from the device time control block (captured runs).
+static __global__ void k_kinematics_dev(const Slide* __restrict__ sl, Kin* __restrict__ kin, int nb,
+                                        const TimeCtl* __restrict__ tc)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb || tc->abort) return;
+    const double t_n = tc->t_base + (double)tc->n * tc->dt;
+    const double t_n1 = tc->t_base + (double)(tc->n + 1) * tc->dt;
+    Slide s = sl[b];
+    Kin k{0.0, 0.0, 0.0, 0.0};
+    if (s.shape == NH_SLIDE_GAUSS_LNCOSH) {
         double zn = t_n / s.t0, z1 = t_n1 / s.t0;
         k.s_n = s.s0 * log(cosh(zn));
         k.s_n1 = s.s0 * log(cosh(z1));
@@ -101,6 +125,7 @@ struct PredArgs {
     double knh;
     int crit;
     int all_global;                           // mark every cell this step
+    const TimeCtl* tc;                        // captured runs: stand down after an abort
 };
 
 // One CTA = one tile of kPredTile cells of one member.  Q^n is loaded with a
@@ -122,6 +147,7 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
 
     const Geo& G = a.G;
     const int b = blockIdx.y, i0 = blockIdx.x * TILE, tid = threadIdx.x;
+    if (a.tc && a.tc->abort) return;
     const size_t mo = (size_t)b * G.pitch;
     const T* __restrict__ Zn = a.z + mo;
     const T* __restrict__ HUn = a.hu + mo;
@@ -131,15 +157,20 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
     const Kin kn = a.kin[b];
     const T g = T(G.g), dx = T(G.dx), dt = T(a.dt), half_dt = T(0.5) * T(a.dt);
     const T idx = T(1.0 / G.dx);
+    const int nxb = member_nx(G, b);
+    if (i0 >= nxb) {   // tile beyond this member's cells (uneven ensemble)
+        if (tid == 0) a.mass_part[(size_t)b * G.ntiles + blockIdx.x] = 0.0;
+        return;
+    }
 
     // A: load Q^n, d0 and the mound at both times.  Cells outside
     // [-6, nx+5] feed only outputs outside [-1, nx]; they get still water.
     for (int l = tid; l < NL; l += TILE) {
         const int j = i0 - H + l;
         T zv = T(0), huv = T(0), hwv = T(0), d0v = T(1), mn = T(0), mn1 = T(0);
-        if (j >= -6 && j <= G.nx + 5) {
+        if (j >= -6 && j <= nxb + 5) {
             int sg;
-            const int c = resolve(j, G.nx, G.bc, &sg);
+            const int c = resolve(j, nxb, G.bc, &sg);
             zv = Zn[c];
             huv = sg > 0 ? HUn[c] : -HUn[c];
             hwv = HWn[c];
@@ -216,7 +247,7 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
         const T hwn = shw[l] + half_dt * (k1w[l] + r2);
         sz[l] = zn; shu[l] = hun; shw[l] = hwn;
         const int j = i0 - H + l;
-        if (j >= i0 && j < i0 + TILE && j < G.nx) {
+        if (j >= i0 && j < i0 + TILE && j < nxb) {
             a.zt[mo + j] = zn; a.hut[mo + j] = hun; a.hwt[mo + j] = hwn;
         }
     }
@@ -225,7 +256,7 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
     // H: criterion (Sec. 5.1) on the tile; marks as one bit per cell
     {
         const int l = tid + H, j = i0 + tid;
-        const bool inside = j < G.nx;
+        const bool inside = j < nxb;
         bool mark = false;
         double mass = 0.0;
         if (inside) {
@@ -261,6 +292,8 @@ __global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
 
 struct CompactArgs {
     int nx, pitch, wpitch, bc, enlarge;
+    const int* nxv;      // per-member cell counts, or null
+    const TimeCtl* tc;   // captured runs: stand down after an abort (keeps the last list)
     const uint32_t* marks;
     uint32_t* act;       // dilated mask words
     int* list;           // active cells, per member region
@@ -279,8 +312,10 @@ static __global__ void __launch_bounds__(kCompactThreads) k_compact(CompactArgs 
     __shared__ int s_wsum[32];
     __shared__ int s_base;
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (a.tc && a.tc->abort) return;
     const int nwarp = blockDim.x >> 5;
-    const int nw = (a.nx + 31) >> 5;
+    const int nx = a.nxv ? a.nxv[b] : a.nx;
+    const int nw = (nx + 31) >> 5;
     const uint32_t* M = a.marks + (size_t)b * a.wpitch;
     for (int w = tid; w < nw; w += blockDim.x) s_m[w] = M[w];
     if (tid == 0) s_base = 0;
@@ -300,15 +335,15 @@ static __global__ void __launch_bounds__(kCompactThreads) k_compact(CompactArgs 
             uint32_t acc = m;
             for (int s = 1; s <= e; ++s)
                 acc |= (m << s) | (lo >> (32 - s)) | (m >> s) | (hi << (32 - s));
-            const int nvalid = a.nx - 32 * w;
+            const int nvalid = nx - 32 * w;
             if (nvalid < 32) acc &= (1u << nvalid) - 1u;
             if (a.bc == NH_BC_PERIODIC && e > 0) {
-                const int c0 = 32 * w, c1 = min(32 * w + 32, a.nx);
+                const int c0 = 32 * w, c1 = min(32 * w + 32, nx);
                 for (int i = c0; i < c1; ++i) {
-                    if (i >= e && i < a.nx - e) continue;
+                    if (i >= e && i < nx - e) continue;
                     for (int k = -e; k <= e; ++k) {
-                        int c = (i + k) % a.nx;
-                        if (c < 0) c += a.nx;
+                        int c = (i + k) % nx;
+                        if (c < 0) c += nx;
                         if ((s_m[c >> 5] >> (c & 31)) & 1u) { acc |= 1u << (i - c0); break; }
                     }
                 }
@@ -470,12 +505,12 @@ struct CellQ {
 template <typename TS>
 __device__ __forceinline__ CellQ cell_q(const AsmArgs<TS>& a, const TS* __restrict__ zt,
                                         const TS* __restrict__ hut, const double* __restrict__ D0,
-                                        int c, const Slide& sl, const Kin& kn)
+                                        int c, int nxb, const Slide& sl, const Kin& kn)
 {
     const Geo& G = a.G;
-    const Bottom<double> B = bottom_full(D0, c, G.nx, G.bc, G.x0, G.dx, sl, kn);
+    const Bottom<double> B = bottom_full(D0, c, nxb, G.bc, G.x0, G.dx, sl, kn);
     int sg;
-    const int cm = resolve(c - 1, G.nx, G.bc, &sg), cp = resolve(c + 1, G.nx, G.bc, &sg);
+    const int cm = resolve(c - 1, nxb, G.bc, &sg), cp = resolve(c + 1, nxb, G.bc, &sg);
     const double etam = (double)zt[cm] + mound_at<double>(cm, G.x0, G.dx, sl, kn.s_n1);
     const double etap = (double)zt[cp] + mound_at<double>(cp, G.x0, G.dx, sl, kn.s_n1);
     const double eta_x = (etap - etam) / (2.0 * G.dx);
@@ -521,11 +556,12 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
         double r2 = 0.0, gmin = INFINITY;
         if (k < n) {
             const int i = a.list[mo + k];
+            const int nxb = member_nx(G, b);
             int sgm, sgp;
-            const int cm = resolve(i - 1, G.nx, G.bc, &sgm), cp = resolve(i + 1, G.nx, G.bc, &sgp);
-            const CellQ qi = cell_q(a, zt, hut, D0, i, sl, kn);
-            const CellQ qm = cell_q(a, zt, hut, D0, cm, sl, kn);
-            const CellQ qp = cell_q(a, zt, hut, D0, cp, sl, kn);
+            const int cm = resolve(i - 1, nxb, G.bc, &sgm), cp = resolve(i + 1, nxb, G.bc, &sgp);
+            const CellQ qi = cell_q(a, zt, hut, D0, i, nxb, sl, kn);
+            const CellQ qm = cell_q(a, zt, hut, D0, cm, nxb, sl, kn);
+            const CellQ qp = cell_q(a, zt, hut, D0, cp, nxb, sl, kn);
             const double idx2 = 1.0 / (G.dx * G.dx);
             const double Kl = 0.5 * (qm.K + qi.K), Kr = 0.5 * (qi.K + qp.K);
             const double bm = sgm > 0 ? qm.beta : -qm.beta, bp = sgp > 0 ? qp.beta : -qp.beta;
@@ -541,10 +577,10 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
                 hasl = bit_at(act, cm);
                 hasr = bit_at(act, cp);
                 if (hasl) kl = (i == 0) ? n - 1 : k - 1;
-                if (hasr) kr = (i == G.nx - 1) ? 0 : k + 1;
+                if (hasr) kr = (i == nxb - 1) ? 0 : k + 1;
             } else {
                 hasl = (i > 0) && bit_at(act, i - 1);
-                hasr = (i < G.nx - 1) && bit_at(act, i + 1);
+                hasr = (i < nxb - 1) && bit_at(act, i + 1);
                 if (hasl) kl = k - 1;
                 if (hasr) kr = k + 1;
             }
@@ -608,6 +644,7 @@ struct SolveArgs {
     T* r1; T* z;               // PCG: second residual buffer, preconditioned residual
     int maxpb;                 // preconditioner blocks per member (upper bound)
     const int2* items; const int2* pitems;
+    const TimeCtl* tc;         // captured runs: guess scale from tc->prev_ok
     MState* ms; Ctl* ctl;
     double* part;              // [3][nb * maxch]
     int* cnt;
@@ -650,7 +687,7 @@ __global__ void __launch_bounds__(kChunk) k_solve_init(SolveArgs<T> a)
         double rr = 0.0;
         if (in) {
             const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
-            const double sc = a.guess_scale;
+            const double sc = a.tc ? (a.tc->prev_ok && a.guess_scale != 0.0 ? 1.0 : 0.0) : a.guess_scale;
             T x0 = T(0), xl = T(0), xr = T(0);
             if (sc != 0.0) {
                 x0 = T(a.psi_prev[mo + a.list[mo + k]] * sc);
@@ -1449,11 +1486,13 @@ struct ClearArgs {
     const int* list_prev;
     const int* nact_prev;
     double* psi;
+    const TimeCtl* tc;
 };
 
 // Zero the dense pressure unknown on the previous step's active cells.
 static __global__ void k_clear_prev(ClearArgs a)
 {
+    if (a.tc && a.tc->abort) return;
     const size_t total = (size_t)a.nb * a.pitch;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (size_t)gridDim.x * blockDim.x) {
@@ -1473,12 +1512,14 @@ struct CorrArgs {
     T* hu; T* hw;          // Q~ buffers, corrected in place into Q^{n+1}
     double* psi;           // dense pressure unknown (for the next warm start)
     const int2* items; const Ctl* ctl;
+    const TimeCtl* tc;
 };
 
 // Eqs. 10-11 on the active cells (h is not corrected, Sec. 3.2).
 template <typename T>
 __global__ void __launch_bounds__(kChunk) k_correct(CorrArgs<T> a)
 {
+    if (a.tc && a.tc->abort) return;
     const int n_items = a.ctl->n_items;
     for (int wi = blockIdx.x; wi < n_items; wi += gridDim.x) {
         const int2 itm = a.items[wi];
@@ -1502,6 +1543,22 @@ __global__ void __launch_bounds__(kChunk) k_correct(CorrArgs<T> a)
     }
 }
 
+static __global__ void k_fill(double* __restrict__ a, double v, size_t n)
+{
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        a[q] = v;
+}
+
+// dst[b * pitch + i] = src[off[b] + i] for i < off[b+1] - off[b]
+static __global__ void k_scatter(const double* __restrict__ src, double* __restrict__ dst, int pitch,
+                                 const long long* __restrict__ off)
+{
+    const int b = blockIdx.y;
+    const long long o0 = off[b], n = off[b + 1] - o0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[(size_t)b * pitch + i] = src[o0 + i];
+}
+
 static __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n)
 {
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
@@ -1512,12 +1569,15 @@ static __global__ void k_to_float(const double* __restrict__ a, float* __restric
 template <typename T>
 __global__ void k_state_in(const double* __restrict__ h, const double* __restrict__ hu,
                            const double* __restrict__ hw, const double* __restrict__ d0,
-                           T* z, T* tu, T* tw, int nb, int nx, int pitch)
+                           T* z, T* tu, T* tw, int nb, int pitch, const long long* __restrict__ off)
 {
-    const size_t total = (size_t)nb * nx;
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = q / nx, i = q - b * nx, o = b * pitch + i;
+    // host layout: member b occupies [off[b], off[b+1]) of the concatenated arrays
+    const int b = blockIdx.y;
+    const long long o0 = off[b], nxb = off[b + 1] - o0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nxb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long q = o0 + i;
+        const size_t o = (size_t)b * pitch + i;
         z[o] = T(h[q] - d0[o]);
         tu[o] = T(hu[q]);
         tw[o] = T(hw[q]);
@@ -1528,12 +1588,14 @@ template <typename T>
 __global__ void k_state_out(const T* __restrict__ z, const T* __restrict__ tu, const T* __restrict__ tw,
                             const double* __restrict__ d0, const double* __restrict__ psi,
                             double* h, double* hu, double* hw, double* p, double rho_over_dt,
-                            int nb, int nx, int pitch)
+                            int nb, int pitch, const long long* __restrict__ off)
 {
-    const size_t total = (size_t)nb * nx;
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = q / nx, i = q - b * nx, o = b * pitch + i;
+    const int b = blockIdx.y;
+    const long long o0 = off[b], nxb = off[b + 1] - o0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nxb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long q = o0 + i;
+        const size_t o = (size_t)b * pitch + i;
         const double hh = (double)z[o] + d0[o];
         h[q] = hh;
         hu[q] = (double)tu[o];
@@ -1675,9 +1737,26 @@ struct Summary {
     double mass;
 };
 
-static __global__ void k_summary(const MState* ms, int nb, const double* mass_part, int nparts, double dx,
-                          Summary* out)
+// Captured runs: accept the step (advance the device time) or abort the run.
+static __global__ void k_commit(const Summary* __restrict__ S, TimeCtl* tc)
 {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || tc->abort) return;
+    if (S->status == NH_OK) {
+        tc->n += 1;
+        tc->done += 1;
+        tc->prev_ok = 1;
+        tc->iters_total += S->iters;
+        tc->active_total += S->n_active;
+    } else {
+        tc->abort = 1;
+        tc->fail_status = S->status;
+    }
+}
+
+static __global__ void k_summary(const MState* ms, int nb, const double* mass_part, int nparts, double dx,
+                          Summary* out, const TimeCtl* tc)
+{
+    if (tc && tc->abort) return;
     __shared__ double red[64];
     double m[1] = {0.0};
     for (int q = threadIdx.x; q < nparts; q += blockDim.x) m[0] += mass_part[q];

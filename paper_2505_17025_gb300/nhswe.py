@@ -34,7 +34,8 @@ NH_SLIDE_NONE, NH_SLIDE_GAUSS_LNCOSH = 0, 1
 EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion",
            "nh_set_solver", "nh_set_preconditioner", "nh_set_state", "nh_put_state", "nh_get_state",
            "nh_get_mask", "nh_step", "nh_run", "nh_set_profiling", "nh_get_profile", "nh_destroy",
-           "nh_status_string", "nh_predict_static")
+           "nh_status_string", "nh_predict_static", "nh_workspace_bytes_ensemble", "nh_create_ensemble",
+           "nh_set_run_mode")
 NH_STATIC_MAX_CELLS = 262144
 KERNEL_CLASSES = ("kinematics", "predict", "compact", "assemble", "solve_init", "precond", "pcg_a",
                   "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct",
@@ -98,6 +99,10 @@ def load():
         L.nh_workspace_bytes.restype = C.c_size_t
         L.nh_create_grid.argtypes = [C.POINTER(nh_grid_desc), _D, C.c_void_p, C.c_size_t, C.c_void_p,
                                      C.POINTER(C.c_void_p)]
+        L.nh_workspace_bytes_ensemble.argtypes = [C.POINTER(nh_grid_desc), C.POINTER(C.c_int)]
+        L.nh_workspace_bytes_ensemble.restype = C.c_size_t
+        L.nh_create_ensemble.argtypes = [C.POINTER(nh_grid_desc), C.POINTER(C.c_int), _D, C.c_void_p,
+                                         C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]
         L.nh_set_bottom_motion.argtypes = [C.c_void_p, C.POINTER(nh_slide_desc)]
         L.nh_set_criterion.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int]
         L.nh_set_solver.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
@@ -107,6 +112,7 @@ def load():
         L.nh_get_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
         L.nh_put_state.argtypes = [C.c_void_p, _D, _D, _D]
         L.nh_set_profiling.argtypes = [C.c_void_p, C.c_int]
+        L.nh_set_run_mode.argtypes = [C.c_void_p, C.c_int]
         L.nh_get_profile.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
         L.nh_get_mask.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), C.POINTER(C.c_int), _D]
         L.nh_step.argtypes = [C.c_void_p, C.c_double, C.POINTER(nh_step_info)]
@@ -120,8 +126,9 @@ def load():
         L.nh_predict_static.restype = C.c_int
         L.nh_status_string.argtypes = [C.c_int]
         L.nh_status_string.restype = C.c_char_p
-        for f in ("nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
+        for f in ("nh_create_grid", "nh_create_ensemble", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
                   "nh_set_preconditioner", "nh_put_state", "nh_set_profiling", "nh_get_profile",
+                  "nh_set_run_mode",
                   "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run"):
             getattr(L, f).restype = C.c_int
         _LIB = L
@@ -155,33 +162,62 @@ def _f64(a, n):
 class Grid:
     """A batch of 1D members on one GPU, stepping through the C ABI.
 
-    Parameters mirror ``nh_grid_desc``; ``d0`` is (nbatch, nx) or (nx,).
-    The workspace is a ``torch.uint8`` tensor on the current CUDA device and the
-    stream is ``torch.cuda.current_stream()`` unless one is given.
+    ``nx`` is one cell count for every member, or a sequence of per-member
+    counts (an uneven ensemble, ``nh_create_ensemble``).  ``d0`` is (nbatch, nx),
+    (nx,) or, for an ensemble, a sequence of per-member arrays.  The workspace
+    is a ``torch.uint8`` tensor on the current CUDA device and the stream is
+    ``torch.cuda.current_stream()`` unless one is given.
     """
 
     def __init__(self, nx, dx, d0, nbatch=1, x0=0.0, bc=NH_BC_WALL, precision=NH_FP64,
                  limiter=NH_LIM_CENTRAL, g=9.81, rho=1000.0, stream=None):
         import torch
         self.L = load()
-        self.desc = nh_grid_desc(1, int(nx), int(nbatch), int(bc), int(precision), int(limiter),
+        if np.ndim(nx) == 0:
+            self.nxs = [int(nx)] * int(nbatch)
+        else:
+            self.nxs = [int(v) for v in nx]
+            nbatch = len(self.nxs)
+        self.uneven = len(set(self.nxs)) > 1 or np.ndim(nx) > 0
+        self.nb = int(nbatch)
+        self.nx = max(self.nxs)
+        self.offsets = np.concatenate([[0], np.cumsum(self.nxs)]).astype(np.int64)
+        self.ncells = int(self.offsets[-1])
+        self.desc = nh_grid_desc(1, self.nx, self.nb, int(bc), int(precision), int(limiter),
                                  float(dx), float(x0), float(g), float(rho))
-        self.nx, self.nb = int(nx), int(nbatch)
-        nbytes = self.L.nh_workspace_bytes(C.byref(self.desc))
+        nxa = (C.c_int * self.nb)(*self.nxs)
+        nbytes = self.L.nh_workspace_bytes_ensemble(C.byref(self.desc), nxa)
         if nbytes == 0:
-            raise NHError(NH_ERR_ARG, "nh_workspace_bytes")
+            raise NHError(NH_ERR_ARG, "nh_workspace_bytes_ensemble")
         self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         base = self.ws.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        d0 = np.broadcast_to(np.asarray(d0, dtype=np.float64).reshape(-1, self.nx), (self.nb, self.nx))
-        d0 = np.ascontiguousarray(d0)
+        d0c = self._concat(d0)
         h = C.c_void_p()
-        _check(self.L.nh_create_grid(C.byref(self.desc), _dptr(d0), C.c_void_p(self._ws_ptr),
-                                     C.c_size_t(nbytes), C.c_void_p(self.stream.cuda_stream),
-                                     C.byref(h)), "nh_create_grid")
+        _check(self.L.nh_create_ensemble(C.byref(self.desc), nxa, _dptr(d0c), C.c_void_p(self._ws_ptr),
+                                         C.c_size_t(nbytes), C.c_void_p(self.stream.cuda_stream),
+                                         C.byref(h)), "nh_create_ensemble")
         self.h = h
         self.workspace_bytes = nbytes
+
+    def _concat(self, a):
+        """Host layout: members concatenated (FP64, contiguous)."""
+        if isinstance(a, (list, tuple)) and len(a) == self.nb and np.ndim(a[0]) == 1:
+            out = np.concatenate([np.asarray(v, dtype=np.float64).reshape(-1) for v in a])
+        else:
+            arr = np.asarray(a, dtype=np.float64)
+            if arr.ndim == 1 and arr.size == self.nx and not self.uneven:
+                arr = np.broadcast_to(arr, (self.nb, self.nx))
+            out = np.ascontiguousarray(arr).reshape(-1)
+        if out.size != self.ncells:
+            raise ValueError(f"expected {self.ncells} values, got {out.size}")
+        return np.ascontiguousarray(out)
+
+    def _split(self, a):
+        if not self.uneven:
+            return a.reshape(self.nb, self.nx)
+        return [a[self.offsets[b]:self.offsets[b + 1]] for b in range(self.nb)]
 
     # -- configuration
     def set_bottom_motion(self, slides):
@@ -209,8 +245,7 @@ class Grid:
 
     # -- state
     def set_state(self, h, hu, hw, t=0.0):
-        n = self.nx * self.nb
-        h, hu, hw = _f64(h, n), _f64(hu, n), _f64(hw, n)
+        h, hu, hw = self._concat(h), self._concat(hu), self._concat(hw)
         _check(self.L.nh_set_state(self.h, _dptr(h), _dptr(hu), _dptr(hw), float(t)), "nh_set_state")
 
     def set_state_ptr(self, h_ptr, hu_ptr, hw_ptr, t=0.0):
@@ -223,6 +258,9 @@ class Grid:
         cast = lambda p: C.cast(C.c_void_p(p), _D)
         _check(self.L.nh_put_state(self.h, cast(h_ptr), cast(hu_ptr), cast(hw_ptr)), "nh_put_state")
 
+    def set_run_mode(self, use_graphs=True):
+        _check(self.L.nh_set_run_mode(self.h, int(bool(use_graphs))), "nh_set_run_mode")
+
     def set_profiling(self, enable=True):
         _check(self.L.nh_set_profiling(self.h, int(bool(enable))), "nh_set_profiling")
 
@@ -234,11 +272,10 @@ class Grid:
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def get_state(self):
-        n = self.nx * self.nb
+        n = self.ncells
         h, hu, hw, p = (np.empty(n) for _ in range(4))
         _check(self.L.nh_get_state(self.h, _dptr(h), _dptr(hu), _dptr(hw), _dptr(p)), "nh_get_state")
-        sh = (self.nb, self.nx)
-        return h.reshape(sh), hu.reshape(sh), hw.reshape(sh), p.reshape(sh)
+        return self._split(h), self._split(hu), self._split(hw), self._split(p)
 
     def get_state_ptr(self, h_ptr, hu_ptr=0, hw_ptr=0, p_ptr=0):
         cast = lambda p: C.cast(C.c_void_p(p), _D) if p else None
@@ -246,12 +283,12 @@ class Grid:
                "nh_get_state")
 
     def get_mask(self):
-        m = np.empty(self.nx * self.nb, dtype=np.uint8)
+        m = np.empty(self.ncells, dtype=np.uint8)
         it = np.empty(self.nb, dtype=np.int32)
         rr = np.empty(self.nb)
         _check(self.L.nh_get_mask(self.h, m.ctypes.data_as(C.POINTER(C.c_ubyte)),
                                   it.ctypes.data_as(C.POINTER(C.c_int)), _dptr(rr)), "nh_get_mask")
-        return m.reshape(self.nb, self.nx), it, rr
+        return self._split(m), it, rr
 
     # -- stepping
     def step(self, dt, check=True):
@@ -282,13 +319,15 @@ class Grid:
 
 
 def grid_from_workload(wl, precision=NH_FP64, limiter=NH_LIM_CENTRAL, bc=None, **kw):
-    """A Grid holding every member of a ``workloads.Workload1D`` with its
-    bottom motion and initial state set."""
+    """A Grid holding every member of a ``workloads.Workload1D`` (uniform or
+    uneven cell counts) with its bottom motion and initial state set."""
     ms = wl.members
     m0 = ms[0]
-    G = Grid(m0.nx, m0.dx, np.stack([m.d0 for m in ms]), nbatch=len(ms), x0=m0.xl,
+    nxs = [m.nx for m in ms]
+    nx = nxs[0] if len(set(nxs)) == 1 else nxs
+    G = Grid(nx, m0.dx, [m.d0 for m in ms], nbatch=len(ms), x0=m0.xl,
              bc=wl.bc if bc is None else bc, precision=precision, limiter=limiter, **kw)
     if any(m.slide for m in ms):
         G.set_bottom_motion([dict(shape=m.slide, A=m.A, L=m.L, xc0=m.xc0, s0=m.s0, t0=m.t0) for m in ms])
-    G.set_state(np.stack([m.h for m in ms]), np.stack([m.hu for m in ms]), np.stack([m.hw for m in ms]))
+    G.set_state([m.h for m in ms], [m.hu for m in ms], [m.hw for m in ms])
     return G

@@ -135,6 +135,32 @@ def slide_1d(n_members=64, nx=50000, length=40.0, h_min=0.05, h_max=1.0, slope=0
                             "s0": s0, "t0": t0, "xc0": xc0, "spread": spread, "seed0": seed0})
 
 
+def ensemble_1d(n_members=32, nx_min=16384, nx_max=131072, dx=0.002, h_min=0.1, h_max=2.0,
+                slope=(0.1, 0.3), A=(0.05, 0.15), L=(0.5, 1.5), s0=(1.0, 3.0), t0=1.0,
+                d_start=0.6, T=1.0, cfl=0.5, g=G):
+    """Ensemble of uneven 1D landslide runs: member k draws, from
+    numpy default_rng(k), its cell count (uniform in [nx_min, nx_max], a
+    multiple of 256), slope tan(theta), mound height A, width L and travel s0
+    from the given uniform ranges; d0 = min(h_min + tan(theta) x, h_max), the
+    mound starts where d0 = d_start.  One dt for the whole ensemble."""
+    members = []
+    for k in range(n_members):
+        rng = np.random.default_rng(k)
+        nx = int(rng.integers(nx_min // 256, nx_max // 256 + 1)) * 256
+        tan, Ak, Lk, sk = (rng.uniform(*slope), rng.uniform(*A), rng.uniform(*L), rng.uniform(*s0))
+        x = (np.arange(nx) + 0.5) * dx
+        d0 = np.minimum(h_min + tan * x, h_max)
+        xc0 = (d_start - h_min) / tan
+        xi = (x - xc0) / Lk
+        d = d0 - Ak * np.exp(-xi * xi)
+        members.append(Member1D(nx=nx, dx=dx, xl=0.0, d0=d0, h=d.copy(), hu=np.zeros(nx),
+                                hw=np.zeros(nx), slide=1, A=Ak, L=Lk, xc0=xc0, s0=sk, t0=t0))
+    dt, n = cfl_dt(T, cfl, dx, math.sqrt(g * h_max))
+    return Workload1D("ensemble_1d", members, dt, n, T, amplitude=A[1],
+                      meta={"nx_range": (nx_min, nx_max), "dx": dx, "slope": slope, "A": A, "L": L,
+                            "s0": s0, "t0": t0})
+
+
 def standing_wave_1d(nx=128, depth=1.0, kh=1.0, amp=1e-4, modes=1, g=G):
     """Small-amplitude standing wave eta = amp cos(k x) in a walled basin of
     length modes * pi / k (k = kh / depth), at rest."""
