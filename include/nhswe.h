@@ -208,6 +208,14 @@ nh_status nh_step(nh_grid* g, double dt, nh_step_info* info);
    returned; info->last describes it).  info may be NULL. */
 nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info);
 
+/* Predictor tile (cells per CTA: 128, 256 or 512).  By default the first
+   nh_step / nh_run of a handle times every candidate on the handle's state
+   with CUDA events and keeps the fastest (cached per shape for the process).
+   tile != 0 forces a tile; tile == 0 keeps the current choice.  chosen
+   (nullable) receives the tile in use, 0 if not chosen yet.
+   Errors: NH_ERR_ARG. */
+nh_status nh_set_tile(nh_grid* g, int tile, int* chosen);
+
 /* use_graphs != 0 (the default): nh_run captures one FP64 step per
    state-buffer parity as a CUDA graph (on a private capture stream, replayed
    on the handle's stream) and replays it n_steps times with a single

@@ -9,6 +9,9 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <array>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -21,6 +24,8 @@ struct nh_grid {
     cudaStream_t stream;
     int nx, nb, pitch, wpitch, ntiles, maxch, sm_count, items_grid, pcr_grid;
     int coop_grid[2];            // persistent PCG CTAs (FP64 / FP32 vectors), 0 = unavailable
+    int tile;                    // predictor tile (cells per CTA), chosen by the autotuner
+    bool tuned;
     long long barrier_budget;    // clock cycles a grid barrier may spin
     size_t es;                   // element size of state / Krylov vectors
     bool mixed;
@@ -117,9 +122,10 @@ size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
 {
     const int nx = d.nx, nb = d.nbatch;
     const bool mixed = d.precision == NH_MIXED;
-    const int pitch = (nx + kPredTile - 1) / kPredTile * kPredTile;
+    const int pitch = (nx + kPredTileMax - 1) / kPredTileMax * kPredTileMax;
     const int wpitch = pitch / 32;
     const int ntiles = pitch / kPredTile;
+    const int ntiles_max = pitch / kPredTileMin;
     const int maxch = (nx + kChunk - 1) / kChunk;
     const int maxpb = (nx + kPcrRows - 1) / kPcrRows;
     const size_t N = (size_t)nb * pitch;
@@ -168,7 +174,7 @@ size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
     G->ctl = (Ctl*)c.take(sizeof(Ctl));
     G->part = (double*)c.take(sizeof(double) * 3 * (size_t)nb * maxch);
     G->cnt = (int*)c.take(sizeof(int) * nb);
-    G->mass_part = (double*)c.take(sizeof(double) * (size_t)nb * ntiles);
+    G->mass_part = (double*)c.take(sizeof(double) * (size_t)nb * ntiles_max);
     G->summary = (Summary*)c.take(sizeof(Summary));
     G->tc = (TimeCtl*)c.take(sizeof(TimeCtl));
     if (g) {
@@ -232,11 +238,43 @@ void prof_fold(nh_grid* g)
         prof_fold(g);                                              \
     } while (0)
 
+template <typename T, int TILE>
+cudaError_t predict_launch_t(int nb, int ntiles, cudaStream_t st, const PredArgs<T>& pa)
+{
+    k_predict<T, TILE><<<dim3(ntiles, nb), TILE, predict_smem_bytes<T, TILE>(), st>>>(pa);
+    return cudaGetLastError();
+}
+
+// k_predict with the handle's tile; pa.G.ntiles must match the tile.
+template <typename T>
+cudaError_t predict_launch(int tile, int nb, int ntiles, cudaStream_t st, const PredArgs<T>& pa)
+{
+    switch (tile) {
+    case 128: return predict_launch_t<T, 128>(nb, ntiles, st, pa);
+    case 512: return predict_launch_t<T, 512>(nb, ntiles, st, pa);
+    default: return predict_launch_t<T, 256>(nb, ntiles, st, pa);
+    }
+}
+
+template <typename T>
+cudaError_t predict_set_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_predict<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)predict_smem_bytes<T, 128>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_predict<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)predict_smem_bytes<T, 256>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_predict<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)predict_smem_bytes<T, 512>());
+    return e;
+}
+
 Geo geo(const nh_grid* g)
 {
     Geo G;
     G.nx = g->nx; G.nb = g->nb; G.pitch = g->pitch; G.wpitch = g->wpitch; G.bc = g->d.bc;
-    G.lim = g->d.limiter; G.ntiles = g->ntiles; G.maxch = g->maxch;
+    G.lim = g->d.limiter; G.ntiles = g->pitch / g->tile; G.maxch = g->maxch;
     G.dx = g->d.dx; G.x0 = g->d.x0; G.g = g->d.g;
     G.nxv = g->uneven ? g->nxd : nullptr;
     return G;
@@ -408,7 +446,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     pa.marks = g->marks; pa.mass_part = g->mass_part; pa.dt = dt; pa.knh = g->knh; pa.crit = g->crit;
     pa.all_global = (g->crit == NH_CRIT_GLOBAL) || (g->first_global && g->steps == 0);
     pa.tc = nullptr;
-    LAUNCH(NH_K_PREDICT, k_predict<T><<<dim3(g->ntiles, g->nb), kPredTile, 0, st>>>(pa));
+    LAUNCH(NH_K_PREDICT, predict_launch<T>(g->tile, g->nb, g->pitch / g->tile, st, pa));
 
     CompactArgs ca;
     ca.nx = g->nx; ca.pitch = g->pitch; ca.wpitch = g->wpitch; ca.bc = g->d.bc; ca.enlarge = g->enlarge;
@@ -444,7 +482,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
         xfinal = (const double*)g->x;
     }
 
-    LAUNCH(NH_K_SUMMARY, k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->ntiles, g->d.dx, g->summary, nullptr));
+    LAUNCH(NH_K_SUMMARY, k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * (g->pitch / g->tile), g->d.dx, g->summary, nullptr));
     Summary S;
     CK(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
     SYNC();
@@ -513,7 +551,7 @@ nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, do
     pa.marks = g->marks; pa.mass_part = g->mass_part; pa.dt = dt; pa.knh = g->knh; pa.crit = g->crit;
     pa.all_global = (g->crit == NH_CRIT_GLOBAL);
     pa.tc = g->tc;
-    k_predict<double><<<dim3(g->ntiles, g->nb), kPredTile, 0, st>>>(pa);
+    CK(predict_launch<double>(g->tile, g->nb, g->pitch / g->tile, st, pa));
     CompactArgs ca;
     ca.nx = g->nx; ca.pitch = g->pitch; ca.wpitch = g->wpitch; ca.bc = g->d.bc; ca.enlarge = g->enlarge;
     ca.marks = g->marks; ca.act = g->act; ca.list = g->list[lnew]; ca.nact = g->nact[lnew];
@@ -556,7 +594,7 @@ nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, do
         long long budget = g->barrier_budget;
         CK(cudaLaunchKernelEx(&cfg, k_pcg_persistent<double, float>, sa, budget));
     }
-    k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->ntiles, g->d.dx, g->summary, g->tc);
+    k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * (g->pitch / g->tile), g->d.dx, g->summary, g->tc);
     k_commit<<<1, 32, 0, st>>>(g->summary, g->tc);
     ClearArgs cl;
     cl.nb = g->nb; cl.pitch = g->pitch; cl.maxlist = g->pitch;
@@ -592,7 +630,7 @@ void graph_destroy(nh_grid* g)
 nh_status graph_prepare(nh_grid* g, double dt)
 {
     const double key[10] = {dt, (double)g->crit, g->knh, (double)g->enlarge, (double)g->solver, g->rtol,
-                            (double)g->max_iter, (double)g->guess, (double)(g->cur ^ g->lcur), 0.0};
+                            (double)g->max_iter, (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->tile};
     if (g->graph_valid && std::memcmp(key, g->graph_key, sizeof(key)) == 0) return NH_OK;
     graph_destroy(g);
     for (int p = 0; p < 2; ++p) {
@@ -657,10 +695,68 @@ nh_status graph_run(nh_grid* g, double dt, long long n_steps, nh_run_info* R)
     return NH_OK;
 }
 
+// Predictor tile autotuner: time each candidate on the handle's current state
+// (outputs go to the step's scratch buffers) and keep the fastest; results are
+// cached per (cells per member, members, precision, limiter) for the process.
+std::mutex g_tune_mutex;
+std::map<std::array<long long, 4>, int> g_tune_cache;
+
+template <typename T>
+nh_status autotune_t(nh_grid* g, double dt)
+{
+    const std::array<long long, 4> key = {g->pitch, g->nb, g->mixed ? 1 : 0, g->d.limiter};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { g->tile = it->second; g->tuned = true; return NH_OK; }
+    }
+    cudaStream_t st = g->stream;
+    const int cur = g->cur, nxt = cur ^ 1;
+    k_kinematics<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slide, g->kin, g->nb, g->t_base, g->t_base + dt);
+    PredArgs<T> pa;
+    pa.G = geo(g);
+    pa.z = (const T*)g->sz[cur]; pa.hu = (const T*)g->shu[cur]; pa.hw = (const T*)g->shw[cur];
+    pa.zt = (T*)g->sz[nxt]; pa.hut = (T*)g->shu[nxt]; pa.hwt = (T*)g->shw[nxt];
+    pa.d0 = (const T*)g->d0; pa.slide = g->slide; pa.kin = g->kin;
+    pa.marks = g->marks; pa.mass_part = g->mass_part; pa.dt = dt; pa.knh = g->knh; pa.crit = g->crit;
+    pa.all_global = 0; pa.tc = nullptr;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return NH_ERR_CUDA; }
+    const int cand[3] = {128, 256, 512};
+    float best = 1e30f;
+    int best_tile = kPredTile;
+    nh_status rc = NH_OK;
+    for (int c = 0; c < 3 && rc == NH_OK; ++c) {
+        pa.G.ntiles = g->pitch / cand[c];
+        for (int w = 0; w < 2; ++w) predict_launch<T>(cand[c], g->nb, pa.G.ntiles, st, pa);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5; ++r) predict_launch<T>(cand[c], g->nb, pa.G.ntiles, st, pa);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = NH_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_tile = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
+    if (rc != NH_OK) return rc;
+    g->tile = best_tile;
+    g->tuned = true;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best_tile;
+    return NH_OK;
+}
+
 nh_status do_step(nh_grid* g, double dt, nh_step_info* info)
 {
     if (!g->has_state) return NH_ERR_STATE;
     if (!(dt > 0.0) || !std::isfinite(dt)) return NH_ERR_ARG;
+    if (!g->tuned) {
+        nh_status rc = g->mixed ? autotune_t<float>(g, dt) : autotune_t<double>(g, dt);
+        if (rc != NH_OK) return rc;
+    }
     return g->mixed ? step_t<float>(g, dt, info) : step_t<double>(g, dt, info);
 }
 
@@ -819,6 +915,7 @@ static nh_status finish_create(nh_grid* g, const double* d0_host, int dev, int s
     g->prof_on = false; g->prof_used = 0;
     for (int k = 0; k < NH_K_COUNT; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
     g->graph[0] = g->graph[1] = nullptr; g->graph_valid = false; g->graph_runs = 0; g->use_graphs = true;
+    g->tile = kPredTile; g->tuned = false;
     if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) g->cap_stream = nullptr;
     cudaStream_t st = g->stream;
     nh_status rc = NH_OK;
@@ -850,6 +947,9 @@ static nh_status finish_create(nh_grid* g, const double* d0_host, int dev, int s
             rc = NH_ERR_CUDA; break;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; break; }
+        if (predict_set_smem<double>() != cudaSuccess || predict_set_smem<float>() != cudaSuccess) {
+            rc = NH_ERR_CUDA; break;
+        }
         if (cudaFuncSetAttribute(k_pcr<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess ||
             cudaFuncSetAttribute(k_pcr<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -964,6 +1064,15 @@ nh_status nh_put_state(nh_grid* g, const double* h, const double* hu, const doub
     return g->mixed ? upload_state<float>(g, h, hu, hw) : upload_state<double>(g, h, hu, hw);
 }
 
+nh_status nh_set_tile(nh_grid* g, int tile, int* chosen)
+{
+    if (!g) return NH_ERR_ARG;
+    if (tile != 0 && tile != 128 && tile != 256 && tile != 512) return NH_ERR_ARG;
+    if (tile != 0) { g->tile = tile; g->tuned = true; }
+    if (chosen) *chosen = g->tuned ? g->tile : 0;
+    return NH_OK;
+}
+
 nh_status nh_set_run_mode(nh_grid* g, int use_graphs)
 {
     if (!g) return NH_ERR_ARG;
@@ -1039,6 +1148,10 @@ nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info)
     nh_run_info R;
     std::memset(&R, 0, sizeof(R));
     nh_status rc = NH_OK;
+    if (!g->tuned) {
+        rc = g->mixed ? autotune_t<float>(g, dt) : autotune_t<double>(g, dt);
+        if (rc != NH_OK) return rc;
+    }
     if (g->use_graphs && n_steps > 0 && graph_eligible(g, dt)) {
         rc = graph_run(g, dt, n_steps, &R);
         if (rc == NH_OK || R.steps == n_steps) {

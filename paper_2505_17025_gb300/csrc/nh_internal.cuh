@@ -27,7 +27,9 @@
 
 namespace nh {
 
-constexpr int kPredTile = 256;   // cells per predictor CTA (multiple of 32)
+constexpr int kPredTile = 256;   // default cells per predictor CTA (autotuned: 128, 256, 512)
+constexpr int kPredTileMax = 512;
+constexpr int kPredTileMin = 128;
 constexpr int kPredHalo = 5;     // two Heun stages + one cell for the criterion
 constexpr int kChunk = 256;      // active cells per solver work item (= blockDim)
 constexpr int kCompactThreads = 1024;

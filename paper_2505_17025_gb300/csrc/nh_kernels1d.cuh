@@ -133,16 +133,35 @@ struct PredArgs {
 // (bottom at t^n) is evaluated on the tile plus 3 cells each side, stage 2
 // (bottom at t^{n+1}) on the tile plus one cell each side, so the criterion's
 // central differences need no second pass.  Q~ = Q^n + dt/2 (k1 + k2).
-template <typename T>
-__global__ void __launch_bounds__(kPredTile) k_predict(PredArgs<T> a)
+// Shared memory of one predictor tile (19 arrays of TILE + 2 halo cells).
+template <typename T, int TILE>
+constexpr size_t predict_smem_bytes() { return sizeof(T) * 19 * (TILE + 2 * kPredHalo); }
+
+template <typename T, int TILE>
+__global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
 {
-    constexpr int TILE = kPredTile, H = kPredHalo, NL = TILE + 2 * H;
-    __shared__ T sz[NL], shu[NL], shw[NL];      // Q^n, later Q~
-    __shared__ T sd0[NL], smn[NL], smn1[NL];    // static depth, mound at t^n, t^{n+1}
-    __shared__ T se[NL], su[NL], sw[NL];        // stage primitives eta, u, w
-    __shared__ T sle[NL], slu[NL], slw[NL];     // limited slopes
-    __shared__ T F0[NL], A1[NL], G1[NL], F2[NL];  // face l: between local cells l-1 and l
-    __shared__ T k1h[NL], k1u[NL], k1w[NL];     // stage-1 rates
+    constexpr int H = kPredHalo, NL = TILE + 2 * H;
+    extern __shared__ __align__(16) unsigned char psm[];
+    T* const sm = reinterpret_cast<T*>(psm);
+    T* const sz = sm;               // Q^n, later Q~
+    T* const shu = sm + NL;
+    T* const shw = sm + 2 * NL;
+    T* const sd0 = sm + 3 * NL;     // static depth, mound at t^n, t^{n+1}
+    T* const smn = sm + 4 * NL;
+    T* const smn1 = sm + 5 * NL;
+    T* const se = sm + 6 * NL;      // stage primitives eta, u, w
+    T* const su = sm + 7 * NL;
+    T* const sw = sm + 8 * NL;
+    T* const sle = sm + 9 * NL;     // limited slopes
+    T* const slu = sm + 10 * NL;
+    T* const slw = sm + 11 * NL;
+    T* const F0 = sm + 12 * NL;     // face l: between local cells l-1 and l
+    T* const A1 = sm + 13 * NL;
+    T* const G1 = sm + 14 * NL;
+    T* const F2 = sm + 15 * NL;
+    T* const k1h = sm + 16 * NL;    // stage-1 rates
+    T* const k1u = sm + 17 * NL;
+    T* const k1w = sm + 18 * NL;
     __shared__ double red[32];
 
     const Geo& G = a.G;

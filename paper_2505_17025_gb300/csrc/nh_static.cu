@@ -134,7 +134,7 @@ extern "C" nh_status nh_predict_static(const double* h, const double* hu, const 
     pa.dt = dt; pa.knh = 0.0; pa.crit = NH_CRIT_HYDROSTATIC; pa.all_global = 0;
     pa.tc = nullptr;
     pa.G.nxv = nullptr;
-    k_predict<double><<<dim3(ntiles, 1), kPredTile, 0, st>>>(pa);
+    k_predict<double, kPredTile><<<dim3(ntiles, 1), kPredTile, predict_smem_bytes<double, kPredTile>(), st>>>(pa);
     k_static_finish<<<1, 1024, 0, st>>>(h_out, d0, nx, sum_dev);
     if (cudaGetLastError() != cudaSuccess) return NH_ERR_CUDA;
     if (mass) {

@@ -35,7 +35,7 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh_set_solver", "nh_set_preconditioner", "nh_set_state", "nh_put_state", "nh_get_state",
            "nh_get_mask", "nh_step", "nh_run", "nh_set_profiling", "nh_get_profile", "nh_destroy",
            "nh_status_string", "nh_predict_static", "nh_workspace_bytes_ensemble", "nh_create_ensemble",
-           "nh_set_run_mode")
+           "nh_set_run_mode", "nh_set_tile")
 NH_STATIC_MAX_CELLS = 262144
 KERNEL_CLASSES = ("kinematics", "predict", "compact", "assemble", "solve_init", "precond", "pcg_a",
                   "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct",
@@ -113,6 +113,7 @@ def load():
         L.nh_put_state.argtypes = [C.c_void_p, _D, _D, _D]
         L.nh_set_profiling.argtypes = [C.c_void_p, C.c_int]
         L.nh_set_run_mode.argtypes = [C.c_void_p, C.c_int]
+        L.nh_set_tile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
         L.nh_get_profile.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
         L.nh_get_mask.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), C.POINTER(C.c_int), _D]
         L.nh_step.argtypes = [C.c_void_p, C.c_double, C.POINTER(nh_step_info)]
@@ -128,7 +129,7 @@ def load():
         L.nh_status_string.restype = C.c_char_p
         for f in ("nh_create_grid", "nh_create_ensemble", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
                   "nh_set_preconditioner", "nh_put_state", "nh_set_profiling", "nh_get_profile",
-                  "nh_set_run_mode",
+                  "nh_set_run_mode", "nh_set_tile",
                   "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run"):
             getattr(L, f).restype = C.c_int
         _LIB = L
@@ -257,6 +258,12 @@ class Grid:
         """Replace the state from raw host addresses, keeping time and warm start."""
         cast = lambda p: C.cast(C.c_void_p(p), _D)
         _check(self.L.nh_put_state(self.h, cast(h_ptr), cast(hu_ptr), cast(hw_ptr)), "nh_put_state")
+
+    def set_tile(self, tile=0):
+        """Force the predictor tile (128/256/512) or, with 0, read the autotuned one."""
+        out = C.c_int(0)
+        _check(self.L.nh_set_tile(self.h, int(tile), C.byref(out)), "nh_set_tile")
+        return out.value
 
     def set_run_mode(self, use_graphs=True):
         _check(self.L.nh_set_run_mode(self.h, int(bool(use_graphs))), "nh_set_run_mode")

@@ -86,3 +86,25 @@ def test_graph_run_stops_at_failed_step_with_state_intact():
     st, info = G.run(wl.dt, 3)
     assert st == N.NH_OK and info["last"]["step"] == 8
     G.close()
+
+
+def test_predictor_tiles_identical_and_autotuned():
+    """Every predictor tile (128, 256, 512 cells per CTA) computes the same
+    cells with the same arithmetic, so forced tiles give identical states;
+    an untouched handle picks one of them on its first step."""
+    wl = W.slide_1d(n_members=2, nx=3000, length=6.0, xc0=1.0, T=0.5, seed0=5)
+    out = []
+    for tile in (128, 256, 512):
+        G = make_gpu(wl, O.CRIT_ETA_D, knh=1e-4)
+        assert G.set_tile(tile) == tile
+        G.run(wl.dt, 40)
+        out.append(G.get_state())
+        G.close()
+    for st in out[1:]:
+        for x, y in zip(st, out[0]):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+    G = make_gpu(wl, O.CRIT_ETA_D)
+    assert G.set_tile(0) == 0
+    G.step(wl.dt)
+    assert G.set_tile(0) in (128, 256, 512)
+    G.close()
