@@ -69,7 +69,8 @@ enum { NH_CRIT_GLOBAL = 0, NH_CRIT_HYDROSTATIC = 1, NH_CRIT_ETA_D = 2,
    for positive definiteness; a few negative gamma cells (e.g. at a kink of
    d0) usually leave the operator definite.  CG / BICGSTAB force one method. */
 enum { NH_SOLVER_AUTO = 0, NH_SOLVER_CG = 1, NH_SOLVER_BICGSTAB = 2 };
-enum { NH_GUESS_ZERO = 0, NH_GUESS_PREV = 1 };
+/* NH_GUESS_CNN: the learned guess of nhswe_cnn.h (needs nh_cnn_attach). */
+enum { NH_GUESS_ZERO = 0, NH_GUESS_PREV = 1, NH_GUESS_CNN = 2 };
 /* Preconditioner of the CG branch.  NH_PRECOND_LINE: the tridiagonal operator
    restricted to blocks of 4096 consecutive active cells, solved by parallel
    cyclic reduction in FP32 (exact up to FP32 rounding on any active segment
@@ -165,7 +166,8 @@ nh_status nh_set_criterion(nh_grid* g, int kind, double k_nh, int enlarge,
 /* Elliptic solve on the marked cells (Sec. 3.2).  rtol: stop when
    ||R - A q||_2 <= rtol ||R||_2 per member (FP64 norms).  max_iter >= 1.
    guess: NH_GUESS_PREV starts from the previous step's pressure on cells
-   active in both steps (zero elsewhere).  NH_MIXED only: ir_max >= 1 outer
+   active in both steps (zero elsewhere); NH_GUESS_CNN from the learned
+   guess (NH_ERR_STATE unless nh_cnn_attach was called).  NH_MIXED only: ir_max >= 1 outer
    refinement passes with an FP64 residual, each an FP32 Krylov solve to
    inner_rtol (relative to its own right-hand side).  Errors: NH_ERR_ARG. */
 nh_status nh_set_solver(nh_grid* g, int kind, double rtol, int max_iter, int guess,
@@ -232,7 +234,8 @@ enum { NH_K_KINEMATICS = 0, NH_K_PREDICT = 1, NH_K_COMPACT = 2, NH_K_ASSEMBLE = 
        NH_K_CG_A = 8, NH_K_CG_B = 9, NH_K_BI_1 = 10, NH_K_BI_2 = 11, NH_K_BI_3 = 12,
        NH_K_SUMMARY = 13, NH_K_CLEAR = 14, NH_K_CORRECT = 15,
        NH_K_PCG_LOOP = 16,   /* all PCG iterations of a solve in one cooperative launch */
-       NH_K_COUNT = 17 };
+       NH_K_CNN = 17,        /* learned guess: history, features, network, guess */
+       NH_K_COUNT = 18 };
 
 /* enable != 0: bracket every kernel launch with CUDA events on the handle's
    stream and accumulate per-class device time (read back at the step's own

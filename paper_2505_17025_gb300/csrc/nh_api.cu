@@ -15,6 +15,7 @@
 #include <new>
 #include <vector>
 
+#include "nh_cnn.cuh"
 #include "nh_kernels1d.cuh"
 
 using namespace nh;
@@ -40,7 +41,7 @@ struct nh_grid {
     cudaStream_t cap_stream;     // private stream used only to capture graphs
     cudaGraphExec_t graph[2];    // one captured step per state-buffer parity
     bool graph_valid;
-    double graph_key[10];        // settings the graphs were captured with
+    double graph_key[12];        // settings the graphs were captured with
     int graph_runs;              // nh_run calls served by graphs (diagnostics)
     bool use_graphs;             // nh_run may replay captured graphs
     double mass0;                // sum of d0 dx over all members (FP64)
@@ -77,6 +78,9 @@ struct nh_grid {
     double* psi;
     MState* ms; Ctl* ctl; double* part; int* cnt;
     double* mass_part; Summary* summary;
+    // learned guess (nh_cnn_attach): solution history, features, network
+    bool cnn_attached, cnn_record;
+    cnn::GuessBufs cnn;
     // profiling: event pairs recorded around launches, folded in at syncs
     bool prof_on;
     double prof_ms[NH_K_COUNT];
@@ -304,6 +308,39 @@ SolveArgs<T> solve_args(nh_grid* g, int lcur, const T* diag, const T* offl, cons
     return a;
 }
 
+// Learned-guess geometry of the step whose mask bits are in g->act.
+cnn::GuessGeo guess_geo(const nh_grid* g, const TimeCtl* tc)
+{
+    cnn::GuessGeo G;
+    G.nb = g->nb; G.pitch = g->pitch; G.wpitch = g->wpitch; G.nxv = g->nxd; G.act = g->act;
+    G.psi = g->psi; G.tc = tc; G.sms = g->sm_count;
+    return G;
+}
+
+bool cnn_features_on(const nh_grid* g)
+{
+    return g->cnn_attached && (g->guess == NH_GUESS_CNN || g->cnn_record);
+}
+
+// Judge the three starting points of the solve (previous pressure,
+// extrapolation, extrapolation + network) by their initial residual with the
+// FP64 operator just assembled, and copy each member's winner into the guess.
+cudaError_t judge_launch(nh_grid* g, int lnew, double gscale, const TimeCtl* tc, cudaStream_t st)
+{
+    JudgeArgs ja;
+    ja.pitch = g->pitch; ja.stride = (size_t)g->nb * g->maxch;
+    ja.list = g->list[lnew]; ja.nbl = g->nbl; ja.nbr = g->nbr;
+    ja.diag = g->diag; ja.offl = g->offl; ja.offr = g->offr; ja.R = g->R;
+    ja.cand0 = g->psi; ja.cand1 = g->cnn.base; ja.cand2 = g->cnn.guess;
+    ja.guess_scale = gscale; ja.tc = tc;
+    ja.items = g->items; ja.ms = g->ms; ja.ctl = g->ctl; ja.part = g->part; ja.cnt = g->cnt;
+    ja.choice = g->cnn.choice; ja.counts = g->cnn.ctl->counts;
+    k_guess_judge<<<g->items_grid, kChunk, 0, st>>>(ja);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cnn::launch_select(g->cnn, guess_geo(g, tc), st);
+}
+
 // Krylov solve on the active cells with the vectors of type T: set-up, then
 // iterations until every member finished (read back every poll_every).
 template <typename T>
@@ -390,14 +427,14 @@ nh_status krylov_pass(nh_grid* g, SolveArgs<T>& sa)
 }
 
 // Mixed path: FP64 iterative refinement around FP32 Krylov solves.
-nh_status refine(nh_grid* g, int lnew, double guess_scale)
+nh_status refine(nh_grid* g, int lnew, double guess_scale, const double* guess_src)
 {
     cudaStream_t st = g->stream;
     IRArgs ia;
     ia.nb = g->nb; ia.pitch = g->pitch; ia.maxch = g->maxch;
     ia.list = g->list[lnew]; ia.nbl = g->nbl; ia.nbr = g->nbr;
     ia.diag = g->diag; ia.offl = g->offl; ia.offr = g->offr; ia.R = g->R;
-    ia.psi_prev = g->psi; ia.guess_scale = guess_scale;
+    ia.psi_prev = guess_src; ia.guess_scale = guess_scale;
     ia.x64 = g->x64; ia.e32 = (const float*)g->x; ia.rhs32 = g->rhs32;
     ia.ms = g->ms; ia.ir = g->ir; ia.ctl = g->ctl; ia.part = g->part; ia.cnt = g->cnt;
     ia.rtol = g->rtol; ia.ir_max = g->ir_max; ia.items = g->items;
@@ -434,7 +471,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     const int cur = g->cur, nxt = cur ^ 1;
     const int lprev = g->lcur, lnew = lprev ^ 1;
     const Geo G = geo(g);
-    const double gscale = (g->guess == NH_GUESS_PREV && g->last_dt > 0.0) ? dt / g->last_dt : 0.0;
+    const double gscale = (g->guess != NH_GUESS_ZERO && g->last_dt > 0.0) ? dt / g->last_dt : 0.0;
 
     LAUNCH(NH_K_KINEMATICS, k_kinematics<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slide, g->kin, g->nb, t_n, t_n1));
 
@@ -467,26 +504,39 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     aa.c6 = (T*)g->c6; aa.cx = (T*)g->cx; aa.phi = (T*)g->phi; aa.ddx = (T*)g->ddx;
     aa.part = g->part; aa.cnt = g->cnt; aa.dt = dt; aa.solver = g->solver;
     aa.items = g->items; aa.ctl = g->ctl;
-    LAUNCH(NH_K_ASSEMBLE, k_assemble<T><<<g->items_grid, kChunk, 0, st>>>(aa));
 
-    const double* xfinal;
-    if (g->mixed) {
-        nh_status rc = refine(g, lnew, gscale);
-        if (rc != NH_OK) return rc;
-        xfinal = g->x64;
-    } else {
-        SolveArgs<double> sa = solve_args<double>(g, lnew, g->diag, g->offl, g->offr, g->R, g->rtol);
-        sa.guess_scale = gscale;
-        nh_status rc = krylov<double>(g, sa);
-        if (rc != NH_OK) return rc;
-        xfinal = (const double*)g->x;
-    }
+    const cnn::GuessGeo GG = guess_geo(g, nullptr);
+    if (cnn_features_on(g)) LAUNCH(NH_K_CNN, CK(cnn::launch_features(g->cnn, GG, st)));
+    bool learned = g->guess == NH_GUESS_CNN && gscale != 0.0;
+    if (learned) LAUNCH(NH_K_CNN, CK(cnn::launch_guess(g->cnn, GG, st)));
 
-    LAUNCH(NH_K_SUMMARY, k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * (g->pitch / g->tile), g->d.dx, g->summary, nullptr));
+    // assembly and solve from the learned guess; a failed solve from it is
+    // redone (assembly included) from the plain warm start
+    const double* xfinal = nullptr;
     Summary S;
-    CK(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
-    SYNC();
-    CK(cudaGetLastError());
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const double* src = learned ? g->cnn.guess : g->psi;
+        LAUNCH(NH_K_ASSEMBLE, k_assemble<T><<<g->items_grid, kChunk, 0, st>>>(aa));
+        if (learned) LAUNCH(NH_K_CNN, CK(judge_launch(g, lnew, gscale, nullptr, st)));
+        if (g->mixed) {
+            nh_status rc = refine(g, lnew, gscale, src);
+            if (rc != NH_OK) return rc;
+            xfinal = g->x64;
+        } else {
+            SolveArgs<double> sa = solve_args<double>(g, lnew, g->diag, g->offl, g->offr, g->R, g->rtol);
+            sa.psi_prev = src;
+            sa.guess_scale = gscale;
+            nh_status rc = krylov<double>(g, sa);
+            if (rc != NH_OK) return rc;
+            xfinal = (const double*)g->x;
+        }
+        LAUNCH(NH_K_SUMMARY, k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * (g->pitch / g->tile), g->d.dx, g->summary, nullptr));
+        CK(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
+        SYNC();
+        CK(cudaGetLastError());
+        if (!learned || S.status == NH_OK) break;
+        learned = false;
+    }
     int ir_passes = 0;
     if (g->mixed) {
         std::vector<IRState> irs(g->nb);
@@ -496,6 +546,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
     }
     nh_status status = (nh_status)S.status;
     if (status == NH_OK) {
+        if (g->cnn_attached) LAUNCH(NH_K_CNN, CK(cnn::launch_shift(g->cnn, GG, st)));
         ClearArgs cl;
         cl.nb = g->nb; cl.pitch = g->pitch; cl.maxlist = g->pitch;
         cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = nullptr;
@@ -570,8 +621,15 @@ nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, do
     aa.part = g->part; aa.cnt = g->cnt; aa.dt = dt; aa.solver = g->solver;
     aa.items = g->items; aa.ctl = g->ctl;
     k_assemble<double><<<g->items_grid, kChunk, 0, st>>>(aa);
+    const cnn::GuessGeo GG = guess_geo(g, g->tc);
+    if (cnn_features_on(g)) CK(cnn::launch_features(g->cnn, GG, st));
+    if (g->guess == NH_GUESS_CNN) {
+        CK(cnn::launch_guess(g->cnn, GG, st));
+        CK(judge_launch(g, lnew, 1.0, g->tc, st));
+    }
     SolveArgs<double> sa = solve_args<double>(g, lnew, g->diag, g->offl, g->offr, g->R, g->rtol);
-    sa.guess_scale = (g->guess == NH_GUESS_PREV) ? 1.0 : 0.0;
+    sa.psi_prev = (g->guess == NH_GUESS_CNN) ? g->cnn.guess : g->psi;
+    sa.guess_scale = (g->guess != NH_GUESS_ZERO) ? 1.0 : 0.0;
     sa.tc = g->tc;
     CK(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
     CK(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
@@ -596,6 +654,7 @@ nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, do
     }
     k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * (g->pitch / g->tile), g->d.dx, g->summary, g->tc);
     k_commit<<<1, 32, 0, st>>>(g->summary, g->tc);
+    if (g->cnn_attached) CK(cnn::launch_shift(g->cnn, GG, st));
     ClearArgs cl;
     cl.nb = g->nb; cl.pitch = g->pitch; cl.maxlist = g->pitch;
     cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = g->tc;
@@ -629,8 +688,9 @@ void graph_destroy(nh_grid* g)
 
 nh_status graph_prepare(nh_grid* g, double dt)
 {
-    const double key[10] = {dt, (double)g->crit, g->knh, (double)g->enlarge, (double)g->solver, g->rtol,
-                            (double)g->max_iter, (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->tile};
+    const double key[12] = {dt, (double)g->crit, g->knh, (double)g->enlarge, (double)g->solver, g->rtol,
+                            (double)g->max_iter, (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->tile,
+                            (double)g->cnn_attached, (double)g->cnn_record};
     if (g->graph_valid && std::memcmp(key, g->graph_key, sizeof(key)) == 0) return NH_OK;
     graph_destroy(g);
     for (int p = 0; p < 2; ++p) {
@@ -841,9 +901,27 @@ nh_status create_impl(const nh_grid_desc* desc_in, const int* nxv, const double*
     return NH_OK;
 }
 
-}  // namespace
+// Learned-guess buffers inside the caller's second workspace.
+size_t cnn_layout(const nh_grid* g, char* base, cnn::GuessBufs* B)
+{
+    const size_t N = (size_t)g->nb * g->pitch;
+    Carver c{base};
+    cnn::GuessBufs t;
+    cnn::GuessBufs& b = B ? *B : t;
+    b.h1 = (double*)c.take(sizeof(double) * N);
+    b.h2 = (double*)c.take(sizeof(double) * N);
+    b.feat = c.take((size_t)NH_CNN_IN * 2 * N);
+    b.y = (float*)c.take(sizeof(float) * N);
+    b.guess = (double*)c.take(sizeof(double) * N);
+    b.d2 = (double*)c.take(sizeof(double) * N);
+    b.base = (double*)c.take(sizeof(double) * N);
+    b.choice = (int*)c.take(sizeof(int) * g->nb);
+    b.params = (float*)c.take(sizeof(float) * NH_CNN_PARAMS);
+    b.ctl = (cnn::GuessCtl*)c.take(sizeof(cnn::GuessCtl));
+    return (c.off + kAlign - 1) / kAlign * kAlign;
+}
 
-extern "C" {}  // namespace
+}  // namespace
 
 extern "C" {
 
@@ -915,6 +993,8 @@ static nh_status finish_create(nh_grid* g, const double* d0_host, int dev, int s
     g->prof_on = false; g->prof_used = 0;
     for (int k = 0; k < NH_K_COUNT; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
     g->graph[0] = g->graph[1] = nullptr; g->graph_valid = false; g->graph_runs = 0; g->use_graphs = true;
+    g->cnn_attached = false; g->cnn_record = false;
+    std::memset(&g->cnn, 0, sizeof(g->cnn));
     g->tile = kPredTile; g->tuned = false;
     if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) g->cap_stream = nullptr;
     cudaStream_t st = g->stream;
@@ -1022,8 +1102,9 @@ nh_status nh_set_solver(nh_grid* g, int kind, double rtol, int max_iter, int gue
 {
     if (!g) return NH_ERR_ARG;
     if (kind < NH_SOLVER_AUTO || kind > NH_SOLVER_BICGSTAB) return NH_ERR_ARG;
-    if (!(rtol > 0.0) || max_iter < 1 || (guess != NH_GUESS_ZERO && guess != NH_GUESS_PREV)) return NH_ERR_ARG;
+    if (!(rtol > 0.0) || max_iter < 1 || guess < NH_GUESS_ZERO || guess > NH_GUESS_CNN) return NH_ERR_ARG;
     if (ir_max < 1 || !(inner_rtol > 0.0)) return NH_ERR_ARG;
+    if (guess == NH_GUESS_CNN && !g->cnn_attached) return NH_ERR_STATE;
     g->solver = kind; g->rtol = rtol; g->max_iter = max_iter; g->guess = guess;
     g->ir_max = ir_max; g->inner_rtol = inner_rtol;
     return NH_OK;
@@ -1051,6 +1132,7 @@ nh_status nh_set_state(nh_grid* g, const double* h, const double* hu, const doub
     CK(cudaMemsetAsync(g->psi, 0, sizeof(double) * (size_t)g->nb * g->pitch, st));
     CK(cudaMemsetAsync(g->nact[0], 0, sizeof(int) * g->nb, st));
     CK(cudaMemsetAsync(g->nact[1], 0, sizeof(int) * g->nb, st));
+    if (g->cnn_attached) CK(cudaMemsetAsync(g->cnn.ctl, 0, sizeof(cnn::GuessCtl), st));
     CK(cudaStreamSynchronize(st));
     g->has_state = true;
     g->t_base = t; g->n_since = 0; g->steps = 0; g->last_dt = 0.0;
@@ -1175,6 +1257,77 @@ nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info)
     }
     if (info) *info = R;
     return rc;
+}
+
+// ------------------------------------------------------------ learned guess
+
+size_t nh_cnn_attach_bytes(const nh_grid* g)
+{
+    if (!g) return 0;
+    return cnn_layout(g, nullptr, nullptr);
+}
+
+nh_status nh_cnn_attach(nh_grid* g, void* ws, size_t ws_bytes)
+{
+    if (!g || !ws) return NH_ERR_ARG;
+    const size_t need = cnn_layout(g, nullptr, nullptr);
+    if (ws_bytes < need || ((uintptr_t)ws % kAlign) != 0) return NH_ERR_ARG;
+    cnn::GuessBufs B;
+    cnn_layout(g, (char*)ws, &B);
+    CK(cudaMemsetAsync(ws, 0, need, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (cnn::prepare_device() != cudaSuccess) return NH_ERR_CUDA;
+    g->cnn = B;
+    g->cnn_attached = true;
+    graph_destroy(g);
+    return NH_OK;
+}
+
+nh_status nh_cnn_set_params(nh_grid* g, const float* params_dev)
+{
+    if (!g || !params_dev) return NH_ERR_ARG;
+    if (!g->cnn_attached) return NH_ERR_STATE;
+    CK(cudaMemcpyAsync(g->cnn.params, params_dev, sizeof(float) * NH_CNN_PARAMS, cudaMemcpyDeviceToDevice,
+                       g->stream));
+    return NH_OK;
+}
+
+nh_status nh_cnn_record(nh_grid* g, int record)
+{
+    if (!g) return NH_ERR_ARG;
+    if (!g->cnn_attached) return NH_ERR_STATE;
+    g->cnn_record = record != 0;
+    return NH_OK;
+}
+
+nh_status nh_cnn_choices(nh_grid* g, long long* counts)
+{
+    if (!g || !counts) return NH_ERR_ARG;
+    if (!g->cnn_attached) return NH_ERR_STATE;
+    cnn::GuessCtl c;
+    CK(cudaMemcpyAsync(&c, g->cnn.ctl, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    for (int k = 0; k < 3; ++k) counts[k] = (long long)c.counts[k];
+    return NH_OK;
+}
+
+nh_status nh_cnn_harvest(nh_grid* g, void* feat_out, float* target_out, unsigned char* mask_out, double* scale,
+                         int* pitch)
+{
+    if (!g || !feat_out || !target_out || !mask_out) return NH_ERR_ARG;
+    if (!g->cnn_attached) return NH_ERR_STATE;
+    cudaStream_t st = g->stream;
+    cnn::GuessCtl c;
+    CK(cudaMemcpyAsync(&c, g->cnn.ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!c.built) return NH_ERR_STATE;
+    const size_t N = (size_t)g->nb * g->pitch;
+    CK(cudaMemcpyAsync(feat_out, g->cnn.feat, (size_t)NH_CNN_IN * 2 * N, cudaMemcpyDeviceToDevice, st));
+    CK(cnn::launch_harvest(g->cnn, guess_geo(g, nullptr), target_out, mask_out, st));
+    CK(cudaStreamSynchronize(st));
+    if (scale) *scale = c.S2_used;
+    if (pitch) *pitch = g->pitch;
+    return NH_OK;
 }
 
 void nh_destroy(nh_grid* g)

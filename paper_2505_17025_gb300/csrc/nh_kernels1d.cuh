@@ -750,6 +750,73 @@ __global__ void __launch_bounds__(kChunk) k_solve_init(SolveArgs<T> a)
     NH_END_ITEMS
 }
 
+// Candidate initial guesses judged by the energy CG minimises: for a
+// symmetric positive definite A with solution x*, ||x - x*||_A^2 =
+// J(x) - J(x*), J(x) = x.Ax - 2 x.R.  Against the warm start x0 (cand0) each
+// candidate c = 1, 2 differs by dJ_c = d.Ad - 2 d.r0 (d = x_c - x0,
+// r0 = R - A x0) = ||e_c||_A^2 - ||e_0||_A^2, summed over each member's active
+// cells from the small quantities d and r0 (no cancellation against J).  The
+// lowest of {0, dJ_1, dJ_2} wins (ties go to the lower index) and is recorded
+// in choice[b] and counts[].  Candidates are scaled like the warm start.
+struct JudgeArgs {
+    int pitch;
+    size_t stride;             // nb * maxch: offset between the partial-sum slots
+    const int* list; const int* nbl; const int* nbr;
+    const double* diag; const double* offl; const double* offr; const double* R;
+    const double* cand0; const double* cand1; const double* cand2;
+    double guess_scale;
+    const TimeCtl* tc;
+    const int2* items; MState* ms; const Ctl* ctl;
+    double* part; int* cnt;
+    int* choice; unsigned long long* counts;
+};
+
+static __global__ void __launch_bounds__(kChunk) k_guess_judge(JudgeArgs a)
+{
+    __shared__ double red[96];
+    if (a.tc && a.tc->abort) return;
+    const double sc = a.tc ? (a.tc->prev_ok && a.guess_scale != 0.0 ? 1.0 : 0.0) : a.guess_scale;
+    NH_FOR_ITEMS(a)
+        double dj[3] = {0.0, 0.0, 0.0};
+        if (in) {
+            const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+            const size_t i0 = mo + a.list[mo + k];
+            const size_t il = kl >= 0 ? mo + a.list[mo + kl] : 0;
+            const size_t ir = kr >= 0 ? mo + a.list[mo + kr] : 0;
+            const double dg = a.diag[mo + k], ol = a.offl[mo + k], orr = a.offr[mo + k];
+            const double x0 = a.cand0[i0] * sc;
+            const double x0l = kl >= 0 ? a.cand0[il] * sc : 0.0;
+            const double x0r = kr >= 0 ? a.cand0[ir] * sc : 0.0;
+            const double r0 = a.R[mo + k] - (dg * x0 + ol * x0l + orr * x0r);
+            const double* c[2] = {a.cand1, a.cand2};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const double d = c[q][i0] * sc - x0;
+                const double dl = kl >= 0 ? c[q][il] * sc - x0l : 0.0;
+                const double dr = kr >= 0 ? c[q][ir] * sc - x0r : 0.0;
+                dj[q + 1] = d * (dg * d + ol * dl + orr * dr) - 2.0 * d * r0;
+            }
+        }
+        block_sum<3>(dj, red);
+        if (threadIdx.x == 0) {
+            a.part[a.stride + wi] = dj[1];
+            a.part[2 * a.stride + wi] = dj[2];
+        }
+        if (arrive_last(a.cnt, b, nch)) {
+            const double s1 = member_sum(a.part + a.stride + ioff, nch, red);
+            const double s2 = member_sum(a.part + 2 * a.stride + ioff, nch, red);
+            if (threadIdx.x == 0) {
+                int best = 0;
+                double bv = 0.0;
+                if (isfinite(s1) && s1 < bv) { best = 1; bv = s1; }
+                if (isfinite(s2) && s2 < bv) { best = 2; bv = s2; }
+                a.choice[b] = best;
+                atomicAdd(&a.counts[best], 1ull);
+            }
+        }
+    NH_END_ITEMS
+}
+
 template <typename T>
 __device__ __forceinline__ void finish_member(MState& s, Ctl* ctl, int status, int iters, double rel)
 {

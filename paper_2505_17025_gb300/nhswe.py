@@ -1,4 +1,4 @@
-"""Thin ctypes binding of the C ABI in ``include/nhswe.h``.
+"""Thin ctypes binding of the C ABI in ``include/nhswe.h`` and ``include/nhswe_cnn.h``.
 
 Argument marshalling only: every step of the method runs in the CUDA library.
 The functions keep the C names (``nh_create_grid``, ``nh_step``, ...); the
@@ -26,7 +26,7 @@ NH_LIM_NONE, NH_LIM_CENTRAL, NH_LIM_MINMOD, NH_LIM_MC = range(4)
 (NH_CRIT_GLOBAL, NH_CRIT_HYDROSTATIC, NH_CRIT_ETA_D, NH_CRIT_ETA_X, NH_CRIT_U, NH_CRIT_U_X,
  NH_CRIT_W, NH_CRIT_W_X) = range(8)
 NH_SOLVER_AUTO, NH_SOLVER_CG, NH_SOLVER_BICGSTAB = range(3)
-NH_GUESS_ZERO, NH_GUESS_PREV = 0, 1
+NH_GUESS_ZERO, NH_GUESS_PREV, NH_GUESS_CNN = 0, 1, 2
 NH_PRECOND_NONE, NH_PRECOND_LINE = 0, 1
 NH_SLIDE_NONE, NH_SLIDE_GAUSS_LNCOSH = 0, 1
 
@@ -35,11 +35,15 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh_set_solver", "nh_set_preconditioner", "nh_set_state", "nh_put_state", "nh_get_state",
            "nh_get_mask", "nh_step", "nh_run", "nh_set_profiling", "nh_get_profile", "nh_destroy",
            "nh_status_string", "nh_predict_static", "nh_workspace_bytes_ensemble", "nh_create_ensemble",
-           "nh_set_run_mode", "nh_set_tile")
+           "nh_set_run_mode", "nh_set_tile", "nh_cnn_forward", "nh_cnn_workspace_bytes",
+           "nh_cnn_loss_grad", "nh_cnn_adam", "nh_cnn_attach_bytes", "nh_cnn_attach",
+           "nh_cnn_set_params", "nh_cnn_record", "nh_cnn_harvest", "nh_cnn_choices")
+NH_CNN_PARAMS = 9328
+NH_CNN_IN = 16
 NH_STATIC_MAX_CELLS = 262144
 KERNEL_CLASSES = ("kinematics", "predict", "compact", "assemble", "solve_init", "precond", "pcg_a",
                   "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct",
-                  "pcg_loop")
+                  "pcg_loop", "cnn")
 
 
 class nh_grid_desc(C.Structure):
@@ -125,12 +129,27 @@ def load():
                                                            C.POINTER(nh_slide_desc), C.c_double,
                                                            C.c_double, _D, C.c_void_p]
         L.nh_predict_static.restype = C.c_int
+        vp, sz = C.c_void_p, C.c_size_t
+        L.nh_cnn_forward.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, C.c_float, vp, vp]
+        L.nh_cnn_workspace_bytes.argtypes = [C.c_int, C.c_int]
+        L.nh_cnn_workspace_bytes.restype = sz
+        L.nh_cnn_loss_grad.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp, C.c_longlong, vp, _D, vp, sz, vp]
+        L.nh_cnn_adam.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, vp]
+        L.nh_cnn_attach_bytes.argtypes = [vp]
+        L.nh_cnn_attach_bytes.restype = sz
+        L.nh_cnn_attach.argtypes = [vp, vp, sz]
+        L.nh_cnn_set_params.argtypes = [vp, vp]
+        L.nh_cnn_record.argtypes = [vp, C.c_int]
+        L.nh_cnn_harvest.argtypes = [vp, vp, vp, vp, _D, C.POINTER(C.c_int)]
+        L.nh_cnn_choices.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.nh_status_string.argtypes = [C.c_int]
         L.nh_status_string.restype = C.c_char_p
         for f in ("nh_create_grid", "nh_create_ensemble", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
                   "nh_set_preconditioner", "nh_put_state", "nh_set_profiling", "nh_get_profile",
                   "nh_set_run_mode", "nh_set_tile",
-                  "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run"):
+                  "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run",
+                  "nh_cnn_forward", "nh_cnn_loss_grad", "nh_cnn_adam", "nh_cnn_attach",
+                  "nh_cnn_set_params", "nh_cnn_record", "nh_cnn_harvest", "nh_cnn_choices"):
             getattr(L, f).restype = C.c_int
         _LIB = L
         return L
@@ -297,6 +316,50 @@ class Grid:
                                   it.ctypes.data_as(C.POINTER(C.c_int)), _dptr(rr)), "nh_get_mask")
         return self._split(m), it, rr
 
+    # -- learned guess (nhswe_cnn.h)
+    def cnn_attach(self):
+        """Allocate the guess buffers (a torch tensor kept by the Grid) and attach them."""
+        import torch
+        n = self.L.nh_cnn_attach_bytes(self.h)
+        self.cnn_ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+        ptr = (self.cnn_ws.data_ptr() + 255) // 256 * 256
+        _check(self.L.nh_cnn_attach(self.h, C.c_void_p(ptr), C.c_size_t(n)), "nh_cnn_attach")
+
+    def cnn_set_params(self, params):
+        """params: CUDA float32 tensor of NH_CNN_PARAMS values (copied)."""
+        _params_check(params)
+        _check(self.L.nh_cnn_set_params(self.h, C.c_void_p(params.data_ptr())), "nh_cnn_set_params")
+
+    def cnn_record(self, record=True):
+        _check(self.L.nh_cnn_record(self.h, int(bool(record))), "nh_cnn_record")
+
+    def cnn_harvest(self):
+        """(features [nb, pitch, 16] bf16, target [nb, pitch] f32, mask [nb, pitch] u8, scale) of
+        the last step, as CUDA tensors."""
+        import torch
+        pitch = C.c_int(0)
+        scale = C.c_double(0.0)
+        probe = (self.nx + 511) // 512 * 512
+        feat = torch.empty((self.nb, probe, NH_CNN_IN), dtype=torch.bfloat16, device="cuda")
+        target = torch.empty((self.nb, probe), dtype=torch.float32, device="cuda")
+        mask = torch.empty((self.nb, probe), dtype=torch.uint8, device="cuda")
+        _check(self.L.nh_cnn_harvest(self.h, C.c_void_p(feat.data_ptr()), C.c_void_p(target.data_ptr()),
+                                     C.c_void_p(mask.data_ptr()), C.byref(scale), C.byref(pitch)),
+               "nh_cnn_harvest")
+        if pitch.value != probe:
+            raise RuntimeError(f"row pitch {pitch.value} != {probe}")
+        return feat, target, mask, scale.value
+
+    def cnn_choices(self):
+        """{previous, extrapolation, network}: solves started from each."""
+        c = (C.c_longlong * 3)()
+        _check(self.L.nh_cnn_choices(self.h, c), "nh_cnn_choices")
+        return {"previous": c[0], "extrapolation": c[1], "network": c[2]}
+
+    def nx_device(self):
+        import torch
+        return torch.tensor(self.nxs, dtype=torch.int32, device="cuda")
+
     # -- stepping
     def step(self, dt, check=True):
         info = nh_step_info()
@@ -323,6 +386,75 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------ network calls (nhswe_cnn.h)
+
+def _params_check(t):
+    import torch
+    if t.dtype != torch.float32 or not t.is_cuda or t.numel() != NH_CNN_PARAMS or not t.is_contiguous():
+        raise ValueError("params must be a contiguous CUDA float32 tensor of NH_CNN_PARAMS values")
+
+
+def _stream_ptr():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def nh_cnn_forward(feat, nx_dev, params, out_scale=1.0, status=None):
+    """feat: CUDA bf16 [nb, pitch, 16]; nx_dev: CUDA int32 [nb]; returns y [nb, pitch] float32
+    (entries at or beyond a member's cell count are 0)."""
+    import torch
+    L = load()
+    _params_check(params)
+    nb, pitch, ch = feat.shape
+    if ch != NH_CNN_IN or feat.dtype != torch.bfloat16 or not feat.is_contiguous():
+        raise ValueError("feat must be a contiguous bf16 tensor [nb, pitch, 16]")
+    y = torch.zeros((nb, pitch), dtype=torch.float32, device=feat.device)
+    sp = C.c_void_p(status.data_ptr()) if status is not None else None
+    _check(L.nh_cnn_forward(C.c_void_p(feat.data_ptr()), C.c_void_p(nx_dev.data_ptr()), nb, pitch,
+                            C.c_void_p(params.data_ptr()), C.c_void_p(y.data_ptr()), float(out_scale), sp,
+                            _stream_ptr()), "nh_cnn_forward")
+    return y
+
+
+class CnnWorkspace:
+    """Scratch of nh_cnn_loss_grad for nb x pitch cells (a torch tensor)."""
+
+    def __init__(self, nb, pitch):
+        import torch
+        L = load()
+        self.nbytes = L.nh_cnn_workspace_bytes(int(nb), int(pitch))
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+
+
+def nh_cnn_loss_grad(feat, nx_dev, params, target, mask, grad, ws=None):
+    """Loss (float) and gradient (written into ``grad``, CUDA float32 [NH_CNN_PARAMS])."""
+    import torch
+    L = load()
+    _params_check(params)
+    _params_check(grad)
+    nb, pitch, _ = feat.shape
+    ws = ws or CnnWorkspace(nb, pitch)
+    # counted cells: mask set and inside the member (cells at or beyond nx are ignored)
+    inside = torch.arange(pitch, device=mask.device)[None, :] < nx_dev.to(torch.int64)[:, None]
+    count = int(((mask != 0) & inside).count_nonzero().item())
+    loss = C.c_double(0.0)
+    _check(L.nh_cnn_loss_grad(C.c_void_p(feat.data_ptr()), C.c_void_p(nx_dev.data_ptr()), nb, pitch,
+                              C.c_void_p(params.data_ptr()), C.c_void_p(target.data_ptr()),
+                              C.c_void_p(mask.data_ptr()), count, C.c_void_p(grad.data_ptr()),
+                              C.byref(loss), C.c_void_p(ws.ptr), C.c_size_t(ws.nbytes), _stream_ptr()),
+           "nh_cnn_loss_grad")
+    return loss.value
+
+
+def nh_cnn_adam(params, grad, m, v, step, lr):
+    L = load()
+    for t in (params, grad, m, v):
+        _params_check(t)
+    _check(L.nh_cnn_adam(C.c_void_p(params.data_ptr()), C.c_void_p(grad.data_ptr()), C.c_void_p(m.data_ptr()),
+                         C.c_void_p(v.data_ptr()), int(step), float(lr), _stream_ptr()), "nh_cnn_adam")
 
 
 def grid_from_workload(wl, precision=NH_FP64, limiter=NH_LIM_CENTRAL, bc=None, **kw):
