@@ -60,6 +60,20 @@ BYTES_PER_UNIT_MIXED = {
     "pcg_loop": 84.0,     # per inner PCG iteration: 36 + 48
     "correct": 50.0,
 }
+# The FP64 predictor is bound by the FP64 pipe, not by HBM: its roofline is
+# FLOP/s against the FP64 peak.  FP64 FLOPs per cell and launch, from ncu's
+# executed-instruction counters (dadd + dmul + 2 dfma) on the 64 x 50000
+# batch ("profiles/k_predict_fp64_slide64x50k.md"); they include the two
+# stages' square roots and reciprocals and the tile halo.
+FLOPS_PER_CELL_FP64_PREDICT = 349.1
+# DRAM bytes per launch of that kernel from the same capture (null once the
+# kernel changes).
+TRAFFIC_FP64_PREDICT = 141697.0e3
+# FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x
+# 2 FLOP x 2.07 GHz (the nominal 1.25 TFLOP/s).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
 def _load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -168,6 +182,110 @@ def run_reference(args):
     }))
 
 
+def compare_forms(wl, G0, t_now, args):
+    """Wall time per step of the method's forms on the same batch, each started
+    from G0's state at t_now: global FP64 with the plain warm start (every cell
+    non-hydrostatic), adaptive FP64, and adaptive FP64 / mixed precision with
+    the learned start (network trained on pairs harvested from the first
+    steps, outside the timed region)."""
+    import torch
+    from paper_2505_17025_gb300 import guess_train as GT
+    from paper_2505_17025_gb300 import nhswe as N
+    h, hu, hw, _ = G0.get_state()
+    forms = [("global_fp64_plain", N.NH_FP64, N.NH_CRIT_GLOBAL, False),
+             ("adaptive_fp64", N.NH_FP64, N.NH_CRIT_ETA_D, False),
+             ("adaptive_fp64_learned", N.NH_FP64, N.NH_CRIT_ETA_D, True),
+             ("adaptive_mixed_learned", N.NH_MIXED, N.NH_CRIT_ETA_D, True)]
+    k_steps = max(1, args.form_steps)
+    cells = sum(m.nx for m in wl.members)
+    out = {}
+    for name, prec, crit, learned in forms:
+        G = N.grid_from_workload(wl, precision=prec)
+        G.set_state(h, hu, hw, t_now)
+        G.set_criterion(crit, 1e-3, 1, False)
+        rtol = 1e-12 if prec == N.NH_FP64 else 1e-10
+        G.set_solver(N.NH_SOLVER_AUTO, rtol, 20000, N.NH_GUESS_PREV)
+        t_train = 0.0
+        if learned:
+            G.cnn_attach()
+            t0 = time.perf_counter()
+            samples = GT.collect(G, wl.dt, args.form_harvest)
+            G.cnn_record(False)
+            if samples:
+                params, _ = GT.train(samples, steps=args.form_train)
+                G.cnn_set_params(params)
+            G.set_solver(N.NH_SOLVER_AUTO, rtol, 20000, N.NH_GUESS_CNN)
+            t_train = time.perf_counter() - t0
+        G.run(wl.dt, max(3, args.warmup))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(G.stream)
+        st, info = G.run(wl.dt, k_steps)
+        e1.record(G.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k_steps
+        rec = {"ms_per_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
+               "krylov_iters_per_step": info["iters_total"] / k_steps,
+               "active_cells_per_step": info["active_total"] / k_steps,
+               "error_bound_vs_oracle": "1e-9 a" if prec == N.NH_FP64 else "1e-4 a (while masks agree)"}
+        if learned:
+            rec["starts"] = G.cnn_choices()
+            rec["harvest_and_train_s"] = t_train
+        out[name] = rec
+        G.close()
+    base = out["global_fp64_plain"]["ms_per_step"]
+    return {"steps": k_steps, "t_start": t_now, "forms": out,
+            "speedup_vs_global_fp64_plain": {k: base / v["ms_per_step"] for k, v in out.items()}}
+
+
+def time_network(wl, args):
+    """The learned-guess network's fused forward (tcgen05, BF16 x BF16 -> FP32)
+    on the whole batch (every cell a network input), CUDA events over 20
+    launches after 3 warm-up launches; FLOPs = 2 x 9216 multiply-adds per
+    cell (the four layers' 3 c_in c_out), tile halos not counted."""
+    import torch
+    from paper_2505_17025_gb300 import guess_train as GT
+    from paper_2505_17025_gb300 import nhswe as N
+    nb = len(wl.members)
+    pitch = (max(m.nx for m in wl.members) + 511) // 512 * 512
+    g = torch.Generator(device="cuda").manual_seed(0)
+    feat = torch.randn((nb, pitch, N.NH_CNN_IN), generator=g, device="cuda").to(torch.bfloat16)
+    nxd = torch.tensor([m.nx for m in wl.members], dtype=torch.int32, device="cuda")
+    params = GT.init_params(0, last_gain=1.0)
+    y = torch.zeros((nb, pitch), dtype=torch.float32, device="cuda")
+    import ctypes as C
+    L = N.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args_c = (C.c_void_p(feat.data_ptr()), C.c_void_p(nxd.data_ptr()), nb, pitch, C.c_void_p(params.data_ptr()),
+              C.c_void_p(y.data_ptr()), 1.0, None, stream)
+
+    def fwd():
+        rc = L.nh_cnn_forward(*args_c)
+        if rc != 0:
+            raise RuntimeError(f"nh_cnn_forward: {rc}")
+
+    for _ in range(3):
+        fwd()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 20
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fwd()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    cells = sum(m.nx for m in wl.members)
+    flops = 2.0 * 9216 * cells
+    peaks, kind = _load_peaks()
+    tf = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "k_forward", "cells": cells, "ms_per_launch": ms, "tflops": tf,
+            "bf16_peak_tflops": peaks.get("bf16_tflops"), "frac": tf / peaks.get("bf16_tflops", 1900.0),
+            "launch": "C ABI nh_cnn_forward on preallocated buffers, back to back on one stream"}
+
+
 def run_ours(args):
     import torch
     from paper_2505_17025_gb300 import nhswe as N
@@ -178,7 +296,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    wl = W.slide_1d(n_members=64, seed0=64 * rank)
+    wl = W.slide_1d(n_members=args.members, seed0=args.members * rank)
     prec = N.NH_FP64 if args.precision == "fp64" else N.NH_MIXED
     G = N.grid_from_workload(wl, precision=prec)
     crit = N.NH_CRIT_GLOBAL if args.mode == "global" else N.NH_CRIT_ETA_D
@@ -204,10 +322,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     G.set_profiling(False)
     clocks.start()
+    # profiler range = the timed steps (an ncu run with --profile-from-start off
+    # records exactly these launches; no effect otherwise)
+    torch.cuda.profiler.start()
     e0.record(stream)
     st, info = G.run(wl.dt, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
     if ws > 1:
         torch.distributed.barrier()
@@ -242,11 +364,23 @@ def run_ours(args):
             # one launch runs every iteration of a solve
             iters2 = info2["iters_total"] / max(args.steps, 1)
             bytes_per_launch *= iters2 * args.steps / dn
-        achieved = bytes_per_launch / (dms * 1e-3 / dn) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": f"k_{name}",
-                "peak_kind": peak_kind, "bytes_per_launch": bytes_per_launch,
-                "launches_per_step": dn / args.steps, "avg_launch_us": 1e3 * dms / dn}
+        t_launch = dms * 1e-3 / dn
+        if name == "predict" and args.precision == "fp64":
+            flops = FLOPS_PER_CELL_FP64_PREDICT * cells
+            achieved = flops / t_launch / 1e12
+            peak = FP64_PEAK_GFLOPS / 1e3
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": TRAFFIC_FP64_PREDICT, "kernel": "k_predict",
+                    "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 pipe)",
+                    "flops_per_launch": flops, "bytes_per_launch": bytes_per_launch,
+                    "hbm_frac": bytes_per_launch / t_launch / 1e9 / peaks["hbm_gbs"],
+                    "launches_per_step": dn / args.steps, "avg_launch_us": 1e6 * t_launch}
+        else:
+            achieved = bytes_per_launch / t_launch / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": f"k_{name}",
+                    "peak_kind": peak_kind, "bytes_per_launch": bytes_per_launch,
+                    "launches_per_step": dn / args.steps, "avg_launch_us": 1e6 * t_launch}
 
     # end to end through the C ABI with pinned host buffers, per step:
     # H2D of the step's input state, the step, D2H of its result
@@ -267,6 +401,14 @@ def run_ours(args):
         e2e = {"value": ws * cells * args.e2e_steps / el, "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * n, "d2h_bytes_per_step": 3 * 8 * n,
                "steps": args.e2e_steps}
+
+    network = None
+    if ws == 1 and args.form_steps > 0:
+        network = time_network(wl, args)
+
+    forms = None
+    if ws == 1 and args.form_steps > 0:
+        forms = compare_forms(wl, G, info2["last"]["t"], args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -297,6 +439,8 @@ def run_ours(args):
             "clocks": clk,
             "kernel_ms": {k: v[0] for k, v in prof.items() if v[1] > 0},
             "kernel_launches": {k: v[1] for k, v in prof.items() if v[1] > 0},
+            "forms": forms,
+            "network": network,
         }
         print(json.dumps(out))
     G.close()
@@ -318,6 +462,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=400)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--form-steps", type=int, default=30, help="timed steps per form (0: skip the comparison)")
+    ap.add_argument("--form-harvest", type=int, default=20)
+    ap.add_argument("--form-train", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -36,6 +36,12 @@ constexpr int kCompactThreads = 1024;
 constexpr int kPcrThreads = 1024;     // preconditioner CTA
 constexpr int kPcrRows = 4096;        // active cells per preconditioner block (power of 2)
 
+// Beyond xi^2 = 40 the Gaussian mound is below exp(-40) A = 4.3e-18 A: under
+// half an ulp (>= 2^-54 d0) of the depth it is subtracted from whenever
+// A < 12 d0, so its value and derivative terms are taken as 0 there instead
+// of evaluating exp.
+constexpr double kMoundCut = 40.0;
+
 // Per-member slide parameters (device copy of nh_slide_desc, FP64).
 struct Slide {
     double A, L, xc0, s0, t0;
@@ -124,6 +130,7 @@ __device__ __forceinline__ float texp(float v) { return expf(v); }
 __device__ __forceinline__ double tsqrt(double v) { return sqrt(v); }
 __device__ __forceinline__ float tsqrt(float v) { return sqrtf(v); }
 
+
 // Height of the moving mound at the centre of cell c (already resolved) at
 // displacement s: m = A exp(-xi^2), xi = (x_c - xc0 - s) / L; the depth is
 // d = d0 - m.
@@ -133,6 +140,7 @@ __device__ __forceinline__ T mound_at(int c, double x0, double dx, const Slide& 
     if (sl.shape != NH_SLIDE_GAUSS_LNCOSH) return T(0);
     const double xc = x0 + (c + 0.5) * dx;
     const T xi = T((xc - sl.xc0 - s) * (1.0 / sl.L));
+    if (xi * xi > T(kMoundCut)) return T(0);
     return T(sl.A) * texp(-xi * xi);
 }
 
@@ -167,7 +175,7 @@ __device__ __forceinline__ Bottom<T> bottom_full(const T* __restrict__ d0m, int 
         const T L = T(sl.L);
         double xc = x0 + (i + 0.5) * dx;
         T xi = T((xc - sl.xc0 - k.s_n1) / sl.L);
-        T m = T(sl.A) * texp(-xi * xi);
+        T m = xi * xi > T(kMoundCut) ? T(0) : T(sl.A) * texp(-xi * xi);
         T sd = T(k.sd_n1), sdd = T(k.sdd_n1);
         T two_xi2m1 = T(2) * xi * xi - T(1);
         T m_x = m * (T(-2) * xi / L);
