@@ -74,6 +74,7 @@ struct nh_grid {
     int *nbl, *nbr;
     void *x, *r, *p0, *p1, *q, *rh, *v0, *v1, *s, *t, *r1, *z;   // Krylov vectors (type T)
     double* x64;                               // mixed: FP64 outer iterate
+    float2* pf; float* prb;                    // line preconditioner factors of the current solve
     IRState* ir;
     double* psi;
     MState* ms; Ctl* ctl; double* part; int* cnt;
@@ -174,6 +175,8 @@ size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
     G->s = c.take(N * es); G->t = c.take(N * es);
     G->r1 = c.take(N * es); G->z = c.take(N * es);
     G->psi = (double*)c.take(sizeof(double) * N);
+    G->pf = (float2*)c.take(sizeof(float2) * kPcrLevels * N);
+    G->prb = (float*)c.take(sizeof(float) * N);
     G->ms = (MState*)c.take(sizeof(MState) * nb);
     G->ctl = (Ctl*)c.take(sizeof(Ctl));
     G->part = (double*)c.take(sizeof(double) * 3 * (size_t)nb * maxch);
@@ -301,6 +304,7 @@ SolveArgs<T> solve_args(nh_grid* g, int lcur, const T* diag, const T* offl, cons
     a.q = (T*)g->q; a.rh = (T*)g->rh; a.v0 = (T*)g->v0; a.v1 = (T*)g->v1;
     a.s = (T*)g->s; a.t = (T*)g->t;
     a.r1 = (T*)g->r1; a.z = (T*)g->z; a.maxpb = g->maxpb;
+    a.pf = g->pf; a.prb = g->prb; a.pf_stride = (size_t)g->nb * g->pitch;
     a.items = g->items; a.pitems = g->pitems;
     a.tc = nullptr;
     a.ms = g->ms; a.ctl = g->ctl; a.part = g->part; a.cnt = g->cnt;
@@ -375,6 +379,8 @@ nh_status krylov_pass(nh_grid* g, SolveArgs<T>& sa)
     SYNC();
     const bool pcg = g->precond == NH_PRECOND_LINE;
     const size_t pcr_smem = 4 * sizeof(float) * (size_t)kPcrRows;
+    if (pcg && (hctl.n_cg > 0 || hctl.n_bicg > 0))
+        LAUNCH(NH_K_PRECOND, k_pcr_factor<T, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa));
     if (hctl.n_cg > 0 && pcg) {
         sa.it = 0;
         LAUNCH(NH_K_PRECOND, k_pcr<T, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG));
@@ -636,6 +642,7 @@ nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, do
     k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa);
     const size_t pcr_smem = 4 * sizeof(float) * (size_t)kPcrRows;
     sa.it = 0;
+    k_pcr_factor<double, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa);
     k_pcr<double, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG);
     CK(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
     {

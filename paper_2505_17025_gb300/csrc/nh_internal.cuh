@@ -35,6 +35,8 @@ constexpr int kChunk = 256;      // active cells per solver work item (= blockDi
 constexpr int kCompactThreads = 1024;
 constexpr int kPcrThreads = 1024;     // preconditioner CTA
 constexpr int kPcrRows = 4096;        // active cells per preconditioner block (power of 2)
+constexpr int kPcrLevels = 12;        // cyclic-reduction levels of a full block
+static_assert((1 << kPcrLevels) == kPcrRows, "kPcrLevels = log2(kPcrRows)");
 
 // Beyond xi^2 = 40 the Gaussian mound is below exp(-40) A = 4.3e-18 A: under
 // half an ulp (>= 2^-54 d0) of the depth it is subtracted from whenever
@@ -154,6 +156,7 @@ __device__ __forceinline__ T depth_at(const T* __restrict__ d0m, int c, double x
 template <typename T>
 struct Bottom {
     T d, d_x, d_xx, d_t, d_xt, d_tt;
+    T m;          // the mound's height (0 without a slide)
 };
 
 // Depth and its x/t derivatives at cell i (in the domain) at t^{n+1}: central
@@ -170,11 +173,11 @@ __device__ __forceinline__ Bottom<T> bottom_full(const T* __restrict__ d0m, int 
     B.d = c;
     B.d_x = (e - a) / (T(2) * dxT);
     B.d_xx = (e - T(2) * c + a) / (dxT * dxT);
-    B.d_t = T(0); B.d_xt = T(0); B.d_tt = T(0);
+    B.d_t = T(0); B.d_xt = T(0); B.d_tt = T(0); B.m = T(0);
     if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
         const T L = T(sl.L);
         double xc = x0 + (i + 0.5) * dx;
-        T xi = T((xc - sl.xc0 - k.s_n1) / sl.L);
+        T xi = T((xc - sl.xc0 - k.s_n1) * (1.0 / sl.L));   // as in mound_at: B.m == mound_at
         T m = xi * xi > T(kMoundCut) ? T(0) : T(sl.A) * texp(-xi * xi);
         T sd = T(k.sd_n1), sdd = T(k.sdd_n1);
         T two_xi2m1 = T(2) * xi * xi - T(1);
@@ -183,7 +186,7 @@ __device__ __forceinline__ Bottom<T> bottom_full(const T* __restrict__ d0m, int 
         T m_t = m * (T(2) * xi / L) * sd;
         T m_xt = -m * (T(2) / (L * L)) * two_xi2m1 * sd;
         T m_tt = m * (T(2) / (L * L)) * (two_xi2m1 * sd * sd + xi * L * sdd);
-        B.d -= m; B.d_x -= m_x; B.d_xx -= m_xx;
+        B.d -= m; B.d_x -= m_x; B.d_xx -= m_xx; B.m = m;
         B.d_t = -m_t; B.d_xt = -m_xt; B.d_tt = -m_tt;
     }
     return B;

@@ -520,18 +520,14 @@ struct CellQ {
 };
 
 // Per-cell quantities of the elliptic equation at an in-domain cell c, in FP64
-// whatever the state precision.
+// whatever the state precision, from the cell's bottom terms B and the surface
+// at its two neighbours.
 template <typename TS>
-__device__ __forceinline__ CellQ cell_q(const AsmArgs<TS>& a, const TS* __restrict__ zt,
-                                        const TS* __restrict__ hut, const double* __restrict__ D0,
-                                        int c, int nxb, const Slide& sl, const Kin& kn)
+__device__ __forceinline__ CellQ cell_q_from(const AsmArgs<TS>& a, const TS* __restrict__ zt,
+                                             const TS* __restrict__ hut, const double* __restrict__ D0,
+                                             int c, const Bottom<double>& B, double etam, double etap)
 {
     const Geo& G = a.G;
-    const Bottom<double> B = bottom_full(D0, c, nxb, G.bc, G.x0, G.dx, sl, kn);
-    int sg;
-    const int cm = resolve(c - 1, nxb, G.bc, &sg), cp = resolve(c + 1, nxb, G.bc, &sg);
-    const double etam = (double)zt[cm] + mound_at<double>(cm, G.x0, G.dx, sl, kn.s_n1);
-    const double etap = (double)zt[cp] + mound_at<double>(cp, G.x0, G.dx, sl, kn.s_n1);
     const double eta_x = (etap - etam) / (2.0 * G.dx);
     CellQ q;
     q.h = (double)zt[c] + D0[c];
@@ -547,6 +543,21 @@ __device__ __forceinline__ CellQ cell_q(const AsmArgs<TS>& a, const TS* __restri
     return q;
 }
 
+// The same with the bottom and the neighbours' surface evaluated here.
+template <typename TS>
+__device__ __forceinline__ CellQ cell_q(const AsmArgs<TS>& a, const TS* __restrict__ zt,
+                                        const TS* __restrict__ hut, const double* __restrict__ D0,
+                                        int c, int nxb, const Slide& sl, const Kin& kn)
+{
+    const Geo& G = a.G;
+    const Bottom<double> B = bottom_full(D0, c, nxb, G.bc, G.x0, G.dx, sl, kn);
+    int sg;
+    const int cm = resolve(c - 1, nxb, G.bc, &sg), cp = resolve(c + 1, nxb, G.bc, &sg);
+    const double etam = (double)zt[cm] + mound_at<double>(cm, G.x0, G.dx, sl, kn.s_n1);
+    const double etap = (double)zt[cp] + mound_at<double>(cp, G.x0, G.dx, sl, kn.s_n1);
+    return cell_q_from(a, zt, hut, D0, c, B, etam, etap);
+}
+
 __device__ __forceinline__ bool bit_at(const uint32_t* w, int i)
 {
     return (w[i >> 5] >> (i & 31)) & 1u;
@@ -556,6 +567,9 @@ template <typename TS>
 __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
 {
     __shared__ double red[64];
+    __shared__ double s_eta[kChunk], s_K[kChunk], s_beta[kChunk], s_V[kChunk];
+    __shared__ int s_cell[kChunk];
+    __shared__ CellQ s_q[kChunk];
     const Geo& G = a.G;
     const int tid = threadIdx.x;
     const int n_items = a.ctl->n_items;
@@ -572,15 +586,43 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
         const Slide sl = a.slide[b];
         const Kin kn = a.kin[b];
         const int k = j * kChunk + tid;
+        const bool in = k < n;
+        const int nxb = member_nx(G, b);
+        // phase 1: own cell's bottom terms and surface (shared with the neighbours)
+        int i = -1;
+        Bottom<double> B;
+        if (in) {
+            i = a.list[mo + k];
+            B = bottom_full(D0, i, nxb, G.bc, G.x0, G.dx, sl, kn);
+            s_eta[tid] = (double)zt[i] + B.m;
+        }
+        s_cell[tid] = i;
+        __syncthreads();
+        // phase 2: own cell's coefficients; a neighbour that is the adjacent
+        // entry of this chunk's list shares its surface, others are evaluated
+        const bool left_here = in && tid > 0 && s_cell[tid - 1] == i - 1;
+        const bool right_here = in && tid + 1 < kChunk && k + 1 < n && s_cell[tid + 1] == i + 1;
+        int sgm = 1, sgp = 1, cm = -1, cp = -1;
+        if (in) {
+            cm = resolve(i - 1, nxb, G.bc, &sgm);
+            cp = resolve(i + 1, nxb, G.bc, &sgp);
+            const double etam = left_here ? s_eta[tid - 1]
+                                          : (double)zt[cm] + mound_at<double>(cm, G.x0, G.dx, sl, kn.s_n1);
+            const double etap = right_here ? s_eta[tid + 1]
+                                           : (double)zt[cp] + mound_at<double>(cp, G.x0, G.dx, sl, kn.s_n1);
+            const CellQ q = cell_q_from(a, zt, hut, D0, i, B, etam, etap);
+            s_K[tid] = q.K; s_beta[tid] = q.beta; s_V[tid] = q.V;
+            s_q[tid] = q;
+        }
+        __syncthreads();
         double r2 = 0.0, gmin = INFINITY;
-        if (k < n) {
-            const int i = a.list[mo + k];
-            const int nxb = member_nx(G, b);
-            int sgm, sgp;
-            const int cm = resolve(i - 1, nxb, G.bc, &sgm), cp = resolve(i + 1, nxb, G.bc, &sgp);
-            const CellQ qi = cell_q(a, zt, hut, D0, i, nxb, sl, kn);
-            const CellQ qm = cell_q(a, zt, hut, D0, cm, nxb, sl, kn);
-            const CellQ qp = cell_q(a, zt, hut, D0, cp, nxb, sl, kn);
+        if (in) {
+            const CellQ qi = s_q[tid];
+            CellQ qm, qp;
+            if (left_here) { qm.K = s_K[tid - 1]; qm.beta = s_beta[tid - 1]; qm.V = s_V[tid - 1]; }
+            else qm = cell_q(a, zt, hut, D0, cm, nxb, sl, kn);
+            if (right_here) { qp.K = s_K[tid + 1]; qp.beta = s_beta[tid + 1]; qp.V = s_V[tid + 1]; }
+            else qp = cell_q(a, zt, hut, D0, cp, nxb, sl, kn);
             const double idx2 = 1.0 / (G.dx * G.dx);
             const double Kl = 0.5 * (qm.K + qi.K), Kr = 0.5 * (qi.K + qp.K);
             const double bm = sgm > 0 ? qm.beta : -qm.beta, bp = sgp > 0 ? qp.beta : -qp.beta;
@@ -661,6 +703,9 @@ struct SolveArgs {
     double guess_scale;        // dt_new / dt_old, or 0 for a zero guess
     T* x; T* r; T* p0; T* p1; T* q; T* rh; T* v0; T* v1; T* s; T* t;
     T* r1; T* z;               // PCG: second residual buffer, preconditioned residual
+    float2* pf;                // line preconditioner: PCR multipliers [kPcrLevels][nb * pitch]
+    float* prb;                // line preconditioner: reciprocal final pivots [nb * pitch]
+    size_t pf_stride;          // nb * pitch
     int maxpb;                 // preconditioner blocks per member (upper bound)
     const int2* items; const int2* pitems;
     const TimeCtl* tc;         // captured runs: guess scale from tc->prev_ok
@@ -1096,6 +1141,102 @@ __device__ __forceinline__ T pcr_rhs(const SolveArgs<T>& a, int mode, int it, si
     return sk;
 }
 
+// Parallel cyclic reduction of one block's tridiagonal rows, factor phase:
+// at level l (stride s = 2^l) row i is combined with rows i - s and i + s
+// using al = -a_i / b_{i-s} and ga = -c_i / b_{i+s} (zero where the row does
+// not exist); the multipliers and, at the end, 1 / b_i are stored, since the
+// matrix is the same for every preconditioner application of one solve.
+// Runs once per solve for every member that still iterates.
+template <typename T, typename TP>
+__global__ void __launch_bounds__(kPcrThreads) k_pcr_factor(SolveArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TP* sa = reinterpret_cast<TP*>(smem_raw);
+    TP* sb = sa + kPcrRows;
+    TP* sc = sb + kPcrRows;
+    constexpr int RPT = kPcrRows / kPcrThreads;
+    const int n_pitems = a.ctl->n_pitems;
+    for (int wi = blockIdx.x; wi < n_pitems; wi += gridDim.x) {
+        const int2 itm = a.pitems[wi];
+        const int b = itm.x, jb = itm.y;
+        if (a.ms[b].done) continue;
+        const int n = a.ms[b].n_active;
+        const size_t mo = (size_t)b * a.pitch;
+        const int k0 = jb * kPcrRows;
+        const int rows = min(kPcrRows, n - k0);
+        for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
+            const int k = k0 + i;
+            const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+            sa[i] = (i > 0 && kl == k - 1) ? TP(a.offl[mo + k]) : TP(0);
+            sc[i] = (i < rows - 1 && kr == k + 1) ? TP(a.offr[mo + k]) : TP(0);
+            sb[i] = TP(a.diag[mo + k]);
+        }
+        __syncthreads();
+        int lev = 0;
+        for (int st = 1; st < rows; st <<= 1, ++lev) {
+            TP na[RPT], nb2[RPT], nc[RPT];
+            float2* f = a.pf + (size_t)lev * a.pf_stride + mo + k0;
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                const int i = threadIdx.x + m * kPcrThreads;
+                if (i < rows) {
+                    const TP ai = sa[i], ci = sc[i];
+                    TP a2 = TP(0), c2 = TP(0), b2 = sb[i], al = TP(0), ga = TP(0);
+                    if (i - st >= 0) {
+                        al = -ai / sb[i - st];
+                        a2 = al * sa[i - st]; b2 += al * sc[i - st];
+                    }
+                    if (i + st < rows) {
+                        ga = -ci / sb[i + st];
+                        c2 = ga * sc[i + st]; b2 += ga * sa[i + st];
+                    }
+                    na[m] = a2; nb2[m] = b2; nc[m] = c2;
+                    f[i] = make_float2((float)al, (float)ga);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                const int i = threadIdx.x + m * kPcrThreads;
+                if (i < rows) { sa[i] = na[m]; sb[i] = nb2[m]; sc[i] = nc[m]; }
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < rows; i += kPcrThreads) a.prb[mo + k0 + i] = (float)(TP(1) / sb[i]);
+        __syncthreads();
+    }
+}
+
+// Apply phase of the factored reduction to the right-hand side held in s0
+// (rows of one block): d_i <- d_i + al d_{i-s} + ga d_{i+s} level by level,
+// ping-ponging between s0 and s1 (one barrier per level).  Returns the buffer
+// holding the reduced right-hand side; z_i = d_i / b_i = d_i prb_i.
+template <typename T, typename TP>
+__device__ __forceinline__ TP* pcr_apply(const SolveArgs<T>& a, TP* s0, TP* s1, int rows, size_t base)
+{
+    constexpr int RPT = kPcrRows / kPcrThreads;
+    TP* src = s0;
+    TP* dst = s1;
+    int lev = 0;
+    for (int st = 1; st < rows; st <<= 1, ++lev) {
+        const float2* f = a.pf + (size_t)lev * a.pf_stride + base;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            const int i = threadIdx.x + m * kPcrThreads;
+            if (i < rows) {
+                const float2 fi = __ldcg(f + i);
+                TP d = src[i];
+                if (i - st >= 0) d += TP(fi.x) * src[i - st];
+                if (i + st < rows) d += TP(fi.y) * src[i + st];
+                dst[i] = d;
+            }
+        }
+        __syncthreads();
+        TP* t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
 // Line preconditioner z = M^{-1} rhs.  M is the tridiagonal operator
 // restricted to blocks of kPcrRows consecutive active cells (couplings across a
 // block edge are dropped; a contiguous active segment inside one block is
@@ -1139,47 +1280,17 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcr(SolveArgs<T> a, int mode)
         double ss = 0.0;
         for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
             const int k = k0 + i;
-            const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
-            sa[i] = (i > 0 && kl == k - 1) ? TP(a.offl[mo + k]) : TP(0);
-            sc[i] = (i < rows - 1 && kr == k + 1) ? TP(a.offr[mo + k]) : TP(0);
-            sb[i] = TP(a.diag[mo + k]);
             const T rhs = pcr_rhs(a, mode, it, mo + k, beta, omega, alpha);
             if (mode == PCR_BI_S || mode == PCR_PCG_STEP) ss += (double)rhs * (double)rhs;
             sd[i] = TP(rhs);
         }
         __syncthreads();
-        for (int s = 1; s < rows; s <<= 1) {
-            TP na[RPT], nb2[RPT], nc[RPT], nd[RPT];
-#pragma unroll
-            for (int m = 0; m < RPT; ++m) {
-                const int i = threadIdx.x + m * kPcrThreads;
-                if (i < rows) {
-                    const TP ai = sa[i], ci = sc[i];
-                    TP a2 = TP(0), c2 = TP(0), b2 = sb[i], d2 = sd[i];
-                    if (i - s >= 0) {
-                        const TP al = -ai / sb[i - s];
-                        a2 = al * sa[i - s]; b2 += al * sc[i - s]; d2 += al * sd[i - s];
-                    }
-                    if (i + s < rows) {
-                        const TP ga = -ci / sb[i + s];
-                        c2 = ga * sc[i + s]; b2 += ga * sa[i + s]; d2 += ga * sd[i + s];
-                    }
-                    na[m] = a2; nb2[m] = b2; nc[m] = c2; nd[m] = d2;
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int m = 0; m < RPT; ++m) {
-                const int i = threadIdx.x + m * kPcrThreads;
-                if (i < rows) { sa[i] = na[m]; sb[i] = nb2[m]; sc[i] = nc[m]; sd[i] = nd[m]; }
-            }
-            __syncthreads();
-        }
+        const TP* red_d = pcr_apply<T, TP>(a, sd, sa, rows, mo + k0);
         double acc[3] = {0.0, 0.0, ss};
         T* out = (mode == PCR_BI_P) ? a.p1 : a.z;
         for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
             const int k = k0 + i;
-            const T zk = T(sd[i] / sb[i]);
+            const T zk = T(red_d[i] * TP(a.prb[mo + k]));
             out[mo + k] = zk;
             if (mode == PCR_PCG || mode == PCR_PCG_STEP) {
                 acc[0] += (double)zk * (double)rnew[mo + k];
@@ -1383,10 +1494,6 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, 
             double ss = 0.0;
             for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
                 const int k = k0 + i;
-                const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
-                sa[i] = (i > 0 && kl == k - 1) ? TP(a.offl[mo + k]) : TP(0);
-                sc[i] = (i < rows - 1 && kr == k + 1) ? TP(a.offr[mo + k]) : TP(0);
-                sb[i] = TP(a.diag[mo + k]);
                 a.x[mo + k] = a.x[mo + k] + alpha * pnew[mo + k];
                 const T rk = rold[mo + k] - alpha * a.q[mo + k];
                 rnew[mo + k] = rk;
@@ -1394,37 +1501,11 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, 
                 sd[i] = TP(rk);
             }
             __syncthreads();
-            for (int s = 1; s < rows; s <<= 1) {
-                TP na[RPT], nb2[RPT], nc[RPT], nd[RPT];
-#pragma unroll
-                for (int m = 0; m < RPT; ++m) {
-                    const int i = threadIdx.x + m * kPcrThreads;
-                    if (i < rows) {
-                        const TP ai = sa[i], ci = sc[i];
-                        TP a2 = TP(0), c2 = TP(0), b2 = sb[i], d2 = sd[i];
-                        if (i - s >= 0) {
-                            const TP al = -ai / sb[i - s];
-                            a2 = al * sa[i - s]; b2 += al * sc[i - s]; d2 += al * sd[i - s];
-                        }
-                        if (i + s < rows) {
-                            const TP ga = -ci / sb[i + s];
-                            c2 = ga * sc[i + s]; b2 += ga * sa[i + s]; d2 += ga * sd[i + s];
-                        }
-                        na[m] = a2; nb2[m] = b2; nc[m] = c2; nd[m] = d2;
-                    }
-                }
-                __syncthreads();
-#pragma unroll
-                for (int m = 0; m < RPT; ++m) {
-                    const int i = threadIdx.x + m * kPcrThreads;
-                    if (i < rows) { sa[i] = na[m]; sb[i] = nb2[m]; sc[i] = nc[m]; sd[i] = nd[m]; }
-                }
-                __syncthreads();
-            }
+            const TP* red_d = pcr_apply<T, TP>(a, sd, sa, rows, mo + k0);
             double acc[3] = {0.0, 0.0, ss};
             for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
                 const int k = k0 + i;
-                const T zk = T(sd[i] / sb[i]);
+                const T zk = T(red_d[i] * TP(a.prb[mo + k]));
                 a.z[mo + k] = zk;
                 acc[0] += (double)zk * (double)rnew[mo + k];
                 acc[1] += (double)zk * (double)rold[mo + k];
