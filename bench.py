@@ -65,10 +65,10 @@ BYTES_PER_UNIT_MIXED = {
 # executed-instruction counters (dadd + dmul + 2 dfma) on the 64 x 50000
 # batch ("profiles/k_predict_fp64_slide64x50k.md"); they include the two
 # stages' square roots and reciprocals and the tile halo.
-FLOPS_PER_CELL_FP64_PREDICT = 349.1
+FLOPS_PER_CELL_FP64_PREDICT = 313.7
 # DRAM bytes per launch of that kernel from the same capture (null once the
 # kernel changes).
-TRAFFIC_FP64_PREDICT = 141697.0e3
+TRAFFIC_FP64_PREDICT = 142112.5e3
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x
 # 2 FLOP x 2.07 GHz (the nominal 1.25 TFLOP/s).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07

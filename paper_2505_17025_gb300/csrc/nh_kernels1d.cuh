@@ -135,7 +135,7 @@ struct PredArgs {
 // central differences need no second pass.  Q~ = Q^n + dt/2 (k1 + k2).
 // Shared memory of one predictor tile (19 arrays of TILE + 2 halo cells).
 template <typename T, int TILE>
-constexpr size_t predict_smem_bytes() { return sizeof(T) * 19 * (TILE + 2 * kPredHalo); }
+constexpr size_t predict_smem_bytes() { return sizeof(T) * 20 * (TILE + 2 * kPredHalo); }
 
 template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
     T* const k1h = sm + 16 * NL;    // stage-1 rates
     T* const k1u = sm + 17 * NL;
     T* const k1w = sm + 18 * NL;
+    T* const sdf = sm + 19 * NL;    // depth at face l of the current stage
     __shared__ double red[32];
 
     const Geo& G = a.G;
@@ -184,6 +185,22 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
 
     // A: load Q^n, d0 and the mound at both times.  Cells outside
     // [-6, nx+5] feed only outputs outside [-1, nx]; they get still water.
+    // Cells whose mound term is nonzero at t^n or t^{n+1} lie in [s_mlo,
+    // s_mhi] (the cut-off of mound_at with a margin, one cell either side);
+    // elsewhere the per-cell evaluation is skipped (it would return 0).
+    __shared__ int s_mlo, s_mhi;
+    if (tid == 0) {
+        int lo = 1, hi = 0;
+        if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
+            const double r = sqrt(kMoundCut * 1.0001) * sl.L;
+            const double ca = (sl.xc0 + fmin(kn.s_n, kn.s_n1) - r - G.x0) / G.dx - 0.5;
+            const double cb = (sl.xc0 + fmax(kn.s_n, kn.s_n1) + r - G.x0) / G.dx - 0.5;
+            lo = (int)fmax(floor(ca) - 1.0, -1073741824.0);
+            hi = (int)fmin(ceil(cb) + 1.0, 1073741824.0);
+        }
+        s_mlo = lo; s_mhi = hi;
+    }
+    __syncthreads();
     for (int l = tid; l < NL; l += TILE) {
         const int j = i0 - H + l;
         T zv = T(0), huv = T(0), hwv = T(0), d0v = T(1), mn = T(0), mn1 = T(0);
@@ -194,8 +211,10 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
             huv = sg > 0 ? HUn[c] : -HUn[c];
             hwv = HWn[c];
             d0v = D0[c];
-            mn = mound_at<T>(c, G.x0, G.dx, sl, kn.s_n);
-            mn1 = mound_at<T>(c, G.x0, G.dx, sl, kn.s_n1);
+            if (c >= s_mlo && c <= s_mhi) {
+                mn = mound_at<T>(c, G.x0, G.dx, sl, kn.s_n);
+                mn1 = mound_at<T>(c, G.x0, G.dx, sl, kn.s_n1);
+            }
         }
         const T rh = T(1) / (zv + d0v);
         sz[l] = zv; shu[l] = huv; shw[l] = hwv; sd0[l] = d0v; smn[l] = mn; smn1[l] = mn1;
@@ -214,6 +233,7 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
     // C: stage-1 face fluxes on faces [2, NL-1); depth continuous at faces
     for (int f = tid + 2; f < NL - 1; f += TILE) {
         const T df = T(0.5) * ((sd0[f - 1] - smn[f - 1]) + (sd0[f] - smn[f]));
+        sdf[f] = df;
         rusanov(g, df, se[f - 1] + T(0.5) * sle[f - 1], su[f - 1] + T(0.5) * slu[f - 1],
                 sw[f - 1] + T(0.5) * slw[f - 1], se[f] - T(0.5) * sle[f], su[f] - T(0.5) * slu[f],
                 sw[f] - T(0.5) * slw[f], F0[f], A1[f], G1[f], F2[f]);
@@ -223,9 +243,8 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
     // D: stage-1 rates and Q* on cells [2, NL-2); Q* stored as primitives
     //    against the bottom at t^{n+1}
     for (int l = tid + 2; l < NL - 2; l += TILE) {
-        const T dm = sd0[l - 1] - smn[l - 1], dc = sd0[l] - smn[l], dp = sd0[l + 1] - smn[l + 1];
-        const T dfl = T(0.5) * (dm + dc), dfr = T(0.5) * (dc + dp);
-        const T hbar = T(0.5) * ((se[l] - T(0.5) * sle[l] + dfl) + (se[l] + T(0.5) * sle[l] + dfr));
+        // mean of the cell's two face thicknesses (eta -+ slope/2 + face depth)
+        const T hbar = se[l] + T(0.5) * (sdf[l] + sdf[l + 1]);
         const T r0 = -(F0[l + 1] - F0[l]) * idx;
         const T r1 = -((A1[l + 1] - A1[l]) + (G1[l + 1] + G1[l]) + g * hbar * sle[l]) * idx;
         const T r2 = -(F2[l + 1] - F2[l]) * idx;
@@ -247,6 +266,7 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
     // F: stage-2 fluxes on faces [4, NL-3)
     for (int f = tid + 4; f < NL - 3; f += TILE) {
         const T df = T(0.5) * ((sd0[f - 1] - smn1[f - 1]) + (sd0[f] - smn1[f]));
+        sdf[f] = df;
         rusanov(g, df, se[f - 1] + T(0.5) * sle[f - 1], su[f - 1] + T(0.5) * slu[f - 1],
                 sw[f - 1] + T(0.5) * slw[f - 1], se[f] - T(0.5) * sle[f], su[f] - T(0.5) * slu[f],
                 sw[f] - T(0.5) * slw[f], F0[f], A1[f], G1[f], F2[f]);
@@ -255,9 +275,7 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
 
     // G: stage-2 rates and Q~ on [4, NL-4) (the tile and one cell each side)
     for (int l = tid + 4; l < NL - 4; l += TILE) {
-        const T dm = sd0[l - 1] - smn1[l - 1], dc = sd0[l] - smn1[l], dp = sd0[l + 1] - smn1[l + 1];
-        const T dfl = T(0.5) * (dm + dc), dfr = T(0.5) * (dc + dp);
-        const T hbar = T(0.5) * ((se[l] - T(0.5) * sle[l] + dfl) + (se[l] + T(0.5) * sle[l] + dfr));
+        const T hbar = se[l] + T(0.5) * (sdf[l] + sdf[l + 1]);
         const T r0 = -(F0[l + 1] - F0[l]) * idx;
         const T r1 = -((A1[l + 1] - A1[l]) + (G1[l + 1] + G1[l]) + g * hbar * sle[l]) * idx;
         const T r2 = -(F2[l + 1] - F2[l]) * idx;
@@ -1217,21 +1235,33 @@ __device__ __forceinline__ TP* pcr_apply(const SolveArgs<T>& a, TP* s0, TP* s1, 
     constexpr int RPT = kPcrRows / kPcrThreads;
     TP* src = s0;
     TP* dst = s1;
+    // the next level's multipliers are fetched before this level's barrier,
+    // so their L2 latency overlaps the wait
+    float2 fi[RPT];
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+        const int i = threadIdx.x + m * kPcrThreads;
+        fi[m] = (i < rows && rows > 1) ? __ldcg(a.pf + base + i) : make_float2(0.f, 0.f);
+    }
     int lev = 0;
     for (int st = 1; st < rows; st <<= 1, ++lev) {
-        const float2* f = a.pf + (size_t)lev * a.pf_stride + base;
+        float2 fn[RPT];
+        const bool more = (st << 1) < rows;
+        const float2* f1 = a.pf + (size_t)(lev + 1) * a.pf_stride + base;
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
             const int i = threadIdx.x + m * kPcrThreads;
+            fn[m] = (more && i < rows) ? __ldcg(f1 + i) : make_float2(0.f, 0.f);
             if (i < rows) {
-                const float2 fi = __ldcg(f + i);
                 TP d = src[i];
-                if (i - st >= 0) d += TP(fi.x) * src[i - st];
-                if (i + st < rows) d += TP(fi.y) * src[i + st];
+                if (i - st >= 0) d += TP(fi[m].x) * src[i - st];
+                if (i + st < rows) d += TP(fi[m].y) * src[i + st];
                 dst[i] = d;
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) fi[m] = fn[m];
         TP* t = src; src = dst; dst = t;
     }
     return src;

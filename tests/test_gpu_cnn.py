@@ -129,7 +129,9 @@ def test_gradient_matches_oracle():
     ms = [inside[b, :n] for b, n in enumerate(nxs)]
     ref_loss, ref_g = OC.loss_and_grad(xs, bf16_weights(params), ts, ms)
     assert abs(loss_in - ref_loss) <= 2e-2 * ref_loss
-    assert torch.allclose(g_out, grad, rtol=1e-5, atol=1e-9)   # atomics: order may differ
+    # FP32 atomics accumulate in a run-dependent order: entries agree to the
+    # rounding of the largest contributions
+    assert torch.allclose(g_out, grad, rtol=1e-4, atol=1e-5 * float(grad.abs().max()))
     for o, n, w in _BLOCKS:
         d = np.linalg.norm(g[o:o + n] - ref_g[o:o + n])
         assert d <= 5e-2 * np.linalg.norm(ref_g[o:o + n]) + 1e-7, (o, n, d, np.linalg.norm(ref_g[o:o + n]))
