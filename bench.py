@@ -135,6 +135,23 @@ def _dist():
     return ws, rank, local
 
 
+def rank_seed0(members, rank):
+    """Seed offset of a rank's batch: rank r draws members r*M .. r*M + M - 1,
+    so every rank runs its own independent members (weak scaling)."""
+    return members * rank
+
+
+def max_over_ranks(x, ws, device):
+    """The slowest rank's time (all ranks get it); x itself when ws == 1."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _oracle_sample(wl, max_steps, budget_s, crit):
     """Oracle (FP64 C, one host thread) on member 0 from t = 0: cell-updates/s."""
     import oracle as O
@@ -296,7 +313,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    wl = W.slide_1d(n_members=args.members, seed0=args.members * rank)
+    wl = W.slide_1d(n_members=args.members, seed0=rank_seed0(args.members, rank))
     prec = N.NH_FP64 if args.precision == "fp64" else N.NH_MIXED
     G = N.grid_from_workload(wl, precision=prec)
     crit = N.NH_CRIT_GLOBAL if args.mode == "global" else N.NH_CRIT_ETA_D
@@ -341,10 +358,7 @@ def run_ours(args):
     prof = G.get_profile()
     G.set_profiling(False)
     launches_profiled = sum(n for _, n in prof.values())
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, "cuda")
     value = ws * cells * args.steps / (ms * 1e-3)
     # kernels per step of the timed (graph-replayed) region: the profiled pass
     # runs the same kernel sequence, so its launch count per step applies
