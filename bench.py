@@ -74,6 +74,20 @@ TRAFFIC_FP64_PREDICT = 142112.5e3
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 
+# FP32 state with an FP64 solve: FP32 predictor and correction state, FP64
+# operator and Krylov vectors.
+BYTES_PER_UNIT_MIXED64 = {
+    "predict": 28.125,
+    "compact": 4.25,
+    "assemble": 80.0,     # read 3 FP32 fields, FP64 d0, list (24); write FP64 op + rhs (32), 4 FP32 coeffs (16), nbrs (8)
+    "solve_init": 84.0,
+    "precond": 88.0,
+    "pcg_a": 64.0,
+    "pcg_loop": 152.0,
+    "correct": 60.0,      # read list, nbrs, x (FP64), 4 FP32 coeffs, hu, hw; write hu, hw, psi
+}
+
+
 def _load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -212,7 +226,9 @@ def compare_forms(wl, G0, t_now, args):
     forms = [("global_fp64_plain", N.NH_FP64, N.NH_CRIT_GLOBAL, False),
              ("adaptive_fp64", N.NH_FP64, N.NH_CRIT_ETA_D, False),
              ("adaptive_fp64_learned", N.NH_FP64, N.NH_CRIT_ETA_D, True),
-             ("adaptive_mixed_learned", N.NH_MIXED, N.NH_CRIT_ETA_D, True)]
+             ("adaptive_mixed_learned", N.NH_MIXED, N.NH_CRIT_ETA_D, True),
+             ("adaptive_fp32state_fp64solve", N.NH_MIXED_FP64_SOLVE, N.NH_CRIT_ETA_D, False),
+             ("adaptive_fp32state_fp64solve_learned", N.NH_MIXED_FP64_SOLVE, N.NH_CRIT_ETA_D, True)]
     k_steps = max(1, args.form_steps)
     cells = sum(m.nx for m in wl.members)
     out = {}
@@ -220,7 +236,7 @@ def compare_forms(wl, G0, t_now, args):
         G = N.grid_from_workload(wl, precision=prec)
         G.set_state(h, hu, hw, t_now)
         G.set_criterion(crit, 1e-3, 1, False)
-        rtol = 1e-12 if prec == N.NH_FP64 else 1e-10
+        rtol = 1e-10 if prec == N.NH_MIXED else 1e-12
         G.set_solver(N.NH_SOLVER_AUTO, rtol, 20000, N.NH_GUESS_PREV)
         t_train = 0.0
         if learned:
@@ -245,7 +261,9 @@ def compare_forms(wl, G0, t_now, args):
         rec = {"ms_per_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
                "krylov_iters_per_step": info["iters_total"] / k_steps,
                "active_cells_per_step": info["active_total"] / k_steps,
-               "error_bound_vs_oracle": "1e-9 a" if prec == N.NH_FP64 else "1e-4 a (while masks agree)"}
+               "error_bound_vs_oracle": "1e-9 a" if prec == N.NH_FP64 else "1e-4 a (while masks agree)",
+               "precision": {N.NH_FP64: "fp64", N.NH_MIXED: "fp32 state + fp32 krylov in fp64 refinement",
+                             N.NH_MIXED_FP64_SOLVE: "fp32 state + fp64 krylov"}[prec]}
         if learned:
             rec["starts"] = G.cnn_choices()
             rec["harvest_and_train_s"] = t_train
@@ -314,11 +332,11 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     wl = W.slide_1d(n_members=args.members, seed0=rank_seed0(args.members, rank))
-    prec = N.NH_FP64 if args.precision == "fp64" else N.NH_MIXED
+    prec = {"fp64": N.NH_FP64, "mixed": N.NH_MIXED, "mixed64": N.NH_MIXED_FP64_SOLVE}[args.precision]
     G = N.grid_from_workload(wl, precision=prec)
     crit = N.NH_CRIT_GLOBAL if args.mode == "global" else N.NH_CRIT_ETA_D
     G.set_criterion(crit, 1e-3, 1, False)
-    rtol = 1e-12 if args.precision == "fp64" else 1e-10
+    rtol = 1e-10 if args.precision == "mixed" else 1e-12
     G.set_solver(N.NH_SOLVER_AUTO, rtol, 20000, N.NH_GUESS_PREV)
     G.set_preconditioner(N.NH_PRECOND_LINE if args.precond == "line" else N.NH_PRECOND_NONE)
     cells = wl.members[0].nx * len(wl.members)
@@ -367,7 +385,8 @@ def run_ours(args):
     iters_mean = info["iters_total"] / max(args.steps, 1)
 
     # dominant kernel class by device time, its algorithmic bytes per launch
-    table = BYTES_PER_UNIT_FP64 if args.precision == "fp64" else BYTES_PER_UNIT_MIXED
+    table = {"fp64": BYTES_PER_UNIT_FP64, "mixed": BYTES_PER_UNIT_MIXED,
+             "mixed64": BYTES_PER_UNIT_MIXED64}[args.precision]
     name, (dms, dn) = max(prof.items(), key=lambda kv: kv[1][0])
     peaks, peak_kind = _load_peaks()
     roof = None
@@ -468,7 +487,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed64"])
     ap.add_argument("--mode", default="adaptive", choices=["adaptive", "global"])
     ap.add_argument("--precond", default="line", choices=["line", "none"])
     ap.add_argument("--t-start", type=float, default=0.5)

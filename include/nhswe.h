@@ -54,8 +54,11 @@ enum { NH_BC_WALL = 0, NH_BC_PERIODIC = 1 };
 /* NH_FP64: every field, coefficient, vector and sum in FP64.
    NH_MIXED: state, predictor, coefficients and Krylov vectors in FP32;
    inner products, norms, mass sums and the iterative-refinement residual in
-   FP64. */
-enum { NH_FP64 = 0, NH_MIXED = 1 };
+   FP64.
+   NH_MIXED_FP64_SOLVE: state, predictor and correction coefficients in
+   FP32; the elliptic operator, the Krylov vectors and every sum in FP64 (one
+   FP64 Krylov solve per step, no refinement passes). */
+enum { NH_FP64 = 0, NH_MIXED = 1, NH_MIXED_FP64_SOLVE = 2 };
 /* Slope limiter of the piecewise-linear reconstruction of eta, u, w. */
 enum { NH_LIM_NONE = 0, NH_LIM_CENTRAL = 1, NH_LIM_MINMOD = 2, NH_LIM_MC = 3 };
 /* Sec. 5.1 criteria.  GLOBAL = every cell (the global model of Sec. 4);
@@ -84,7 +87,7 @@ typedef struct {
     int    nx;         /* cells per member, 8 <= nx <= 2^20                  */
     int    nbatch;     /* members, >= 1                                     */
     int    bc;         /* NH_BC_WALL or NH_BC_PERIODIC (both ends)          */
-    int    precision;  /* NH_FP64 or NH_MIXED                               */
+    int    precision;  /* NH_FP64, NH_MIXED or NH_MIXED_FP64_SOLVE          */
     int    limiter;    /* NH_LIM_*                                          */
     double dx;         /* cell width (m), > 0                               */
     double x0;         /* left end of the domain (m)                        */

@@ -28,8 +28,9 @@ struct nh_grid {
     int tile;                    // predictor tile (cells per CTA), chosen by the autotuner
     bool tuned;
     long long barrier_budget;    // clock cycles a grid barrier may spin
-    size_t es;                   // element size of state / Krylov vectors
-    bool mixed;
+    size_t es;                   // element size of the Krylov vectors
+    bool mixed;                  // FP32 state and predictor (NH_MIXED, NH_MIXED_FP64_SOLVE)
+    bool ir_mode;                // FP32 Krylov inside FP64 refinement (NH_MIXED)
     bool uneven;                 // members have different cell counts
     std::vector<int> nxh;        // cells per member
     std::vector<long long> offh; // host layout: member b at [offh[b], offh[b+1])
@@ -115,7 +116,7 @@ bool desc_ok(const nh_grid_desc* d)
     if (d->nbatch < 1 || d->nbatch > 65535) return false;
     if ((long long)d->nx * d->nbatch > (1LL << 30)) return false;
     if (d->bc != NH_BC_WALL && d->bc != NH_BC_PERIODIC) return false;
-    if (d->precision != NH_FP64 && d->precision != NH_MIXED) return false;
+    if (d->precision != NH_FP64 && d->precision != NH_MIXED && d->precision != NH_MIXED_FP64_SOLVE) return false;
     if (d->limiter < NH_LIM_NONE || d->limiter > NH_LIM_MC) return false;
     if (!(d->dx > 0.0) || !(d->g > 0.0) || !(d->rho > 0.0) || !std::isfinite(d->x0)) return false;
     return true;
@@ -126,7 +127,8 @@ bool desc_ok(const nh_grid_desc* d)
 size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
 {
     const int nx = d.nx, nb = d.nbatch;
-    const bool mixed = d.precision == NH_MIXED;
+    const bool mixed = d.precision != NH_FP64;
+    const bool ir_mode = d.precision == NH_MIXED;
     const int pitch = (nx + kPredTileMax - 1) / kPredTileMax * kPredTileMax;
     const int wpitch = pitch / 32;
     const int ntiles = pitch / kPredTile;
@@ -134,7 +136,8 @@ size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
     const int maxch = (nx + kChunk - 1) / kChunk;
     const int maxpb = (nx + kPcrRows - 1) / kPcrRows;
     const size_t N = (size_t)nb * pitch;
-    const size_t es = mixed ? 4 : 8;
+    const size_t es = mixed ? 4 : 8;        // state and correction coefficients
+    const size_t ev = ir_mode ? 4 : 8;      // Krylov vectors
     Carver c{base};
     nh_grid tmp;
     nh_grid* G = g ? g : &tmp;
@@ -158,7 +161,7 @@ size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
     G->pitems = (int2*)c.take(sizeof(int2) * (size_t)nb * maxpb);
     G->diag = (double*)c.take(N * 8); G->offl = (double*)c.take(N * 8);
     G->offr = (double*)c.take(N * 8); G->R = (double*)c.take(N * 8);
-    if (mixed) {
+    if (ir_mode) {
         G->diag32 = (float*)c.take(N * 4); G->offl32 = (float*)c.take(N * 4);
         G->offr32 = (float*)c.take(N * 4); G->rhs32 = (float*)c.take(N * 4);
         G->x64 = (double*)c.take(N * 8);
@@ -170,10 +173,10 @@ size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
     }
     G->c6 = c.take(N * es); G->cx = c.take(N * es); G->phi = c.take(N * es); G->ddx = c.take(N * es);
     G->nbl = (int*)c.take(sizeof(int) * N); G->nbr = (int*)c.take(sizeof(int) * N);
-    G->x = c.take(N * es); G->r = c.take(N * es); G->p0 = c.take(N * es); G->p1 = c.take(N * es);
-    G->q = c.take(N * es); G->rh = c.take(N * es); G->v0 = c.take(N * es); G->v1 = c.take(N * es);
-    G->s = c.take(N * es); G->t = c.take(N * es);
-    G->r1 = c.take(N * es); G->z = c.take(N * es);
+    G->x = c.take(N * ev); G->r = c.take(N * ev); G->p0 = c.take(N * ev); G->p1 = c.take(N * ev);
+    G->q = c.take(N * ev); G->rh = c.take(N * ev); G->v0 = c.take(N * ev); G->v1 = c.take(N * ev);
+    G->s = c.take(N * ev); G->t = c.take(N * ev);
+    G->r1 = c.take(N * ev); G->z = c.take(N * ev);
     G->psi = (double*)c.take(sizeof(double) * N);
     G->pf = (float2*)c.take(sizeof(float2) * kPcrLevels * N);
     G->prb = (float*)c.take(sizeof(float) * N);
@@ -186,7 +189,7 @@ size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
     G->tc = (TimeCtl*)c.take(sizeof(TimeCtl));
     if (g) {
         g->nx = nx; g->nb = nb; g->pitch = pitch; g->wpitch = wpitch; g->ntiles = ntiles;
-        g->maxch = maxch; g->es = es; g->maxpb = maxpb; g->mixed = mixed;
+        g->maxch = maxch; g->es = ev; g->maxpb = maxpb; g->mixed = mixed; g->ir_mode = ir_mode;
     }
     return (c.off + kAlign - 1) / kAlign * kAlign;
 }
@@ -524,7 +527,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
         const double* src = learned ? g->cnn.guess : g->psi;
         LAUNCH(NH_K_ASSEMBLE, k_assemble<T><<<g->items_grid, kChunk, 0, st>>>(aa));
         if (learned) LAUNCH(NH_K_CNN, CK(judge_launch(g, lnew, gscale, nullptr, st)));
-        if (g->mixed) {
+        if (g->ir_mode) {
             nh_status rc = refine(g, lnew, gscale, src);
             if (rc != NH_OK) return rc;
             xfinal = g->x64;
@@ -544,7 +547,7 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
         learned = false;
     }
     int ir_passes = 0;
-    if (g->mixed) {
+    if (g->ir_mode) {
         std::vector<IRState> irs(g->nb);
         CK(cudaMemcpyAsync(irs.data(), g->ir, sizeof(IRState) * g->nb, cudaMemcpyDeviceToHost, st));
         SYNC();
@@ -592,41 +595,43 @@ nh_status step_t(nh_grid* g, double dt, nh_step_info* info)
 
 // ---------------------------------------------------------- captured runs
 
-// Enqueue one FP64 step on `st` with fixed buffer roles (no host round trip):
+// Enqueue one step (FP64 solve; FP64 or FP32 state) on `st` with fixed buffer
+// roles (no host round trip):
 // the device time control block supplies t, the commit kernel accepts the step
 // or aborts the run.  Used only while capturing a graph.
+template <typename T>
 nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, double dt)
 {
     const int nxt = cur ^ 1, lnew = lprev ^ 1;
     const Geo G = geo(g);
     k_kinematics_dev<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slide, g->kin, g->nb, g->tc);
-    PredArgs<double> pa;
+    PredArgs<T> pa;
     pa.G = G;
-    pa.z = (const double*)g->sz[cur]; pa.hu = (const double*)g->shu[cur]; pa.hw = (const double*)g->shw[cur];
-    pa.zt = (double*)g->sz[nxt]; pa.hut = (double*)g->shu[nxt]; pa.hwt = (double*)g->shw[nxt];
-    pa.d0 = (const double*)g->d0; pa.slide = g->slide; pa.kin = g->kin;
+    pa.z = (const T*)g->sz[cur]; pa.hu = (const T*)g->shu[cur]; pa.hw = (const T*)g->shw[cur];
+    pa.zt = (T*)g->sz[nxt]; pa.hut = (T*)g->shu[nxt]; pa.hwt = (T*)g->shw[nxt];
+    pa.d0 = (const T*)g->d0; pa.slide = g->slide; pa.kin = g->kin;
     pa.marks = g->marks; pa.mass_part = g->mass_part; pa.dt = dt; pa.knh = g->knh; pa.crit = g->crit;
     pa.all_global = (g->crit == NH_CRIT_GLOBAL);
     pa.tc = g->tc;
-    CK(predict_launch<double>(g->tile, g->nb, g->pitch / g->tile, st, pa));
+    CK(predict_launch<T>(g->tile, g->nb, g->pitch / g->tile, st, pa));
     CompactArgs ca;
     ca.nx = g->nx; ca.pitch = g->pitch; ca.wpitch = g->wpitch; ca.bc = g->d.bc; ca.enlarge = g->enlarge;
     ca.marks = g->marks; ca.act = g->act; ca.list = g->list[lnew]; ca.nact = g->nact[lnew];
     ca.ms = g->ms; ca.ctl = g->ctl; ca.nxv = g->uneven ? g->nxd : nullptr; ca.tc = g->tc;
     k_compact<<<g->nb, kCompactThreads, sizeof(uint32_t) * (size_t)((g->nx + 31) / 32), st>>>(ca);
     k_items<<<1, 1024, 0, st>>>(g->ms, g->nb, g->items, g->pitems, g->ctl);
-    AsmArgs<double> aa;
+    AsmArgs<T> aa;
     aa.G = G;
-    aa.zt = (const double*)g->sz[nxt]; aa.hut = (const double*)g->shu[nxt]; aa.hwt = (const double*)g->shw[nxt];
+    aa.zt = (const T*)g->sz[nxt]; aa.hut = (const T*)g->shu[nxt]; aa.hwt = (const T*)g->shw[nxt];
     aa.d0 = g->d0d; aa.slide = g->slide; aa.kin = g->kin;
     aa.list = g->list[lnew]; aa.act = g->act; aa.ms = g->ms;
     aa.diag = g->diag; aa.offl = g->offl; aa.offr = g->offr; aa.R = g->R;
     aa.diag32 = nullptr; aa.offl32 = nullptr; aa.offr32 = nullptr;
     aa.nbl = g->nbl; aa.nbr = g->nbr;
-    aa.c6 = (double*)g->c6; aa.cx = (double*)g->cx; aa.phi = (double*)g->phi; aa.ddx = (double*)g->ddx;
+    aa.c6 = (T*)g->c6; aa.cx = (T*)g->cx; aa.phi = (T*)g->phi; aa.ddx = (T*)g->ddx;
     aa.part = g->part; aa.cnt = g->cnt; aa.dt = dt; aa.solver = g->solver;
     aa.items = g->items; aa.ctl = g->ctl;
-    k_assemble<double><<<g->items_grid, kChunk, 0, st>>>(aa);
+    k_assemble<T><<<g->items_grid, kChunk, 0, st>>>(aa);
     const cnn::GuessGeo GG = guess_geo(g, g->tc);
     if (cnn_features_on(g)) CK(cnn::launch_features(g->cnn, GG, st));
     if (g->guess == NH_GUESS_CNN) {
@@ -667,21 +672,21 @@ nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, do
     cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = g->tc;
     const size_t total = (size_t)g->nb * g->pitch;
     k_clear_prev<<<(int)std::min<size_t>((total + 255) / 256, (size_t)g->sm_count * 8), 256, 0, st>>>(cl);
-    CorrArgs<double> co;
+    CorrArgs<T> co;
     co.nb = g->nb; co.pitch = g->pitch; co.maxch = g->maxch; co.dx = g->d.dx;
     co.list = g->list[lnew]; co.nbl = g->nbl; co.nbr = g->nbr; co.x = (const double*)g->x;
-    co.c6 = (const double*)g->c6; co.cx = (const double*)g->cx; co.phi = (const double*)g->phi;
-    co.ddx = (const double*)g->ddx; co.ms = g->ms;
-    co.hu = (double*)g->shu[nxt]; co.hw = (double*)g->shw[nxt]; co.psi = g->psi;
+    co.c6 = (const T*)g->c6; co.cx = (const T*)g->cx; co.phi = (const T*)g->phi;
+    co.ddx = (const T*)g->ddx; co.ms = g->ms;
+    co.hu = (T*)g->shu[nxt]; co.hw = (T*)g->shw[nxt]; co.psi = g->psi;
     co.items = g->items; co.ctl = g->ctl; co.tc = g->tc;
-    k_correct<double><<<g->items_grid, kChunk, 0, st>>>(co);
+    k_correct<T><<<g->items_grid, kChunk, 0, st>>>(co);
     CK(cudaGetLastError());
     return NH_OK;
 }
 
 bool graph_eligible(const nh_grid* g, double dt)
 {
-    return !g->mixed && g->precond == NH_PRECOND_LINE && g->solver != NH_SOLVER_BICGSTAB &&
+    return !g->ir_mode && g->precond == NH_PRECOND_LINE && g->solver != NH_SOLVER_BICGSTAB &&
            g->coop_grid[0] > 0 && !g->prof_on && !(g->first_global && g->steps == 0) &&
            (g->last_dt == 0.0 || g->last_dt == dt) && g->cap_stream != nullptr;
 }
@@ -704,7 +709,8 @@ nh_status graph_prepare(nh_grid* g, double dt)
         const int cur = p, lprev = p ^ g->cur ^ g->lcur;
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
-        nh_status rc = enqueue_graph_step(g, g->cap_stream, cur, lprev, dt);
+        nh_status rc = g->mixed ? enqueue_graph_step<float>(g, g->cap_stream, cur, lprev, dt)
+                                : enqueue_graph_step<double>(g, g->cap_stream, cur, lprev, dt);
         cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
         if (rc != NH_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);

@@ -21,7 +21,7 @@ from . import build as _build
 # enums (mirror include/nhswe.h)
 NH_OK, NH_ERR_ARG, NH_ERR_CUDA, NH_ERR_NOT_CONVERGED, NH_ERR_NONFINITE, NH_ERR_TIMEOUT, NH_ERR_STATE = range(7)
 NH_BC_WALL, NH_BC_PERIODIC = 0, 1
-NH_FP64, NH_MIXED = 0, 1
+NH_FP64, NH_MIXED, NH_MIXED_FP64_SOLVE = 0, 1, 2
 NH_LIM_NONE, NH_LIM_CENTRAL, NH_LIM_MINMOD, NH_LIM_MC = range(4)
 (NH_CRIT_GLOBAL, NH_CRIT_HYDROSTATIC, NH_CRIT_ETA_D, NH_CRIT_ETA_X, NH_CRIT_U, NH_CRIT_U_X,
  NH_CRIT_W, NH_CRIT_W_X) = range(8)

@@ -111,3 +111,39 @@ def test_mixed_matches_fp64_path_globally():
     assert abs(i32["last"]["mass"] - i0["mass"]) <= 1e-9 * i0["mass"]
     G64.close()
     G32.close()
+
+
+# ------------------------------------------- FP32 state with an FP64 solve
+
+@pytest.mark.parametrize("crit", [O.CRIT_GLOBAL, O.CRIT_HYDROSTATIC])
+def test_fp32_state_fp64_solve_fixed_mask(crit):
+    """NH_MIXED_FP64_SOLVE: FP32 state and predictor, FP64 operator and Krylov
+    (rtol 1e-12, no refinement passes); same tolerance as the mixed path."""
+    wl = _slide()
+    n = 300
+    ref = run_oracle(wl, n, crit=crit)
+    G = make_gpu(wl, crit, precision=N.NH_MIXED_FP64_SOLVE, rtol=1e-12)
+    st, info = G.run(wl.dt, n)
+    if crit == O.CRIT_GLOBAL:
+        assert info["last"]["ir_passes"] == 0
+        assert info["last"]["rel_res"] <= 1e-12
+    worst = compare(wl, G, ref, tol_eta=1e-4, what=f"fp32 state crit={crit}")
+    print(f"fp32 state / fp64 solve crit={crit}: max |d eta| / a = {worst:.2e}")
+    G.close()
+
+
+def test_fp32_state_fp64_solve_graph_equals_steps():
+    """The captured-graph run of NH_MIXED_FP64_SOLVE equals its step-by-step run."""
+    wl = _slide()
+    out = []
+    for graphs in (False, True):
+        G = make_gpu(wl, O.CRIT_ETA_D, knh=1e-5, precision=N.NH_MIXED_FP64_SOLVE, rtol=1e-12)
+        G.set_run_mode(graphs)
+        st, info = G.run(wl.dt, 40)
+        out.append((G.get_state(), info["iters_total"]))
+        G.close()
+    (s0, i0), (s1, i1) = out
+    assert i0 > 0 and i0 == i1
+    for k in range(3):
+        a, b = np.asarray(s0[k]), np.asarray(s1[k])
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(1.0, np.max(np.abs(a)))
