@@ -75,7 +75,7 @@ enum { NH_SOLVER_AUTO = 0, NH_SOLVER_CG = 1, NH_SOLVER_BICGSTAB = 2 };
 /* NH_GUESS_CNN: the learned guess of nhswe_cnn.h (needs nh_cnn_attach). */
 enum { NH_GUESS_ZERO = 0, NH_GUESS_PREV = 1, NH_GUESS_CNN = 2 };
 /* Preconditioner of the CG branch.  NH_PRECOND_LINE: the tridiagonal operator
-   restricted to blocks of 4096 consecutive active cells, solved by parallel
+   restricted to blocks of 8192 consecutive active cells, solved by parallel
    cyclic reduction in FP32 (exact up to FP32 rounding on any active segment
    that fits in one block), inside a flexible (Polak-Ribiere) PCG whose
    vectors, dots and stopping test stay in the handle's precision. */

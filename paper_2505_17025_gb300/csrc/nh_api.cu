@@ -381,7 +381,7 @@ nh_status krylov_pass(nh_grid* g, SolveArgs<T>& sa)
     CK(cudaMemcpyAsync(&hctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     SYNC();
     const bool pcg = g->precond == NH_PRECOND_LINE;
-    const size_t pcr_smem = 4 * sizeof(float) * (size_t)kPcrRows;
+    const size_t pcr_smem = 2 * sizeof(float) * (size_t)kPcrRows;
     if (pcg && (hctl.n_cg > 0 || hctl.n_bicg > 0))
         LAUNCH(NH_K_PRECOND, k_pcr_factor<T, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa));
     if (hctl.n_cg > 0 && pcg) {
@@ -645,7 +645,7 @@ nh_status enqueue_graph_step(nh_grid* g, cudaStream_t st, int cur, int lprev, do
     CK(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
     CK(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
     k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa);
-    const size_t pcr_smem = 4 * sizeof(float) * (size_t)kPcrRows;
+    const size_t pcr_smem = 2 * sizeof(float) * (size_t)kPcrRows;
     sa.it = 0;
     k_pcr_factor<double, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa);
     k_pcr<double, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG);
@@ -1044,21 +1044,27 @@ static nh_status finish_create(nh_grid* g, const double* d0_host, int dev, int s
             rc = NH_ERR_CUDA; break;
         }
         if (cudaFuncSetAttribute(k_pcr<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess ||
+                                 (int)(2 * sizeof(float) * kPcrRows)) != cudaSuccess ||
             cudaFuncSetAttribute(k_pcr<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess) {
+                                 (int)(2 * sizeof(float) * kPcrRows)) != cudaSuccess) {
+            rc = NH_ERR_CUDA; break;
+        }
+        if (cudaFuncSetAttribute(k_pcr_factor<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(3 * sizeof(float) * kPcrRows)) != cudaSuccess ||
+            cudaFuncSetAttribute(k_pcr_factor<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(3 * sizeof(float) * kPcrRows)) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
         }
         if (cudaFuncSetAttribute(k_pcg_persistent<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess ||
+                                 (int)(2 * sizeof(float) * kPcrRows)) != cudaSuccess ||
             cudaFuncSetAttribute(k_pcg_persistent<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(4 * sizeof(float) * kPcrRows)) != cudaSuccess) {
+                                 (int)(2 * sizeof(float) * kPcrRows)) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
         }
         {
             int coop = 0, per_sm = 0;
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-            const size_t sm_bytes = 4 * sizeof(float) * kPcrRows;
+            const size_t sm_bytes = 2 * sizeof(float) * kPcrRows;
             g->coop_grid[0] = g->coop_grid[1] = 0;
             if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<double, float>,
                                                                       kPcrThreads, sm_bytes) == cudaSuccess)

@@ -34,8 +34,8 @@ constexpr int kPredHalo = 5;     // two Heun stages + one cell for the criterion
 constexpr int kChunk = 256;      // active cells per solver work item (= blockDim)
 constexpr int kCompactThreads = 1024;
 constexpr int kPcrThreads = 1024;     // preconditioner CTA
-constexpr int kPcrRows = 4096;        // active cells per preconditioner block (power of 2)
-constexpr int kPcrLevels = 12;        // cyclic-reduction levels of a full block
+constexpr int kPcrRows = 8192;        // active cells per preconditioner block (power of 2)
+constexpr int kPcrLevels = 13;        // cyclic-reduction levels of a full block
 static_assert((1 << kPcrLevels) == kPcrRows, "kPcrLevels = log2(kPcrRows)");
 
 // Beyond xi^2 = 40 the Gaussian mound is below exp(-40) A = 4.3e-18 A: under

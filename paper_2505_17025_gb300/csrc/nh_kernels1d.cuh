@@ -1284,10 +1284,8 @@ template <typename T, typename TP>
 __global__ void __launch_bounds__(kPcrThreads) k_pcr(SolveArgs<T> a, int mode)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TP* sa = reinterpret_cast<TP*>(smem_raw);
-    TP* sb = sa + kPcrRows;
-    TP* sc = sb + kPcrRows;
-    TP* sd = sc + kPcrRows;
+    TP* sa = reinterpret_cast<TP*>(smem_raw);   // reduction ping-pong buffers
+    TP* sd = sa + kPcrRows;
     __shared__ double red[96];
     constexpr int RPT = kPcrRows / kPcrThreads;
     const int it = a.it;
@@ -1457,10 +1455,8 @@ template <typename T, typename TP>
 __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, long long budget)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TP* sa = reinterpret_cast<TP*>(smem_raw);
-    TP* sb = sa + kPcrRows;
-    TP* sc = sb + kPcrRows;
-    TP* sd = sc + kPcrRows;
+    TP* sa = reinterpret_cast<TP*>(smem_raw);   // reduction ping-pong buffers
+    TP* sd = sa + kPcrRows;
     __shared__ double red[96];
     constexpr int RPT = kPcrRows / kPcrThreads;
     const size_t stride = (size_t)a.nb * a.maxch;
