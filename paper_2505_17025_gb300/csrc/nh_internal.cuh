@@ -113,7 +113,7 @@ struct Ctl {
     unsigned bar_count;         // grid barrier: arrivals
     unsigned bar_gen;           // grid barrier: generation
     int go[2];                  // persistent solve: continue flag per iteration parity
-    int pad2;
+    int max_npb;                // largest number of preconditioner blocks of a member this step
 };
 
 __device__ __forceinline__ int resolve(int j, int n, int bc, int* sgn)

@@ -458,12 +458,14 @@ static __global__ void __launch_bounds__(1024) k_items(MState* ms, int nb, int2*
 {
     __shared__ int s_w[2][32];
     __shared__ int s_base[2];
+    __shared__ int s_maxpb;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
-    if (tid == 0) { s_base[0] = 0; s_base[1] = 0; }
+    if (tid == 0) { s_base[0] = 0; s_base[1] = 0; s_maxpb = 0; }
     __syncthreads();
     for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
         const int b = b0 + tid;
         const int c0 = b < nb ? ms[b].nchunks : 0, c1 = b < nb ? ms[b].npb : 0;
+        if (c1 > 1) atomicMax(&s_maxpb, c1);
         int i0 = c0, i1 = c1;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -494,7 +496,7 @@ static __global__ void __launch_bounds__(1024) k_items(MState* ms, int nb, int2*
         if (tid == 0) { s_base[0] += s_w[0][nwarp - 1]; s_base[1] += s_w[1][nwarp - 1]; }
         __syncthreads();
     }
-    if (tid == 0) { ctl->n_items = s_base[0]; ctl->n_pitems = s_base[1]; }
+    if (tid == 0) { ctl->n_items = s_base[0]; ctl->n_pitems = s_base[1]; ctl->max_npb = s_maxpb; }
 }
 
 // Deterministic block-wide sum of part[0..n) (thread 0 gets it).
@@ -1445,6 +1447,93 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, long lo
     return s_ok != 0;
 }
 
+// Member-local PCG: when no member has more than one preconditioner block,
+// a member's whole solve lives in one CTA (its rows are one block), so every
+// iteration needs only block barriers and block reductions: no grid barrier,
+// no cross-CTA reduction, and members finish independently.  Same algorithm
+// and arithmetic as the grid-wide loop below (p = z + beta p_old, q = A p,
+// alpha = rz / <p, q>, x and r update, z = M^{-1} r, flexible beta).
+template <typename T, typename TP>
+__device__ void pcg_member_local(const SolveArgs<T>& a, TP* sa, TP* sd, double* red)
+{
+    constexpr int kBreakdown = -2;
+    __shared__ double s_bc[4];
+    const int n_pitems = a.ctl->n_pitems;
+    for (int wi = blockIdx.x; wi < n_pitems; wi += gridDim.x) {
+        const int b = a.pitems[wi].x;
+        MState& st = a.ms[b];
+        if (st.done || st.kind != NH_SOLVER_CG) continue;
+        const int n = st.n_active;
+        const size_t mo = (size_t)b * a.pitch;
+        double rz = st.rz, beta = 0.0, rel = 0.0;
+        const double bnorm = st.bnorm;
+        int status = NH_ERR_NOT_CONVERGED, iters = 0;
+        for (int it = 1; it <= a.max_iter; ++it) {
+            const T* pold = (it & 1) ? a.p0 : a.p1;
+            T* pnew = (it & 1) ? a.p1 : a.p0;
+            const T* rold = (it & 1) ? a.r : a.r1;
+            T* rnew = (it & 1) ? a.r1 : a.r;
+            iters = it;
+            for (int k = threadIdx.x; k < n; k += kPcrThreads)
+                pnew[mo + k] = a.z[mo + k] + T(beta) * pold[mo + k];
+            __syncthreads();
+            double v[1] = {0.0};
+            for (int k = threadIdx.x; k < n; k += kPcrThreads) {
+                const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+                const T pk = pnew[mo + k];
+                const T pl = kl >= 0 ? pnew[mo + kl] : T(0);
+                const T pr = kr >= 0 ? pnew[mo + kr] : T(0);
+                const T qk = apply_row(a, mo, k, pk, pl, pr);
+                a.q[mo + k] = qk;
+                v[0] += (double)pk * (double)qk;
+            }
+            block_sum<1>(v, red);
+            if (threadIdx.x == 0) s_bc[0] = v[0];
+            __syncthreads();
+            const double spq = s_bc[0];
+            if (!isfinite(spq) || !(spq > 0.0)) { status = kBreakdown; break; }
+            const T alpha = T(rz / spq);
+            double acc[3] = {0.0, 0.0, 0.0};
+            for (int k = threadIdx.x; k < n; k += kPcrThreads) {
+                a.x[mo + k] = a.x[mo + k] + alpha * pnew[mo + k];
+                const T rk = rold[mo + k] - alpha * a.q[mo + k];
+                rnew[mo + k] = rk;
+                acc[2] += (double)rk * (double)rk;
+                sd[k] = TP(rk);
+            }
+            __syncthreads();
+            const TP* red_d = pcr_apply<T, TP>(a, sd, sa, n, mo);
+            for (int k = threadIdx.x; k < n; k += kPcrThreads) {
+                const T zk = T(red_d[k] * TP(a.prb[mo + k]));
+                a.z[mo + k] = zk;
+                acc[0] += (double)zk * (double)rnew[mo + k];
+                acc[1] += (double)zk * (double)rold[mo + k];
+            }
+            block_sum<3>(acc, red);
+            if (threadIdx.x == 0) { s_bc[1] = acc[0]; s_bc[2] = acc[1]; s_bc[3] = acc[2]; }
+            __syncthreads();
+            const double zr = s_bc[1], zro = s_bc[2], rr = s_bc[3];
+            if (!isfinite(rr)) { status = NH_ERR_NONFINITE; rel = NAN; break; }
+            rel = sqrt(rr) / bnorm;
+            if (sqrt(rr) <= a.rtol * bnorm) { status = NH_OK; break; }
+            if (it >= a.max_iter) { status = NH_ERR_NOT_CONVERGED; break; }
+            if (!isfinite(zr) || !(zr > 0.0)) { status = kBreakdown; break; }
+            beta = (zr - zro) / rz;
+            rz = zr;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (status == kBreakdown) {
+                cg_breakdown<T>(st, a.ctl, iters);
+            } else {
+                st.beta = beta; st.rz = rz;
+                finish_member<T>(st, a.ctl, status, iters, rel);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // All PCG iterations of one solve in one cooperative launch: per iteration
 // phase A (p = z + beta p_old, q = A p, <p, q> -> alpha) and phase B (x, r
 // update, ||r||, line preconditioner, beta), separated by grid barriers.  Work
@@ -1463,6 +1552,10 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, 
     const int n_pitems = a.ctl->n_pitems;
     Ctl* ctl = a.ctl;
     const unsigned nblk = gridDim.x;
+    if (ctl->max_npb <= 1) {          // the same for every CTA: no grid barrier needed
+        pcg_member_local<T, TP>(a, sa, sd, red);
+        return;
+    }
     for (int it = 1; it <= a.max_iter; ++it) {
         const T* pold = (it & 1) ? a.p0 : a.p1;
         T* pnew = (it & 1) ? a.p1 : a.p0;
