@@ -44,7 +44,8 @@ def build(force: bool = False) -> str:
     src = [os.path.join(_HERE, "nh_oracle.c"), os.path.join(_HERE, "nh_oracle2d.c")]
     src = [s for s in src if os.path.exists(s)]
     out = os.path.join(_BUILD, "libnh_oracle.so")
-    newest = max(os.path.getmtime(s) for s in src + [os.path.join(_HERE, "nh_oracle.h")])
+    hdrs = [os.path.join(_HERE, h) for h in ("nh_oracle.h", "nh_oracle2d.h") if os.path.exists(os.path.join(_HERE, h))]
+    newest = max(os.path.getmtime(s) for s in src + hdrs)
     if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
         tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",

@@ -1,0 +1,307 @@
+"""Pins of the 2D oracle (oracle/nh_oracle2d.c) against what the paper and
+mathematics fix.  The paper's model is 1D; its 2D form here is the
+generalisation that must (a) reduce exactly to the 1D oracle when nothing
+depends on y, (b) treat x and y alike (transposition symmetry), (c) keep the
+1D invariants (lake at rest, mass), (d) give the Green-Naghdi dispersion
+relation for an oblique wave, (e) produce a symmetric operator whose Krylov
+solve matches a dense LU, and (f) leave a corrected state that satisfies the
+2D constraint (Eq. 4 with gradients) to the truncation error of its
+evaluation, so a dropped term or a wrong sign in the derived elliptic
+equation shows as an O(1) residual.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.oracle2d as O2
+from paper_2505_17025_gb300 import workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _p2(nx, ny, dx, dy, **kw):
+    return O2.Params2D(nx=nx, ny=ny, dx=dx, dy=dy, **kw)
+
+
+# ------------------------------------------------------- reduction to 1D
+
+@pytest.mark.parametrize("case", ["solitary_global", "solitary_adaptive", "slide_adaptive"])
+def test_y_uniform_reduces_to_1d(case):
+    """Replicating a 1D problem along y (periodic in y) gives the 1D oracle's
+    result in every row, with hv = 0."""
+    ny = 4
+    if case.startswith("solitary"):
+        wl = W.solitary_1d(nx=400, length=40.0, a=0.1, T=2.0)
+        m = wl.members[0]
+        crit = O.CRIT_GLOBAL if case == "solitary_global" else O.CRIT_ETA_D
+        kw1 = dict(crit=crit, knh=1e-3)
+        kw2 = dict(crit=crit, knh=1e-3)
+        n = 40
+    else:
+        wl = W.slide_1d(n_members=1, nx=300, length=6.0, xc0=1.0, T=0.5)
+        m = wl.members[0]
+        kw1 = dict(crit=O.CRIT_ETA_D, knh=1e-5, slide=m.slide, A=m.A, L=m.L, xc0=m.xc0, s0=m.s0, t0=m.t0)
+        # a mound of unbounded extent in y: exp(-zeta^2) == 1 to round-off
+        kw2 = dict(crit=O.CRIT_ETA_D, knh=1e-5, slide=m.slide, A=m.A, Lx=m.L, Ly=1e30, xc0=m.xc0,
+                   yc0=0.0, s0=m.s0, t0=m.t0)
+        n = 60
+    p1 = O.Params(nx=m.nx, dx=m.dx, xl=m.xl, rtol=1e-13, **kw1)
+    s1 = O.State(m.h, m.hu, m.hw)
+    O.run(p1, m.d0, 0.0, 0, wl.dt, n, s1)
+    p2 = _p2(m.nx, ny, m.dx, 0.37, x0=m.xl, bcy=O.BC_PERIODIC, rtol=1e-13, **kw2)
+    rep = lambda a: np.tile(np.asarray(a, dtype=np.float64), (ny, 1))
+    s2 = O2.State2D(rep(m.h), rep(m.hu), np.zeros((ny, m.nx)), rep(m.hw))
+    st, info, _, _ = O2.run(p2, rep(m.d0), 0.0, 0, wl.dt, n, s2)
+    assert st == O.OK
+    h, hu, hv, hw, q = s2.fields(p2)
+    scale_h = np.max(np.abs(m.h - m.d0)) + 1e-3
+    for row in range(ny):
+        assert np.max(np.abs(h[row] - s1.h)) <= 1e-11 * scale_h
+        assert np.max(np.abs(hu[row] - s1.hu)) <= 1e-11 * max(1e-3, np.max(np.abs(s1.hu)))
+        assert np.max(np.abs(hw[row] - s1.hw)) <= 1e-9 * max(1e-3, np.max(np.abs(s1.hw)))
+    assert np.max(np.abs(hv)) <= 1e-14
+
+
+# ------------------------------------------------- transposition symmetry
+
+def _bumpy(nx, ny, dx, dy):
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    X, Y = np.meshgrid(x, y)
+    d0 = 0.6 + 0.15 * X - 0.05 * Y + 0.04 * np.sin(2.1 * X + 0.7 * Y)
+    eta = 0.02 * np.exp(-((X - 1.1) ** 2 + (Y - 0.8) ** 2) / 0.15)
+    return d0, eta
+
+
+def test_transposition_symmetry():
+    """Swapping x and y (grid, spacings, bottom, initial state, hu <-> hv)
+    transposes the result: the y code paths equal the x ones."""
+    nx, ny, dx, dy = 36, 28, 0.07, 0.08
+    d0, eta = _bumpy(nx, ny, dx, dy)
+    h = d0 + eta
+    hu = 0.01 * eta
+    hv = -0.02 * eta
+    hw = 0.003 * eta
+    kw = dict(crit=O.CRIT_ETA_D, knh=2e-3, enlarge=1, rtol=1e-13)
+    pa = _p2(nx, ny, dx, dy, **kw)
+    pb = _p2(ny, nx, dy, dx, **kw)
+    dt = 0.3 * min(dx, dy) / math.sqrt(9.81 * h.max())
+    sa = O2.State2D(h, hu, hv, hw)
+    sb = O2.State2D(h.T, hv.T, hu.T, hw.T)
+    O2.run(pa, d0, 0.0, 0, dt, 25, sa)
+    O2.run(pb, np.ascontiguousarray(d0.T), 0.0, 0, dt, 25, sb)
+    A = sa.fields(pa)
+    B = sb.fields(pb)
+    assert np.max(np.abs(A[0] - B[0].T)) <= 1e-12
+    assert np.max(np.abs(A[1] - B[2].T)) <= 1e-12
+    assert np.max(np.abs(A[2] - B[1].T)) <= 1e-12
+    assert np.max(np.abs(A[3] - B[3].T)) <= 1e-12
+
+
+# ------------------------------------------------------------ invariants
+
+def test_lake_at_rest_2d():
+    """Still water over a bumpy sloping bottom with a resting 2D mound stays at
+    rest to round-off under the full NH step, for every limiter."""
+    nx, ny, dx, dy = 30, 24, 0.08, 0.09
+    d0, _ = _bumpy(nx, ny, dx, dy)
+    for lim in (O.LIM_CENTRAL, O.LIM_MINMOD, O.LIM_MC):
+        p = _p2(nx, ny, dx, dy, crit=O.CRIT_GLOBAL, limiter=lim, rtol=1e-12, slide=O.SLIDE_GAUSS_LNCOSH,
+                A=0.05, Lx=0.4, Ly=0.3, xc0=1.2, yc0=1.0, s0=0.0, t0=1.0)
+        dmound = np.array([[O2.bottom(p, d0, i, j, 0.0)[0] for i in range(nx)] for j in range(ny)])
+        s = O2.State2D(dmound, np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+        dt = 0.3 * dx / math.sqrt(9.81 * dmound.max())
+        O2.run(p, d0, 0.0, 0, dt, 20, s)
+        h, hu, hv, hw, q = s.fields(p)
+        assert np.max(np.abs(h - dmound)) < 1e-13
+        assert max(np.max(np.abs(hu)), np.max(np.abs(hv)), np.max(np.abs(hw))) < 1e-13
+
+
+def test_mass_conservation_2d_slide():
+    """With walls on every side the total mass is constant to round-off while
+    the 2D slide moves the bottom (h is not corrected, Sec. 3.2)."""
+    nx, ny, dx, dy = 40, 30, 0.1, 0.1
+    x = (np.arange(nx) + 0.5) * dx
+    d0 = np.tile(np.minimum(0.1 + 0.2 * x, 2.0), (ny, 1))
+    p = _p2(nx, ny, dx, dy, crit=O.CRIT_ETA_D, knh=1e-4, rtol=1e-12, slide=O.SLIDE_GAUSS_LNCOSH,
+            A=0.1, Lx=0.6, Ly=0.4, xc0=1.5, yc0=1.5, s0=2.0, t0=1.0)
+    h0 = np.array([[O2.bottom(p, d0, i, j, 0.0)[0] for i in range(nx)] for j in range(ny)])
+    s = O2.State2D(h0, np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    dt = 0.3 * dx / math.sqrt(9.81 * 2.0)
+    m0 = s.h.sum()
+    st, info, it, act = O2.run(p, d0, 0.0, 0, dt, 60, s)
+    assert st == O.OK and act > 0
+    assert abs(s.h.sum() - m0) <= 1e-12 * m0
+
+
+# ------------------------------------------------------------- dispersion
+
+def _standing_period_2d(kh, crit, cells=32):
+    """Standing wave eta = amp cos(kx x) cos(ky y), kx = ky = k / sqrt(2), in a
+    walled square box of one wavelength per direction."""
+    k = kh / 1.0
+    kx = k / math.sqrt(2.0)
+    length = 2.0 * math.pi / kx
+    n = cells
+    dx = length / n
+    x = (np.arange(n) + 0.5) * dx
+    X, Y = np.meshgrid(x, x)
+    amp = 1e-5
+    h = 1.0 + amp * np.cos(kx * X) * np.cos(kx * Y)
+    d0 = np.ones((n, n))
+    omega_gn = k * math.sqrt(9.81 / (1.0 + kh * kh / 3.0))
+    T = 2.0 * 2 * math.pi / omega_gn
+    dt = 0.2 * dx / math.sqrt(9.81)
+    nsteps = int(T / dt)
+    p = _p2(n, n, dx, dx, crit=crit, rtol=1e-13)
+    s = O2.State2D(h, np.zeros((n, n)), np.zeros((n, n)), np.zeros((n, n)))
+    series = [s.h[0] - 1.0]
+    for i in range(nsteps):
+        O2.step(p, d0, i * dt, i, dt, s)
+        series.append(s.h[0] - 1.0)
+    y = np.array(series)
+    z = [i + y[i] / (y[i] - y[i + 1]) for i in range(len(y) - 1) if y[i] * y[i + 1] < 0]
+    half = np.mean(np.diff(z)) * dt
+    return math.pi / half, omega_gn, k
+
+
+def test_oblique_dispersion():
+    """omega^2 = g h |k|^2 / (1 + (|k| h)^2 / 3) for a wave along the diagonal
+    (|k| h = 1) within 1.5 %; the hydrostatic model is off by > 3 %."""
+    omega, omega_gn, k = _standing_period_2d(1.0, O.CRIT_GLOBAL)
+    assert abs(omega / omega_gn - 1.0) < 0.015
+    omega_h, _, _ = _standing_period_2d(1.0, O.CRIT_HYDROSTATIC)
+    assert abs(omega_h / omega_gn - 1.0) > 0.03
+
+
+# ------------------------------------------------------------ the operator
+
+def _sloped_case(nx=14, ny=11, dx=0.11, dy=0.13):
+    x = (np.arange(nx) + 0.5) * dx
+    d0 = np.tile(0.3 + 0.25 * x, (ny, 1))
+    p = _p2(nx, ny, dx, dy, crit=O.CRIT_GLOBAL, rtol=1e-14, slide=O.SLIDE_GAUSS_LNCOSH,
+            A=0.08, Lx=0.5, Ly=0.35, xc0=0.8, yc0=0.7, s0=1.0, t0=1.0)
+    h = np.array([[O2.bottom(p, d0, i, j, 0.3)[0] for i in range(nx)] for j in range(ny)])
+    rng = np.random.default_rng(3)
+    h = h + 0.01 * rng.standard_normal((ny, nx))
+    hu = 0.02 * rng.standard_normal((ny, nx))
+    hv = 0.02 * rng.standard_normal((ny, nx))
+    hw = 0.005 * rng.standard_normal((ny, nx))
+    return p, d0, h, hu, hv, hw
+
+
+@pytest.mark.parametrize("bc", [O.BC_WALL, O.BC_PERIODIC])
+def test_operator_symmetric_and_krylov_matches_dense(bc):
+    """With cross terms present (sloping bottom, 2D mound) the 9-point
+    operator is symmetric on a partial mask, and CG / BiCGStab agree with
+    dense LU."""
+    p, d0, h, hu, hv, hw = _sloped_case()
+    p.bcx = p.bcy = bc
+    coef, gam, R = O2.assemble(p, d0, 0.3, 0.01, h, hu, hv, hw)
+    assert np.max(np.abs(coef[5:])) > 0.0                  # cross terms in play
+    mask = np.ones((p.ny, p.nx), dtype=np.uint8)
+    mask[3:6, 4:9] = 0
+    mask[9, 1] = 0
+    n = p.nx * p.ny
+    act = np.flatnonzero(mask.reshape(-1))
+    M = np.zeros((act.size, act.size))
+    for col, k in enumerate(act):
+        e = np.zeros(n); e[k] = 1.0
+        M[:, col] = O2.apply(p, mask, coef, e).reshape(-1)[act]
+    assert np.max(np.abs(M - M.T)) <= 1e-12 * np.max(np.abs(M))
+    p.solver = O.SOLVER_DENSE
+    qd, st, _ = O2.solve(p, mask, coef, gam, R)
+    assert st == O.OK
+    for solver in (O.SOLVER_CG, O.SOLVER_BICGSTAB):
+        p.solver = solver
+        q, st, info = O2.solve(p, mask, coef, gam, R)
+        assert st == O.OK
+        assert np.max(np.abs(q - qd)) <= 1e-9 * np.max(np.abs(qd))
+    # and the dense solve is what numpy says
+    qn = np.linalg.solve(M, R.reshape(-1)[act])
+    assert np.allclose(qd.reshape(-1)[act], qn, rtol=1e-9, atol=1e-14)
+
+
+def _smooth_step_2d(n, rho=1000.0):
+    """One global NH step on a smooth periodic problem (bottom with slope
+    and ripples in both directions, a 2D slide, a surface hump with a
+    flow), n x n cells on [0, 4]^2."""
+    L = 4.0
+    dx = L / n
+    x = (np.arange(n) + 0.5) * dx
+    X, Y = np.meshgrid(x, x)
+    d0 = 0.8 + 0.1 * np.sin(2 * np.pi * X / L) * np.cos(2 * np.pi * Y / L) + 0.05 * np.cos(4 * np.pi * Y / L)
+    p = _p2(n, n, dx, dx, bcx=O.BC_PERIODIC, bcy=O.BC_PERIODIC, crit=O.CRIT_GLOBAL, rtol=1e-14,
+            rho=rho, slide=O.SLIDE_GAUSS_LNCOSH, A=0.05, Lx=0.35, Ly=0.3, xc0=1.8, yc0=2.1, s0=0.4, t0=1.0)
+    eta = 0.03 * np.exp(-((X - 2.2) ** 2 + (Y - 1.9) ** 2) / 0.2)
+    t, dt = 0.4, 0.002
+    dn = np.array([[O2.bottom(p, d0, i, j, t)[0] for i in range(n)] for j in range(n)])
+    h = dn + eta
+    hu = 0.05 * h * np.sin(2 * np.pi * Y / L)
+    hv = 0.04 * h * np.cos(2 * np.pi * X / L)
+    hw = 0.002 * h * np.sin(2 * np.pi * (X + Y) / L)
+    ht, hut, hvt, hwt = O2.predict(p, d0, t, dt, h, hu, hv, hw)
+    t1 = t + dt
+    coef, gam, R = O2.assemble(p, d0, t1, dt, ht, hut, hvt, hwt)
+    mask = np.ones((n, n), dtype=np.uint8)
+    q, st, _ = O2.solve(p, mask, coef, gam, R)
+    assert st == O.OK
+    H, HU, HV, HW = O2.correct(p, d0, t1, dt, mask, q, ht, hut, hvt, hwt)
+    b = np.array([[O2.bottom(p, d0, i, j, t1) for i in range(n)] for j in range(n)])
+    return dict(h=H, hu=HU, hv=HV, hw=HW, q=q, d=b[..., 0], d_t=b[..., 6], dx=dx, hwt=hwt, ht=ht,
+                phi_terms=(b, hut, hvt, ht), p=p, d0=d0, t1=t1, dt=dt)
+
+
+def _constraint_residual(s):
+    """max |2 hw + U . grad(2 d - h) + 2 h d_t + h div U| / scale over the
+    cells, central differences (periodic)."""
+    dx = s["dx"]
+    h, hu, hv, hw, d = s["h"], s["hu"], s["hv"], s["hw"], s["d"]
+    cx = lambda f: (np.roll(f, -1, axis=1) - np.roll(f, 1, axis=1)) / (2 * dx)
+    cy = lambda f: (np.roll(f, -1, axis=0) - np.roll(f, 1, axis=0)) / (2 * dx)
+    g = 2 * d - h
+    r = 2 * hw + hu * cx(g) + hv * cy(g) + 2 * h * s["d_t"] + h * (cx(hu) + cy(hv))
+    scale = np.max(np.abs(2 * hw)) + np.max(np.abs(h * (cx(hu) + cy(hv))))
+    return np.max(np.abs(r)) / scale
+
+
+def test_corrected_state_satisfies_2d_constraint():
+    """After one NH step the corrected (h, hu, hv, hw) satisfy the 2D
+    constraint (Eq. 4 with gradients) up to the truncation error of the
+    central differences: the residual falls by ~4 per halving of dx, while
+    the predicted state violates it at O(1)."""
+    coarse = _constraint_residual(_smooth_step_2d(48))
+    fine = _constraint_residual(_smooth_step_2d(96))
+    assert fine < 0.03, fine
+    assert 3.5 < coarse / fine < 4.5, (coarse, fine)
+    s = _smooth_step_2d(48)
+    pred = dict(s)
+    pred.update(h=s["ht"], hu=s["phi_terms"][1], hv=s["phi_terms"][2], hw=s["hwt"])
+    assert _constraint_residual(pred) > 5 * coarse
+
+
+def test_rho_independent_2d():
+    a = _smooth_step_2d(32, rho=1000.0)
+    b = _smooth_step_2d(32, rho=1.0)
+    for k in ("h", "hu", "hv", "hw"):
+        assert np.allclose(a[k], b[k], rtol=1e-11, atol=1e-15)
+    assert np.allclose(a["q"], 1000.0 * b["q"], rtol=1e-9)
+
+
+def test_mask_moore_enlargement():
+    """Marked cells grow to their 3 x 3 Moore neighbourhood (enlarge = 1), and
+    not beyond a wall."""
+    nx, ny = 9, 7
+    d0 = np.full((ny, nx), 2.0)
+    h = d0.copy()
+    h[3, 4] += 0.01        # |eta/d| = 5e-3 at (4, 3)
+    h[0, 8] += 0.01        # corner cell (8, 0)
+    z = np.zeros((ny, nx))
+    p = _p2(nx, ny, 0.5, 0.5, crit=O.CRIT_ETA_D, knh=1e-3, enlarge=0)
+    m = O2.mask(p, d0, 0.0, 3, h, z, z, z)
+    assert sorted(zip(*np.nonzero(m))) == [(0, 8), (3, 4)]
+    p.enlarge = 1
+    m = O2.mask(p, d0, 0.0, 3, h, z, z, z)
+    expect = {(j, i) for j in range(2, 5) for i in range(3, 6)} | {(0, 7), (0, 8), (1, 7), (1, 8)}
+    assert set(zip(*np.nonzero(m))) == expect
