@@ -1,0 +1,92 @@
+/* nhswe2d.h -- the method on a two-dimensional grid (FP64).
+ *
+ * The paper's model is one-dimensional (Sec. 2) and names the extension to
+ * two horizontal dimensions as future work (Sec. 6).  These calls run its
+ * generalisation in which every x-derivative of Eqs. 1-5 and 10-11 becomes a
+ * gradient: a hydrostatic Heun predictor (Eqs. 8-9) with Rusanov fluxes in x
+ * and y, the criteria of Sec. 5.1 in their 2D form (|eta/d|, |grad eta|,
+ * |u|, |grad u|, |w|, |grad w|), enlargement to the Moore neighbourhood
+ * (Sec. 5.2), and the projection (Eqs. 10-11), whose elimination into the
+ * constraint (Eq. 4) gives the self-adjoint equation
+ *     -div(K grad q) + gamma q = R,  K = (dt/rho)/h (I - grad d grad d^T / D),
+ *     D = 4 + |grad d|^2, q = h p,
+ * on the marked cells (q = 0 elsewhere and outside walled sides), discretised
+ * with a symmetric 9-point stencil and solved by CG preconditioned with exact
+ * x-line (tridiagonal) solves.  A problem that does not depend on y gives the
+ * 1D method's result.
+ *
+ * Layout: host arrays are nx * ny FP64, row-major with x fastest (cell (i, j)
+ * at j * nx + i).  Device memory is the caller's workspace
+ * (nh2d_workspace_bytes, 256-byte aligned, alive until nh2d_destroy); the
+ * library allocates nothing.  Calls are ordered on the handle's stream;
+ * nh2d_step / nh2d_run synchronise it.  Errors as in nhswe.h: NH_ERR_ARG (bad
+ * argument), NH_ERR_CUDA, NH_ERR_NOT_CONVERGED / NH_ERR_NONFINITE (the step
+ * is not taken: the state stays at the last accepted step), NH_ERR_TIMEOUT,
+ * NH_ERR_STATE (no state set).
+ */
+#ifndef NHSWE2D_H
+#define NHSWE2D_H
+
+#include "nhswe.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nh_grid2d nh_grid2d;
+
+typedef struct {
+    int    nx, ny;       /* cells; 3 <= nx, ny; nx * ny <= 2^26                  */
+    int    bc_x, bc_y;   /* NH_BC_WALL or NH_BC_PERIODIC                         */
+    int    limiter;      /* NH_LIM_*                                              */
+    double dx, dy;       /* cell size (m)                                        */
+    double x0, y0;       /* lower-left corner: cell (i, j) centre at
+                            (x0 + (i + 1/2) dx, y0 + (j + 1/2) dy)                */
+    double g, rho;       /* gravity (m/s^2), density (kg/m^3)                    */
+} nh_grid2d_desc;
+
+/* Moving bottom (Sec. 4.2 form, elliptic mound): d(x, y, t) = d0(x, y) -
+   A exp(-((x - xc0 - s(t))/Lx)^2 - ((y - yc0)/Ly)^2), s = s0 ln cosh(t/t0). */
+typedef struct {
+    int    shape;        /* NH_SLIDE_NONE or NH_SLIDE_GAUSS_LNCOSH */
+    double A, Lx, Ly, xc0, yc0, s0, t0;
+} nh_slide2d_desc;
+
+size_t nh2d_workspace_bytes(const nh_grid2d_desc* desc);
+
+/* d0_host: static depth d0 (m, > 0), nx * ny values. */
+nh_status nh2d_create(const nh_grid2d_desc* desc, const double* d0_host, void* ws, size_t ws_bytes,
+                      void* stream, nh_grid2d** out);
+
+/* NULL: static bottom. */
+nh_status nh2d_set_bottom_motion(nh_grid2d* g, const nh_slide2d_desc* slide);
+
+/* As nh_set_criterion (NH_CRIT_*, k_nh > 0, 0 <= enlarge <= 16). */
+nh_status nh2d_set_criterion(nh_grid2d* g, int kind, double k_nh, int enlarge, int first_step_global);
+
+/* rtol: ||R - A q||_2 <= rtol ||R||_2; guess NH_GUESS_ZERO or NH_GUESS_PREV.
+   Defaults 1e-12, 20000, NH_GUESS_PREV.  A CG breakdown (indefinite
+   operator) is solved again by unpreconditioned BiCGStab. */
+nh_status nh2d_set_solver(nh_grid2d* g, double rtol, int max_iter, int guess);
+
+/* h > 0 (m), hu, hv, hw (m^2/s) at time t; clears the warm start. */
+nh_status nh2d_set_state(nh_grid2d* g, const double* h, const double* hu, const double* hv,
+                         const double* hw, double t);
+
+/* Any pointer may be NULL.  p_nh: non-hydrostatic pressure of the last step
+   (Pa; 0 on cells that were hydrostatic). */
+nh_status nh2d_get_state(nh_grid2d* g, double* h, double* hu, double* hv, double* hw, double* p_nh);
+
+/* Last step's non-hydrostatic mask (nx * ny bytes). */
+nh_status nh2d_get_mask(nh_grid2d* g, unsigned char* mask);
+
+/* info (may be NULL): as nh_step_info; mass = sum(h) dx dy. */
+nh_status nh2d_step(nh_grid2d* g, double dt, nh_step_info* info);
+nh_status nh2d_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* info);
+
+void nh2d_destroy(nh_grid2d* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NHSWE2D_H */

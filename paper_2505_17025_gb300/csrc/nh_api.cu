@@ -308,6 +308,7 @@ SolveArgs<T> solve_args(nh_grid* g, int lcur, const T* diag, const T* offl, cons
     a.s = (T*)g->s; a.t = (T*)g->t;
     a.r1 = (T*)g->r1; a.z = (T*)g->z; a.maxpb = g->maxpb;
     a.pf = g->pf; a.prb = g->prb; a.pf_stride = (size_t)g->nb * g->pitch;
+    a.n_ext = 0; a.ext_c = nullptr; a.ext_k = nullptr; a.ext_stride = 0;
     a.items = g->items; a.pitems = g->pitems;
     a.tc = nullptr;
     a.ms = g->ms; a.ctl = g->ctl; a.part = g->part; a.cnt = g->cnt;

@@ -726,6 +726,12 @@ struct SolveArgs {
     float2* pf;                // line preconditioner: PCR multipliers [kPcrLevels][nb * pitch]
     float* prb;                // line preconditioner: reciprocal final pivots [nb * pitch]
     size_t pf_stride;          // nb * pitch
+    // extra couplings of a row beyond its list neighbours (2D grids: S, N and
+    // the four diagonals); n_ext = 0 for 1D members
+    int n_ext;
+    const double* ext_c;       // [n_ext][nb * pitch] coefficients
+    const int* ext_k;          // [n_ext][nb * pitch] compact index of the neighbour, or -1
+    size_t ext_stride;         // nb * pitch
     int maxpb;                 // preconditioner blocks per member (upper bound)
     const int2* items; const int2* pitems;
     const TimeCtl* tc;         // captured runs: guess scale from tc->prev_ok
@@ -744,6 +750,20 @@ __device__ __forceinline__ T apply_row(const SolveArgs<T>& a, size_t mo, int k, 
     y += a.offl[mo + k] * xl;
     y += a.offr[mo + k] * xr;
     return y;
+}
+
+// Sum of the extra couplings of row k: sum_e c_e v(k_e), v(j) the vector's
+// value at compact index j (a callable).
+template <typename T, typename F>
+__device__ __forceinline__ T ext_terms(const SolveArgs<T>& a, size_t mo, int k, F v)
+{
+    T s = T(0);
+    for (int e = 0; e < a.n_ext; ++e) {
+        const size_t o = (size_t)e * a.ext_stride + mo + k;
+        const int j = a.ext_k[o];
+        if (j >= 0) s += T(a.ext_c[o]) * v(j);
+    }
+    return s;
 }
 
 // Shared prologue of the solve kernels: loop over (member, chunk) work items.
@@ -778,7 +798,10 @@ __global__ void __launch_bounds__(kChunk) k_solve_init(SolveArgs<T> a)
                 if (kl >= 0) xl = T(a.psi_prev[mo + a.list[mo + kl]] * sc);
                 if (kr >= 0) xr = T(a.psi_prev[mo + a.list[mo + kr]] * sc);
             }
-            const T rk = a.R[mo + k] - apply_row(a, mo, k, x0, xl, xr);
+            T ax = apply_row(a, mo, k, x0, xl, xr);
+            if (a.n_ext && sc != 0.0)
+                ax += ext_terms(a, mo, k, [&](int j) { return T(a.psi_prev[mo + a.list[mo + j]] * sc); });
+            const T rk = a.R[mo + k] - ax;
             a.x[mo + k] = x0;
             a.r[mo + k] = rk;
             a.p0[mo + k] = T(0);
@@ -926,7 +949,8 @@ __global__ void __launch_bounds__(kChunk) k_cg_a(SolveArgs<T> a)
             const T pk = a.r[mo + k] + beta * pold[mo + k];
             const T pl = kl >= 0 ? a.r[mo + kl] + beta * pold[mo + kl] : T(0);
             const T pr = kr >= 0 ? a.r[mo + kr] + beta * pold[mo + kr] : T(0);
-            const T qk = apply_row(a, mo, k, pk, pl, pr);
+            T qk = apply_row(a, mo, k, pk, pl, pr);
+            if (a.n_ext) qk += ext_terms(a, mo, k, [&](int j) { return a.r[mo + j] + beta * pold[mo + j]; });
             pnew[mo + k] = pk;
             a.q[mo + k] = qk;
             pq = (double)pk * (double)qk;
@@ -1001,7 +1025,9 @@ __global__ void __launch_bounds__(kChunk) k_bi_1(SolveArgs<T> a)
             const T pk = a.r[mo + k] + beta * (pold[mo + k] - omega * vold[mo + k]);
             const T pl = kl >= 0 ? a.r[mo + kl] + beta * (pold[mo + kl] - omega * vold[mo + kl]) : T(0);
             const T pr = kr >= 0 ? a.r[mo + kr] + beta * (pold[mo + kr] - omega * vold[mo + kr]) : T(0);
-            const T vk = apply_row(a, mo, k, pk, pl, pr);
+            T vk = apply_row(a, mo, k, pk, pl, pr);
+            if (a.n_ext)
+                vk += ext_terms(a, mo, k, [&](int j) { return a.r[mo + j] + beta * (pold[mo + j] - omega * vold[mo + j]); });
             pnew[mo + k] = pk;
             vnew[mo + k] = vk;
             rv = (double)a.rh[mo + k] * (double)vk;
@@ -1038,7 +1064,8 @@ __global__ void __launch_bounds__(kChunk) k_bi_2(SolveArgs<T> a)
             const T sk = a.r[mo + k] - alpha * v[mo + k];
             const T sl = kl >= 0 ? a.r[mo + kl] - alpha * v[mo + kl] : T(0);
             const T sr = kr >= 0 ? a.r[mo + kr] - alpha * v[mo + kr] : T(0);
-            const T tk = apply_row(a, mo, k, sk, sl, sr);
+            T tk = apply_row(a, mo, k, sk, sl, sr);
+            if (a.n_ext) tk += ext_terms(a, mo, k, [&](int j) { return a.r[mo + j] - alpha * v[mo + j]; });
             a.s[mo + k] = sk;
             a.t[mo + k] = tk;
             acc[0] = (double)tk * (double)sk;
@@ -1389,7 +1416,8 @@ __global__ void __launch_bounds__(kChunk) k_pcg_a(SolveArgs<T> a)
             else if (kl >= 0) pl = a.z[mo + kl] + beta * pold[mo + kl];
             if (kr == k + 1) pr = zp + beta * op;
             else if (kr >= 0) pr = a.z[mo + kr] + beta * pold[mo + kr];
-            const T qk = apply_row(a, mo, k, pk, pl, pr);
+            T qk = apply_row(a, mo, k, pk, pl, pr);
+            if (a.n_ext) qk += ext_terms(a, mo, k, [&](int j) { return a.z[mo + j] + beta * pold[mo + j]; });
             pnew[mo + k] = pk;
             a.q[mo + k] = qk;
             pq = (double)pk * (double)qk;
@@ -1483,7 +1511,8 @@ __device__ void pcg_member_local(const SolveArgs<T>& a, TP* sa, TP* sd, double* 
                 const T pk = pnew[mo + k];
                 const T pl = kl >= 0 ? pnew[mo + kl] : T(0);
                 const T pr = kr >= 0 ? pnew[mo + kr] : T(0);
-                const T qk = apply_row(a, mo, k, pk, pl, pr);
+                T qk = apply_row(a, mo, k, pk, pl, pr);
+                if (a.n_ext) qk += ext_terms(a, mo, k, [&](int j) { return pnew[mo + j]; });
                 a.q[mo + k] = qk;
                 v[0] += (double)pk * (double)qk;
             }
@@ -1583,7 +1612,8 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, 
                 else if (kl >= 0) pl = a.z[mo + kl] + beta * pold[mo + kl];
                 if (kr == k + 1) pr = zp + beta * op;
                 else if (kr >= 0) pr = a.z[mo + kr] + beta * pold[mo + kr];
-                const T qk = apply_row(a, mo, k, pk, pl, pr);
+                T qk = apply_row(a, mo, k, pk, pl, pr);
+                if (a.n_ext) qk += ext_terms(a, mo, k, [&](int j) { return a.z[mo + j] + beta * pold[mo + j]; });
                 pnew[mo + k] = pk;
                 a.q[mo + k] = qk;
                 pq += (double)pk * (double)qk;
@@ -1679,7 +1709,8 @@ __global__ void __launch_bounds__(kChunk) k_pbi_mv(SolveArgs<T> a, int which)
             const T xk = xin[mo + k];
             const T xl = kl >= 0 ? xin[mo + kl] : T(0);
             const T xr = kr >= 0 ? xin[mo + kr] : T(0);
-            const T yk = apply_row(a, mo, k, xk, xl, xr);
+            T yk = apply_row(a, mo, k, xk, xl, xr);
+            if (a.n_ext) yk += ext_terms(a, mo, k, [&](int j) { return xin[mo + j]; });
             yout[mo + k] = yk;
             if (which == 0) {
                 acc[0] = (double)a.rh[mo + k] * (double)yk;

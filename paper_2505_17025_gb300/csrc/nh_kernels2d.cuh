@@ -1,0 +1,573 @@
+// nh_kernels2d.cuh -- kernels of the two-dimensional grid (FP64).
+//
+//  k2_depth      bottom depth d = d0 - mound at one time               (a1)
+//  k2_stage      one Heun stage of the hydrostatic predictor: x and y
+//                Rusanov fluxes of MUSCL states, well-balanced sources    (a2)
+//  k2_marks      criterion of Sec. 5.1 (2D form) on the predicted state  (a3)
+//  k2_dilate     Moore enlargement of the marks                          (a3)
+//  k2_count / k2_scan / k2_emit   row-major compaction into the active
+//                list and the cell -> list-index map                      (a3)
+//  k2_assemble   9-point rows of -div(K grad psi) + gamma psi = R        (a4)
+//  k2_correct    Eqs. 10-11 in 2D on the active cells                    (a6)
+// The Krylov solve (a5) is the 1D members' (nh_kernels1d.cuh) on one member
+// holding all active cells in row-major order: the W / E neighbours are the
+// list neighbours (so the line preconditioner solves x-lines), S, N and the
+// four diagonal couplings are the solver's extra couplings.
+//
+// The 2D equations generalise the paper's 1D Eqs. 1-5 and 10-11 by replacing
+// x-derivatives with gradients; the elimination of the corrected momenta into
+// the constraint (Eq. 4) gives -div(K grad q) + gamma q = R with the tensor
+// K = (a/h)(I - grad d grad d^T / D), D = 4 + |grad d|^2.  Here psi = a q
+// (a = dt / rho), so the stored K, beta and gamma carry no factor a and the
+// stored phi is a phi.
+#pragma once
+
+#include "nh_kernels1d.cuh"
+
+namespace nh {
+
+struct Geo2 {
+    int nx, ny, bcx, bcy, lim;
+    double dx, dy, x0, y0, g;
+};
+
+// 2D slide: mound A exp(-xi^2 - zeta^2), xi = (x - xc0 - s)/Lx, zeta = (y - yc0)/Ly.
+struct Slide2 {
+    double A, Lx, Ly, xc0, yc0;
+    int shape, pad;
+};
+
+// Slide position, velocity and acceleration at one time.
+struct Kin2 {
+    double s, sd, sdd;
+};
+
+__device__ __forceinline__ int g2_index1(int bc, int n, int i, double* odd)
+{
+    *odd = 1.0;
+    if (i >= 0 && i < n) return i;
+    if (bc == NH_BC_PERIODIC) return ((i % n) + n) % n;
+    *odd = -1.0;
+    return (i < 0) ? (-1 - i) : (2 * n - 1 - i);
+}
+
+// Flat index of the in-domain (mirrored / wrapped) cell of (i, j) and the
+// parities of quantities odd in x and in y.
+__device__ __forceinline__ int g2_cell(const Geo2& G, int i, int j, double* ox, double* oy)
+{
+    const int ci = g2_index1(G.bcx, G.nx, i, ox);
+    const int cj = g2_index1(G.bcy, G.ny, j, oy);
+    return cj * G.nx + ci;
+}
+
+// Flat index of the unknown at (i, j), or -1 outside a walled side.
+__device__ __forceinline__ int g2_inner(const Geo2& G, int i, int j)
+{
+    if (i < 0 || i >= G.nx) {
+        if (G.bcx != NH_BC_PERIODIC) return -1;
+        i = ((i % G.nx) + G.nx) % G.nx;
+    }
+    if (j < 0 || j >= G.ny) {
+        if (G.bcy != NH_BC_PERIODIC) return -1;
+        j = ((j % G.ny) + G.ny) % G.ny;
+    }
+    return j * G.nx + i;
+}
+
+// Mound height at cell (i, j) for slide position s.
+__device__ __forceinline__ double mound2(const Geo2& G, const Slide2& S, int i, int j, double s)
+{
+    if (S.shape != NH_SLIDE_GAUSS_LNCOSH) return 0.0;
+    const double x = G.x0 + (i + 0.5) * G.dx, y = G.y0 + (j + 0.5) * G.dy;
+    const double xi = (x - S.xc0 - s) / S.Lx, ze = (y - S.yc0) / S.Ly;
+    return S.A * exp(-xi * xi - ze * ze);
+}
+
+// d, d_x, d_y, d_xx, d_yy, d_xy, d_t, d_xt, d_yt, d_tt at cell (i, j):
+// central differences of d0 (mirrored / wrapped neighbours) and the mound's
+// terms by the chain rule (dxi/dt = -s'/Lx).
+__device__ __forceinline__ void bottom2(const Geo2& G, const double* __restrict__ d0, const Slide2& S,
+                                        const Kin2& K, int i, int j, double out[10])
+{
+    double o1, o2;
+    const double dx = G.dx, dy = G.dy;
+    const double c = d0[j * G.nx + i];
+    const double xm = d0[g2_cell(G, i - 1, j, &o1, &o2)], xp = d0[g2_cell(G, i + 1, j, &o1, &o2)];
+    const double ym = d0[g2_cell(G, i, j - 1, &o1, &o2)], yp = d0[g2_cell(G, i, j + 1, &o1, &o2)];
+    const double mm = d0[g2_cell(G, i - 1, j - 1, &o1, &o2)], pm = d0[g2_cell(G, i + 1, j - 1, &o1, &o2)];
+    const double mp = d0[g2_cell(G, i - 1, j + 1, &o1, &o2)], pp = d0[g2_cell(G, i + 1, j + 1, &o1, &o2)];
+    double d = c;
+    double d_x = (xp - xm) / (2.0 * dx), d_y = (yp - ym) / (2.0 * dy);
+    double d_xx = (xp - 2.0 * c + xm) / (dx * dx), d_yy = (yp - 2.0 * c + ym) / (dy * dy);
+    double d_xy = (pp - pm - mp + mm) / (4.0 * dx * dy);
+    double d_t = 0.0, d_xt = 0.0, d_yt = 0.0, d_tt = 0.0;
+    if (S.shape == NH_SLIDE_GAUSS_LNCOSH) {
+        const double x = G.x0 + (i + 0.5) * dx, y = G.y0 + (j + 0.5) * dy;
+        const double Lx = S.Lx, Ly = S.Ly, sd = K.sd, sdd = K.sdd;
+        const double xi = (x - S.xc0 - K.s) / Lx, ze = (y - S.yc0) / Ly;
+        const double m = S.A * exp(-xi * xi - ze * ze);
+        const double m_x = m * (-2.0 * xi / Lx), m_y = m * (-2.0 * ze / Ly);
+        const double m_xx = m * (4.0 * xi * xi - 2.0) / (Lx * Lx);
+        const double m_yy = m * (4.0 * ze * ze - 2.0) / (Ly * Ly);
+        const double m_xy = m * (4.0 * xi * ze) / (Lx * Ly);
+        const double m_t = m * (2.0 * xi / Lx) * sd;
+        const double m_xt = -m * (2.0 / (Lx * Lx)) * (2.0 * xi * xi - 1.0) * sd;
+        const double m_yt = -m * (4.0 * xi * ze / (Lx * Ly)) * sd;
+        const double m_tt = m * (2.0 / (Lx * Lx)) * ((2.0 * xi * xi - 1.0) * sd * sd + xi * Lx * sdd);
+        d -= m; d_x -= m_x; d_y -= m_y; d_xx -= m_xx; d_yy -= m_yy; d_xy -= m_xy;
+        d_t = -m_t; d_xt = -m_xt; d_yt = -m_yt; d_tt = -m_tt;
+    }
+    out[0] = d; out[1] = d_x; out[2] = d_y; out[3] = d_xx; out[4] = d_yy; out[5] = d_xy;
+    out[6] = d_t; out[7] = d_xt; out[8] = d_yt; out[9] = d_tt;
+}
+
+static __global__ void k2_depth(Geo2 G, const double* __restrict__ d0, Slide2 S, double s, double* d)
+{
+    const int N = G.nx * G.ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+        d[c] = d0[c] - mound2(G, S, c % G.nx, c / G.nx, s);
+}
+
+__device__ __forceinline__ double slope2(int lim, double vm, double v0, double vp)
+{
+    return limited_slope(lim, vm, v0, vp);
+}
+
+// Rusanov flux normal to a face of (hun, hun un + g h^2/2, hun ut, hun w) from
+// left / right (h, un, ut, w).
+__device__ __forceinline__ void rusanov2(double g, double hL, double nL, double tL, double wL,
+                                         double hR, double nR, double tR, double wR, double F[4])
+{
+    const double FL0 = hL * nL, FL1 = hL * nL * nL + 0.5 * g * hL * hL, FL2 = hL * nL * tL, FL3 = hL * nL * wL;
+    const double FR0 = hR * nR, FR1 = hR * nR * nR + 0.5 * g * hR * hR, FR2 = hR * nR * tR, FR3 = hR * nR * wR;
+    const double sL = fabs(nL) + sqrt(g * hL), sR = fabs(nR) + sqrt(g * hR);
+    const double s = (sL > sR) ? sL : sR;
+    F[0] = 0.5 * (FL0 + FR0) - 0.5 * s * (hR - hL);
+    F[1] = 0.5 * (FL1 + FR1) - 0.5 * s * (hR * nR - hL * nL);
+    F[2] = 0.5 * (FL2 + FR2) - 0.5 * s * (hR * tR - hL * tL);
+    F[3] = 0.5 * (FL3 + FR3) - 0.5 * s * (hR * wR - hL * wL);
+}
+
+struct StageArgs {
+    Geo2 G;
+    const double *h, *hu, *hv, *hw;        // state the rate is evaluated on
+    const double* d;                       // depth at that state's time
+    const double *h0, *hu0, *hv0, *hw0;    // Q^n
+    double *k1h, *k1u, *k1v, *k1w;         // stage-1 rates (written at stage 1, read at stage 2)
+    double *oh, *ohu, *ohv, *ohw;          // output: Q* (stage 1) or Q~ (stage 2)
+    double dt;
+    int stage;
+};
+
+// One direction's contribution to the rates of cell (i, j): flux divergence
+// and, for the normal momentum, the bottom source g h_mean (d_{+1/2} -
+// d_{-1/2}) / ds with the depth continuous at faces.
+__device__ __forceinline__ void stage_dir(const StageArgs& a, int i, int j, int dir, double r[4])
+{
+    const Geo2& G = a.G;
+    double eta[5], un[5], ut[5], w[5], dd[5];
+    for (int m = 0; m < 5; ++m) {
+        double ox, oy;
+        const int c = dir == 0 ? g2_cell(G, i + m - 2, j, &ox, &oy) : g2_cell(G, i, j + m - 2, &ox, &oy);
+        const double hc = a.h[c];
+        dd[m] = a.d[c];
+        eta[m] = hc - dd[m];
+        const double u = ox * a.hu[c] / hc, v = oy * a.hv[c] / hc;
+        un[m] = dir == 0 ? u : v;
+        ut[m] = dir == 0 ? v : u;
+        w[m] = a.hw[c] / hc;
+    }
+    double se[3], sn[3], st[3], sw[3];
+    for (int q = 0; q < 3; ++q) {   // slopes of cells -1, 0, +1
+        se[q] = slope2(G.lim, eta[q], eta[q + 1], eta[q + 2]);
+        sn[q] = slope2(G.lim, un[q], un[q + 1], un[q + 2]);
+        st[q] = slope2(G.lim, ut[q], ut[q + 1], ut[q + 2]);
+        sw[q] = slope2(G.lim, w[q], w[q + 1], w[q + 2]);
+    }
+    double F[2][4], df[2];
+    for (int f = 0; f < 2; ++f) {   // face f: between cells f-1 and f (relative)
+        const int L = f, R = f + 1;  // indices into the slope arrays (cell -1 + f, cell f)
+        df[f] = 0.5 * (dd[L + 1] + dd[R + 1]);
+        const double hL = eta[L + 1] + 0.5 * se[L] + df[f];
+        const double hR = eta[R + 1] - 0.5 * se[R] + df[f];
+        rusanov2(G.g, hL, un[L + 1] + 0.5 * sn[L], ut[L + 1] + 0.5 * st[L], w[L + 1] + 0.5 * sw[L],
+                 hR, un[R + 1] - 0.5 * sn[R], ut[R + 1] - 0.5 * st[R], w[R + 1] - 0.5 * sw[R], F[f]);
+    }
+    const double ds = dir == 0 ? G.dx : G.dy;
+    const double hplus = eta[2] - 0.5 * se[1] + df[0];
+    const double hminus = eta[2] + 0.5 * se[1] + df[1];
+    const double S = G.g * 0.5 * (hplus + hminus) * (df[1] - df[0]) / ds;
+    r[0] = -(F[1][0] - F[0][0]) / ds;
+    r[1] = -(F[1][1] - F[0][1]) / ds + S;   // normal momentum
+    r[2] = -(F[1][2] - F[0][2]) / ds;       // tangential momentum
+    r[3] = -(F[1][3] - F[0][3]) / ds;
+}
+
+static __global__ void k2_stage(StageArgs a)
+{
+    const int N = a.G.nx * a.G.ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int i = c % a.G.nx, j = c / a.G.nx;
+        double rx[4], ry[4];
+        stage_dir(a, i, j, 0, rx);
+        stage_dir(a, i, j, 1, ry);
+        double rh = 0.0, ru = 0.0, rv = 0.0, rw = 0.0;
+        rh += rx[0]; ru += rx[1]; rv += rx[2]; rw += rx[3];
+        rh += ry[0]; rv += ry[1]; ru += ry[2]; rw += ry[3];
+        if (a.stage == 1) {
+            a.k1h[c] = rh; a.k1u[c] = ru; a.k1v[c] = rv; a.k1w[c] = rw;
+            a.oh[c] = a.h0[c] + a.dt * rh;
+            a.ohu[c] = a.hu0[c] + a.dt * ru;
+            a.ohv[c] = a.hv0[c] + a.dt * rv;
+            a.ohw[c] = a.hw0[c] + a.dt * rw;
+        } else {
+            a.oh[c] = a.h0[c] + 0.5 * a.dt * (a.k1h[c] + rh);
+            a.ohu[c] = a.hu0[c] + 0.5 * a.dt * (a.k1u[c] + ru);
+            a.ohv[c] = a.hv0[c] + 0.5 * a.dt * (a.k1v[c] + rv);
+            a.ohw[c] = a.hw0[c] + 0.5 * a.dt * (a.k1w[c] + rw);
+        }
+    }
+}
+
+// Criterion (Sec. 5.1, 2D form: |eta/d|, |grad eta|, |u|, |grad u|
+// (Frobenius), |w|, |grad w|; central differences), strict > k_nh.
+static __global__ void k2_marks(Geo2 G, const double* __restrict__ h, const double* __restrict__ hu,
+                                const double* __restrict__ hv, const double* __restrict__ hw,
+                                const double* __restrict__ d, int crit, double knh, unsigned char* marks)
+{
+    const int N = G.nx * G.ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int i = c % G.nx, j = c / G.nx;
+        double o[4][2];
+        const int nb[4] = {g2_cell(G, i - 1, j, &o[0][0], &o[0][1]), g2_cell(G, i + 1, j, &o[1][0], &o[1][1]),
+                           g2_cell(G, i, j - 1, &o[2][0], &o[2][1]), g2_cell(G, i, j + 1, &o[3][0], &o[3][1])};
+        double eta[4], u[4], v[4], w[4];
+        for (int q = 0; q < 4; ++q) {
+            const int m = nb[q];
+            eta[q] = h[m] - d[m];
+            u[q] = o[q][0] * hu[m] / h[m];
+            v[q] = o[q][1] * hv[m] / h[m];
+            w[q] = hw[m] / h[m];
+        }
+        const double dk = d[c];
+        const double eta_k = h[c] - dk, uk = hu[c] / h[c], vk = hv[c] / h[c], wk = hw[c] / h[c];
+        const double ex = (eta[1] - eta[0]) / (2.0 * G.dx), ey = (eta[3] - eta[2]) / (2.0 * G.dy);
+        const double ux = (u[1] - u[0]) / (2.0 * G.dx), uy = (u[3] - u[2]) / (2.0 * G.dy);
+        const double vx = (v[1] - v[0]) / (2.0 * G.dx), vy = (v[3] - v[2]) / (2.0 * G.dy);
+        const double wx = (w[1] - w[0]) / (2.0 * G.dx), wy = (w[3] - w[2]) / (2.0 * G.dy);
+        double val;
+        switch (crit) {
+        case NH_CRIT_ETA_D: val = fabs(eta_k / dk); break;
+        case NH_CRIT_ETA_X: val = sqrt(ex * ex + ey * ey); break;
+        case NH_CRIT_U:     val = sqrt(uk * uk + vk * vk); break;
+        case NH_CRIT_U_X:   val = sqrt(ux * ux + uy * uy + vx * vx + vy * vy); break;
+        case NH_CRIT_W:     val = fabs(wk); break;
+        case NH_CRIT_W_X:   val = sqrt(wx * wx + wy * wy); break;
+        default:            val = 0.0; break;
+        }
+        marks[c] = val > knh ? 1 : 0;
+    }
+}
+
+// Moore enlargement of radius e (walls stop it, periodic sides wrap).
+static __global__ void k2_dilate(Geo2 G, const unsigned char* __restrict__ marks, int e, unsigned char* act)
+{
+    const int N = G.nx * G.ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int i = c % G.nx, j = c / G.nx;
+        unsigned char m = 0;
+        for (int b = -e; b <= e && !m; ++b)
+            for (int a2 = -e; a2 <= e; ++a2) {
+                const int q = g2_inner(G, i + a2, j + b);
+                if (q >= 0 && marks[q]) { m = 1; break; }
+            }
+        act[c] = m;
+    }
+}
+
+constexpr int kCompact2 = 1024;   // cells per compaction block
+
+static __global__ void __launch_bounds__(kCompact2) k2_count(const unsigned char* __restrict__ act, int N, int* cnt)
+{
+    __shared__ int s[32];
+    const int c = blockIdx.x * kCompact2 + threadIdx.x;
+    const int v = (c < N && act[c]) ? 1 : 0;
+    const int wsum = __popc(__ballot_sync(0xffffffffu, v));
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int q = 0; q < kCompact2 / 32; ++q) t += s[q];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the block counts (one CTA); the member's solver state is
+// reset as the 1D compaction does, with n_active = the total.
+static __global__ void __launch_bounds__(1024) k2_scan(const int* __restrict__ cnt, int nblk, int* off, int* nact,
+                                                       MState* ms)
+{
+    __shared__ int s_w[32];
+    __shared__ int s_base;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblk; b0 += 1024) {
+        const int b = b0 + tid;
+        const int v = b < nblk ? cnt[b] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int x = s_w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            s_w[lane] = x;
+        }
+        __syncthreads();
+        if (b < nblk) off[b] = s_base + incl - v + (wid > 0 ? s_w[wid - 1] : 0);
+        __syncthreads();
+        if (tid == 0) s_base += s_w[31];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int n = s_base;
+        *nact = n;
+        MState s;
+        s.bnorm2 = 0.0; s.bnorm = 0.0; s.rr = 0.0; s.alpha = 1.0; s.beta = 0.0; s.omega = 1.0;
+        s.rel_res = 0.0; s.min_gamma = 0.0; s.snorm = 0.0; s.rz = 0.0;
+        s.status = NH_OK; s.iters = 0; s.done = (n == 0); s.kind = -1; s.zero_sol = 0;
+        s.s_conv = 0; s.n_active = n; s.nchunks = (n + kChunk - 1) / kChunk;
+        s.auto_kind = 0; s.npb = (n + kPcrRows - 1) / kPcrRows; s.ioff = 0; s.poff = 0;
+        ms[0] = s;
+    }
+}
+
+// list[k] = k-th active cell in row-major order; inv[c] = k, or -1.
+static __global__ void __launch_bounds__(kCompact2) k2_emit(const unsigned char* __restrict__ act, int N,
+                                                           const int* __restrict__ off, int* list, int* inv)
+{
+    __shared__ int s_w[32];
+    const int c = blockIdx.x * kCompact2 + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool v = c < N && act[c];
+    const unsigned bal = __ballot_sync(0xffffffffu, v);
+    if (lane == 0) s_w[wid] = __popc(bal);
+    __syncthreads();
+    if (wid == 0) {
+        int x = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        s_w[lane] = x;   // inclusive
+    }
+    __syncthreads();
+    if (c < N) {
+        if (v) {
+            const int k = off[blockIdx.x] + (wid > 0 ? s_w[wid - 1] : 0) + __popc(bal & ((1u << lane) - 1u));
+            list[k] = c;
+            inv[c] = k;
+        } else {
+            inv[c] = -1;
+        }
+    }
+}
+
+// Per-cell quantities of the elliptic equation (psi form).
+struct CellQ2 {
+    double h, Kxx, Kyy, Kxy, bx, by, Vx, Vy, U0, V0, phi, d_x, d_y, d_t, G, D;
+};
+
+struct Asm2Args {
+    Geo2 G;
+    const double *ht, *hut, *hvt, *hwt;    // Q~
+    const double* d0;
+    const double* d1;                      // depth at t^{n+1}
+    Slide2 S; Kin2 K;                      // bottom motion at t^{n+1}
+    double dt;
+    const int* list; const int* inv;
+    MState* ms;
+    double *diag, *offl, *offr, *R;
+    int *nbl, *nbr;
+    double* ext_c; int* ext_k; size_t ext_stride;   // S, N, SW, SE, NW, NE
+    double *c6, *cx, *cy, *phi, *ddx, *ddy;
+    double* part; int* cnt;
+    int solver;
+    const int2* items; const Ctl* ctl;
+};
+
+__device__ __forceinline__ CellQ2 cell_q2(const Asm2Args& a, int i, int j)
+{
+    const Geo2& G = a.G;
+    double b[10], o1, o2;
+    bottom2(G, a.d0, a.S, a.K, i, j, b);
+    const int kw = g2_cell(G, i - 1, j, &o1, &o2), ke = g2_cell(G, i + 1, j, &o1, &o2);
+    const int ks = g2_cell(G, i, j - 1, &o1, &o2), kn = g2_cell(G, i, j + 1, &o1, &o2);
+    const double eta_x = ((a.ht[ke] - a.d1[ke]) - (a.ht[kw] - a.d1[kw])) / (2.0 * G.dx);
+    const double eta_y = ((a.ht[kn] - a.d1[kn]) - (a.ht[ks] - a.d1[ks])) / (2.0 * G.dy);
+    const int k = j * G.nx + i;
+    CellQ2 q;
+    q.h = a.ht[k];
+    const double u = a.hut[k] / q.h, v = a.hvt[k] / q.h;
+    q.d_x = b[1]; q.d_y = b[2]; q.d_t = b[6];
+    const double d_xx = b[3], d_yy = b[4], d_xy = b[5], d_xt = b[7], d_yt = b[8], d_tt = b[9];
+    q.G = q.d_x * q.d_x + q.d_y * q.d_y;
+    q.D = 4.0 + q.G;
+    q.phi = a.dt * q.h / q.D * (G.g * (q.d_x * eta_x + q.d_y * eta_y) - d_tt - 2.0 * (u * d_xt + v * d_yt)
+                                 - (u * u * d_xx + 2.0 * u * v * d_xy + v * v * d_yy));
+    q.Kxx = 1.0 / q.h * (1.0 - q.d_x * q.d_x / q.D);
+    q.Kyy = 1.0 / q.h * (1.0 - q.d_y * q.d_y / q.D);
+    q.Kxy = -1.0 / q.h * q.d_x * q.d_y / q.D;
+    q.bx = 6.0 * q.d_x / (q.h * q.h * q.D);
+    q.by = 6.0 * q.d_y / (q.h * q.h * q.D);
+    q.U0 = a.hut[k] + q.phi * q.d_x;
+    q.V0 = a.hvt[k] + q.phi * q.d_y;
+    q.Vx = q.U0 / q.h;
+    q.Vy = q.V0 / q.h;
+    return q;
+}
+
+// The same seen from a neighbour: mirrored cells flip their odd components.
+__device__ __forceinline__ CellQ2 cell_q2_at(const Asm2Args& a, int i, int j)
+{
+    double ox, oy;
+    const int c = g2_cell(a.G, i, j, &ox, &oy);
+    CellQ2 q = cell_q2(a, c % a.G.nx, c / a.G.nx);
+    q.Kxy *= ox * oy;
+    q.bx *= ox; q.by *= oy;
+    q.Vx *= ox; q.Vy *= oy;
+    return q;
+}
+
+// Rows of the 9-point operator on the active cells (one member; work items
+// of kChunk list entries) and the member's ||R||^2 and min gamma.
+static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args a)
+{
+    __shared__ double red[64];
+    const Geo2& G = a.G;
+    const int n_items = a.ctl->n_items;
+    const double idx2 = 1.0 / (G.dx * G.dx), idy2 = 1.0 / (G.dy * G.dy), ixy = 1.0 / (4.0 * G.dx * G.dy);
+    for (int wi = blockIdx.x; wi < n_items; wi += gridDim.x) {
+        const int2 itm = a.items[wi];
+        const int b = itm.x, jj = itm.y;
+        const int n = a.ms[b].n_active, nch = a.ms[b].nchunks, ioff = a.ms[b].ioff;
+        const int k = jj * kChunk + threadIdx.x;
+        double r2 = 0.0, gmin = INFINITY;
+        if (k < n) {
+            const int c = a.list[k];
+            const int i = c % G.nx, j = c / G.nx;
+            const CellQ2 q = cell_q2(a, i, j);
+            const CellQ2 W = cell_q2_at(a, i - 1, j), E = cell_q2_at(a, i + 1, j);
+            const CellQ2 S = cell_q2_at(a, i, j - 1), N = cell_q2_at(a, i, j + 1);
+            const double Kw = 0.5 * (W.Kxx + q.Kxx), Ke = 0.5 * (q.Kxx + E.Kxx);
+            const double Ks = 0.5 * (S.Kyy + q.Kyy), Kn = 0.5 * (q.Kyy + N.Kyy);
+            const double div_beta = (E.bx - W.bx) / (2.0 * G.dx) + (N.by - S.by) / (2.0 * G.dy);
+            const double div_V = (E.Vx - W.Vx) / (2.0 * G.dx) + (N.Vy - S.Vy) / (2.0 * G.dy);
+            const double h = q.h, h2 = h * h;
+            const double gam = div_beta + 12.0 * (1.0 + q.G) / (h2 * h * q.D);
+            const double Rk = -(div_V + 2.0 * (q.d_x * q.U0 + q.d_y * q.V0) / h2 + 2.0 * a.hwt[c] / h2
+                                + 2.0 * q.phi / h2 + 2.0 * q.d_t / h);
+            const double cW = -Kw * idx2, cE = -Ke * idx2, cS = -Ks * idy2, cN = -Kn * idy2;
+            const double cNE = -(E.Kxy + N.Kxy) * ixy, cSW = -(W.Kxy + S.Kxy) * ixy;
+            const double cSE = (E.Kxy + S.Kxy) * ixy, cNW = (W.Kxy + N.Kxy) * ixy;
+            auto nbk = [&](int di, int dj) {
+                const int qc = g2_inner(G, i + di, j + dj);
+                return qc >= 0 ? a.inv[qc] : -1;
+            };
+            const int kW = nbk(-1, 0), kE = nbk(1, 0);
+            const int ke[6] = {nbk(0, -1), nbk(0, 1), nbk(-1, -1), nbk(1, -1), nbk(-1, 1), nbk(1, 1)};
+            const double ce[6] = {cS, cN, cSW, cSE, cNW, cNE};
+            a.diag[k] = (Kw + Ke) * idx2 + (Ks + Kn) * idy2 + gam;
+            a.offl[k] = kW >= 0 ? cW : 0.0;
+            a.offr[k] = kE >= 0 ? cE : 0.0;
+            a.nbl[k] = kW;
+            a.nbr[k] = kE;
+            for (int e = 0; e < 6; ++e) {
+                a.ext_c[e * a.ext_stride + k] = ke[e] >= 0 ? ce[e] : 0.0;
+                a.ext_k[e * a.ext_stride + k] = ke[e];
+            }
+            a.R[k] = Rk;
+            a.c6[k] = 6.0 / (h * q.D);
+            a.cx[k] = q.d_x / q.D;
+            a.cy[k] = q.d_y / q.D;
+            a.phi[k] = q.phi;
+            a.ddx[k] = q.d_x;
+            a.ddy[k] = q.d_y;
+            r2 = Rk * Rk;
+            gmin = gam;
+        }
+        double v[1] = {r2};
+        block_sum<1>(v, red);
+        const double gm = block_min(gmin, red);
+        double* P0 = a.part;
+        double* P1 = a.part + nch;   // one member: its nch items are items 0 .. nch-1
+        if (threadIdx.x == 0) { P0[wi] = v[0]; P1[wi] = gm; }
+        if (arrive_last(a.cnt, b, nch)) {
+            const double bn2 = member_sum(P0 + ioff, nch, red);
+            const double gmn = member_min(P1 + ioff, nch, red);
+            if (threadIdx.x == 0) {
+                MState& s = a.ms[b];
+                s.bnorm2 = bn2;
+                s.bnorm = sqrt(bn2);
+                s.min_gamma = gmn;
+                s.auto_kind = (a.solver == NH_SOLVER_AUTO);
+                s.kind = (a.solver == NH_SOLVER_BICGSTAB) ? NH_SOLVER_BICGSTAB : NH_SOLVER_CG;
+            }
+        }
+    }
+}
+
+struct Corr2Args {
+    Geo2 G;
+    int n;                       // active cells
+    const int* list;
+    const int* nbl; const int* nbr; const int* ext_k; size_t ext_stride;
+    const double* x;             // psi on the active cells
+    const double *c6, *cx, *cy, *phi, *ddx, *ddy;
+    const MState* ms;
+    double *hu, *hv, *hw;        // Q~, corrected in place
+    double* psi;                 // dense psi (warm start, pressure output)
+};
+
+// Eqs. 10-11 in 2D: with psi = a q, P = c6 psi + cx psi_x + cy psi_y + a phi;
+// U = U~ - grad psi + grad d P, hw = hw~ + P; psi = 0 off the mask.
+static __global__ void k2_correct(Corr2Args a)
+{
+    const bool zero = a.ms[0].zero_sol != 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
+        const int kw = a.nbl[k], ke = a.nbr[k];
+        const int ks = a.ext_k[k], kn = a.ext_k[a.ext_stride + k];
+        const double ps = zero ? 0.0 : a.x[k];
+        const double pw = (zero || kw < 0) ? 0.0 : a.x[kw], pe = (zero || ke < 0) ? 0.0 : a.x[ke];
+        const double pss = (zero || ks < 0) ? 0.0 : a.x[ks], pn = (zero || kn < 0) ? 0.0 : a.x[kn];
+        const double px = (pe - pw) / (2.0 * a.G.dx), py = (pn - pss) / (2.0 * a.G.dy);
+        const double P = a.c6[k] * ps + a.cx[k] * px + a.cy[k] * py + a.phi[k];
+        const int c = a.list[k];
+        a.hu[c] = a.hu[c] + (-px + a.ddx[k] * P);
+        a.hv[c] = a.hv[c] + (-py + a.ddy[k] * P);
+        a.hw[c] = a.hw[c] + P;
+        a.psi[c] = ps;
+    }
+}
+
+// Block partial sums of h (FP64).
+static __global__ void __launch_bounds__(256) k2_mass(const double* __restrict__ h, int N, double* part)
+{
+    __shared__ double red[32];
+    double v[1] = {0.0};
+    for (int c = blockIdx.x * 256 + threadIdx.x; c < N; c += gridDim.x * 256) v[0] += h[c];
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+}  // namespace nh

@@ -37,7 +37,10 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh_status_string", "nh_predict_static", "nh_workspace_bytes_ensemble", "nh_create_ensemble",
            "nh_set_run_mode", "nh_set_tile", "nh_cnn_forward", "nh_cnn_workspace_bytes",
            "nh_cnn_loss_grad", "nh_cnn_adam", "nh_cnn_attach_bytes", "nh_cnn_attach",
-           "nh_cnn_set_params", "nh_cnn_record", "nh_cnn_harvest", "nh_cnn_choices")
+           "nh_cnn_set_params", "nh_cnn_record", "nh_cnn_harvest", "nh_cnn_choices",
+           "nh2d_workspace_bytes", "nh2d_create", "nh2d_set_bottom_motion", "nh2d_set_criterion",
+           "nh2d_set_solver", "nh2d_set_state", "nh2d_get_state", "nh2d_get_mask", "nh2d_step",
+           "nh2d_run", "nh2d_destroy")
 NH_CNN_PARAMS = 9328
 NH_CNN_IN = 16
 NH_STATIC_MAX_CELLS = 262144
@@ -65,6 +68,17 @@ class nh_step_info(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class nh_grid2d_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("bc_x", C.c_int), ("bc_y", C.c_int),
+                ("limiter", C.c_int), ("dx", C.c_double), ("dy", C.c_double), ("x0", C.c_double),
+                ("y0", C.c_double), ("g", C.c_double), ("rho", C.c_double)]
+
+
+class nh_slide2d_desc(C.Structure):
+    _fields_ = [("shape", C.c_int), ("A", C.c_double), ("Lx", C.c_double), ("Ly", C.c_double),
+                ("xc0", C.c_double), ("yc0", C.c_double), ("s0", C.c_double), ("t0", C.c_double)]
 
 
 class nh_run_info(C.Structure):
@@ -142,6 +156,22 @@ def load():
         L.nh_cnn_record.argtypes = [vp, C.c_int]
         L.nh_cnn_harvest.argtypes = [vp, vp, vp, vp, _D, C.POINTER(C.c_int)]
         L.nh_cnn_choices.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.nh2d_workspace_bytes.argtypes = [C.POINTER(nh_grid2d_desc)]
+        L.nh2d_workspace_bytes.restype = sz
+        L.nh2d_create.argtypes = [C.POINTER(nh_grid2d_desc), _D, vp, sz, vp, C.POINTER(C.c_void_p)]
+        L.nh2d_set_bottom_motion.argtypes = [vp, C.POINTER(nh_slide2d_desc)]
+        L.nh2d_set_criterion.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int]
+        L.nh2d_set_solver.argtypes = [vp, C.c_double, C.c_int, C.c_int]
+        L.nh2d_set_state.argtypes = [vp, _D, _D, _D, _D, C.c_double]
+        L.nh2d_get_state.argtypes = [vp, _D, _D, _D, _D, _D]
+        L.nh2d_get_mask.argtypes = [vp, C.POINTER(C.c_ubyte)]
+        L.nh2d_step.argtypes = [vp, C.c_double, C.POINTER(nh_step_info)]
+        L.nh2d_run.argtypes = [vp, C.c_double, C.c_longlong, C.POINTER(nh_run_info)]
+        L.nh2d_destroy.argtypes = [vp]
+        L.nh2d_destroy.restype = None
+        for f in ("nh2d_create", "nh2d_set_bottom_motion", "nh2d_set_criterion", "nh2d_set_solver",
+                  "nh2d_set_state", "nh2d_get_state", "nh2d_get_mask", "nh2d_step", "nh2d_run"):
+            getattr(L, f).restype = C.c_int
         L.nh_status_string.argtypes = [C.c_int]
         L.nh_status_string.restype = C.c_char_p
         for f in ("nh_create_grid", "nh_create_ensemble", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
@@ -455,6 +485,90 @@ def nh_cnn_adam(params, grad, m, v, step, lr):
         _params_check(t)
     _check(L.nh_cnn_adam(C.c_void_p(params.data_ptr()), C.c_void_p(grad.data_ptr()), C.c_void_p(m.data_ptr()),
                          C.c_void_p(v.data_ptr()), int(step), float(lr), _stream_ptr()), "nh_cnn_adam")
+
+
+class Grid2D:
+    """One 2D grid (nhswe2d.h).  Arrays are (ny, nx), x fastest; the workspace
+    is a torch.uint8 tensor on the current CUDA device."""
+
+    def __init__(self, nx, ny, dx, dy, d0, bc_x=NH_BC_WALL, bc_y=NH_BC_WALL, limiter=NH_LIM_CENTRAL,
+                 x0=0.0, y0=0.0, g=9.81, rho=1000.0, stream=None):
+        import torch
+        self.L = load()
+        self.nx, self.ny = int(nx), int(ny)
+        self.desc = nh_grid2d_desc(self.nx, self.ny, int(bc_x), int(bc_y), int(limiter), float(dx), float(dy),
+                                   float(x0), float(y0), float(g), float(rho))
+        n = self.L.nh2d_workspace_bytes(C.byref(self.desc))
+        if n == 0:
+            raise NHError(NH_ERR_ARG, "nh2d_workspace_bytes")
+        self.ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+        ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(self.L.nh2d_create(C.byref(self.desc), _dptr(self._f(d0)), C.c_void_p(ptr), C.c_size_t(n),
+                                  C.c_void_p(self.stream.cuda_stream), C.byref(h)), "nh2d_create")
+        self.h = h
+
+    def _f(self, a):
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (self.ny, self.nx)))
+        return a.reshape(-1)
+
+    def set_bottom_motion(self, slide=None):
+        if slide is None:
+            _check(self.L.nh2d_set_bottom_motion(self.h, None), "nh2d_set_bottom_motion")
+            return
+        s = nh_slide2d_desc(int(slide.get("shape", NH_SLIDE_GAUSS_LNCOSH)), float(slide["A"]), float(slide["Lx"]),
+                            float(slide["Ly"]), float(slide["xc0"]), float(slide["yc0"]), float(slide["s0"]),
+                            float(slide["t0"]))
+        _check(self.L.nh2d_set_bottom_motion(self.h, C.byref(s)), "nh2d_set_bottom_motion")
+
+    def set_criterion(self, kind, k_nh=1e-3, enlarge=1, first_step_global=False):
+        _check(self.L.nh2d_set_criterion(self.h, int(kind), float(k_nh), int(enlarge), int(bool(first_step_global))),
+               "nh2d_set_criterion")
+
+    def set_solver(self, rtol=1e-12, max_iter=20000, guess=NH_GUESS_PREV):
+        _check(self.L.nh2d_set_solver(self.h, float(rtol), int(max_iter), int(guess)), "nh2d_set_solver")
+
+    def set_state(self, h, hu, hv, hw, t=0.0):
+        a = [self._f(v) for v in (h, hu, hv, hw)]
+        _check(self.L.nh2d_set_state(self.h, *[_dptr(v) for v in a], float(t)), "nh2d_set_state")
+
+    def get_state(self):
+        n = self.nx * self.ny
+        out = [np.empty(n) for _ in range(5)]
+        _check(self.L.nh2d_get_state(self.h, *[_dptr(v) for v in out]), "nh2d_get_state")
+        return [v.reshape(self.ny, self.nx) for v in out]
+
+    def get_mask(self):
+        m = np.empty(self.nx * self.ny, dtype=np.uint8)
+        _check(self.L.nh2d_get_mask(self.h, m.ctypes.data_as(C.POINTER(C.c_ubyte))), "nh2d_get_mask")
+        return m.reshape(self.ny, self.nx)
+
+    def step(self, dt, check=True):
+        info = nh_step_info()
+        st = self.L.nh2d_step(self.h, float(dt), C.byref(info))
+        if check:
+            _check(st, "nh2d_step")
+        return st, info.as_dict()
+
+    def run(self, dt, n_steps, check=True):
+        info = nh_run_info()
+        st = self.L.nh2d_run(self.h, float(dt), int(n_steps), C.byref(info))
+        if check:
+            _check(st, "nh2d_run")
+        return st, {"steps": info.steps, "iters_total": info.iters_total,
+                    "active_total": info.active_total, "last": info.last.as_dict()}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.nh2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def grid_from_workload(wl, precision=NH_FP64, limiter=NH_LIM_CENTRAL, bc=None, **kw):

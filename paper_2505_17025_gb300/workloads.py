@@ -172,3 +172,66 @@ def standing_wave_1d(nx=128, depth=1.0, kh=1.0, amp=1e-4, modes=1, g=G):
     m = Member1D(nx=nx, dx=dx, xl=0.0, d0=np.full(nx, depth), h=h,
                  hu=np.zeros(nx), hw=np.zeros(nx))
     return m, k, length
+
+
+# ------------------------------------------------------------------- 2D grids
+
+@dataclass
+class Workload2D:
+    """One 2D grid: arrays (ny, nx), x fastest."""
+    name: str
+    nx: int
+    ny: int
+    dx: float
+    dy: float
+    d0: np.ndarray
+    h: np.ndarray
+    hu: np.ndarray
+    hv: np.ndarray
+    hw: np.ndarray
+    dt: float
+    bc_x: int = 0
+    bc_y: int = 0
+    amplitude: float = 0.0
+    slide: dict = None
+    meta: dict = field(default_factory=dict)
+
+
+def cfl_dt_2d(cfl, dx, dy, speed):
+    """dt = cfl / (speed (1/dx + 1/dy))."""
+    return cfl / (speed * (1.0 / dx + 1.0 / dy))
+
+
+def line_soliton_2d(nx=1024, ny=1024, dx=0.05, depth=1.0, a=0.2, x0=None, cfl=0.5, g=G):
+    """Line soliton (Eq. 18 in x, uniform in y) on a flat bottom, periodic in
+    x and y (default: h = 1 m, a/h = 0.2, 1024 x 1024 cells, dx = 0.05 m)."""
+    length = nx * dx
+    x0 = length / 4.0 if x0 is None else x0
+    x = (np.arange(nx) + 0.5) * dx
+    eta, u, hw = solitary_fields(x, 0.0, a, depth, x0, g)
+    h1 = depth + eta
+    tile = lambda v: np.tile(v, (ny, 1))
+    speed = float(np.max(np.abs(u) + np.sqrt(g * h1)))
+    dt = cfl_dt_2d(cfl, dx, dx, speed)
+    return Workload2D("line_soliton_2d", nx, ny, dx, dx, np.full((ny, nx), depth), tile(h1), tile(h1 * u),
+                      np.zeros((ny, nx)), tile(hw), dt, bc_x=1, bc_y=1, amplitude=a,
+                      meta={"depth": depth, "a": a, "x0": x0})
+
+
+def landslide_2d(n=2048, dx=0.02, h_min=0.1, h_max=2.0, slope=0.2, A=0.1, Lx=1.0, Ly=0.5, s0=2.0, t0=1.0,
+                 d_start=0.6, cfl=0.5, g=G):
+    """Elliptic Gaussian slide on a plane slope d0 = min(h_min + slope x, h_max)
+    (default: 2048 x 2048 cells, dx = 0.02 m, A = 0.1 m, Lx = 1 m, Ly = 0.5 m,
+    s0 = 2 m, t0 = 1 s), starting where d0 = d_start, centred in y; still
+    water, walls."""
+    x = (np.arange(n) + 0.5) * dx
+    d0 = np.tile(np.minimum(h_min + slope * x, h_max), (n, 1))
+    xc0 = (d_start - h_min) / slope
+    yc0 = n * dx / 2.0
+    X, Y = np.meshgrid(x, x)
+    h = d0 - A * np.exp(-((X - xc0) / Lx) ** 2 - ((Y - yc0) / Ly) ** 2)
+    dt = cfl_dt_2d(cfl, dx, dx, math.sqrt(g * h_max))
+    z = np.zeros((n, n))
+    return Workload2D("landslide_2d", n, n, dx, dx, d0, h, z, z.copy(), z.copy(), dt, amplitude=A,
+                      slide=dict(A=A, Lx=Lx, Ly=Ly, xc0=xc0, yc0=yc0, s0=s0, t0=t0),
+                      meta={"h_min": h_min, "h_max": h_max, "slope": slope})

@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a and exports every entry point that
-include/nhswe.h declares (no GPU needed: symbols only, no compute call)."""
+the headers in include/ declare (no GPU needed: symbols only, no compute
+call)."""
 import ctypes
 import os
 import re
@@ -16,7 +17,7 @@ def _declared():
         if f.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", f)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(nh_[a-z0-9_]+)\s*\(", txt))
+            names |= set(re.findall(r"\b(nh[a-z0-9]*_[a-z0-9_]+)\s*\(", txt))
     return names
 
 
@@ -47,3 +48,13 @@ def test_status_strings_need_no_gpu():
     lib.nh_status_string.restype = ctypes.c_char_p
     for s in range(7):
         assert lib.nh_status_string(s).startswith(b"NH_")
+
+
+def test_workspace_size_2d_needs_no_gpu():
+    lib = ctypes.CDLL(B.build())
+    lib.nh2d_workspace_bytes.argtypes = [ctypes.POINTER(nhswe.nh_grid2d_desc)]
+    lib.nh2d_workspace_bytes.restype = ctypes.c_size_t
+    d = nhswe.nh_grid2d_desc(1024, 1024, 1, 1, 1, 0.05, 0.05, 0.0, 0.0, 9.81, 1000.0)
+    assert lib.nh2d_workspace_bytes(ctypes.byref(d)) > 1024 * 1024 * 8 * 40
+    bad = nhswe.nh_grid2d_desc(2, 1024, 0, 0, 1, 0.05, 0.05, 0.0, 0.0, 9.81, 1000.0)   # nx < 3
+    assert lib.nh2d_workspace_bytes(ctypes.byref(bad)) == 0
