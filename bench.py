@@ -321,58 +321,90 @@ def time_network(wl, args):
             "launch": "C ABI nh_cnn_forward on preallocated buffers, back to back on one stream"}
 
 
+def _landslide_h(wl, t):
+    """Still water over the slide's position at time t."""
+    sl = wl.slide
+    s = sl["s0"] * math.log(math.cosh(t / sl["t0"]))
+    x = (np.arange(wl.nx) + 0.5) * wl.dx
+    y = (np.arange(wl.ny) + 0.5) * wl.dy
+    X, Y = np.meshgrid(x, y)
+    return wl.d0 - sl["A"] * np.exp(-((X - sl["xc0"] - s) / sl["Lx"]) ** 2 - ((Y - sl["yc0"]) / sl["Ly"]) ** 2)
+
+
 def run_2d(args):
     """The 2D workloads (not the default line): --workload line_soliton_2d
-    (1024^2 line soliton, periodic, a/h = 0.2) or landslide_2d (2048^2 slide on
-    a 0.2 slope, walls), adaptive |eta/d| > k (or --mode global), FP64,
-    cell-updates/s over --steps timed steps after --warmup."""
+    (1024^2 line soliton, periodic, a/h = 0.2), landslide_2d (2048^2 slide on
+    a 0.2 slope, walls) or landslide_ensemble_2d (32 uneven landslide runs of
+    256^2 to 1024^2 cells with drawn slope, A, L, s0, one handle), adaptive
+    |eta/d| > k (or --mode global), FP64, cell-updates/s over --steps timed
+    steps (captured-graph replays) after --warmup; a second pass of the same
+    steps enqueued step by step from the host is reported beside it."""
     import torch
     from paper_2505_17025_gb300 import nhswe as N
     from paper_2505_17025_gb300 import workloads as W
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     if args.workload == "line_soliton_2d":
-        wl = W.line_soliton_2d()
-        knh = 1e-3
-        t_start = 0.0
+        wls = [W.line_soliton_2d()]
+        dt = wls[0].dt
+        knh, t_start = 1e-3, 0.0
+        name = f"line_soliton_2d {wls[0].nx}x{wls[0].ny}, dx {wls[0].dx}"
+    elif args.workload == "landslide_2d":
+        wls = [W.landslide_2d()]
+        dt = wls[0].dt
+        knh, t_start = 1e-4, 0.3
+        name = f"landslide_2d {wls[0].nx}x{wls[0].ny}, dx {wls[0].dx}"
     else:
-        wl = W.landslide_2d()
-        knh = 1e-4
-        t_start = 0.3
-    G = N.Grid2D(wl.nx, wl.ny, wl.dx, wl.dy, wl.d0, bc_x=wl.bc_x, bc_y=wl.bc_y)
-    h = wl.h
-    if wl.slide:
-        G.set_bottom_motion(wl.slide)
-        sl = wl.slide
-        s = sl["s0"] * math.log(math.cosh(t_start / sl["t0"]))
-        x = (np.arange(wl.nx) + 0.5) * wl.dx
-        X, Y = np.meshgrid(x, x)
-        h = wl.d0 - sl["A"] * np.exp(-((X - sl["xc0"] - s) / sl["Lx"]) ** 2 - ((Y - sl["yc0"]) / sl["Ly"]) ** 2)
+        wls, dt = W.landslide_ensemble_2d()
+        knh, t_start = 1e-4, 0.3
+        sizes = sorted(w.nx for w in wls)
+        name = (f"landslide_ensemble_2d: {len(wls)} runs, n x n with n in [{sizes[0]}, {sizes[-1]}] "
+                f"(seed 0), 10.24 m basin, drawn slope/A/L/s0")
+    G = N.Grid2D.ensemble([dict(nx=w.nx, ny=w.ny, dx=w.dx, dy=w.dy, d0=w.d0, bc_x=w.bc_x, bc_y=w.bc_y)
+                           for w in wls])
+    for i, w in enumerate(wls):
+        h = w.h
+        if w.slide:
+            G.set_bottom_motion(w.slide, member=i)
+            h = _landslide_h(w, t_start)
+        G.set_state(h, w.hu, w.hv, w.hw, t=t_start, member=i)
     G.set_criterion(N.NH_CRIT_GLOBAL if args.mode == "global" else N.NH_CRIT_ETA_D, knh, 1)
     G.set_solver(1e-12, 20000, N.NH_GUESS_PREV)
-    G.set_state(h, wl.hu, wl.hv, wl.hw, t=t_start)
-    G.run(wl.dt, max(3, args.warmup))
+    warm = max(3, args.warmup)
+    G.run(dt, warm)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
     clocks.start()
     e0.record(G.stream)
-    st, info = G.run(wl.dt, args.steps)
+    st, info = G.run(dt, args.steps)
     e1.record(G.stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    cells = wl.nx * wl.ny
+    graph_runs = G.graph_runs
+    # the same number of further steps enqueued from the host, for comparison
+    G.set_graphs(False)
+    torch.cuda.synchronize()
+    e0.record(G.stream)
+    st2, info2 = G.run(dt, args.steps)
+    e1.record(G.stream)
+    torch.cuda.synchronize()
+    ms_host = e0.elapsed_time(e1)
+    cells = sum(w.nx * w.ny for w in wls)
     out = {"metric": METRIC, "value": cells * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+           "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{wl.name} {wl.nx}x{wl.ny}, dx {wl.dx}", "mode": args.mode,
-                      "k_nh": knh, "t_start": t_start,
+           "config": {"workload": name, "cells": cells, "members": len(wls), "mode": args.mode,
+                      "k_nh": knh, "t_start": t_start, "dt": dt,
                       "mean_active_cells_per_step": info["active_total"] / max(1, args.steps),
                       "mean_krylov_iters_per_step": info["iters_total"] / max(1, args.steps),
                       "l2": "state (4 x 8 B per cell) and solver arrays exceed the 129 MB L2; no flush"},
-           "clocks": clk, "timed_region": "nh2d_run, step by step (host-driven Krylov set-up)"}
+           "clocks": clk,
+           "timed_region": f"nh2d_run: captured-graph replays ({graph_runs} graph run(s) so far)",
+           "host_enqueued": {"ms_per_step": ms_host / args.steps,
+                             "mean_krylov_iters_per_step": info2["iters_total"] / max(1, args.steps)}}
     print(json.dumps(out))
     G.close()
 
@@ -552,7 +584,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=400)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--members", type=int, default=64)
-    ap.add_argument("--workload", default="slide_1d", choices=["slide_1d", "line_soliton_2d", "landslide_2d"])
+    ap.add_argument("--workload", default="slide_1d", choices=["slide_1d", "line_soliton_2d", "landslide_2d", "landslide_ensemble_2d"])
     ap.add_argument("--form-steps", type=int, default=30, help="timed steps per form (0: skip the comparison)")
     ap.add_argument("--form-harvest", type=int, default=20)
     ap.add_argument("--form-train", type=int, default=200)

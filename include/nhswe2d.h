@@ -15,10 +15,22 @@
  * x-line (tridiagonal) solves.  A problem that does not depend on y gives the
  * 1D method's result.
  *
+ * Ensembles: one handle may hold n_members grids, each with its own size,
+ * spacing, sides, static depth and slide (the drawn-parameter landslide runs
+ * of Sec. 4.2 side by side), stepped together with one dt and one criterion
+ * and solver setting.  Every kernel of a step covers all members; their
+ * Krylov solves share one cooperative launch, and nh2d_run replays the whole
+ * step from a captured CUDA graph.  A single grid is the one-member
+ * ensemble; the calls without "member" act on member 0 (set_bottom_motion:
+ * on all members).
+ *
  * Layout: host arrays are nx * ny FP64, row-major with x fastest (cell (i, j)
- * at j * nx + i).  Device memory is the caller's workspace
- * (nh2d_workspace_bytes, 256-byte aligned, alive until nh2d_destroy); the
- * library allocates nothing.  Calls are ordered on the handle's stream;
+ * at j * nx + i).  On the device member m's cells sit at m * pitch in every
+ * per-cell buffer, pitch = the largest member's cell count rounded up to 256.
+ * Device memory is the caller's workspace (nh2d_workspace_bytes /
+ * nh2d_ensemble_workspace_bytes, 256-byte aligned, alive until
+ * nh2d_destroy); the handle creates one extra (capture) stream and otherwise
+ * allocates no device memory.  Calls are ordered on the handle's stream;
  * nh2d_step / nh2d_run synchronise it.  Errors as in nhswe.h: NH_ERR_ARG (bad
  * argument), NH_ERR_CUDA, NH_ERR_NOT_CONVERGED / NH_ERR_NONFINITE (the step
  * is not taken: the state stays at the last accepted step), NH_ERR_TIMEOUT,
@@ -52,14 +64,26 @@ typedef struct {
     double A, Lx, Ly, xc0, yc0, s0, t0;
 } nh_slide2d_desc;
 
+/* 0 for an invalid description. */
 size_t nh2d_workspace_bytes(const nh_grid2d_desc* desc);
+
+/* 1 <= n_members <= 4096, n_members * pitch <= 2^28; 0 when invalid. */
+size_t nh2d_ensemble_workspace_bytes(int n_members, const nh_grid2d_desc* descs);
 
 /* d0_host: static depth d0 (m, > 0), nx * ny values. */
 nh_status nh2d_create(const nh_grid2d_desc* desc, const double* d0_host, void* ws, size_t ws_bytes,
                       void* stream, nh_grid2d** out);
 
-/* NULL: static bottom. */
+/* descs[m], d0_host[m]: member m's grid and static depth. */
+nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const double* const* d0_host,
+                               void* ws, size_t ws_bytes, void* stream, nh_grid2d** out);
+
+/* Number of members (0 for NULL). */
+int nh2d_members(const nh_grid2d* g);
+
+/* NULL: static bottom.  nh2d_set_bottom_motion sets every member's. */
 nh_status nh2d_set_bottom_motion(nh_grid2d* g, const nh_slide2d_desc* slide);
+nh_status nh2d_set_member_bottom_motion(nh_grid2d* g, int member, const nh_slide2d_desc* slide);
 
 /* As nh_set_criterion (NH_CRIT_*, k_nh > 0, 0 <= enlarge <= 16). */
 nh_status nh2d_set_criterion(nh_grid2d* g, int kind, double k_nh, int enlarge, int first_step_global);
@@ -69,20 +93,39 @@ nh_status nh2d_set_criterion(nh_grid2d* g, int kind, double k_nh, int enlarge, i
    operator) is solved again by unpreconditioned BiCGStab. */
 nh_status nh2d_set_solver(nh_grid2d* g, double rtol, int max_iter, int guess);
 
-/* h > 0 (m), hu, hv, hw (m^2/s) at time t; clears the warm start. */
+/* 1 (default): nh2d_run replays captured graphs when it can (not for a
+   first step that is global by request, nor right after a change of dt);
+   0: every step is enqueued from the host. */
+nh_status nh2d_set_graphs(nh_grid2d* g, int on);
+
+/* h > 0 (m), hu, hv, hw (m^2/s) of member m; sets the whole ensemble's time
+   to t and clears member m's warm start.  Steps need every member set. */
 nh_status nh2d_set_state(nh_grid2d* g, const double* h, const double* hu, const double* hv,
                          const double* hw, double t);
+nh_status nh2d_set_member_state(nh_grid2d* g, int member, const double* h, const double* hu,
+                                const double* hv, const double* hw, double t);
 
 /* Any pointer may be NULL.  p_nh: non-hydrostatic pressure of the last step
    (Pa; 0 on cells that were hydrostatic). */
 nh_status nh2d_get_state(nh_grid2d* g, double* h, double* hu, double* hv, double* hw, double* p_nh);
+nh_status nh2d_get_member_state(nh_grid2d* g, int member, double* h, double* hu, double* hv, double* hw,
+                                double* p_nh);
 
 /* Last step's non-hydrostatic mask (nx * ny bytes). */
 nh_status nh2d_get_mask(nh_grid2d* g, unsigned char* mask);
+nh_status nh2d_get_member_mask(nh_grid2d* g, int member, unsigned char* mask);
 
-/* info (may be NULL): as nh_step_info; mass = sum(h) dx dy. */
+/* info (may be NULL): as nh_step_info, summed (n_active, mass) or taken
+   worst (iters, rel_res, status) over members; mass = sum(h) dx dy. */
 nh_status nh2d_step(nh_grid2d* g, double dt, nh_step_info* info);
 nh_status nh2d_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* info);
+
+/* Member m's figures of the last step (n_active, iters, rel_res, min_gamma,
+   solver, status) and the mass sum(h) dx dy of its new state. */
+nh_status nh2d_get_member_info(nh_grid2d* g, int member, nh_step_info* info);
+
+/* Number of captured-graph runs nh2d_run has made (-1 for NULL). */
+long long nh2d_graph_runs(const nh_grid2d* g);
 
 void nh2d_destroy(nh_grid2d* g);
 

@@ -1,10 +1,15 @@
-// nh_api2d.cu -- host runtime behind include/nhswe2d.h (one 2D grid, FP64).
+// nh_api2d.cu -- host runtime behind include/nhswe2d.h (2D grids, FP64).
 //
-// The handle carves every device buffer out of the caller's workspace and
-// runs one step as: depth at t^n and t^{n+1}, two Heun stages, criterion and
-// Moore enlargement, row-major compaction, 9-point assembly, the line-
-// preconditioned CG of the 1D members (one member holding the whole active
-// set; S, N and the diagonal couplings as extra couplings), correction.
+// A handle holds an ensemble of nb grids (one for nh2d_create), each with its
+// own size, spacing, sides, static depth and slide; member b's cells sit at
+// b * pitch in every per-cell buffer, all carved out of the caller's
+// workspace.  One step runs, over all members at once: slide kinematics,
+// depth at t^n and t^{n+1}, two Heun stages, criterion and Moore
+// enlargement, row-major compaction, 9-point assembly, the line-
+// preconditioned CG of the 1D members (each grid one member; S, N and the
+// diagonal couplings as extra couplings) in one cooperative launch, and the
+// correction.  nh2d_run replays that step from a captured CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -17,12 +22,13 @@
 using namespace nh;
 
 struct nh_grid2d {
-    nh_grid2d_desc d;
-    cudaStream_t stream;
-    int nx, ny, N, maxch, maxpb, nblk, nmass, sms, items_grid, pcr_grid, elem_grid, coop_grid;
+    int nb, pitch;
+    std::vector<nh_grid2d_desc> d;
+    std::vector<Slide2> slide_h;
+    std::vector<char> member_set;
+    cudaStream_t stream, cap_stream;
+    int maxch, maxpb, nblk, nmass, sms, items_grid, pcr_grid, egx, coop_grid;
     long long barrier_budget;
-    Slide2 slide;
-    double s0, t0;
     int crit, enlarge, first_global;
     double knh;
     double rtol;
@@ -31,12 +37,13 @@ struct nh_grid2d {
     double t_base, last_dt;
     long long n_since, steps;
     int cur, lcur;
+    // device buffers ([nb * pitch] per field unless noted)
     double* q[2][4];
     double* qs[4];
     double* k1[4];
     double *d0, *dn, *dn1;
     unsigned char *marks, *act;
-    int *inv, *list[2], *nact[2], *bcnt, *boff;
+    int *inv, *list[2], *nact[2], *bcnt, *boff;   // nact [nb]; bcnt, boff [nb * nblk]
     int2 *items, *pitems;
     double *diag, *offl, *offr, *R, *ext_c;
     int *ext_k, *nbl, *nbr;
@@ -50,11 +57,21 @@ struct nh_grid2d {
     int* cnt;
     double* mass_part;
     Summary* summary;
+    Geo2* geos;
+    Slide2* slides;
+    Kin2* kin;
+    TimeCtl* tc;
+    // captured step: graph[p] starts from state buffer p
+    cudaGraphExec_t graph[2];
+    bool graph_valid, use_graphs;
+    double graph_key[9];
+    long long graph_runs;
 };
 
 namespace {
 
 constexpr size_t kAlign2 = 256;
+constexpr int kPitchQuantum = 256;   // cells; keeps every member's slice 256-byte aligned
 
 struct Carver2 {
     char* base;
@@ -82,41 +99,58 @@ bool desc2_ok(const nh_grid2d_desc* d)
     return true;
 }
 
-int mass_blocks(int N) { return std::max(1, std::min((N + 255) / 256, 1024)); }
-
-size_t carve2(const nh_grid2d_desc& d, nh_grid2d* g, char* base)
+// Cells per member slot, or 0 when the ensemble is invalid or too large.
+long long ens_pitch(int nb, const nh_grid2d_desc* descs)
 {
-    const int N = d.nx * d.ny;
-    const int maxch = (N + kChunk - 1) / kChunk;
-    const int maxpb = (N + kPcrRows - 1) / kPcrRows;
-    const int nblk = (N + kCompact2 - 1) / kCompact2;
+    if (nb < 1 || nb > 4096 || !descs) return 0;
+    long long mx = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (!desc2_ok(&descs[b])) return 0;
+        mx = std::max(mx, (long long)descs[b].nx * descs[b].ny);
+    }
+    const long long pitch = (mx + kPitchQuantum - 1) / kPitchQuantum * kPitchQuantum;
+    if (pitch * nb > (1LL << 28)) return 0;
+    return pitch;
+}
+
+int mass_blocks(int pitch) { return std::max(1, std::min((pitch + 255) / 256, 64)); }
+
+size_t carve2(int nb, int pitch, nh_grid2d* g, char* base)
+{
+    const size_t T = (size_t)nb * pitch;
+    const int maxch = (pitch + kChunk - 1) / kChunk;
+    const int maxpb = (pitch + kPcrRows - 1) / kPcrRows;
+    const int nblk = (pitch + kCompact2 - 1) / kCompact2;
+    const int nmass = mass_blocks(pitch);
     Carver2 c{base};
     nh_grid2d tmp;
     nh_grid2d* G = g ? g : &tmp;
     for (int b = 0; b < 2; ++b)
-        for (int f = 0; f < 4; ++f) G->q[b][f] = c.take<double>(N);
-    for (int f = 0; f < 4; ++f) { G->qs[f] = c.take<double>(N); G->k1[f] = c.take<double>(N); }
-    G->d0 = c.take<double>(N); G->dn = c.take<double>(N); G->dn1 = c.take<double>(N);
-    G->marks = c.take<unsigned char>(N); G->act = c.take<unsigned char>(N);
-    G->inv = c.take<int>(N);
-    for (int b = 0; b < 2; ++b) { G->list[b] = c.take<int>(N); G->nact[b] = c.take<int>(1); }
-    G->bcnt = c.take<int>(nblk); G->boff = c.take<int>(nblk);
-    G->items = c.take<int2>(maxch); G->pitems = c.take<int2>(maxpb);
-    G->diag = c.take<double>(N); G->offl = c.take<double>(N); G->offr = c.take<double>(N);
-    G->R = c.take<double>(N);
-    G->ext_c = c.take<double>(6 * (size_t)N); G->ext_k = c.take<int>(6 * (size_t)N);
-    G->nbl = c.take<int>(N); G->nbr = c.take<int>(N);
-    G->c6 = c.take<double>(N); G->cx = c.take<double>(N); G->cy = c.take<double>(N);
-    G->phi = c.take<double>(N); G->ddx = c.take<double>(N); G->ddy = c.take<double>(N);
-    G->psi = c.take<double>(N);
-    G->x = c.take<double>(N); G->r = c.take<double>(N); G->p0 = c.take<double>(N); G->p1 = c.take<double>(N);
-    G->qv = c.take<double>(N); G->rh = c.take<double>(N); G->v0 = c.take<double>(N); G->v1 = c.take<double>(N);
-    G->s = c.take<double>(N); G->t = c.take<double>(N); G->r1 = c.take<double>(N); G->z = c.take<double>(N);
-    G->pf = c.take<float2>((size_t)kPcrLevels * N); G->prb = c.take<float>(N);
-    G->ms = c.take<MState>(1); G->ctl = c.take<Ctl>(1);
-    G->part = c.take<double>(3 * (size_t)maxch); G->cnt = c.take<int>(1);
-    G->mass_part = c.take<double>(mass_blocks(N)); G->summary = c.take<Summary>(1);
-    if (g) { g->N = N; g->maxch = maxch; g->maxpb = maxpb; g->nblk = nblk; g->nmass = mass_blocks(N); }
+        for (int f = 0; f < 4; ++f) G->q[b][f] = c.take<double>(T);
+    for (int f = 0; f < 4; ++f) { G->qs[f] = c.take<double>(T); G->k1[f] = c.take<double>(T); }
+    G->d0 = c.take<double>(T); G->dn = c.take<double>(T); G->dn1 = c.take<double>(T);
+    G->marks = c.take<unsigned char>(T); G->act = c.take<unsigned char>(T);
+    G->inv = c.take<int>(T);
+    for (int b = 0; b < 2; ++b) { G->list[b] = c.take<int>(T); G->nact[b] = c.take<int>(nb); }
+    G->bcnt = c.take<int>((size_t)nb * nblk); G->boff = c.take<int>((size_t)nb * nblk);
+    G->items = c.take<int2>((size_t)nb * maxch); G->pitems = c.take<int2>((size_t)nb * maxpb);
+    G->diag = c.take<double>(T); G->offl = c.take<double>(T); G->offr = c.take<double>(T);
+    G->R = c.take<double>(T);
+    G->ext_c = c.take<double>(6 * T); G->ext_k = c.take<int>(6 * T);
+    G->nbl = c.take<int>(T); G->nbr = c.take<int>(T);
+    G->c6 = c.take<double>(T); G->cx = c.take<double>(T); G->cy = c.take<double>(T);
+    G->phi = c.take<double>(T); G->ddx = c.take<double>(T); G->ddy = c.take<double>(T);
+    G->psi = c.take<double>(T);
+    G->x = c.take<double>(T); G->r = c.take<double>(T); G->p0 = c.take<double>(T); G->p1 = c.take<double>(T);
+    G->qv = c.take<double>(T); G->rh = c.take<double>(T); G->v0 = c.take<double>(T); G->v1 = c.take<double>(T);
+    G->s = c.take<double>(T); G->t = c.take<double>(T); G->r1 = c.take<double>(T); G->z = c.take<double>(T);
+    G->pf = c.take<float2>((size_t)kPcrLevels * T); G->prb = c.take<float>(T);
+    G->ms = c.take<MState>(nb); G->ctl = c.take<Ctl>(1);
+    G->part = c.take<double>(3 * (size_t)nb * maxch); G->cnt = c.take<int>(nb);
+    G->mass_part = c.take<double>((size_t)nb * nmass); G->summary = c.take<Summary>(1);
+    G->geos = c.take<Geo2>(nb); G->slides = c.take<Slide2>(nb); G->kin = c.take<Kin2>(2 * (size_t)nb);
+    G->tc = c.take<TimeCtl>(1);
+    if (g) { g->maxch = maxch; g->maxpb = maxpb; g->nblk = nblk; g->nmass = nmass; }
     return (c.off + kAlign2 - 1) / kAlign2 * kAlign2;
 }
 
@@ -125,51 +159,131 @@ size_t carve2(const nh_grid2d_desc& d, nh_grid2d* g, char* base)
         if ((call) != cudaSuccess) return NH_ERR_CUDA;  \
     } while (0)
 
-Kin2 kin_at(const nh_grid2d* g, double t)
-{
-    Kin2 k{0.0, 0.0, 0.0};
-    if (g->slide.shape == NH_SLIDE_GAUSS_LNCOSH) {
-        const double z = t / g->t0;
-        k.s = g->s0 * std::log(std::cosh(z));
-        k.sd = (g->s0 / g->t0) * std::tanh(z);
-        k.sdd = (g->s0 / (g->t0 * g->t0)) / (std::cosh(z) * std::cosh(z));
-    }
-    return k;
-}
-
-Geo2 geo2(const nh_grid2d* g)
+Geo2 geo2(const nh_grid2d_desc& d)
 {
     Geo2 G;
-    G.nx = g->nx; G.ny = g->ny; G.bcx = g->d.bc_x; G.bcy = g->d.bc_y; G.lim = g->d.limiter;
-    G.dx = g->d.dx; G.dy = g->d.dy; G.x0 = g->d.x0; G.y0 = g->d.y0; G.g = g->d.g;
+    G.nx = d.nx; G.ny = d.ny; G.bcx = d.bc_x; G.bcy = d.bc_y; G.lim = d.limiter;
+    G.dx = d.dx; G.dy = d.dy; G.x0 = d.x0; G.y0 = d.y0; G.g = d.g;
     return G;
 }
 
-SolveArgs<double> solve_args2(nh_grid2d* g, int lnew, double gscale)
+SolveArgs<double> solve_args2(nh_grid2d* g, int lnew, double gscale, const TimeCtl* tc)
 {
     SolveArgs<double> a;
-    a.nb = 1; a.pitch = g->N; a.maxch = g->maxch;
+    a.nb = g->nb; a.pitch = g->pitch; a.maxch = g->maxch;
+    const size_t T = (size_t)g->nb * g->pitch;
     a.list = g->list[lnew];
     a.diag = g->diag; a.offl = g->offl; a.offr = g->offr; a.R = g->R;
     a.nbl = g->nbl; a.nbr = g->nbr;
     a.psi_prev = g->psi; a.guess_scale = gscale;
     a.x = g->x; a.r = g->r; a.p0 = g->p0; a.p1 = g->p1; a.q = g->qv; a.rh = g->rh;
     a.v0 = g->v0; a.v1 = g->v1; a.s = g->s; a.t = g->t; a.r1 = g->r1; a.z = g->z;
-    a.pf = g->pf; a.prb = g->prb; a.pf_stride = (size_t)g->N;
-    a.n_ext = 6; a.ext_c = g->ext_c; a.ext_k = g->ext_k; a.ext_stride = (size_t)g->N;
+    a.pf = g->pf; a.prb = g->prb; a.pf_stride = T;
+    a.n_ext = 6; a.ext_c = g->ext_c; a.ext_k = g->ext_k; a.ext_stride = T;
     a.maxpb = g->maxpb; a.items = g->items; a.pitems = g->pitems;
-    a.tc = nullptr; a.ms = g->ms; a.ctl = g->ctl; a.part = g->part; a.cnt = g->cnt;
+    a.tc = tc; a.ms = g->ms; a.ctl = g->ctl; a.part = g->part; a.cnt = g->cnt;
     a.rtol = g->rtol; a.max_iter = g->max_iter; a.it = 0;
     return a;
 }
 
+// Everything of one step up to the assembled systems: kinematics, depth,
+// predictor, criterion, mask, compaction, work items, assembly, mass.
+nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double dt, double t_n, double t_n1,
+                        bool all, const TimeCtl* tc)
+{
+    const int nxt = cur ^ 1;
+    const size_t T = (size_t)g->nb * g->pitch;
+    const size_t P = (size_t)g->pitch;
+    const dim3 eg(g->egx, g->nb);
+    k2_kin<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slides, g->nb, t_n, t_n1, tc, g->kin);
+    k2_depth<<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 0, P, g->d0, g->dn, tc);
+    k2_depth<<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 1, P, g->d0, g->dn1, tc);
+    StageArgs sa1;
+    sa1.geos = g->geos; sa1.pitch = P;
+    sa1.h = g->q[cur][0]; sa1.hu = g->q[cur][1]; sa1.hv = g->q[cur][2]; sa1.hw = g->q[cur][3]; sa1.d = g->dn;
+    sa1.h0 = g->q[cur][0]; sa1.hu0 = g->q[cur][1]; sa1.hv0 = g->q[cur][2]; sa1.hw0 = g->q[cur][3];
+    sa1.k1h = g->k1[0]; sa1.k1u = g->k1[1]; sa1.k1v = g->k1[2]; sa1.k1w = g->k1[3];
+    sa1.oh = g->qs[0]; sa1.ohu = g->qs[1]; sa1.ohv = g->qs[2]; sa1.ohw = g->qs[3];
+    sa1.dt = dt; sa1.stage = 1; sa1.tc = tc;
+    k2_stage<<<eg, 256, 0, st>>>(sa1);
+    StageArgs sa2 = sa1;
+    sa2.h = g->qs[0]; sa2.hu = g->qs[1]; sa2.hv = g->qs[2]; sa2.hw = g->qs[3]; sa2.d = g->dn1;
+    sa2.oh = g->q[nxt][0]; sa2.ohu = g->q[nxt][1]; sa2.ohv = g->q[nxt][2]; sa2.ohw = g->q[nxt][3];
+    sa2.stage = 2;
+    k2_stage<<<eg, 256, 0, st>>>(sa2);
+
+    if (all) CK2(cudaMemsetAsync(g->marks, 1, T, st));
+    else if (g->crit == NH_CRIT_HYDROSTATIC) CK2(cudaMemsetAsync(g->marks, 0, T, st));
+    else k2_marks<<<eg, 256, 0, st>>>(g->geos, P, g->q[nxt][0], g->q[nxt][1], g->q[nxt][2], g->q[nxt][3],
+                                     g->dn1, g->crit, g->knh, g->marks);
+    k2_dilate<<<eg, 256, 0, st>>>(g->geos, P, g->marks, all ? 0 : g->enlarge, g->act, tc);
+    k2_count<<<dim3(g->nblk, g->nb), kCompact2, 0, st>>>(g->geos, P, g->act, g->nblk, g->bcnt);
+    k2_scan<<<g->nb, 1024, 0, st>>>(g->bcnt, g->nblk, g->boff, g->nact[lnew], g->ms, tc);
+    k2_emit<<<dim3(g->nblk, g->nb), kCompact2, 0, st>>>(g->geos, P, g->act, g->nblk, g->boff, g->list[lnew],
+                                                          g->inv, tc);
+    k_items<<<1, 1024, 0, st>>>(g->ms, g->nb, g->items, g->pitems, g->ctl);
+    CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
+
+    Asm2Args aa;
+    aa.geos = g->geos; aa.slides = g->slides; aa.kin = g->kin;
+    aa.nb = g->nb; aa.pitch = g->pitch; aa.maxch = g->maxch;
+    aa.ht = g->q[nxt][0]; aa.hut = g->q[nxt][1]; aa.hvt = g->q[nxt][2]; aa.hwt = g->q[nxt][3];
+    aa.d0 = g->d0; aa.d1 = g->dn1; aa.dt = dt;
+    aa.list = g->list[lnew]; aa.inv = g->inv; aa.ms = g->ms;
+    aa.diag = g->diag; aa.offl = g->offl; aa.offr = g->offr; aa.R = g->R;
+    aa.nbl = g->nbl; aa.nbr = g->nbr;
+    aa.ext_c = g->ext_c; aa.ext_k = g->ext_k; aa.ext_stride = T;
+    aa.c6 = g->c6; aa.cx = g->cx; aa.cy = g->cy; aa.phi = g->phi; aa.ddx = g->ddx; aa.ddy = g->ddy;
+    aa.part = g->part; aa.cnt = g->cnt; aa.solver = NH_SOLVER_AUTO;
+    aa.items = g->items; aa.ctl = g->ctl;
+    k2_assemble<<<g->items_grid, kChunk, 0, st>>>(aa);
+    k2_mass<<<dim3(g->nmass, g->nb), 256, 0, st>>>(g->geos, P, g->q[nxt][0], g->mass_part);
+    return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
+}
+
+// The accepted step's tail: zero psi on the previous mask, correct on the new one.
+nh_status enqueue_back(nh_grid2d* g, cudaStream_t st, int nxt, int lprev, int lnew, const TimeCtl* tc)
+{
+    const size_t T = (size_t)g->nb * g->pitch;
+    ClearArgs cl;
+    cl.nb = g->nb; cl.pitch = g->pitch; cl.maxlist = g->pitch;
+    cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = tc;
+    k_clear_prev<<<(int)std::min<size_t>((T + 255) / 256, (size_t)g->sms * 8), 256, 0, st>>>(cl);
+    Corr2Args co;
+    co.geos = g->geos; co.pitch = g->pitch; co.list = g->list[lnew];
+    co.nbl = g->nbl; co.nbr = g->nbr; co.ext_k = g->ext_k; co.ext_stride = T;
+    co.x = g->x; co.c6 = g->c6; co.cx = g->cx; co.cy = g->cy; co.phi = g->phi;
+    co.ddx = g->ddx; co.ddy = g->ddy; co.ms = g->ms;
+    co.hu = g->q[nxt][1]; co.hv = g->q[nxt][2]; co.hw = g->q[nxt][3]; co.psi = g->psi;
+    co.items = g->items; co.ctl = g->ctl; co.tc = tc;
+    k2_correct<<<g->items_grid, kChunk, 0, st>>>(co);
+    return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
+}
+
+nh_status launch_persistent(nh_grid2d* g, SolveArgs<double>& sa, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g->coop_grid);
+    cfg.blockDim = dim3(kPcrThreads);
+    cfg.dynamicSmemBytes = 2 * sizeof(float) * (size_t)kPcrRows;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    long long budget = g->barrier_budget;
+    CK2(cudaLaunchKernelEx(&cfg, k_pcg_persistent<double, float>, sa, budget));
+    return NH_OK;
+}
+
 // One Krylov pass: set-up, then preconditioned CG in one cooperative launch,
-// or preconditioned BiCGStab driven from the host.
+// and preconditioned BiCGStab driven from the host for members that need it.
 nh_status krylov2_pass(nh_grid2d* g, SolveArgs<double>& sa)
 {
     cudaStream_t st = g->stream;
     CK2(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
-    CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int), st));
+    CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
     k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa);
     Ctl h;
     CK2(cudaMemcpyAsync(&h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -182,20 +296,20 @@ nh_status krylov2_pass(nh_grid2d* g, SolveArgs<double>& sa)
         k_pcr<double, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG);
     }
     if (h.not_done <= 0) return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
-    if (h.n_cg > 0 && g->coop_grid > 0) {
+    const bool coop_cg = h.n_cg > 0 && g->coop_grid > 0;
+    if (coop_cg) {
         CK2(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
-        long long budget = g->barrier_budget;
-        void* args[] = {(void*)&sa, (void*)&budget};
-        CK2(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<double, float>, dim3(g->coop_grid),
-                                        dim3(kPcrThreads), args, pcr_smem, st));
+        nh_status rc = launch_persistent(g, sa, st);
+        if (rc != NH_OK) return rc;
         int to = 0;
         CK2(cudaMemcpyAsync(&to, &g->ctl->timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK2(cudaStreamSynchronize(st));
-        return to ? NH_ERR_TIMEOUT : NH_OK;
+        if (to) return NH_ERR_TIMEOUT;
+        if (h.n_bicg == 0) return NH_OK;
     }
     for (int it = 1; it <= g->max_iter; ++it) {
         sa.it = it;
-        if (h.n_cg > 0) {
+        if (h.n_cg > 0 && !coop_cg) {
             k_pcg_a<double><<<g->items_grid, kChunk, 0, st>>>(sa);
             k_pcr<double, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG_STEP);
         }
@@ -226,8 +340,23 @@ nh_status krylov2(nh_grid2d* g, SolveArgs<double>& sa)
     CK2(cudaMemcpyAsync(&nfb, &g->ctl->n_fallback, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK2(cudaStreamSynchronize(st));
     if (nfb == 0) return NH_OK;
-    k_fallback_reset<<<1, 32, 0, st>>>(g->ms, 1);
+    k_fallback_reset<<<(g->nb + 127) / 128, 128, 0, st>>>(g->ms, g->nb);
     return krylov2_pass(g, sa);
+}
+
+void fill_info(const nh_grid2d* g, const Summary& S, nh_status status, double t, nh_step_info* info)
+{
+    info->step = g->steps;
+    info->t = t;
+    info->n_active = S.n_active;
+    info->n_active_max = S.n_active_max;
+    info->iters = S.iters;
+    info->ir_passes = 0;
+    info->solver = S.n_active == 0 ? -1 : (S.any_bicg ? NH_SOLVER_BICGSTAB : NH_SOLVER_CG);
+    info->status = status;
+    info->rel_res = S.rel_res;
+    info->min_gamma = S.min_gamma;
+    info->mass = S.mass;
 }
 
 nh_status step2(nh_grid2d* g, double dt, nh_step_info* info)
@@ -240,139 +369,188 @@ nh_status step2(nh_grid2d* g, double dt, nh_step_info* info)
     const double t_n = g->t_base + (double)g->n_since * dt;
     const double t_n1 = g->t_base + (double)(g->n_since + 1) * dt;
     const int cur = g->cur, nxt = cur ^ 1, lprev = g->lcur, lnew = lprev ^ 1;
-    const Geo2 G = geo2(g);
-    const Kin2 Kn = kin_at(g, t_n), Kn1 = kin_at(g, t_n1);
-    const int eg = g->elem_grid;
-
-    k2_depth<<<eg, 256, 0, st>>>(G, g->d0, g->slide, Kn.s, g->dn);
-    k2_depth<<<eg, 256, 0, st>>>(G, g->d0, g->slide, Kn1.s, g->dn1);
-    StageArgs sa1;
-    sa1.G = G;
-    sa1.h = g->q[cur][0]; sa1.hu = g->q[cur][1]; sa1.hv = g->q[cur][2]; sa1.hw = g->q[cur][3]; sa1.d = g->dn;
-    sa1.h0 = g->q[cur][0]; sa1.hu0 = g->q[cur][1]; sa1.hv0 = g->q[cur][2]; sa1.hw0 = g->q[cur][3];
-    sa1.k1h = g->k1[0]; sa1.k1u = g->k1[1]; sa1.k1v = g->k1[2]; sa1.k1w = g->k1[3];
-    sa1.oh = g->qs[0]; sa1.ohu = g->qs[1]; sa1.ohv = g->qs[2]; sa1.ohw = g->qs[3];
-    sa1.dt = dt; sa1.stage = 1;
-    k2_stage<<<eg, 256, 0, st>>>(sa1);
-    StageArgs sa2 = sa1;
-    sa2.h = g->qs[0]; sa2.hu = g->qs[1]; sa2.hv = g->qs[2]; sa2.hw = g->qs[3]; sa2.d = g->dn1;
-    sa2.oh = g->q[nxt][0]; sa2.ohu = g->q[nxt][1]; sa2.ohv = g->q[nxt][2]; sa2.ohw = g->q[nxt][3];
-    sa2.stage = 2;
-    k2_stage<<<eg, 256, 0, st>>>(sa2);
-
     const bool all = g->crit == NH_CRIT_GLOBAL || (g->first_global && g->steps == 0);
-    if (all) CK2(cudaMemsetAsync(g->marks, 1, g->N, st));
-    else if (g->crit == NH_CRIT_HYDROSTATIC) CK2(cudaMemsetAsync(g->marks, 0, g->N, st));
-    else k2_marks<<<eg, 256, 0, st>>>(G, g->q[nxt][0], g->q[nxt][1], g->q[nxt][2], g->q[nxt][3], g->dn1,
-                                     g->crit, g->knh, g->marks);
-    k2_dilate<<<eg, 256, 0, st>>>(G, g->marks, all ? 0 : g->enlarge, g->act);
-    k2_count<<<g->nblk, kCompact2, 0, st>>>(g->act, g->N, g->bcnt);
-    k2_scan<<<1, 1024, 0, st>>>(g->bcnt, g->nblk, g->boff, g->nact[lnew], g->ms);
-    k2_emit<<<g->nblk, kCompact2, 0, st>>>(g->act, g->N, g->boff, g->list[lnew], g->inv);
-    k_items<<<1, 1024, 0, st>>>(g->ms, 1, g->items, g->pitems, g->ctl);
-    CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int), st));
-
-    Asm2Args aa;
-    aa.G = G;
-    aa.ht = g->q[nxt][0]; aa.hut = g->q[nxt][1]; aa.hvt = g->q[nxt][2]; aa.hwt = g->q[nxt][3];
-    aa.d0 = g->d0; aa.d1 = g->dn1; aa.S = g->slide; aa.K = Kn1; aa.dt = dt;
-    aa.list = g->list[lnew]; aa.inv = g->inv; aa.ms = g->ms;
-    aa.diag = g->diag; aa.offl = g->offl; aa.offr = g->offr; aa.R = g->R;
-    aa.nbl = g->nbl; aa.nbr = g->nbr;
-    aa.ext_c = g->ext_c; aa.ext_k = g->ext_k; aa.ext_stride = (size_t)g->N;
-    aa.c6 = g->c6; aa.cx = g->cx; aa.cy = g->cy; aa.phi = g->phi; aa.ddx = g->ddx; aa.ddy = g->ddy;
-    aa.part = g->part; aa.cnt = g->cnt; aa.solver = NH_SOLVER_AUTO;
-    aa.items = g->items; aa.ctl = g->ctl;
-    k2_assemble<<<g->items_grid, kChunk, 0, st>>>(aa);
-    CK2(cudaGetLastError());
-
-    const double gscale = (g->guess == NH_GUESS_PREV && g->last_dt > 0.0) ? dt / g->last_dt : 0.0;
-    SolveArgs<double> sa = solve_args2(g, lnew, gscale);
-    nh_status rc = krylov2(g, sa);
+    nh_status rc = enqueue_front(g, st, cur, lnew, dt, t_n, t_n1, all, nullptr);
     if (rc != NH_OK) return rc;
-
-    k2_mass<<<g->nmass, 256, 0, st>>>(g->q[nxt][0], g->N, g->mass_part);
-    k_summary<<<1, 256, 0, st>>>(g->ms, 1, g->mass_part, g->nmass, g->d.dx * g->d.dy, g->summary, nullptr);
+    const double gscale = (g->guess == NH_GUESS_PREV && g->last_dt > 0.0) ? dt / g->last_dt : 0.0;
+    SolveArgs<double> sa = solve_args2(g, lnew, gscale, nullptr);
+    rc = krylov2(g, sa);
+    if (rc != NH_OK) return rc;
+    k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->nmass, 1.0, g->summary, nullptr);
     Summary S;
     CK2(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
     CK2(cudaStreamSynchronize(st));
     CK2(cudaGetLastError());
     const nh_status status = (nh_status)S.status;
     if (status == NH_OK) {
-        ClearArgs cl;
-        cl.nb = 1; cl.pitch = g->N; cl.maxlist = g->N;
-        cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = nullptr;
-        k_clear_prev<<<eg, 256, 0, st>>>(cl);
-        if (S.n_active > 0) {
-            Corr2Args co;
-            co.G = G; co.n = (int)S.n_active; co.list = g->list[lnew];
-            co.nbl = g->nbl; co.nbr = g->nbr; co.ext_k = g->ext_k; co.ext_stride = (size_t)g->N;
-            co.x = g->x; co.c6 = g->c6; co.cx = g->cx; co.cy = g->cy; co.phi = g->phi;
-            co.ddx = g->ddx; co.ddy = g->ddy; co.ms = g->ms;
-            co.hu = g->q[nxt][1]; co.hv = g->q[nxt][2]; co.hw = g->q[nxt][3]; co.psi = g->psi;
-            k2_correct<<<eg, 256, 0, st>>>(co);
-        }
-        CK2(cudaGetLastError());
+        rc = enqueue_back(g, st, nxt, lprev, lnew, nullptr);
+        if (rc != NH_OK) return rc;
         g->cur = nxt;
         g->lcur = lnew;
         g->n_since += 1;
         g->steps += 1;
         g->last_dt = dt;
     }
-    if (info) {
-        info->step = g->steps;
-        info->t = status == NH_OK ? t_n1 : t_n;
-        info->n_active = S.n_active;
-        info->n_active_max = S.n_active_max;
-        info->iters = S.iters;
-        info->ir_passes = 0;
-        info->solver = S.n_active == 0 ? -1 : (S.any_bicg ? NH_SOLVER_BICGSTAB : NH_SOLVER_CG);
-        info->status = status;
-        info->rel_res = S.rel_res;
-        info->min_gamma = S.min_gamma;
-        info->mass = S.mass;
-    }
+    if (info) fill_info(g, S, status, status == NH_OK ? t_n1 : t_n, info);
     return status;
 }
+
+// ------------------------------------------------------------ captured runs
+
+// One step with fixed buffer roles and no host round trip: the time control
+// block supplies t, the commit kernel accepts the step or aborts the run, and
+// every kernel that writes state skips after an abort.
+nh_status enqueue_graph_step(nh_grid2d* g, cudaStream_t st, int cur, int lprev, double dt)
+{
+    const int nxt = cur ^ 1, lnew = lprev ^ 1;
+    nh_status rc = enqueue_front(g, st, cur, lnew, dt, 0.0, 0.0, g->crit == NH_CRIT_GLOBAL, g->tc);
+    if (rc != NH_OK) return rc;
+    SolveArgs<double> sa = solve_args2(g, lnew, g->guess == NH_GUESS_PREV ? 1.0 : 0.0, g->tc);
+    CK2(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
+    CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
+    k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa);
+    k_pcr_factor<double, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa);
+    k_pcr<double, float><<<g->pcr_grid, kPcrThreads, 2 * sizeof(float) * kPcrRows, st>>>(sa, PCR_PCG);
+    CK2(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
+    rc = launch_persistent(g, sa, st);
+    if (rc != NH_OK) return rc;
+    k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->nmass, 1.0, g->summary, g->tc);
+    k_commit<<<1, 32, 0, st>>>(g->summary, g->tc);
+    return enqueue_back(g, st, nxt, lprev, lnew, g->tc);
+}
+
+bool graph_eligible(const nh_grid2d* g, double dt)
+{
+    return g->use_graphs && g->coop_grid > 0 && g->cap_stream != nullptr &&
+           !(g->first_global && g->steps == 0) && (g->last_dt == 0.0 || g->last_dt == dt);
+}
+
+void graph_destroy(nh_grid2d* g)
+{
+    for (int p = 0; p < 2; ++p)
+        if (g->graph[p]) { cudaGraphExecDestroy(g->graph[p]); g->graph[p] = nullptr; }
+    g->graph_valid = false;
+}
+
+nh_status graph_prepare(nh_grid2d* g, double dt)
+{
+    const double key[9] = {dt, (double)g->crit, g->knh, (double)g->enlarge, g->rtol, (double)g->max_iter,
+                           (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->first_global};
+    if (g->graph_valid && std::memcmp(key, g->graph_key, sizeof(key)) == 0) return NH_OK;
+    graph_destroy(g);
+    for (int p = 0; p < 2; ++p) {
+        const int cur = p, lprev = p ^ g->cur ^ g->lcur;
+        cudaGraph_t graph = nullptr;
+        CK2(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+        nh_status rc = enqueue_graph_step(g, g->cap_stream, cur, lprev, dt);
+        cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+        if (rc != NH_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            graph_destroy(g);
+            return rc != NH_OK ? rc : NH_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&g->graph[p], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { g->graph[p] = nullptr; graph_destroy(g); return NH_ERR_CUDA; }
+    }
+    std::memcpy(g->graph_key, key, sizeof(key));
+    g->graph_valid = true;
+    return NH_OK;
+}
+
+// n_steps steps by replaying the captured graphs on the handle's stream; one
+// synchronisation at the end.
+nh_status graph_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* R)
+{
+    if (g->last_dt != 0.0 && dt != g->last_dt) {
+        g->t_base += (double)g->n_since * g->last_dt;
+        g->n_since = 0;
+    }
+    nh_status rc = graph_prepare(g, dt);
+    if (rc != NH_OK) return rc;
+    cudaStream_t st = g->stream;
+    TimeCtl tc;
+    std::memset(&tc, 0, sizeof(tc));
+    tc.t_base = g->t_base; tc.dt = dt; tc.n = g->n_since; tc.done = 0; tc.abort = 0;
+    tc.prev_ok = (g->last_dt == dt) ? 1 : 0;
+    CK2(cudaMemcpyAsync(g->tc, &tc, sizeof(tc), cudaMemcpyHostToDevice, st));
+    for (long long k = 0; k < n_steps; ++k) CK2(cudaGraphLaunch(g->graph[(g->cur + k) & 1], st));
+    Summary S;
+    CK2(cudaMemcpyAsync(&tc, g->tc, sizeof(tc), cudaMemcpyDeviceToHost, st));
+    CK2(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
+    CK2(cudaStreamSynchronize(st));
+    const long long done = tc.done;
+    if (done & 1) { g->cur ^= 1; g->lcur ^= 1; }
+    g->steps += done;
+    g->n_since += done;
+    if (done > 0) g->last_dt = dt;
+    g->graph_runs += 1;
+    R->steps = done;
+    R->iters_total = tc.iters_total;
+    R->active_total = tc.active_total;
+    const nh_status st_last = tc.abort ? (nh_status)tc.fail_status : NH_OK;
+    fill_info(g, S, st_last, g->t_base + (double)g->n_since * dt, &R->last);
+    if (tc.abort)
+        return (nh_status)(tc.fail_status == kStatusFallback ? NH_ERR_NONFINITE : tc.fail_status);
+    return NH_OK;
+}
+
+bool member_ok(const nh_grid2d* g, int m) { return g && m >= 0 && m < g->nb; }
 
 }  // namespace
 
 extern "C" {
 
-size_t nh2d_workspace_bytes(const nh_grid2d_desc* desc)
+size_t nh2d_ensemble_workspace_bytes(int n_members, const nh_grid2d_desc* descs)
 {
-    if (!desc2_ok(desc)) return 0;
-    return carve2(*desc, nullptr, nullptr);
+    const long long pitch = ens_pitch(n_members, descs);
+    if (pitch == 0) return 0;
+    return carve2(n_members, (int)pitch, nullptr, nullptr);
 }
 
-nh_status nh2d_create(const nh_grid2d_desc* desc, const double* d0_host, void* ws, size_t ws_bytes,
-                      void* stream, nh_grid2d** out)
+size_t nh2d_workspace_bytes(const nh_grid2d_desc* desc) { return nh2d_ensemble_workspace_bytes(1, desc); }
+
+nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const double* const* d0_host, void* ws,
+                               size_t ws_bytes, void* stream, nh_grid2d** out)
 {
-    if (!out || !desc2_ok(desc) || !d0_host || !ws) return NH_ERR_ARG;
+    if (!out) return NH_ERR_ARG;
     *out = nullptr;
-    const size_t need = carve2(*desc, nullptr, nullptr);
+    const long long pitch = ens_pitch(n_members, descs);
+    if (pitch == 0 || !d0_host || !ws) return NH_ERR_ARG;
+    const size_t need = carve2(n_members, (int)pitch, nullptr, nullptr);
     if (ws_bytes < need || ((uintptr_t)ws % kAlign2) != 0) return NH_ERR_ARG;
-    const long long N = (long long)desc->nx * desc->ny;
-    for (long long q = 0; q < N; ++q)
-        if (!(d0_host[q] > 0.0) || !std::isfinite(d0_host[q])) return NH_ERR_ARG;
+    for (int b = 0; b < n_members; ++b) {
+        if (!d0_host[b]) return NH_ERR_ARG;
+        const long long N = (long long)descs[b].nx * descs[b].ny;
+        for (long long q = 0; q < N; ++q)
+            if (!(d0_host[b][q] > 0.0) || !std::isfinite(d0_host[b][q])) return NH_ERR_ARG;
+    }
     nh_grid2d* g = new (std::nothrow) nh_grid2d;
     if (!g) return NH_ERR_CUDA;
-    std::memset(static_cast<void*>(g), 0, sizeof(*g));
-    g->d = *desc;
+    g->nb = n_members;
+    g->pitch = (int)pitch;
+    g->d.assign(descs, descs + n_members);
+    g->slide_h.assign(n_members, Slide2{0.0, 1.0, 1.0, 0.0, 0.0, 0.0, 1.0, NH_SLIDE_NONE, 0});
+    g->member_set.assign(n_members, 0);
     g->stream = static_cast<cudaStream_t>(stream);
-    g->nx = desc->nx; g->ny = desc->ny;
-    carve2(*desc, g, static_cast<char*>(ws));
+    g->cap_stream = nullptr;
+    carve2(n_members, (int)pitch, g, static_cast<char*>(ws));
     int dev = 0;
     cudaGetDevice(&dev);
+    g->sms = 1;
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
     if (g->sms < 1) g->sms = 1;
-    g->items_grid = std::max(1, std::min(g->maxch, g->sms * 8));
-    g->pcr_grid = std::max(1, std::min(g->maxpb, g->sms * 2));
-    g->elem_grid = std::max(1, std::min((g->N + 255) / 256, g->sms * 8));
-    g->slide.shape = NH_SLIDE_NONE; g->slide.A = 0.0; g->slide.Lx = g->slide.Ly = 1.0;
-    g->s0 = 0.0; g->t0 = 1.0;
+    g->items_grid = (int)std::max(1LL, std::min((long long)g->maxch * g->nb, (long long)g->sms * 8));
+    g->pcr_grid = (int)std::max(1LL, std::min((long long)g->maxpb * g->nb, (long long)g->sms * 2));
+    g->egx = std::max(1, std::min((g->pitch + 255) / 256, (g->sms * 8 + g->nb - 1) / g->nb));
     g->crit = NH_CRIT_GLOBAL; g->knh = 1e-3; g->enlarge = 1; g->first_global = 0;
     g->rtol = 1e-12; g->max_iter = 20000; g->guess = NH_GUESS_PREV;
+    g->has_state = false;
+    g->t_base = 0.0; g->last_dt = 0.0; g->n_since = 0; g->steps = 0; g->cur = 0; g->lcur = 0;
+    g->graph[0] = g->graph[1] = nullptr;
+    g->graph_valid = false; g->use_graphs = true; g->graph_runs = 0;
+    std::memset(g->graph_key, 0, sizeof(g->graph_key));
     nh_status rc = NH_OK;
     cudaStream_t st = g->stream;
     do {
@@ -395,30 +573,68 @@ nh_status nh2d_create(const nh_grid2d_desc* desc, const double* d0_host, void* w
         int clk_khz = 0;
         cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
         g->barrier_budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL;   // about one second
+        if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            g->cap_stream = nullptr; rc = NH_ERR_CUDA; break;
+        }
+        std::vector<Geo2> geo_h(n_members);
+        for (int b = 0; b < n_members; ++b) geo_h[b] = geo2(descs[b]);
         if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess ||
-            cudaMemcpyAsync(g->d0, d0_host, sizeof(double) * N, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaMemcpyAsync(g->geos, geo_h.data(), sizeof(Geo2) * n_members, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(g->slides, g->slide_h.data(), sizeof(Slide2) * n_members, cudaMemcpyHostToDevice,
+                            st) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
         }
+        for (int b = 0; b < n_members && rc == NH_OK; ++b)
+            if (cudaMemcpyAsync(g->d0 + (size_t)b * g->pitch, d0_host[b],
+                                sizeof(double) * descs[b].nx * descs[b].ny, cudaMemcpyHostToDevice,
+                                st) != cudaSuccess)
+                rc = NH_ERR_CUDA;
+        // the host copies above are pageable: finish them before geo_h goes
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
     } while (0);
-    if (rc != NH_OK) { delete g; return rc; }
+    if (rc != NH_OK) {
+        if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+        delete g;
+        return rc;
+    }
     *out = g;
+    return NH_OK;
+}
+
+nh_status nh2d_create(const nh_grid2d_desc* desc, const double* d0_host, void* ws, size_t ws_bytes,
+                      void* stream, nh_grid2d** out)
+{
+    const double* d0s[1] = {d0_host};
+    return nh2d_create_ensemble(1, desc, d0s, ws, ws_bytes, stream, out);
+}
+
+int nh2d_members(const nh_grid2d* g) { return g ? g->nb : 0; }
+
+nh_status nh2d_set_member_bottom_motion(nh_grid2d* g, int m, const nh_slide2d_desc* s)
+{
+    if (!member_ok(g, m)) return NH_ERR_ARG;
+    Slide2 S{0.0, 1.0, 1.0, 0.0, 0.0, 0.0, 1.0, NH_SLIDE_NONE, 0};
+    if (s && s->shape != NH_SLIDE_NONE) {
+        if (s->shape != NH_SLIDE_GAUSS_LNCOSH || !(s->Lx > 0.0) || !(s->Ly > 0.0) || !(s->t0 > 0.0) ||
+            !std::isfinite(s->A) || !std::isfinite(s->xc0) || !std::isfinite(s->yc0) || !std::isfinite(s->s0))
+            return NH_ERR_ARG;
+        S.shape = NH_SLIDE_GAUSS_LNCOSH;
+        S.A = s->A; S.Lx = s->Lx; S.Ly = s->Ly; S.xc0 = s->xc0; S.yc0 = s->yc0; S.s0 = s->s0; S.t0 = s->t0;
+    }
+    g->slide_h[m] = S;
+    CK2(cudaMemcpyAsync(g->slides + m, &g->slide_h[m], sizeof(Slide2), cudaMemcpyHostToDevice, g->stream));
+    CK2(cudaStreamSynchronize(g->stream));
     return NH_OK;
 }
 
 nh_status nh2d_set_bottom_motion(nh_grid2d* g, const nh_slide2d_desc* s)
 {
     if (!g) return NH_ERR_ARG;
-    if (!s || s->shape == NH_SLIDE_NONE) {
-        g->slide.shape = NH_SLIDE_NONE;
-        return NH_OK;
+    for (int m = 0; m < g->nb; ++m) {
+        const nh_status rc = nh2d_set_member_bottom_motion(g, m, s);
+        if (rc != NH_OK) return rc;
     }
-    if (s->shape != NH_SLIDE_GAUSS_LNCOSH || !(s->Lx > 0.0) || !(s->Ly > 0.0) || !(s->t0 > 0.0) ||
-        !std::isfinite(s->A) || !std::isfinite(s->xc0) || !std::isfinite(s->yc0) || !std::isfinite(s->s0))
-        return NH_ERR_ARG;
-    g->slide.shape = NH_SLIDE_GAUSS_LNCOSH;
-    g->slide.A = s->A; g->slide.Lx = s->Lx; g->slide.Ly = s->Ly; g->slide.xc0 = s->xc0; g->slide.yc0 = s->yc0;
-    g->s0 = s->s0; g->t0 = s->t0;
     return NH_OK;
 }
 
@@ -438,58 +654,108 @@ nh_status nh2d_set_solver(nh_grid2d* g, double rtol, int max_iter, int guess)
     return NH_OK;
 }
 
-nh_status nh2d_set_state(nh_grid2d* g, const double* h, const double* hu, const double* hv, const double* hw,
-                         double t)
+nh_status nh2d_set_graphs(nh_grid2d* g, int on)
 {
-    if (!g || !h || !hu || !hv || !hw || !std::isfinite(t)) return NH_ERR_ARG;
-    const size_t N = (size_t)g->N;
+    if (!g) return NH_ERR_ARG;
+    g->use_graphs = on != 0;
+    if (!g->use_graphs) graph_destroy(g);
+    return NH_OK;
+}
+
+nh_status nh2d_set_member_state(nh_grid2d* g, int m, const double* h, const double* hu, const double* hv,
+                                const double* hw, double t)
+{
+    if (!member_ok(g, m) || !h || !hu || !hv || !hw || !std::isfinite(t)) return NH_ERR_ARG;
+    const size_t N = (size_t)g->d[m].nx * g->d[m].ny;
     for (size_t q = 0; q < N; ++q)
         if (!(h[q] > 0.0) || !std::isfinite(h[q]) || !std::isfinite(hu[q]) || !std::isfinite(hv[q]) ||
             !std::isfinite(hw[q]))
             return NH_ERR_ARG;
     cudaStream_t st = g->stream;
+    const size_t mo = (size_t)m * g->pitch;
     const double* src[4] = {h, hu, hv, hw};
     for (int f = 0; f < 4; ++f)
-        CK2(cudaMemcpyAsync(g->q[0][f], src[f], sizeof(double) * N, cudaMemcpyHostToDevice, st));
-    CK2(cudaMemsetAsync(g->psi, 0, sizeof(double) * N, st));
-    CK2(cudaMemsetAsync(g->nact[0], 0, sizeof(int), st));
-    CK2(cudaMemsetAsync(g->nact[1], 0, sizeof(int), st));
-    CK2(cudaMemsetAsync(g->act, 0, N, st));
+        CK2(cudaMemcpyAsync(g->q[g->cur][f] + mo, src[f], sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    CK2(cudaMemsetAsync(g->psi + mo, 0, sizeof(double) * g->pitch, st));
+    CK2(cudaMemsetAsync(g->nact[0] + m, 0, sizeof(int), st));
+    CK2(cudaMemsetAsync(g->nact[1] + m, 0, sizeof(int), st));
+    CK2(cudaMemsetAsync(g->act + mo, 0, g->pitch, st));
     CK2(cudaStreamSynchronize(st));
-    g->cur = 0; g->lcur = 0;
-    g->has_state = true;
+    g->member_set[m] = 1;
+    g->has_state = std::all_of(g->member_set.begin(), g->member_set.end(), [](char c) { return c != 0; });
     g->t_base = t; g->n_since = 0; g->steps = 0; g->last_dt = 0.0;
     return NH_OK;
 }
 
-nh_status nh2d_get_state(nh_grid2d* g, double* h, double* hu, double* hv, double* hw, double* p_nh)
+nh_status nh2d_set_state(nh_grid2d* g, const double* h, const double* hu, const double* hv, const double* hw,
+                         double t)
 {
-    if (!g) return NH_ERR_ARG;
+    return nh2d_set_member_state(g, 0, h, hu, hv, hw, t);
+}
+
+nh_status nh2d_get_member_state(nh_grid2d* g, int m, double* h, double* hu, double* hv, double* hw, double* p_nh)
+{
+    if (!member_ok(g, m)) return NH_ERR_ARG;
     if (!g->has_state) return NH_ERR_STATE;
     cudaStream_t st = g->stream;
-    const size_t N = (size_t)g->N;
+    const size_t N = (size_t)g->d[m].nx * g->d[m].ny;
+    const size_t mo = (size_t)m * g->pitch;
     double* dst[4] = {h, hu, hv, hw};
     for (int f = 0; f < 4; ++f)
-        if (dst[f]) CK2(cudaMemcpyAsync(dst[f], g->q[g->cur][f], sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        if (dst[f])
+            CK2(cudaMemcpyAsync(dst[f], g->q[g->cur][f] + mo, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     std::vector<double> hh, ps;
     if (p_nh) {
         hh.resize(N); ps.resize(N);
-        CK2(cudaMemcpyAsync(hh.data(), g->q[g->cur][0], sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-        CK2(cudaMemcpyAsync(ps.data(), g->psi, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        CK2(cudaMemcpyAsync(hh.data(), g->q[g->cur][0] + mo, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        CK2(cudaMemcpyAsync(ps.data(), g->psi + mo, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     }
     CK2(cudaStreamSynchronize(st));
     if (p_nh) {
-        const double sc = g->last_dt > 0.0 ? g->d.rho / g->last_dt : 0.0;   // p = rho psi / (dt h)
+        const double sc = g->last_dt > 0.0 ? g->d[m].rho / g->last_dt : 0.0;   // p = rho psi / (dt h)
         for (size_t q = 0; q < N; ++q) p_nh[q] = sc * ps[q] / hh[q];
     }
     return NH_OK;
 }
 
-nh_status nh2d_get_mask(nh_grid2d* g, unsigned char* mask)
+nh_status nh2d_get_state(nh_grid2d* g, double* h, double* hu, double* hv, double* hw, double* p_nh)
 {
-    if (!g || !mask) return NH_ERR_ARG;
-    CK2(cudaMemcpyAsync(mask, g->act, (size_t)g->N, cudaMemcpyDeviceToHost, g->stream));
+    return nh2d_get_member_state(g, 0, h, hu, hv, hw, p_nh);
+}
+
+nh_status nh2d_get_member_mask(nh_grid2d* g, int m, unsigned char* mask)
+{
+    if (!member_ok(g, m) || !mask) return NH_ERR_ARG;
+    const size_t N = (size_t)g->d[m].nx * g->d[m].ny;
+    CK2(cudaMemcpyAsync(mask, g->act + (size_t)m * g->pitch, N, cudaMemcpyDeviceToHost, g->stream));
     CK2(cudaStreamSynchronize(g->stream));
+    return NH_OK;
+}
+
+nh_status nh2d_get_mask(nh_grid2d* g, unsigned char* mask) { return nh2d_get_member_mask(g, 0, mask); }
+
+nh_status nh2d_get_member_info(nh_grid2d* g, int m, nh_step_info* info)
+{
+    if (!member_ok(g, m) || !info) return NH_ERR_ARG;
+    MState s;
+    std::vector<double> mp(g->nmass);
+    CK2(cudaMemcpyAsync(&s, g->ms + m, sizeof(MState), cudaMemcpyDeviceToHost, g->stream));
+    CK2(cudaMemcpyAsync(mp.data(), g->mass_part + (size_t)m * g->nmass, sizeof(double) * g->nmass,
+                        cudaMemcpyDeviceToHost, g->stream));
+    CK2(cudaStreamSynchronize(g->stream));
+    double mass = 0.0;
+    for (double v : mp) mass += v;
+    info->step = g->steps;
+    info->t = g->t_base + (double)g->n_since * g->last_dt;
+    info->n_active = s.n_active;
+    info->n_active_max = s.n_active;
+    info->iters = s.iters;
+    info->ir_passes = 0;
+    info->solver = s.n_active == 0 ? -1 : s.kind;
+    info->status = s.status;
+    info->rel_res = s.rel_res;
+    info->min_gamma = s.n_active > 0 ? s.min_gamma : 0.0;
+    info->mass = mass;
     return NH_OK;
 }
 
@@ -509,6 +775,33 @@ nh_status nh2d_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* info
     nh_run_info R;
     std::memset(&R, 0, sizeof(R));
     nh_status rc = NH_OK;
+    // a first step that is global by request runs on its own
+    if (n_steps > 0 && g->first_global && g->steps == 0) {
+        nh_step_info si;
+        rc = step2(g, dt, &si);
+        R.last = si;
+        if (rc != NH_OK) {
+            if (info) *info = R;
+            return rc;
+        }
+        R.steps = 1; R.iters_total = si.iters; R.active_total = si.n_active;
+        n_steps -= 1;
+    }
+    if (n_steps > 0 && graph_eligible(g, dt)) {
+        nh_run_info Rg;
+        std::memset(&Rg, 0, sizeof(Rg));
+        rc = graph_run(g, dt, n_steps, &Rg);
+        R.steps += Rg.steps; R.iters_total += Rg.iters_total; R.active_total += Rg.active_total;
+        R.last = Rg.last;
+        if (rc == NH_OK || Rg.steps == n_steps) {
+            if (info) *info = R;
+            return rc;
+        }
+        // a step failed inside the captured run: redo it step by step (this
+        // also gives members whose CG broke down their BiCGStab fallback)
+        n_steps -= Rg.steps;
+        rc = NH_OK;
+    }
     for (long long k = 0; k < n_steps; ++k) {
         nh_step_info si;
         rc = step2(g, dt, &si);
@@ -522,10 +815,14 @@ nh_status nh2d_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* info
     return rc;
 }
 
+long long nh2d_graph_runs(const nh_grid2d* g) { return g ? g->graph_runs : -1; }
+
 void nh2d_destroy(nh_grid2d* g)
 {
     if (!g) return;
     cudaStreamSynchronize(g->stream);
+    graph_destroy(g);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
 }
 

@@ -9,10 +9,13 @@
 //                list and the cell -> list-index map                      (a3)
 //  k2_assemble   9-point rows of -div(K grad psi) + gamma psi = R        (a4)
 //  k2_correct    Eqs. 10-11 in 2D on the active cells                    (a6)
-// The Krylov solve (a5) is the 1D members' (nh_kernels1d.cuh) on one member
-// holding all active cells in row-major order: the W / E neighbours are the
-// list neighbours (so the line preconditioner solves x-lines), S, N and the
-// four diagonal couplings are the solver's extra couplings.
+// The Krylov solve (a5) is the 1D members' (nh_kernels1d.cuh): each 2D grid
+// of an ensemble is one member holding its active cells in row-major order,
+// so the W / E neighbours are the list neighbours (the line preconditioner
+// solves x-lines) and S, N and the four diagonal couplings are the solver's
+// extra couplings.  Members (grids of their own sizes, spacings, sides and
+// slides) sit at b * pitch in every per-cell array; kernels take the member
+// from blockIdx.y (or from the work item) and its geometry from geos[b].
 //
 // The 2D equations generalise the paper's 1D Eqs. 1-5 and 10-11 by replacing
 // x-derivatives with gradients; the elimination of the corrected momenta into
@@ -32,8 +35,9 @@ struct Geo2 {
 };
 
 // 2D slide: mound A exp(-xi^2 - zeta^2), xi = (x - xc0 - s)/Lx, zeta = (y - yc0)/Ly.
+// Its position s(t) = s0 ln cosh(t / t0) (Sec. 4.2).
 struct Slide2 {
-    double A, Lx, Ly, xc0, yc0;
+    double A, Lx, Ly, xc0, yc0, s0, t0;
     int shape, pad;
 };
 
@@ -41,6 +45,31 @@ struct Slide2 {
 struct Kin2 {
     double s, sd, sdd;
 };
+
+// kin[2b] at t^n, kin[2b + 1] at t^{n+1}: s = s0 ln cosh(t/t0),
+// s' = (s0/t0) tanh(t/t0), s'' = (s0/t0^2) / cosh^2(t/t0).  Times from the
+// arguments, or from the captured run's control block when tc is set.
+static __global__ void k2_kin(const Slide2* __restrict__ slides, int nb, double t_n, double t_n1,
+                              const TimeCtl* __restrict__ tc, Kin2* kin)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb || (tc && tc->abort)) return;
+    if (tc) {
+        t_n = tc->t_base + (double)tc->n * tc->dt;
+        t_n1 = tc->t_base + (double)(tc->n + 1) * tc->dt;
+    }
+    const Slide2 S = slides[b];
+    for (int w = 0; w < 2; ++w) {
+        Kin2 k{0.0, 0.0, 0.0};
+        if (S.shape == NH_SLIDE_GAUSS_LNCOSH) {
+            const double z = (w ? t_n1 : t_n) / S.t0, c = cosh(z);
+            k.s = S.s0 * log(c);
+            k.sd = (S.s0 / S.t0) * tanh(z);
+            k.sdd = (S.s0 / (S.t0 * S.t0)) / (c * c);
+        }
+        kin[2 * b + w] = k;
+    }
+}
 
 __device__ __forceinline__ int g2_index1(int bc, int n, int i, double* odd)
 {
@@ -121,11 +150,20 @@ __device__ __forceinline__ void bottom2(const Geo2& G, const double* __restrict_
     out[6] = d_t; out[7] = d_xt; out[8] = d_yt; out[9] = d_tt;
 }
 
-static __global__ void k2_depth(Geo2 G, const double* __restrict__ d0, Slide2 S, double s, double* d)
+// Depth at t^n (which = 0) or t^{n+1} (which = 1).
+static __global__ void k2_depth(const Geo2* __restrict__ geos, const Slide2* __restrict__ slides,
+                                const Kin2* __restrict__ kin, int which, size_t pitch,
+                                const double* __restrict__ d0, double* d, const TimeCtl* __restrict__ tc)
 {
+    if (tc && tc->abort) return;
+    const int b = blockIdx.y;
+    const Geo2 G = geos[b];
+    const Slide2 S = slides[b];
+    const double s = kin[2 * b + which].s;
+    const size_t mo = (size_t)b * pitch;
     const int N = G.nx * G.ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
-        d[c] = d0[c] - mound2(G, S, c % G.nx, c / G.nx, s);
+        d[mo + c] = d0[mo + c] - mound2(G, S, c % G.nx, c / G.nx, s);
 }
 
 __device__ __forceinline__ double slope2(int lim, double vm, double v0, double vp)
@@ -149,14 +187,17 @@ __device__ __forceinline__ void rusanov2(double g, double hL, double nL, double 
 }
 
 struct StageArgs {
-    Geo2 G;
-    const double *h, *hu, *hv, *hw;        // state the rate is evaluated on
+    Geo2 G;                                // this member's geometry (set in the kernel)
+    const Geo2* geos;
+    size_t pitch;
+    const double *h, *hu, *hv, *hw;        // state the rate is evaluated on (member-offset in the kernel)
     const double* d;                       // depth at that state's time
     const double *h0, *hu0, *hv0, *hw0;    // Q^n
     double *k1h, *k1u, *k1v, *k1w;         // stage-1 rates (written at stage 1, read at stage 2)
     double *oh, *ohu, *ohv, *ohw;          // output: Q* (stage 1) or Q~ (stage 2)
     double dt;
     int stage;
+    const TimeCtl* tc;                     // captured runs: skip after an aborted step
 };
 
 // One direction's contribution to the rates of cell (i, j): flux divergence
@@ -205,6 +246,14 @@ __device__ __forceinline__ void stage_dir(const StageArgs& a, int i, int j, int 
 
 static __global__ void k2_stage(StageArgs a)
 {
+    if (a.tc && a.tc->abort) return;
+    const int b = blockIdx.y;
+    const size_t mo = (size_t)b * a.pitch;
+    a.G = a.geos[b];
+    a.h += mo; a.hu += mo; a.hv += mo; a.hw += mo; a.d += mo;
+    a.h0 += mo; a.hu0 += mo; a.hv0 += mo; a.hw0 += mo;
+    a.k1h += mo; a.k1u += mo; a.k1v += mo; a.k1w += mo;
+    a.oh += mo; a.ohu += mo; a.ohv += mo; a.ohw += mo;
     const int N = a.G.nx * a.G.ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int i = c % a.G.nx, j = c / a.G.nx;
@@ -231,10 +280,15 @@ static __global__ void k2_stage(StageArgs a)
 
 // Criterion (Sec. 5.1, 2D form: |eta/d|, |grad eta|, |u|, |grad u|
 // (Frobenius), |w|, |grad w|; central differences), strict > k_nh.
-static __global__ void k2_marks(Geo2 G, const double* __restrict__ h, const double* __restrict__ hu,
-                                const double* __restrict__ hv, const double* __restrict__ hw,
-                                const double* __restrict__ d, int crit, double knh, unsigned char* marks)
+static __global__ void k2_marks(const Geo2* __restrict__ geos, size_t pitch, const double* __restrict__ h,
+                                const double* __restrict__ hu, const double* __restrict__ hv,
+                                const double* __restrict__ hw, const double* __restrict__ d, int crit, double knh,
+                                unsigned char* marks)
 {
+    const int b = blockIdx.y;
+    const Geo2 G = geos[b];
+    const size_t mo = (size_t)b * pitch;
+    h += mo; hu += mo; hv += mo; hw += mo; d += mo; marks += mo;
     const int N = G.nx * G.ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int i = c % G.nx, j = c / G.nx;
@@ -270,8 +324,14 @@ static __global__ void k2_marks(Geo2 G, const double* __restrict__ h, const doub
 }
 
 // Moore enlargement of radius e (walls stop it, periodic sides wrap).
-static __global__ void k2_dilate(Geo2 G, const unsigned char* __restrict__ marks, int e, unsigned char* act)
+static __global__ void k2_dilate(const Geo2* __restrict__ geos, size_t pitch, const unsigned char* __restrict__ marks,
+                                 int e, unsigned char* act, const TimeCtl* __restrict__ tc)
 {
+    if (tc && tc->abort) return;
+    const int b = blockIdx.y;
+    const Geo2 G = geos[b];
+    const size_t mo = (size_t)b * pitch;
+    marks += mo; act += mo;
     const int N = G.nx * G.ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int i = c % G.nx, j = c / G.nx;
@@ -287,9 +347,14 @@ static __global__ void k2_dilate(Geo2 G, const unsigned char* __restrict__ marks
 
 constexpr int kCompact2 = 1024;   // cells per compaction block
 
-static __global__ void __launch_bounds__(kCompact2) k2_count(const unsigned char* __restrict__ act, int N, int* cnt)
+static __global__ void __launch_bounds__(kCompact2) k2_count(const Geo2* __restrict__ geos, size_t pitch,
+                                                            const unsigned char* __restrict__ act, int nblk, int* cnt)
 {
     __shared__ int s[32];
+    const int b = blockIdx.y;
+    const int N = geos[b].nx * geos[b].ny;
+    act += (size_t)b * pitch;
+    cnt += (size_t)b * nblk;
     const int c = blockIdx.x * kCompact2 + threadIdx.x;
     const int v = (c < N && act[c]) ? 1 : 0;
     const int wsum = __popc(__ballot_sync(0xffffffffu, v));
@@ -302,14 +367,24 @@ static __global__ void __launch_bounds__(kCompact2) k2_count(const unsigned char
     }
 }
 
-// Exclusive scan of the block counts (one CTA); the member's solver state is
-// reset as the 1D compaction does, with n_active = the total.
+// Exclusive scan of a member's block counts (one CTA per member); the
+// member's solver state is reset as the 1D compaction does, with n_active =
+// the total.
 static __global__ void __launch_bounds__(1024) k2_scan(const int* __restrict__ cnt, int nblk, int* off, int* nact,
-                                                       MState* ms)
+                                                       MState* ms, const TimeCtl* __restrict__ tc)
 {
     __shared__ int s_w[32];
     __shared__ int s_base;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int mb = blockIdx.x;   // member
+    cnt += (size_t)mb * nblk;
+    off += (size_t)mb * nblk;
+    nact += mb;
+    ms += mb;
+    if (tc && tc->abort) {   // captured run after a failed step: park the solver
+        if (tid == 0) ms->done = 1;
+        return;
+    }
     if (tid == 0) s_base = 0;
     __syncthreads();
     for (int b0 = 0; b0 < nblk; b0 += 1024) {
@@ -352,10 +427,17 @@ static __global__ void __launch_bounds__(1024) k2_scan(const int* __restrict__ c
 }
 
 // list[k] = k-th active cell in row-major order; inv[c] = k, or -1.
-static __global__ void __launch_bounds__(kCompact2) k2_emit(const unsigned char* __restrict__ act, int N,
-                                                           const int* __restrict__ off, int* list, int* inv)
+static __global__ void __launch_bounds__(kCompact2) k2_emit(const Geo2* __restrict__ geos, size_t pitch,
+                                                           const unsigned char* __restrict__ act, int nblk,
+                                                           const int* __restrict__ off, int* list, int* inv,
+                                                           const TimeCtl* __restrict__ tc)
 {
+    if (tc && tc->abort) return;
     __shared__ int s_w[32];
+    const int b = blockIdx.y;
+    const int N = geos[b].nx * geos[b].ny;
+    act += (size_t)b * pitch; list += (size_t)b * pitch; inv += (size_t)b * pitch;
+    off += (size_t)b * nblk;
     const int c = blockIdx.x * kCompact2 + threadIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool v = c < N && act[c];
@@ -389,24 +471,32 @@ struct CellQ2 {
 };
 
 struct Asm2Args {
-    Geo2 G;
+    const Geo2* geos; const Slide2* slides;
+    const Kin2* kin;                       // kin[2b + 1]: bottom motion at t^{n+1}
+    int nb, pitch, maxch;
     const double *ht, *hut, *hvt, *hwt;    // Q~
     const double* d0;
     const double* d1;                      // depth at t^{n+1}
-    Slide2 S; Kin2 K;                      // bottom motion at t^{n+1}
     double dt;
     const int* list; const int* inv;
     MState* ms;
     double *diag, *offl, *offr, *R;
     int *nbl, *nbr;
-    double* ext_c; int* ext_k; size_t ext_stride;   // S, N, SW, SE, NW, NE
+    double* ext_c; int* ext_k; size_t ext_stride;   // S, N, SW, SE, NW, NE; stride nb * pitch
     double *c6, *cx, *cy, *phi, *ddx, *ddy;
-    double* part; int* cnt;
+    double* part; int* cnt;                // part: [2][nb * maxch]
     int solver;
     const int2* items; const Ctl* ctl;
 };
 
-__device__ __forceinline__ CellQ2 cell_q2(const Asm2Args& a, int i, int j)
+// One member's fields as seen by the assembly (pointers at the member's slice).
+struct Mem2 {
+    Geo2 G; Slide2 S; Kin2 K;
+    const double *ht, *hut, *hvt, *d0, *d1;
+    double dt;
+};
+
+__device__ __forceinline__ CellQ2 cell_q2(const Mem2& a, int i, int j)
 {
     const Geo2& G = a.G;
     double b[10], o1, o2;
@@ -438,7 +528,7 @@ __device__ __forceinline__ CellQ2 cell_q2(const Asm2Args& a, int i, int j)
 }
 
 // The same seen from a neighbour: mirrored cells flip their odd components.
-__device__ __forceinline__ CellQ2 cell_q2_at(const Asm2Args& a, int i, int j)
+__device__ __forceinline__ CellQ2 cell_q2_at(const Mem2& a, int i, int j)
 {
     double ox, oy;
     const int c = g2_cell(a.G, i, j, &ox, &oy);
@@ -449,60 +539,67 @@ __device__ __forceinline__ CellQ2 cell_q2_at(const Asm2Args& a, int i, int j)
     return q;
 }
 
-// Rows of the 9-point operator on the active cells (one member; work items
-// of kChunk list entries) and the member's ||R||^2 and min gamma.
+// Rows of the 9-point operator on the active cells (work items of kChunk
+// list entries of one member) and each member's ||R||^2 and min gamma.
 static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args a)
 {
     __shared__ double red[64];
-    const Geo2& G = a.G;
     const int n_items = a.ctl->n_items;
-    const double idx2 = 1.0 / (G.dx * G.dx), idy2 = 1.0 / (G.dy * G.dy), ixy = 1.0 / (4.0 * G.dx * G.dy);
     for (int wi = blockIdx.x; wi < n_items; wi += gridDim.x) {
         const int2 itm = a.items[wi];
         const int b = itm.x, jj = itm.y;
         const int n = a.ms[b].n_active, nch = a.ms[b].nchunks, ioff = a.ms[b].ioff;
+        const size_t mo = (size_t)b * a.pitch;
+        Mem2 m;
+        m.G = a.geos[b]; m.S = a.slides[b]; m.K = a.kin[2 * b + 1];
+        m.ht = a.ht + mo; m.hut = a.hut + mo; m.hvt = a.hvt + mo; m.d0 = a.d0 + mo; m.d1 = a.d1 + mo;
+        m.dt = a.dt;
+        const Geo2& G = m.G;
+        const int* inv = a.inv + mo;
+        const double idx2 = 1.0 / (G.dx * G.dx), idy2 = 1.0 / (G.dy * G.dy), ixy = 1.0 / (4.0 * G.dx * G.dy);
         const int k = jj * kChunk + threadIdx.x;
         double r2 = 0.0, gmin = INFINITY;
         if (k < n) {
-            const int c = a.list[k];
+            const size_t o = mo + k;
+            const int c = a.list[o];
             const int i = c % G.nx, j = c / G.nx;
-            const CellQ2 q = cell_q2(a, i, j);
-            const CellQ2 W = cell_q2_at(a, i - 1, j), E = cell_q2_at(a, i + 1, j);
-            const CellQ2 S = cell_q2_at(a, i, j - 1), N = cell_q2_at(a, i, j + 1);
+            const CellQ2 q = cell_q2(m, i, j);
+            const CellQ2 W = cell_q2_at(m, i - 1, j), E = cell_q2_at(m, i + 1, j);
+            const CellQ2 S = cell_q2_at(m, i, j - 1), N = cell_q2_at(m, i, j + 1);
             const double Kw = 0.5 * (W.Kxx + q.Kxx), Ke = 0.5 * (q.Kxx + E.Kxx);
             const double Ks = 0.5 * (S.Kyy + q.Kyy), Kn = 0.5 * (q.Kyy + N.Kyy);
             const double div_beta = (E.bx - W.bx) / (2.0 * G.dx) + (N.by - S.by) / (2.0 * G.dy);
             const double div_V = (E.Vx - W.Vx) / (2.0 * G.dx) + (N.Vy - S.Vy) / (2.0 * G.dy);
             const double h = q.h, h2 = h * h;
             const double gam = div_beta + 12.0 * (1.0 + q.G) / (h2 * h * q.D);
-            const double Rk = -(div_V + 2.0 * (q.d_x * q.U0 + q.d_y * q.V0) / h2 + 2.0 * a.hwt[c] / h2
+            const double Rk = -(div_V + 2.0 * (q.d_x * q.U0 + q.d_y * q.V0) / h2 + 2.0 * a.hwt[mo + c] / h2
                                 + 2.0 * q.phi / h2 + 2.0 * q.d_t / h);
             const double cW = -Kw * idx2, cE = -Ke * idx2, cS = -Ks * idy2, cN = -Kn * idy2;
             const double cNE = -(E.Kxy + N.Kxy) * ixy, cSW = -(W.Kxy + S.Kxy) * ixy;
             const double cSE = (E.Kxy + S.Kxy) * ixy, cNW = (W.Kxy + N.Kxy) * ixy;
             auto nbk = [&](int di, int dj) {
                 const int qc = g2_inner(G, i + di, j + dj);
-                return qc >= 0 ? a.inv[qc] : -1;
+                return qc >= 0 ? inv[qc] : -1;
             };
             const int kW = nbk(-1, 0), kE = nbk(1, 0);
             const int ke[6] = {nbk(0, -1), nbk(0, 1), nbk(-1, -1), nbk(1, -1), nbk(-1, 1), nbk(1, 1)};
             const double ce[6] = {cS, cN, cSW, cSE, cNW, cNE};
-            a.diag[k] = (Kw + Ke) * idx2 + (Ks + Kn) * idy2 + gam;
-            a.offl[k] = kW >= 0 ? cW : 0.0;
-            a.offr[k] = kE >= 0 ? cE : 0.0;
-            a.nbl[k] = kW;
-            a.nbr[k] = kE;
+            a.diag[o] = (Kw + Ke) * idx2 + (Ks + Kn) * idy2 + gam;
+            a.offl[o] = kW >= 0 ? cW : 0.0;
+            a.offr[o] = kE >= 0 ? cE : 0.0;
+            a.nbl[o] = kW;
+            a.nbr[o] = kE;
             for (int e = 0; e < 6; ++e) {
-                a.ext_c[e * a.ext_stride + k] = ke[e] >= 0 ? ce[e] : 0.0;
-                a.ext_k[e * a.ext_stride + k] = ke[e];
+                a.ext_c[e * a.ext_stride + o] = ke[e] >= 0 ? ce[e] : 0.0;
+                a.ext_k[e * a.ext_stride + o] = ke[e];
             }
-            a.R[k] = Rk;
-            a.c6[k] = 6.0 / (h * q.D);
-            a.cx[k] = q.d_x / q.D;
-            a.cy[k] = q.d_y / q.D;
-            a.phi[k] = q.phi;
-            a.ddx[k] = q.d_x;
-            a.ddy[k] = q.d_y;
+            a.R[o] = Rk;
+            a.c6[o] = 6.0 / (h * q.D);
+            a.cx[o] = q.d_x / q.D;
+            a.cy[o] = q.d_y / q.D;
+            a.phi[o] = q.phi;
+            a.ddx[o] = q.d_x;
+            a.ddy[o] = q.d_y;
             r2 = Rk * Rk;
             gmin = gam;
         }
@@ -510,7 +607,7 @@ static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args a)
         block_sum<1>(v, red);
         const double gm = block_min(gmin, red);
         double* P0 = a.part;
-        double* P1 = a.part + nch;   // one member: its nch items are items 0 .. nch-1
+        double* P1 = a.part + (size_t)a.nb * a.maxch;
         if (threadIdx.x == 0) { P0[wi] = v[0]; P1[wi] = gm; }
         if (arrive_last(a.cnt, b, nch)) {
             const double bn2 = member_sum(P0 + ioff, nch, red);
@@ -528,8 +625,8 @@ static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args a)
 }
 
 struct Corr2Args {
-    Geo2 G;
-    int n;                       // active cells
+    const Geo2* geos;
+    int pitch;
     const int* list;
     const int* nbl; const int* nbr; const int* ext_k; size_t ext_stride;
     const double* x;             // psi on the active cells
@@ -537,37 +634,52 @@ struct Corr2Args {
     const MState* ms;
     double *hu, *hv, *hw;        // Q~, corrected in place
     double* psi;                 // dense psi (warm start, pressure output)
+    const int2* items; const Ctl* ctl;
+    const TimeCtl* tc;           // captured runs: skip unless the step was accepted
 };
 
 // Eqs. 10-11 in 2D: with psi = a q, P = c6 psi + cx psi_x + cy psi_y + a phi;
 // U = U~ - grad psi + grad d P, hw = hw~ + P; psi = 0 off the mask.
-static __global__ void k2_correct(Corr2Args a)
+static __global__ void __launch_bounds__(kChunk) k2_correct(Corr2Args a)
 {
-    const bool zero = a.ms[0].zero_sol != 0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
-        const int kw = a.nbl[k], ke = a.nbr[k];
-        const int ks = a.ext_k[k], kn = a.ext_k[a.ext_stride + k];
-        const double ps = zero ? 0.0 : a.x[k];
-        const double pw = (zero || kw < 0) ? 0.0 : a.x[kw], pe = (zero || ke < 0) ? 0.0 : a.x[ke];
-        const double pss = (zero || ks < 0) ? 0.0 : a.x[ks], pn = (zero || kn < 0) ? 0.0 : a.x[kn];
-        const double px = (pe - pw) / (2.0 * a.G.dx), py = (pn - pss) / (2.0 * a.G.dy);
-        const double P = a.c6[k] * ps + a.cx[k] * px + a.cy[k] * py + a.phi[k];
-        const int c = a.list[k];
-        a.hu[c] = a.hu[c] + (-px + a.ddx[k] * P);
-        a.hv[c] = a.hv[c] + (-py + a.ddy[k] * P);
+    if (a.tc && a.tc->abort) return;
+    const int n_items = a.ctl->n_items;
+    for (int wi = blockIdx.x; wi < n_items; wi += gridDim.x) {
+        const int2 itm = a.items[wi];
+        const int b = itm.x;
+        const int k = itm.y * kChunk + threadIdx.x;
+        if (k >= a.ms[b].n_active) continue;
+        const bool zero = a.ms[b].zero_sol != 0;
+        const size_t mo = (size_t)b * a.pitch, o = mo + k;
+        const double dx = a.geos[b].dx, dy = a.geos[b].dy;
+        const double* x = a.x + mo;
+        const int kw = a.nbl[o], ke = a.nbr[o];
+        const int ks = a.ext_k[o], kn = a.ext_k[a.ext_stride + o];
+        const double ps = zero ? 0.0 : x[k];
+        const double pw = (zero || kw < 0) ? 0.0 : x[kw], pe = (zero || ke < 0) ? 0.0 : x[ke];
+        const double pss = (zero || ks < 0) ? 0.0 : x[ks], pn = (zero || kn < 0) ? 0.0 : x[kn];
+        const double px = (pe - pw) / (2.0 * dx), py = (pn - pss) / (2.0 * dy);
+        const double P = a.c6[o] * ps + a.cx[o] * px + a.cy[o] * py + a.phi[o];
+        const size_t c = mo + a.list[o];
+        a.hu[c] = a.hu[c] + (-px + a.ddx[o] * P);
+        a.hv[c] = a.hv[c] + (-py + a.ddy[o] * P);
         a.hw[c] = a.hw[c] + P;
         a.psi[c] = ps;
     }
 }
 
-// Block partial sums of h (FP64).
-static __global__ void __launch_bounds__(256) k2_mass(const double* __restrict__ h, int N, double* part)
+// Block partial sums of h dx dy (FP64): part[b * gridDim.x + blockIdx.x].
+static __global__ void __launch_bounds__(256) k2_mass(const Geo2* __restrict__ geos, size_t pitch,
+                                                     const double* __restrict__ h, double* part)
 {
     __shared__ double red[32];
+    const int b = blockIdx.y;
+    const int N = geos[b].nx * geos[b].ny;
+    h += (size_t)b * pitch;
     double v[1] = {0.0};
     for (int c = blockIdx.x * 256 + threadIdx.x; c < N; c += gridDim.x * 256) v[0] += h[c];
     block_sum<1>(v, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+    if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = v[0] * geos[b].dx * geos[b].dy;
 }
 
 }  // namespace nh

@@ -40,7 +40,9 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh_cnn_set_params", "nh_cnn_record", "nh_cnn_harvest", "nh_cnn_choices",
            "nh2d_workspace_bytes", "nh2d_create", "nh2d_set_bottom_motion", "nh2d_set_criterion",
            "nh2d_set_solver", "nh2d_set_state", "nh2d_get_state", "nh2d_get_mask", "nh2d_step",
-           "nh2d_run", "nh2d_destroy")
+           "nh2d_run", "nh2d_destroy", "nh2d_ensemble_workspace_bytes", "nh2d_create_ensemble", "nh2d_members",
+           "nh2d_set_member_bottom_motion", "nh2d_set_graphs", "nh2d_set_member_state", "nh2d_get_member_state",
+           "nh2d_get_member_mask", "nh2d_get_member_info", "nh2d_graph_runs")
 NH_CNN_PARAMS = 9328
 NH_CNN_IN = 16
 NH_STATIC_MAX_CELLS = 262144
@@ -169,8 +171,25 @@ def load():
         L.nh2d_run.argtypes = [vp, C.c_double, C.c_longlong, C.POINTER(nh_run_info)]
         L.nh2d_destroy.argtypes = [vp]
         L.nh2d_destroy.restype = None
+        L.nh2d_ensemble_workspace_bytes.argtypes = [C.c_int, C.POINTER(nh_grid2d_desc)]
+        L.nh2d_ensemble_workspace_bytes.restype = sz
+        L.nh2d_create_ensemble.argtypes = [C.c_int, C.POINTER(nh_grid2d_desc), C.POINTER(_D), vp, sz, vp,
+                                           C.POINTER(C.c_void_p)]
+        L.nh2d_members.argtypes = [vp]
+        L.nh2d_members.restype = C.c_int
+        L.nh2d_set_member_bottom_motion.argtypes = [vp, C.c_int, C.POINTER(nh_slide2d_desc)]
+        L.nh2d_set_graphs.argtypes = [vp, C.c_int]
+        L.nh2d_set_member_state.argtypes = [vp, C.c_int, _D, _D, _D, _D, C.c_double]
+        L.nh2d_get_member_state.argtypes = [vp, C.c_int, _D, _D, _D, _D, _D]
+        L.nh2d_get_member_mask.argtypes = [vp, C.c_int, C.POINTER(C.c_ubyte)]
+        L.nh2d_get_member_info.argtypes = [vp, C.c_int, C.POINTER(nh_step_info)]
+        L.nh2d_graph_runs.argtypes = [vp]
+        L.nh2d_graph_runs.restype = C.c_longlong
         for f in ("nh2d_create", "nh2d_set_bottom_motion", "nh2d_set_criterion", "nh2d_set_solver",
-                  "nh2d_set_state", "nh2d_get_state", "nh2d_get_mask", "nh2d_step", "nh2d_run"):
+                  "nh2d_set_state", "nh2d_get_state", "nh2d_get_mask", "nh2d_step", "nh2d_run",
+                  "nh2d_create_ensemble", "nh2d_set_member_bottom_motion", "nh2d_set_graphs",
+                  "nh2d_set_member_state", "nh2d_get_member_state", "nh2d_get_member_mask",
+                  "nh2d_get_member_info"):
             getattr(L, f).restype = C.c_int
         L.nh_status_string.argtypes = [C.c_int]
         L.nh_status_string.restype = C.c_char_p
@@ -488,39 +507,76 @@ def nh_cnn_adam(params, grad, m, v, step, lr):
 
 
 class Grid2D:
-    """One 2D grid (nhswe2d.h).  Arrays are (ny, nx), x fastest; the workspace
-    is a torch.uint8 tensor on the current CUDA device."""
+    """2D grids (nhswe2d.h): one grid, or an ensemble of grids stepped
+    together (``Grid2D.ensemble``).  Arrays are (ny, nx), x fastest; the
+    workspace is a torch.uint8 tensor on the current CUDA device."""
 
     def __init__(self, nx, ny, dx, dy, d0, bc_x=NH_BC_WALL, bc_y=NH_BC_WALL, limiter=NH_LIM_CENTRAL,
                  x0=0.0, y0=0.0, g=9.81, rho=1000.0, stream=None):
+        self._create([dict(nx=nx, ny=ny, dx=dx, dy=dy, d0=d0, bc_x=bc_x, bc_y=bc_y, limiter=limiter,
+                           x0=x0, y0=y0, g=g, rho=rho)], stream)
+
+    @classmethod
+    def ensemble(cls, members, stream=None):
+        """members: dicts with nx, ny, dx, dy, d0 and optionally bc_x, bc_y,
+        limiter, x0, y0, g, rho (the single-grid constructor's arguments)."""
+        self = cls.__new__(cls)
+        self._create(list(members), stream)
+        return self
+
+    def _create(self, members, stream):
         import torch
         self.L = load()
-        self.nx, self.ny = int(nx), int(ny)
-        self.desc = nh_grid2d_desc(self.nx, self.ny, int(bc_x), int(bc_y), int(limiter), float(dx), float(dy),
-                                   float(x0), float(y0), float(g), float(rho))
-        n = self.L.nh2d_workspace_bytes(C.byref(self.desc))
+        self.h = None
+        self.shapes = [(int(m["ny"]), int(m["nx"])) for m in members]
+        self.nx, self.ny = self.shapes[0][1], self.shapes[0][0]
+        n_m = len(members)
+        descs = (nh_grid2d_desc * n_m)()
+        for i, m in enumerate(members):
+            descs[i] = nh_grid2d_desc(int(m["nx"]), int(m["ny"]), int(m.get("bc_x", NH_BC_WALL)),
+                                      int(m.get("bc_y", NH_BC_WALL)), int(m.get("limiter", NH_LIM_CENTRAL)),
+                                      float(m["dx"]), float(m["dy"]), float(m.get("x0", 0.0)),
+                                      float(m.get("y0", 0.0)), float(m.get("g", 9.81)), float(m.get("rho", 1000.0)))
+        self.descs = descs
+        self.desc = descs[0]
+        n = self.L.nh2d_ensemble_workspace_bytes(n_m, descs)
         if n == 0:
-            raise NHError(NH_ERR_ARG, "nh2d_workspace_bytes")
+            raise NHError(NH_ERR_ARG, "nh2d_ensemble_workspace_bytes")
         self.ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
         ptr = (self.ws.data_ptr() + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d0s = [self._f(m["d0"], i) for i, m in enumerate(members)]
+        arr = (_D * n_m)(*[_dptr(v) for v in d0s])
         h = C.c_void_p()
-        _check(self.L.nh2d_create(C.byref(self.desc), _dptr(self._f(d0)), C.c_void_p(ptr), C.c_size_t(n),
-                                  C.c_void_p(self.stream.cuda_stream), C.byref(h)), "nh2d_create")
+        _check(self.L.nh2d_create_ensemble(n_m, descs, arr, C.c_void_p(ptr), C.c_size_t(n),
+                                           C.c_void_p(self.stream.cuda_stream), C.byref(h)), "nh2d_create_ensemble")
         self.h = h
 
-    def _f(self, a):
-        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (self.ny, self.nx)))
+    @property
+    def members(self):
+        return self.L.nh2d_members(self.h)
+
+    def _shape(self, member):
+        # an out-of-range member reaches the library, which rejects it
+        return self.shapes[member] if 0 <= member < len(self.shapes) else (1, 1)
+
+    def _f(self, a, member=0):
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), self._shape(member)))
         return a.reshape(-1)
 
-    def set_bottom_motion(self, slide=None):
-        if slide is None:
-            _check(self.L.nh2d_set_bottom_motion(self.h, None), "nh2d_set_bottom_motion")
-            return
-        s = nh_slide2d_desc(int(slide.get("shape", NH_SLIDE_GAUSS_LNCOSH)), float(slide["A"]), float(slide["Lx"]),
-                            float(slide["Ly"]), float(slide["xc0"]), float(slide["yc0"]), float(slide["s0"]),
-                            float(slide["t0"]))
-        _check(self.L.nh2d_set_bottom_motion(self.h, C.byref(s)), "nh2d_set_bottom_motion")
+    @staticmethod
+    def _slide(slide):
+        return nh_slide2d_desc(int(slide.get("shape", NH_SLIDE_GAUSS_LNCOSH)), float(slide["A"]),
+                               float(slide["Lx"]), float(slide["Ly"]), float(slide["xc0"]), float(slide["yc0"]),
+                               float(slide["s0"]), float(slide["t0"]))
+
+    def set_bottom_motion(self, slide=None, member=None):
+        """slide: dict (A, Lx, Ly, xc0, yc0, s0, t0) or None; member None = all."""
+        ref = None if slide is None else C.byref(self._slide(slide))
+        if member is None:
+            _check(self.L.nh2d_set_bottom_motion(self.h, ref), "nh2d_set_bottom_motion")
+        else:
+            _check(self.L.nh2d_set_member_bottom_motion(self.h, int(member), ref), "nh2d_set_member_bottom_motion")
 
     def set_criterion(self, kind, k_nh=1e-3, enlarge=1, first_step_global=False):
         _check(self.L.nh2d_set_criterion(self.h, int(kind), float(k_nh), int(enlarge), int(bool(first_step_global))),
@@ -529,20 +585,35 @@ class Grid2D:
     def set_solver(self, rtol=1e-12, max_iter=20000, guess=NH_GUESS_PREV):
         _check(self.L.nh2d_set_solver(self.h, float(rtol), int(max_iter), int(guess)), "nh2d_set_solver")
 
-    def set_state(self, h, hu, hv, hw, t=0.0):
-        a = [self._f(v) for v in (h, hu, hv, hw)]
-        _check(self.L.nh2d_set_state(self.h, *[_dptr(v) for v in a], float(t)), "nh2d_set_state")
+    def set_graphs(self, on):
+        _check(self.L.nh2d_set_graphs(self.h, int(bool(on))), "nh2d_set_graphs")
 
-    def get_state(self):
-        n = self.nx * self.ny
-        out = [np.empty(n) for _ in range(5)]
-        _check(self.L.nh2d_get_state(self.h, *[_dptr(v) for v in out]), "nh2d_get_state")
-        return [v.reshape(self.ny, self.nx) for v in out]
+    def set_state(self, h, hu, hv, hw, t=0.0, member=0):
+        a = [self._f(v, member) for v in (h, hu, hv, hw)]
+        _check(self.L.nh2d_set_member_state(self.h, int(member), *[_dptr(v) for v in a], float(t)),
+               "nh2d_set_member_state")
 
-    def get_mask(self):
-        m = np.empty(self.nx * self.ny, dtype=np.uint8)
-        _check(self.L.nh2d_get_mask(self.h, m.ctypes.data_as(C.POINTER(C.c_ubyte))), "nh2d_get_mask")
-        return m.reshape(self.ny, self.nx)
+    def get_state(self, member=0):
+        ny, nx = self._shape(member)
+        out = [np.empty(nx * ny) for _ in range(5)]
+        _check(self.L.nh2d_get_member_state(self.h, int(member), *[_dptr(v) for v in out]), "nh2d_get_member_state")
+        return [v.reshape(ny, nx) for v in out]
+
+    def get_mask(self, member=0):
+        ny, nx = self._shape(member)
+        m = np.empty(nx * ny, dtype=np.uint8)
+        _check(self.L.nh2d_get_member_mask(self.h, int(member), m.ctypes.data_as(C.POINTER(C.c_ubyte))),
+               "nh2d_get_member_mask")
+        return m.reshape(ny, nx)
+
+    def member_info(self, member):
+        info = nh_step_info()
+        _check(self.L.nh2d_get_member_info(self.h, int(member), C.byref(info)), "nh2d_get_member_info")
+        return info.as_dict()
+
+    @property
+    def graph_runs(self):
+        return self.L.nh2d_graph_runs(self.h)
 
     def step(self, dt, check=True):
         info = nh_step_info()

@@ -58,3 +58,24 @@ def test_workspace_size_2d_needs_no_gpu():
     assert lib.nh2d_workspace_bytes(ctypes.byref(d)) > 1024 * 1024 * 8 * 40
     bad = nhswe.nh_grid2d_desc(2, 1024, 0, 0, 1, 0.05, 0.05, 0.0, 0.0, 9.81, 1000.0)   # nx < 3
     assert lib.nh2d_workspace_bytes(ctypes.byref(bad)) == 0
+
+
+def test_ensemble_workspace_2d_needs_no_gpu():
+    """Every member gets a slot of the largest member's cells (rounded up to
+    256); an invalid member or an empty ensemble gives 0."""
+    lib = ctypes.CDLL(B.build())
+    lib.nh2d_ensemble_workspace_bytes.argtypes = [ctypes.c_int, ctypes.POINTER(nhswe.nh_grid2d_desc)]
+    lib.nh2d_ensemble_workspace_bytes.restype = ctypes.c_size_t
+    lib.nh2d_workspace_bytes.argtypes = [ctypes.POINTER(nhswe.nh_grid2d_desc)]
+    lib.nh2d_workspace_bytes.restype = ctypes.c_size_t
+    D = nhswe.nh_grid2d_desc
+    big = D(512, 500, 0, 0, 1, 0.02, 0.02, 0.0, 0.0, 9.81, 1000.0)
+    small = D(40, 30, 1, 0, 2, 0.05, 0.04, 0.0, 0.0, 9.81, 1000.0)
+    one = lib.nh2d_workspace_bytes(ctypes.byref(big))
+    arr = (D * 3)(small, big, small)
+    three = lib.nh2d_ensemble_workspace_bytes(3, arr)
+    assert 2.9 * one < three < 3.1 * one
+    assert lib.nh2d_ensemble_workspace_bytes(1, arr) < lib.nh2d_ensemble_workspace_bytes(2, arr)
+    assert lib.nh2d_ensemble_workspace_bytes(0, arr) == 0
+    arr[2] = D(40, 2, 1, 0, 2, 0.05, 0.04, 0.0, 0.0, 9.81, 1000.0)   # ny < 3
+    assert lib.nh2d_ensemble_workspace_bytes(3, arr) == 0
