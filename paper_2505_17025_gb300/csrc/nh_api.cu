@@ -182,7 +182,7 @@ size_t carve(const nh_grid_desc& d, long long ncells, nh_grid* g, char* base)
     G->prb = (float*)c.take(sizeof(float) * N);
     G->ms = (MState*)c.take(sizeof(MState) * nb);
     G->ctl = (Ctl*)c.take(sizeof(Ctl));
-    G->part = (double*)c.take(sizeof(double) * 3 * (size_t)nb * maxch);
+    G->part = (double*)c.take(sizeof(double) * 4 * (size_t)nb * maxch);
     G->cnt = (int*)c.take(sizeof(int) * nb);
     G->mass_part = (double*)c.take(sizeof(double) * (size_t)nb * ntiles_max);
     G->summary = (Summary*)c.take(sizeof(Summary));

@@ -146,7 +146,7 @@ size_t carve2(int nb, int pitch, nh_grid2d* g, char* base)
     G->s = c.take<double>(T); G->t = c.take<double>(T); G->r1 = c.take<double>(T); G->z = c.take<double>(T);
     G->pf = c.take<float2>((size_t)kPcrLevels * T); G->prb = c.take<float>(T);
     G->ms = c.take<MState>(nb); G->ctl = c.take<Ctl>(1);
-    G->part = c.take<double>(3 * (size_t)nb * maxch); G->cnt = c.take<int>(nb);
+    G->part = c.take<double>(4 * (size_t)nb * maxch); G->cnt = c.take<int>(nb);
     G->mass_part = c.take<double>((size_t)nb * nmass); G->summary = c.take<Summary>(1);
     G->geos = c.take<Geo2>(nb); G->slides = c.take<Slide2>(nb); G->kin = c.take<Kin2>(2 * (size_t)nb);
     G->tc = c.take<TimeCtl>(1);

@@ -32,6 +32,7 @@ constexpr int kPredTileMax = 512;
 constexpr int kPredTileMin = 128;
 constexpr int kPredHalo = 5;     // two Heun stages + one cell for the criterion
 constexpr int kChunk = 256;      // active cells per solver work item (= blockDim)
+constexpr int kMaxExt = 6;       // extra couplings of a row beyond its list neighbours (2D: S, N, 4 diagonals)
 constexpr int kCompactThreads = 1024;
 constexpr int kPcrThreads = 1024;     // preconditioner CTA
 constexpr int kPcrRows = 8192;        // active cells per preconditioner block (power of 2)

@@ -736,7 +736,7 @@ struct SolveArgs {
     const int2* items; const int2* pitems;
     const TimeCtl* tc;         // captured runs: guess scale from tc->prev_ok
     MState* ms; Ctl* ctl;
-    double* part;              // [3][nb * maxch]
+    double* part;              // [4][nb * maxch]; slot 3: the persistent PCG's <p, q> item partials
     int* cnt;
     double rtol;
     int max_iter;
@@ -757,12 +757,16 @@ __device__ __forceinline__ T apply_row(const SolveArgs<T>& a, size_t mo, int k, 
 template <typename T, typename F>
 __device__ __forceinline__ T ext_terms(const SolveArgs<T>& a, size_t mo, int k, F v)
 {
+    // all neighbour indices first, then the values: the loads of the
+    // couplings overlap instead of forming a chain per coupling
+    int jj[kMaxExt];
+#pragma unroll
+    for (int e = 0; e < kMaxExt; ++e)
+        jj[e] = e < a.n_ext ? __ldg(a.ext_k + (size_t)e * a.ext_stride + mo + k) : -1;
     T s = T(0);
-    for (int e = 0; e < a.n_ext; ++e) {
-        const size_t o = (size_t)e * a.ext_stride + mo + k;
-        const int j = a.ext_k[o];
-        if (j >= 0) s += T(a.ext_c[o]) * v(j);
-    }
+#pragma unroll
+    for (int e = 0; e < kMaxExt; ++e)
+        if (jj[e] >= 0) s += T(__ldg(a.ext_c + (size_t)e * a.ext_stride + mo + k)) * v(jj[e]);
     return s;
 }
 
@@ -1564,11 +1568,16 @@ __device__ void pcg_member_local(const SolveArgs<T>& a, TP* sa, TP* sd, double* 
 }
 
 // All PCG iterations of one solve in one cooperative launch: per iteration
-// phase A (p = z + beta p_old, q = A p, <p, q> -> alpha) and phase B (x, r
-// update, ||r||, line preconditioner, beta), separated by grid barriers.  Work
-// is split by preconditioner blocks (kPcrRows active cells, kPcrThreads
-// threads).  Members finish independently; the loop ends when no member is
-// left, after max_iter, or when a barrier times out (ctl->timeout).
+// phase A (p = z + beta p_old, q = A p, partial <p, q>) and phase B (alpha,
+// x, r update, ||r||, line preconditioner, beta), separated by grid barriers.
+// Phase A is spread over every CTA in kChunk-row work items (one row per
+// thread, kPcrThreads / kChunk items per CTA pass), so a small active set
+// still uses the whole GPU; its partials go to the fourth partial slot.
+// Phase B works per preconditioner block (kPcrRows active cells, one CTA):
+// each block's CTA sums its member's <p, q> partials in a fixed order, so all
+// blocks of a member form the same alpha.  Members finish independently; the
+// loop ends when no member is left, after max_iter, or when a barrier times
+// out (ctl->timeout).
 template <typename T, typename TP>
 __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, long long budget)
 {
@@ -1576,88 +1585,125 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, 
     TP* sa = reinterpret_cast<TP*>(smem_raw);   // reduction ping-pong buffers
     TP* sd = sa + kPcrRows;
     __shared__ double red[96];
-    constexpr int RPT = kPcrRows / kPcrThreads;
+    __shared__ double s_pq;
+    __shared__ int s_skip;
+    constexpr int kGroups = kPcrThreads / kChunk;
+    static_assert(kGroups * kChunk == kPcrThreads, "whole work items per CTA pass");
     const size_t stride = (size_t)a.nb * a.maxch;
+    double* part_pq = a.part + 3 * stride;
     const int n_pitems = a.ctl->n_pitems;
+    const int n_items = a.ctl->n_items;
     Ctl* ctl = a.ctl;
     const unsigned nblk = gridDim.x;
     if (ctl->max_npb <= 1) {          // the same for every CTA: no grid barrier needed
         pcg_member_local<T, TP>(a, sa, sd, red);
         return;
     }
+    const int grp = threadIdx.x / kChunk, lt = threadIdx.x % kChunk;
     for (int it = 1; it <= a.max_iter; ++it) {
         const T* pold = (it & 1) ? a.p0 : a.p1;
         T* pnew = (it & 1) ? a.p1 : a.p0;
         const T* rold = (it & 1) ? a.r : a.r1;
         T* rnew = (it & 1) ? a.r1 : a.r;
-        // ---- phase A
-        for (int wi = blockIdx.x; wi < n_pitems; wi += gridDim.x) {
-            const int2 itm = a.pitems[wi];
-            const int b = itm.x, jb = itm.y;
-            if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_CG) continue;
-            const int n = a.ms[b].n_active, npb = a.ms[b].npb, poff = a.ms[b].poff;
-            const size_t mo = (size_t)b * a.pitch;
-            const int k0 = jb * kPcrRows, rows = min(kPcrRows, n - k0);
-            const T beta = (it == 1) ? T(0) : T(a.ms[b].beta);
+        // ---- phase A: kChunk-row items over all CTAs
+        for (int u = blockIdx.x; u * kGroups < n_items; u += gridDim.x) {
+            const int w = u * kGroups + grp;
             double pq = 0.0;
-            for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
-                const int k = k0 + i;
-                const int km = k > 0 ? k - 1 : k, kp = k + 1 < n ? k + 1 : k;
-                const T zk = a.z[mo + k], zm = a.z[mo + km], zp = a.z[mo + kp];
-                const T ok = pold[mo + k], om = pold[mo + km], op = pold[mo + kp];
-                const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
-                const T pk = zk + beta * ok;
-                T pl = T(0), pr = T(0);
-                if (kl == k - 1) pl = zm + beta * om;
-                else if (kl >= 0) pl = a.z[mo + kl] + beta * pold[mo + kl];
-                if (kr == k + 1) pr = zp + beta * op;
-                else if (kr >= 0) pr = a.z[mo + kr] + beta * pold[mo + kr];
-                T qk = apply_row(a, mo, k, pk, pl, pr);
-                if (a.n_ext) qk += ext_terms(a, mo, k, [&](int j) { return a.z[mo + j] + beta * pold[mo + j]; });
-                pnew[mo + k] = pk;
-                a.q[mo + k] = qk;
-                pq += (double)pk * (double)qk;
-            }
-            double v[1] = {pq};
-            block_sum<1>(v, red);
-            if (threadIdx.x == 0) a.part[wi] = v[0];
-            if (arrive_last(a.cnt, b, npb)) {
-                const double s_pq = member_sum(a.part + poff, npb, red);
-                if (threadIdx.x == 0) {
-                    MState& s = a.ms[b];
-                    if (!isfinite(s_pq) || !(s_pq > 0.0)) cg_breakdown<T>(s, ctl, it);
-                    else s.alpha = s.rz / s_pq;
+            bool live = false;
+            if (w < n_items) {
+                const int2 itm = a.items[w];
+                const int b = itm.x;
+                if (!a.ms[b].done && a.ms[b].kind == NH_SOLVER_CG) {
+                    live = true;
+                    const int n = a.ms[b].n_active;
+                    const size_t mo = (size_t)b * a.pitch;
+                    const int k = itm.y * kChunk + lt;
+                    const T beta = (it == 1) ? T(0) : T(a.ms[b].beta);
+                    if (k < n) {
+                        const int km = k > 0 ? k - 1 : k, kp = k + 1 < n ? k + 1 : k;
+                        const T zk = a.z[mo + k], zm = a.z[mo + km], zp = a.z[mo + kp];
+                        const T ok = pold[mo + k], om = pold[mo + km], op = pold[mo + kp];
+                        const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
+                        const T pk = zk + beta * ok;
+                        T pl = T(0), pr = T(0);
+                        if (kl == k - 1) pl = zm + beta * om;
+                        else if (kl >= 0) pl = a.z[mo + kl] + beta * pold[mo + kl];
+                        if (kr == k + 1) pr = zp + beta * op;
+                        else if (kr >= 0) pr = a.z[mo + kr] + beta * pold[mo + kr];
+                        T qk = apply_row(a, mo, k, pk, pl, pr);
+                        if (a.n_ext)
+                            qk += ext_terms(a, mo, k, [&](int j) { return a.z[mo + j] + beta * pold[mo + j]; });
+                        pnew[mo + k] = pk;
+                        a.q[mo + k] = qk;
+                        pq = (double)pk * (double)qk;
+                    }
                 }
             }
+            // per-item sum in a fixed order: warps, then the item's warps
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pq += __shfl_down_sync(0xffffffffu, pq, o);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pq;
+            __syncthreads();
+            if (lt == 0 && live) {
+                double t = 0.0;
+                for (int q = 0; q < kChunk / 32; ++q) t += red[grp * (kChunk / 32) + q];
+                part_pq[w] = t;
+            }
+            __syncthreads();
         }
         if (!grid_barrier(ctl, nblk, budget, [] {})) return;
-        // ---- phase B
+        // ---- phase B: one preconditioner block per CTA
         for (int wi = blockIdx.x; wi < n_pitems; wi += gridDim.x) {
             const int2 itm = a.pitems[wi];
             const int b = itm.x, jb = itm.y;
-            if (a.ms[b].done || a.ms[b].kind != NH_SOLVER_CG) continue;
+            if (threadIdx.x == 0) s_skip = a.ms[b].done || a.ms[b].kind != NH_SOLVER_CG;
+            __syncthreads();
+            if (s_skip) continue;
             const int n = a.ms[b].n_active, npb = a.ms[b].npb, poff = a.ms[b].poff;
+            const int nch = a.ms[b].nchunks, ioff = a.ms[b].ioff;
+            const double spq0 = member_sum(part_pq + ioff, nch, red);
+            if (threadIdx.x == 0) s_pq = spq0;
+            __syncthreads();
+            const double spq = s_pq;
+            if (!isfinite(spq) || !(spq > 0.0)) {   // the same decision in every block of the member
+                if (jb == 0 && threadIdx.x == 0) cg_breakdown<T>(a.ms[b], ctl, it);
+                __syncthreads();
+                continue;
+            }
             const size_t mo = (size_t)b * a.pitch;
             const int k0 = jb * kPcrRows, rows = min(kPcrRows, n - k0);
-            const T alpha = T(a.ms[b].alpha);
+            const T alpha = T(a.ms[b].rz / spq);
+            const T* __restrict__ pb = pnew + mo + k0;
+            const T* __restrict__ qb = a.q + mo + k0;
+            const T* __restrict__ rob = rold + mo + k0;
+            T* __restrict__ xb = a.x + mo + k0;
+            T* __restrict__ rnb = rnew + mo + k0;
             double ss = 0.0;
-            for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
-                const int k = k0 + i;
-                a.x[mo + k] = a.x[mo + k] + alpha * pnew[mo + k];
-                const T rk = rold[mo + k] - alpha * a.q[mo + k];
-                rnew[mo + k] = rk;
-                ss += (double)rk * (double)rk;
-                sd[i] = TP(rk);
+#pragma unroll
+            for (int m = 0; m < kPcrRows / kPcrThreads; ++m) {
+                const int i = threadIdx.x + m * kPcrThreads;
+                if (i < rows) {
+                    xb[i] = xb[i] + alpha * pb[i];
+                    const T rk = rob[i] - alpha * qb[i];
+                    rnb[i] = rk;
+                    ss += (double)rk * (double)rk;
+                    sd[i] = TP(rk);
+                }
             }
             __syncthreads();
             const TP* red_d = pcr_apply<T, TP>(a, sd, sa, rows, mo + k0);
             double acc[3] = {0.0, 0.0, ss};
-            for (int i = threadIdx.x; i < rows; i += kPcrThreads) {
-                const int k = k0 + i;
-                const T zk = T(red_d[i] * TP(a.prb[mo + k]));
-                a.z[mo + k] = zk;
-                acc[0] += (double)zk * (double)rnew[mo + k];
-                acc[1] += (double)zk * (double)rold[mo + k];
+            const float* __restrict__ prb = a.prb + mo + k0;
+            T* __restrict__ zb = a.z + mo + k0;
+#pragma unroll
+            for (int m = 0; m < kPcrRows / kPcrThreads; ++m) {
+                const int i = threadIdx.x + m * kPcrThreads;
+                if (i < rows) {
+                    const T zk = T(red_d[i] * TP(prb[i]));
+                    zb[i] = zk;
+                    acc[0] += (double)zk * (double)rnb[i];
+                    acc[1] += (double)zk * (double)rob[i];
+                }
             }
             block_sum<3>(acc, red);
             if (threadIdx.x == 0) {
@@ -1669,6 +1715,7 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, 
                 const double rr = member_sum(a.part + 2 * stride + poff, npb, red);
                 if (threadIdx.x == 0) {
                     MState& st = a.ms[b];
+                    st.alpha = (double)alpha;
                     const double rel = sqrt(rr) / st.bnorm;
                     if (!isfinite(rr)) finish_member<T>(st, ctl, NH_ERR_NONFINITE, it, NAN);
                     else if (sqrt(rr) <= a.rtol * st.bnorm) finish_member<T>(st, ctl, NH_OK, it, rel);

@@ -561,7 +561,9 @@ class Grid2D:
         return self.shapes[member] if 0 <= member < len(self.shapes) else (1, 1)
 
     def _f(self, a, member=0):
-        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), self._shape(member)))
+        if not 0 <= member < len(self.shapes):
+            return np.zeros(1)
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), self.shapes[member]))
         return a.reshape(-1)
 
     @staticmethod
