@@ -357,9 +357,8 @@ def run_2d(args):
     else:
         wls, dt = W.landslide_ensemble_2d()
         knh, t_start = 1e-4, 0.3
-        sizes = sorted(w.nx for w in wls)
-        name = (f"landslide_ensemble_2d: {len(wls)} runs, n x n with n in [{sizes[0]}, {sizes[-1]}] "
-                f"(seed 0), 10.24 m basin, drawn slope/A/L/s0")
+        name = (f"landslide_ensemble_2d: {len(wls)} runs, nx, ny drawn from 256..1024 (step 64), dx 0.02 m, "
+                f"tan(theta) U(0.1,0.3), A U(0.05,0.15), Lx U(0.5,1.5), s0 U(1,3); member m seeded with m")
     G = N.Grid2D.ensemble([dict(nx=w.nx, ny=w.ny, dx=w.dx, dy=w.dy, d0=w.d0, bc_x=w.bc_x, bc_y=w.bc_y)
                            for w in wls])
     for i, w in enumerate(wls):

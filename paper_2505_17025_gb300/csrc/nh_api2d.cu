@@ -113,7 +113,8 @@ long long ens_pitch(int nb, const nh_grid2d_desc* descs)
     return pitch;
 }
 
-int mass_blocks(int pitch) { return std::max(1, std::min((pitch + 255) / 256, 64)); }
+// Mass partial sums per member: about 4096 cells per 256-thread block.
+int mass_blocks(int pitch) { return std::max(1, std::min((pitch + 4095) / 4096, 512)); }
 
 size_t carve2(int nb, int pitch, nh_grid2d* g, char* base)
 {
@@ -531,7 +532,7 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
     g->nb = n_members;
     g->pitch = (int)pitch;
     g->d.assign(descs, descs + n_members);
-    g->slide_h.assign(n_members, Slide2{0.0, 1.0, 1.0, 0.0, 0.0, 0.0, 1.0, NH_SLIDE_NONE, 0});
+    g->slide_h.assign(n_members, Slide2{0.0, 1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, NH_SLIDE_NONE, 0});
     g->member_set.assign(n_members, 0);
     g->stream = static_cast<cudaStream_t>(stream);
     g->cap_stream = nullptr;
@@ -614,13 +615,14 @@ int nh2d_members(const nh_grid2d* g) { return g ? g->nb : 0; }
 nh_status nh2d_set_member_bottom_motion(nh_grid2d* g, int m, const nh_slide2d_desc* s)
 {
     if (!member_ok(g, m)) return NH_ERR_ARG;
-    Slide2 S{0.0, 1.0, 1.0, 0.0, 0.0, 0.0, 1.0, NH_SLIDE_NONE, 0};
+    Slide2 S{0.0, 1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, NH_SLIDE_NONE, 0};
     if (s && s->shape != NH_SLIDE_NONE) {
         if (s->shape != NH_SLIDE_GAUSS_LNCOSH || !(s->Lx > 0.0) || !(s->Ly > 0.0) || !(s->t0 > 0.0) ||
             !std::isfinite(s->A) || !std::isfinite(s->xc0) || !std::isfinite(s->yc0) || !std::isfinite(s->s0))
             return NH_ERR_ARG;
         S.shape = NH_SLIDE_GAUSS_LNCOSH;
         S.A = s->A; S.Lx = s->Lx; S.Ly = s->Ly; S.xc0 = s->xc0; S.yc0 = s->yc0; S.s0 = s->s0; S.t0 = s->t0;
+        S.iLx = 1.0 / s->Lx; S.iLy = 1.0 / s->Ly;
     }
     g->slide_h[m] = S;
     CK2(cudaMemcpyAsync(g->slides + m, &g->slide_h[m], sizeof(Slide2), cudaMemcpyHostToDevice, g->stream));

@@ -507,6 +507,19 @@ __device__ __forceinline__ double member_sum(const double* part, int n, double* 
     block_sum<1>(v, sh);
     return v[0];
 }
+
+// The same for three partial arrays at part, part + stride, part + 2 stride
+// in one block reduction (thread 0 gets v[0..2]).
+__device__ __forceinline__ void member_sum3(const double* part, size_t stride, int n, double* sh, double (&v)[3])
+{
+    v[0] = v[1] = v[2] = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        v[0] += __ldcg(part + q);
+        v[1] += __ldcg(part + stride + q);
+        v[2] += __ldcg(part + 2 * stride + q);
+    }
+    block_sum<3>(v, sh);
+}
 __device__ __forceinline__ double member_min(const double* part, int n, double* sh)
 {
     double v = INFINITY;
@@ -1710,9 +1723,9 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcg_persistent(SolveArgs<T> a, 
                 a.part[wi] = acc[0]; a.part[stride + wi] = acc[1]; a.part[2 * stride + wi] = acc[2];
             }
             if (arrive_last(a.cnt, b, npb)) {
-                const double zr = member_sum(a.part + poff, npb, red);
-                const double zro = member_sum(a.part + stride + poff, npb, red);
-                const double rr = member_sum(a.part + 2 * stride + poff, npb, red);
+                double sums[3];
+                member_sum3(a.part + poff, stride, npb, red, sums);
+                const double zr = sums[0], zro = sums[1], rr = sums[2];
                 if (threadIdx.x == 0) {
                     MState& st = a.ms[b];
                     st.alpha = (double)alpha;

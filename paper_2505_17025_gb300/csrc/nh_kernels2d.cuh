@@ -38,6 +38,7 @@ struct Geo2 {
 // Its position s(t) = s0 ln cosh(t / t0) (Sec. 4.2).
 struct Slide2 {
     double A, Lx, Ly, xc0, yc0, s0, t0;
+    double iLx, iLy;   // 1 / Lx, 1 / Ly
     int shape, pad;
 };
 
@@ -103,13 +104,16 @@ __device__ __forceinline__ int g2_inner(const Geo2& G, int i, int j)
     return j * G.nx + i;
 }
 
-// Mound height at cell (i, j) for slide position s.
+// Mound height at cell (i, j) for slide position s; 0 where xi^2 + zeta^2 >
+// kMoundCut (below half an ulp of any depth it is subtracted from when
+// A < 12 d0, so the depth is the same double).
 __device__ __forceinline__ double mound2(const Geo2& G, const Slide2& S, int i, int j, double s)
 {
     if (S.shape != NH_SLIDE_GAUSS_LNCOSH) return 0.0;
     const double x = G.x0 + (i + 0.5) * G.dx, y = G.y0 + (j + 0.5) * G.dy;
-    const double xi = (x - S.xc0 - s) / S.Lx, ze = (y - S.yc0) / S.Ly;
-    return S.A * exp(-xi * xi - ze * ze);
+    const double xi = (x - S.xc0 - s) * S.iLx, ze = (y - S.yc0) * S.iLy;
+    const double r2 = xi * xi + ze * ze;
+    return r2 > kMoundCut ? 0.0 : S.A * exp(-r2);
 }
 
 // d, d_x, d_y, d_xx, d_yy, d_xy, d_t, d_xt, d_yt, d_tt at cell (i, j):
@@ -187,10 +191,9 @@ __device__ __forceinline__ void rusanov2(double g, double hL, double nL, double 
 }
 
 struct StageArgs {
-    Geo2 G;                                // this member's geometry (set in the kernel)
     const Geo2* geos;
-    size_t pitch;
-    const double *h, *hu, *hv, *hw;        // state the rate is evaluated on (member-offset in the kernel)
+    size_t pitch;                          // member b's cells at b * pitch in every array
+    const double *h, *hu, *hv, *hw;        // state the rate is evaluated on
     const double* d;                       // depth at that state's time
     const double *h0, *hu0, *hv0, *hw0;    // Q^n
     double *k1h, *k1u, *k1v, *k1w;         // stage-1 rates (written at stage 1, read at stage 2)
@@ -200,81 +203,119 @@ struct StageArgs {
     const TimeCtl* tc;                     // captured runs: skip after an aborted step
 };
 
-// One direction's contribution to the rates of cell (i, j): flux divergence
-// and, for the normal momentum, the bottom source g h_mean (d_{+1/2} -
-// d_{-1/2}) / ds with the depth continuous at faces.
-__device__ __forceinline__ void stage_dir(const StageArgs& a, int i, int j, int dir, double r[4])
+// Predictor stage on a kTX x kTY tile of cells held in shared memory with a
+// two-cell halo in x (for the tile's rows) and in y (for its columns):
+//  1. every tile and halo cell (mirrored / wrapped by g2_cell, odd parity on
+//     the normal velocity) -> eta, u, v, w, d once (one reciprocal of h);
+//  2. every x-face and y-face of the tile -> limited slopes of its two cells
+//     and the Rusanov flux, once per face;
+//  3. every cell -> flux differences plus the bottom source
+//     g hbar (d_{+1/2} - d_{-1/2}) / ds per direction (depth continuous at
+//     faces, hbar from the cell's own face thicknesses), then the Heun stage.
+constexpr int kTX = 32, kTY = 8;                 // 256 threads, one cell each
+constexpr int kHX = kTX + 4, kHY = kTY + 4;      // tile with halo
+constexpr int kFX = (kTX + 1) * kTY;             // x-faces of a tile
+constexpr int kFY = kTX * (kTY + 1);             // y-faces
+
+__device__ __forceinline__ void face_flux(double g, int lim, const double* e, const double* un, const double* ut,
+                                          const double* w, const double* d, int s, double F[4])
 {
-    const Geo2& G = a.G;
-    double eta[5], un[5], ut[5], w[5], dd[5];
-    for (int m = 0; m < 5; ++m) {
-        double ox, oy;
-        const int c = dir == 0 ? g2_cell(G, i + m - 2, j, &ox, &oy) : g2_cell(G, i, j + m - 2, &ox, &oy);
-        const double hc = a.h[c];
-        dd[m] = a.d[c];
-        eta[m] = hc - dd[m];
-        const double u = ox * a.hu[c] / hc, v = oy * a.hv[c] / hc;
-        un[m] = dir == 0 ? u : v;
-        ut[m] = dir == 0 ? v : u;
-        w[m] = a.hw[c] / hc;
-    }
-    double se[3], sn[3], st[3], sw[3];
-    for (int q = 0; q < 3; ++q) {   // slopes of cells -1, 0, +1
-        se[q] = slope2(G.lim, eta[q], eta[q + 1], eta[q + 2]);
-        sn[q] = slope2(G.lim, un[q], un[q + 1], un[q + 2]);
-        st[q] = slope2(G.lim, ut[q], ut[q + 1], ut[q + 2]);
-        sw[q] = slope2(G.lim, w[q], w[q + 1], w[q + 2]);
-    }
-    double F[2][4], df[2];
-    for (int f = 0; f < 2; ++f) {   // face f: between cells f-1 and f (relative)
-        const int L = f, R = f + 1;  // indices into the slope arrays (cell -1 + f, cell f)
-        df[f] = 0.5 * (dd[L + 1] + dd[R + 1]);
-        const double hL = eta[L + 1] + 0.5 * se[L] + df[f];
-        const double hR = eta[R + 1] - 0.5 * se[R] + df[f];
-        rusanov2(G.g, hL, un[L + 1] + 0.5 * sn[L], ut[L + 1] + 0.5 * st[L], w[L + 1] + 0.5 * sw[L],
-                 hR, un[R + 1] - 0.5 * sn[R], ut[R + 1] - 0.5 * st[R], w[R + 1] - 0.5 * sw[R], F[f]);
-    }
-    const double ds = dir == 0 ? G.dx : G.dy;
-    const double hplus = eta[2] - 0.5 * se[1] + df[0];
-    const double hminus = eta[2] + 0.5 * se[1] + df[1];
-    const double S = G.g * 0.5 * (hplus + hminus) * (df[1] - df[0]) / ds;
-    r[0] = -(F[1][0] - F[0][0]) / ds;
-    r[1] = -(F[1][1] - F[0][1]) / ds + S;   // normal momentum
-    r[2] = -(F[1][2] - F[0][2]) / ds;       // tangential momentum
-    r[3] = -(F[1][3] - F[0][3]) / ds;
+    // cells L = -1, R = 0 relative to the face; e[k * s] is cell k's value
+    const double seL = slope2(lim, e[-2 * s], e[-s], e[0]), seR = slope2(lim, e[-s], e[0], e[s]);
+    const double snL = slope2(lim, un[-2 * s], un[-s], un[0]), snR = slope2(lim, un[-s], un[0], un[s]);
+    const double stL = slope2(lim, ut[-2 * s], ut[-s], ut[0]), stR = slope2(lim, ut[-s], ut[0], ut[s]);
+    const double swL = slope2(lim, w[-2 * s], w[-s], w[0]), swR = slope2(lim, w[-s], w[0], w[s]);
+    const double df = 0.5 * (d[-s] + d[0]);
+    rusanov2(g, e[-s] + 0.5 * seL + df, un[-s] + 0.5 * snL, ut[-s] + 0.5 * stL, w[-s] + 0.5 * swL,
+             e[0] - 0.5 * seR + df, un[0] - 0.5 * snR, ut[0] - 0.5 * stR, w[0] - 0.5 * swR, F);
 }
 
-static __global__ void k2_stage(StageArgs a)
+static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs a)
 {
     if (a.tc && a.tc->abort) return;
+    __shared__ double s_e[kHY][kHX], s_u[kHY][kHX], s_v[kHY][kHX], s_w[kHY][kHX], s_d[kHY][kHX];
+    __shared__ double s_fx[4][kTY][kTX + 1], s_fy[4][kTY + 1][kTX];
     const int b = blockIdx.y;
     const size_t mo = (size_t)b * a.pitch;
-    a.G = a.geos[b];
-    a.h += mo; a.hu += mo; a.hv += mo; a.hw += mo; a.d += mo;
-    a.h0 += mo; a.hu0 += mo; a.hv0 += mo; a.hw0 += mo;
-    a.k1h += mo; a.k1u += mo; a.k1v += mo; a.k1w += mo;
-    a.oh += mo; a.ohu += mo; a.ohv += mo; a.ohw += mo;
-    const int N = a.G.nx * a.G.ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const int i = c % a.G.nx, j = c / a.G.nx;
-        double rx[4], ry[4];
-        stage_dir(a, i, j, 0, rx);
-        stage_dir(a, i, j, 1, ry);
-        double rh = 0.0, ru = 0.0, rv = 0.0, rw = 0.0;
-        rh += rx[0]; ru += rx[1]; rv += rx[2]; rw += rx[3];
-        rh += ry[0]; rv += ry[1]; ru += ry[2]; rw += ry[3];
-        if (a.stage == 1) {
-            a.k1h[c] = rh; a.k1u[c] = ru; a.k1v[c] = rv; a.k1w[c] = rw;
-            a.oh[c] = a.h0[c] + a.dt * rh;
-            a.ohu[c] = a.hu0[c] + a.dt * ru;
-            a.ohv[c] = a.hv0[c] + a.dt * rv;
-            a.ohw[c] = a.hw0[c] + a.dt * rw;
-        } else {
-            a.oh[c] = a.h0[c] + 0.5 * a.dt * (a.k1h[c] + rh);
-            a.ohu[c] = a.hu0[c] + 0.5 * a.dt * (a.k1u[c] + ru);
-            a.ohv[c] = a.hv0[c] + 0.5 * a.dt * (a.k1v[c] + rv);
-            a.ohw[c] = a.hw0[c] + 0.5 * a.dt * (a.k1w[c] + rw);
+    const Geo2 G = a.geos[b];
+    const int tiles_x = (G.nx + kTX - 1) / kTX, tiles = tiles_x * ((G.ny + kTY - 1) / kTY);
+    const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+    const double* h = a.h + mo; const double* hu = a.hu + mo; const double* hv = a.hv + mo;
+    const double* hw = a.hw + mo; const double* dd = a.d + mo;
+    const double idx = 1.0 / G.dx, idy = 1.0 / G.dy;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int i0 = (tile % tiles_x) * kTX, j0 = (tile / tiles_x) * kTY;
+        // 1. primitives of the tile and its cross-shaped halo
+        for (int q = tid; q < kHX * kHY; q += kTX * kTY) {
+            const int lx = q % kHX, ly = q / kHX;
+            const bool in_x = lx >= 2 && lx < kTX + 2, in_y = ly >= 2 && ly < kTY + 2;
+            if (!in_x && !in_y) continue;   // corners: no stencil reaches them
+            double ox, oy;
+            const int c = g2_cell(G, i0 + lx - 2, j0 + ly - 2, &ox, &oy);
+            const double hc = h[c], rh = 1.0 / hc, dc = dd[c];
+            s_e[ly][lx] = hc - dc;
+            s_d[ly][lx] = dc;
+            s_u[ly][lx] = ox * hu[c] * rh;
+            s_v[ly][lx] = oy * hv[c] * rh;
+            s_w[ly][lx] = hw[c] * rh;
         }
+        __syncthreads();
+        // 2. face fluxes: x-face (fx, ty) between cells fx-1 and fx of row ty;
+        //    y-face (tx, fy) between cells fy-1 and fy of column tx
+        for (int q = tid; q < kFX + kFY; q += kTX * kTY) {
+            double F[4];
+            if (q < kFX) {
+                const int fx = q % (kTX + 1), r = q / (kTX + 1);
+                const int ly = r + 2, lx = fx + 2;
+                face_flux(G.g, G.lim, &s_e[ly][lx], &s_u[ly][lx], &s_v[ly][lx], &s_w[ly][lx], &s_d[ly][lx], 1, F);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) s_fx[k][r][fx] = F[k];
+            } else {
+                const int q2 = q - kFX, col = q2 % kTX, fy = q2 / kTX;
+                const int ly = fy + 2, lx = col + 2;
+                face_flux(G.g, G.lim, &s_e[ly][lx], &s_v[ly][lx], &s_u[ly][lx], &s_w[ly][lx], &s_d[ly][lx], kHX, F);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) s_fy[k][fy][col] = F[k];
+            }
+        }
+        __syncthreads();
+        // 3. rates and the stage
+        const int i = i0 + tx, j = j0 + ty;
+        if (i < G.nx && j < G.ny) {
+            const int lx = tx + 2, ly = ty + 2;
+            const double ec = s_e[ly][lx], dc = s_d[ly][lx];
+            // x: bottom source with the cell's face thicknesses
+            const double sex = slope2(G.lim, s_e[ly][lx - 1], ec, s_e[ly][lx + 1]);
+            const double dfw = 0.5 * (s_d[ly][lx - 1] + dc), dfe = 0.5 * (dc + s_d[ly][lx + 1]);
+            const double Sx = G.g * 0.5 * ((ec - 0.5 * sex + dfw) + (ec + 0.5 * sex + dfe)) * (dfe - dfw) * idx;
+            const double sey = slope2(G.lim, s_e[ly - 1][lx], ec, s_e[ly + 1][lx]);
+            const double dfs = 0.5 * (s_d[ly - 1][lx] + dc), dfn = 0.5 * (dc + s_d[ly + 1][lx]);
+            const double Sy = G.g * 0.5 * ((ec - 0.5 * sey + dfs) + (ec + 0.5 * sey + dfn)) * (dfn - dfs) * idy;
+            double rx[4], ry[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                rx[k] = -(s_fx[k][ty][tx + 1] - s_fx[k][ty][tx]) * idx;
+                ry[k] = -(s_fy[k][ty + 1][tx] - s_fy[k][ty][tx]) * idy;
+            }
+            const double rh = rx[0] + ry[0];
+            const double ru = (rx[1] + Sx) + ry[2];     // x-normal momentum, y-tangential
+            const double rv = rx[2] + (ry[1] + Sy);     // x-tangential, y-normal momentum
+            const double rw = rx[3] + ry[3];
+            const size_t c = mo + (size_t)j * G.nx + i;
+            if (a.stage == 1) {
+                a.k1h[c] = rh; a.k1u[c] = ru; a.k1v[c] = rv; a.k1w[c] = rw;
+                a.oh[c] = a.h0[c] + a.dt * rh;
+                a.ohu[c] = a.hu0[c] + a.dt * ru;
+                a.ohv[c] = a.hv0[c] + a.dt * rv;
+                a.ohw[c] = a.hw0[c] + a.dt * rw;
+            } else {
+                a.oh[c] = a.h0[c] + 0.5 * a.dt * (a.k1h[c] + rh);
+                a.ohu[c] = a.hu0[c] + 0.5 * a.dt * (a.k1u[c] + ru);
+                a.ohv[c] = a.hv0[c] + 0.5 * a.dt * (a.k1v[c] + rv);
+                a.ohw[c] = a.hw0[c] + 0.5 * a.dt * (a.k1w[c] + rw);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -292,32 +333,40 @@ static __global__ void k2_marks(const Geo2* __restrict__ geos, size_t pitch, con
     const int N = G.nx * G.ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int i = c % G.nx, j = c / G.nx;
-        double o[4][2];
-        const int nb[4] = {g2_cell(G, i - 1, j, &o[0][0], &o[0][1]), g2_cell(G, i + 1, j, &o[1][0], &o[1][1]),
-                           g2_cell(G, i, j - 1, &o[2][0], &o[2][1]), g2_cell(G, i, j + 1, &o[3][0], &o[3][1])};
-        double eta[4], u[4], v[4], w[4];
-        for (int q = 0; q < 4; ++q) {
-            const int m = nb[q];
-            eta[q] = h[m] - d[m];
-            u[q] = o[q][0] * hu[m] / h[m];
-            v[q] = o[q][1] * hv[m] / h[m];
-            w[q] = hw[m] / h[m];
-        }
-        const double dk = d[c];
-        const double eta_k = h[c] - dk, uk = hu[c] / h[c], vk = hv[c] / h[c], wk = hw[c] / h[c];
-        const double ex = (eta[1] - eta[0]) / (2.0 * G.dx), ey = (eta[3] - eta[2]) / (2.0 * G.dy);
-        const double ux = (u[1] - u[0]) / (2.0 * G.dx), uy = (u[3] - u[2]) / (2.0 * G.dy);
-        const double vx = (v[1] - v[0]) / (2.0 * G.dx), vy = (v[3] - v[2]) / (2.0 * G.dy);
-        const double wx = (w[1] - w[0]) / (2.0 * G.dx), wy = (w[3] - w[2]) / (2.0 * G.dy);
-        double val;
-        switch (crit) {
-        case NH_CRIT_ETA_D: val = fabs(eta_k / dk); break;
-        case NH_CRIT_ETA_X: val = sqrt(ex * ex + ey * ey); break;
-        case NH_CRIT_U:     val = sqrt(uk * uk + vk * vk); break;
-        case NH_CRIT_U_X:   val = sqrt(ux * ux + uy * uy + vx * vx + vy * vy); break;
-        case NH_CRIT_W:     val = fabs(wk); break;
-        case NH_CRIT_W_X:   val = sqrt(wx * wx + wy * wy); break;
-        default:            val = 0.0; break;
+        double val = 0.0;
+        if (crit == NH_CRIT_ETA_D) {
+            const double dk = d[c];
+            val = fabs((h[c] - dk) / dk);
+        } else if (crit == NH_CRIT_U) {
+            const double uk = hu[c] / h[c], vk = hv[c] / h[c];
+            val = sqrt(uk * uk + vk * vk);
+        } else if (crit == NH_CRIT_W) {
+            val = fabs(hw[c] / h[c]);
+        } else {   // the gradient criteria: central differences over the four neighbours
+            double o[4][2];
+            const int nb[4] = {g2_cell(G, i - 1, j, &o[0][0], &o[0][1]), g2_cell(G, i + 1, j, &o[1][0], &o[1][1]),
+                               g2_cell(G, i, j - 1, &o[2][0], &o[2][1]), g2_cell(G, i, j + 1, &o[3][0], &o[3][1])};
+            if (crit == NH_CRIT_ETA_X) {
+                double eta[4];
+                for (int q = 0; q < 4; ++q) eta[q] = h[nb[q]] - d[nb[q]];
+                const double ex = (eta[1] - eta[0]) / (2.0 * G.dx), ey = (eta[3] - eta[2]) / (2.0 * G.dy);
+                val = sqrt(ex * ex + ey * ey);
+            } else if (crit == NH_CRIT_U_X) {
+                double u[4], v[4];
+                for (int q = 0; q < 4; ++q) {
+                    const int m = nb[q];
+                    u[q] = o[q][0] * hu[m] / h[m];
+                    v[q] = o[q][1] * hv[m] / h[m];
+                }
+                const double ux = (u[1] - u[0]) / (2.0 * G.dx), uy = (u[3] - u[2]) / (2.0 * G.dy);
+                const double vx = (v[1] - v[0]) / (2.0 * G.dx), vy = (v[3] - v[2]) / (2.0 * G.dy);
+                val = sqrt(ux * ux + uy * uy + vx * vx + vy * vy);
+            } else if (crit == NH_CRIT_W_X) {
+                double w[4];
+                for (int q = 0; q < 4; ++q) w[q] = hw[nb[q]] / h[nb[q]];
+                const double wx = (w[1] - w[0]) / (2.0 * G.dx), wy = (w[3] - w[2]) / (2.0 * G.dy);
+                val = sqrt(wx * wx + wy * wy);
+            }
         }
         marks[c] = val > knh ? 1 : 0;
     }

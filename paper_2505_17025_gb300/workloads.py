@@ -237,39 +237,38 @@ def landslide_2d(n=2048, dx=0.02, h_min=0.1, h_max=2.0, slope=0.2, A=0.1, Lx=1.0
                       meta={"h_min": h_min, "h_max": h_max, "slope": slope})
 
 
-def landslide_ensemble_2d(n_members=32, n_min=256, n_max=1024, length=10.24, h_min=0.1, h_max=2.0,
-                          slope=(0.15, 0.25), A=(0.07, 0.13), L=(0.7, 1.3), s0=(1.4, 2.6), t0=1.0,
-                          d_start=0.6, cfl=0.5, seed=0, g=G):
-    """Ensemble of uneven 2D landslide runs: member m is an n x n grid over
-    the same length x length basin (n drawn uniformly from the multiples of
-    64 in [n_min, n_max], so dx = length / n), with slope, mound amplitude A,
-    length Lx (Ly = Lx / 2) and run-out s0 drawn uniformly from the given
-    ranges (seeded); each slide starts where d0 = d_start, centred in y; still
-    water, walls.  One dt for all members: CFL cfl on the finest grid.
-    Returns (members, dt)."""
-    rng = np.random.default_rng(seed)
-    sizes = np.arange(n_min, n_max + 1, 64)
+def landslide_ensemble_2d(n_members=32, sizes=tuple(range(256, 1025, 64)), dx=0.02, h_min=0.1, h_max=2.0,
+                          slope=(0.1, 0.3), A=(0.05, 0.15), L=(0.5, 1.5), s0=(1.0, 3.0), t0=1.0,
+                          d_start=0.6, x_frac_max=0.3, cfl=0.5, g=G):
+    """Ensemble of uneven 2D landslide runs: member m draws, from
+    numpy.random.default_rng(m), nx and ny independently from `sizes`, the
+    plane slope tan(theta), the mound amplitude A, its length Lx (Ly = Lx / 2)
+    and run-out s0 uniformly from the given ranges; d0 = min(h_min + slope x,
+    h_max) at spacing dx in x and y; the slide starts where d0 = d_start (at
+    most x_frac_max of the basin length), centred in y; still water, walls.
+    One dt for all members: CFL cfl at depth h_max.  Returns (members, dt)."""
     out = []
     for m in range(n_members):
-        n = int(rng.choice(sizes))
+        rng = np.random.default_rng(m)
+        nx = int(rng.choice(sizes))
+        ny = int(rng.choice(sizes))
         sl_m = float(rng.uniform(*slope))
         A_m = float(rng.uniform(*A))
         Lx = float(rng.uniform(*L))
         s0_m = float(rng.uniform(*s0))
-        dx = length / n
-        x = (np.arange(n) + 0.5) * dx
-        d0 = np.tile(np.minimum(h_min + sl_m * x, h_max), (n, 1))
-        xc0 = (d_start - h_min) / sl_m
-        yc0 = length / 2.0
-        X, Y = np.meshgrid(x, x)
+        x = (np.arange(nx) + 0.5) * dx
+        y = (np.arange(ny) + 0.5) * dx
+        d0 = np.tile(np.minimum(h_min + sl_m * x, h_max), (ny, 1))
+        xc0 = min((d_start - h_min) / sl_m, x_frac_max * nx * dx)
+        yc0 = ny * dx / 2.0
+        X, Y = np.meshgrid(x, y)
         h = d0 - A_m * np.exp(-((X - xc0) / Lx) ** 2 - ((Y - yc0) / (Lx / 2.0)) ** 2)
-        z = np.zeros((n, n))
-        out.append(Workload2D(f"landslide_ens_{m}", n, n, dx, dx, d0, h, z, z.copy(), z.copy(), 0.0,
+        z = np.zeros((ny, nx))
+        out.append(Workload2D(f"landslide_ens_{m}", nx, ny, dx, dx, d0, h, z, z.copy(), z.copy(), 0.0,
                               amplitude=A_m,
                               slide=dict(A=A_m, Lx=Lx, Ly=Lx / 2.0, xc0=xc0, yc0=yc0, s0=s0_m, t0=t0),
                               meta={"h_min": h_min, "h_max": h_max, "slope": sl_m}))
-    dx_min = min(w.dx for w in out)
-    dt = cfl_dt_2d(cfl, dx_min, dx_min, math.sqrt(g * h_max))
+    dt = cfl_dt_2d(cfl, dx, dx, math.sqrt(g * h_max))
     for w in out:
         w.dt = dt
     return out, dt

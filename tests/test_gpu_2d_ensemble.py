@@ -182,14 +182,16 @@ def _landslide_at(w, t0):
     sl = w.slide
     s = sl["s0"] * math.log(math.cosh(t0 / sl["t0"]))
     x = (np.arange(w.nx) + 0.5) * w.dx
-    X, Y = np.meshgrid(x, x)
+    y = (np.arange(w.ny) + 0.5) * w.dy
+    X, Y = np.meshgrid(x, y)
     return w.d0 - sl["A"] * np.exp(-((X - sl["xc0"] - s) / sl["Lx"]) ** 2 - ((Y - sl["yc0"]) / sl["Ly"]) ** 2)
 
 
 def test_landslide_ensemble_full_size():
-    """32 uneven landslide runs (256^2 to 1024^2 cells, drawn slope, A, L, s0)
-    for 3 captured steps from t = 0.3 s: every member's mass; the smallest
-    and the largest member against the oracle, every cell and mask."""
+    """32 uneven landslide runs (nx, ny drawn from 256 .. 1024, dx = 0.02 m,
+    drawn slope, A, L, s0) for 3 captured steps from t = 0.3 s: every
+    member's mass; the smallest and the largest member against the oracle,
+    every cell and mask."""
     ws, dt = W.landslide_ensemble_2d()
     t0 = 0.3
     hs = [_landslide_at(w, t0) for w in ws]
@@ -206,7 +208,7 @@ def test_landslide_ensemble_full_size():
     for i, w in enumerate(ws):
         m0 = hs[i].sum() * w.dx * w.dy
         assert abs(G.member_info(i)["mass"] - m0) <= 1e-12 * m0, i
-    sizes = [w.nx for w in ws]
+    sizes = [w.nx * w.ny for w in ws]
     for i in (int(np.argmin(sizes)), int(np.argmax(sizes))):
         w = ws[i]
         p = O2.Params2D(nx=w.nx, ny=w.ny, dx=w.dx, dy=w.dy, crit=O.CRIT_ETA_D, knh=1e-4, enlarge=1, rtol=1e-13,
@@ -217,4 +219,4 @@ def test_landslide_ensemble_full_size():
             r, oi, mk = O2.step(p, w.d0, t0 + k * dt, k, dt, s, want_mask=True)
             assert r == O.OK
         assert np.array_equal(G.get_mask(i), mk), i
-        _compare(s.fields(p), G.get_state(i), w.amplitude, w.d0.max(), f"landslide member {i} ({w.nx}^2)")
+        _compare(s.fields(p), G.get_state(i), w.amplitude, w.d0.max(), f"landslide member {i} ({w.nx}x{w.ny})")
