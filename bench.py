@@ -361,6 +361,10 @@ def run_2d(args):
                 f"tan(theta) U(0.1,0.3), A U(0.05,0.15), Lx U(0.5,1.5), s0 U(1,3); member m seeded with m")
     G = N.Grid2D.ensemble([dict(nx=w.nx, ny=w.ny, dx=w.dx, dy=w.dy, d0=w.d0, bc_x=w.bc_x, bc_y=w.bc_y)
                            for w in wls])
+    if args.precision == "mixed":
+        raise SystemExit("2D grids: --precision fp64 or mixed64 (FP32 state, FP64 solve)")
+    if args.precision == "mixed64":
+        G.set_precision(N.NH_MIXED_FP64_SOLVE)
     for i, w in enumerate(wls):
         h = w.h
         if w.slide:
@@ -394,8 +398,10 @@ def run_2d(args):
     cells = sum(w.nx * w.ny for w in wls)
     out = {"metric": METRIC, "value": cells * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32 state, f64 solve", "data": "synthetic",
            "config": {"workload": name, "cells": cells, "members": len(wls), "mode": args.mode,
+                      "precision": args.precision,
                       "k_nh": knh, "t_start": t_start, "dt": dt,
                       "mean_active_cells_per_step": info["active_total"] / max(1, args.steps),
                       "mean_krylov_iters_per_step": info["iters_total"] / max(1, args.steps),

@@ -1,4 +1,4 @@
-/* nhswe2d.h -- the method on a two-dimensional grid (FP64).
+/* nhswe2d.h -- the method on two-dimensional grids (FP64, or FP32 state).
  *
  * The paper's model is one-dimensional (Sec. 2) and names the extension to
  * two horizontal dimensions as future work (Sec. 6).  These calls run its
@@ -92,6 +92,13 @@ nh_status nh2d_set_criterion(nh_grid2d* g, int kind, double k_nh, int enlarge, i
    Defaults 1e-12, 20000, NH_GUESS_PREV.  A CG breakdown (indefinite
    operator) is solved again by unpreconditioned BiCGStab. */
 nh_status nh2d_set_solver(nh_grid2d* g, double rtol, int max_iter, int guess);
+
+/* NH_FP64 (default) or NH_MIXED_FP64_SOLVE: the state is stored in FP32 as
+   zeta = h - d0, hu, hv, hw (so eta = zeta + mound keeps its digits), the
+   predictor and the criterion run in FP32, the assembly, the Krylov solve,
+   the correction's arithmetic and every reduction stay FP64.  A change
+   clears every member's state (set it again before stepping). */
+nh_status nh2d_set_precision(nh_grid2d* g, int precision);
 
 /* 1 (default): nh2d_run replays captured graphs when it can (not for a
    first step that is global by request, nor right after a change of dt);

@@ -8,7 +8,10 @@
 // enlargement, row-major compaction, 9-point assembly, the line-
 // preconditioned CG of the 1D members (each grid one member; S, N and the
 // diagonal couplings as extra couplings) in one cooperative launch, and the
-// correction.  nh2d_run replays that step from a captured CUDA graph.
+// correction.  nh2d_run replays that step from a captured CUDA graph.  With
+// NH_MIXED_FP64_SOLVE the state lives in FP32 (zeta = h - d0, hu, hv, hw) in
+// the same buffers and the predictor and criterion run in FP32; assembly,
+// solve and the correction's arithmetic stay FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -33,6 +36,7 @@ struct nh_grid2d {
     double knh;
     double rtol;
     int max_iter, guess;
+    int prec;                                       // NH_FP64 or NH_MIXED_FP64_SOLVE
     bool has_state;
     double t_base, last_dt;
     long long n_since, steps;
@@ -41,7 +45,8 @@ struct nh_grid2d {
     double* q[2][4];
     double* qs[4];
     double* k1[4];
-    double *d0, *dn, *dn1;
+    double *d0, *dn, *dn1;                          // dn, dn1: depth (FP64) or mound (FP32 storage)
+    float* d0f;                                     // FP32 copy of d0
     unsigned char *marks, *act;
     int *inv, *list[2], *nact[2], *bcnt, *boff;   // nact [nb]; bcnt, boff [nb * nblk]
     int2 *items, *pitems;
@@ -130,6 +135,7 @@ size_t carve2(int nb, int pitch, nh_grid2d* g, char* base)
         for (int f = 0; f < 4; ++f) G->q[b][f] = c.take<double>(T);
     for (int f = 0; f < 4; ++f) { G->qs[f] = c.take<double>(T); G->k1[f] = c.take<double>(T); }
     G->d0 = c.take<double>(T); G->dn = c.take<double>(T); G->dn1 = c.take<double>(T);
+    G->d0f = c.take<float>(T);
     G->marks = c.take<unsigned char>(T); G->act = c.take<unsigned char>(T);
     G->inv = c.take<int>(T);
     for (int b = 0; b < 2; ++b) { G->list[b] = c.take<int>(T); G->nact[b] = c.take<int>(nb); }
@@ -189,6 +195,17 @@ SolveArgs<double> solve_args2(nh_grid2d* g, int lnew, double gscale, const TimeC
 
 // Everything of one step up to the assembled systems: kinematics, depth,
 // predictor, criterion, mask, compaction, work items, assembly, mass.
+template <typename TS>
+TS* as(double* p) { return reinterpret_cast<TS*>(p); }
+
+template <typename TS>
+const TS* d0_storage(const nh_grid2d* g)
+{
+    if constexpr (sizeof(TS) == 8) return nullptr;
+    else return g->d0f;
+}
+
+template <typename TS>
 nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double dt, double t_n, double t_n1,
                         bool all, const TimeCtl* tc)
 {
@@ -197,26 +214,29 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     const size_t P = (size_t)g->pitch;
     const dim3 eg(g->egx, g->nb);
     k2_kin<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slides, g->nb, t_n, t_n1, tc, g->kin);
-    k2_depth<<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 0, P, g->d0, g->dn, tc);
-    k2_depth<<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 1, P, g->d0, g->dn1, tc);
-    StageArgs sa1;
-    sa1.geos = g->geos; sa1.pitch = P;
-    sa1.h = g->q[cur][0]; sa1.hu = g->q[cur][1]; sa1.hv = g->q[cur][2]; sa1.hw = g->q[cur][3]; sa1.d = g->dn;
-    sa1.h0 = g->q[cur][0]; sa1.hu0 = g->q[cur][1]; sa1.hv0 = g->q[cur][2]; sa1.hw0 = g->q[cur][3];
-    sa1.k1h = g->k1[0]; sa1.k1u = g->k1[1]; sa1.k1v = g->k1[2]; sa1.k1w = g->k1[3];
-    sa1.oh = g->qs[0]; sa1.ohu = g->qs[1]; sa1.ohv = g->qs[2]; sa1.ohw = g->qs[3];
+    const TS* d0s = d0_storage<TS>(g);
+    k2_depth<TS><<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 0, P, g->d0, as<TS>(g->dn), tc);
+    k2_depth<TS><<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 1, P, g->d0, as<TS>(g->dn1), tc);
+    StageArgs<TS> sa1;
+    sa1.geos = g->geos; sa1.pitch = P; sa1.d0s = d0s;
+    sa1.h = as<TS>(g->q[cur][0]); sa1.hu = as<TS>(g->q[cur][1]); sa1.hv = as<TS>(g->q[cur][2]);
+    sa1.hw = as<TS>(g->q[cur][3]); sa1.d = as<TS>(g->dn);
+    sa1.h0 = sa1.h; sa1.hu0 = sa1.hu; sa1.hv0 = sa1.hv; sa1.hw0 = sa1.hw;
+    sa1.k1h = as<TS>(g->k1[0]); sa1.k1u = as<TS>(g->k1[1]); sa1.k1v = as<TS>(g->k1[2]); sa1.k1w = as<TS>(g->k1[3]);
+    sa1.oh = as<TS>(g->qs[0]); sa1.ohu = as<TS>(g->qs[1]); sa1.ohv = as<TS>(g->qs[2]); sa1.ohw = as<TS>(g->qs[3]);
     sa1.dt = dt; sa1.stage = 1; sa1.tc = tc;
-    k2_stage<<<eg, 256, 0, st>>>(sa1);
-    StageArgs sa2 = sa1;
-    sa2.h = g->qs[0]; sa2.hu = g->qs[1]; sa2.hv = g->qs[2]; sa2.hw = g->qs[3]; sa2.d = g->dn1;
-    sa2.oh = g->q[nxt][0]; sa2.ohu = g->q[nxt][1]; sa2.ohv = g->q[nxt][2]; sa2.ohw = g->q[nxt][3];
+    k2_stage<TS><<<eg, kTX * kTY, 0, st>>>(sa1);
+    StageArgs<TS> sa2 = sa1;
+    sa2.h = sa1.oh; sa2.hu = sa1.ohu; sa2.hv = sa1.ohv; sa2.hw = sa1.ohw; sa2.d = as<TS>(g->dn1);
+    sa2.oh = as<TS>(g->q[nxt][0]); sa2.ohu = as<TS>(g->q[nxt][1]); sa2.ohv = as<TS>(g->q[nxt][2]);
+    sa2.ohw = as<TS>(g->q[nxt][3]);
     sa2.stage = 2;
-    k2_stage<<<eg, 256, 0, st>>>(sa2);
+    k2_stage<TS><<<eg, kTX * kTY, 0, st>>>(sa2);
 
     if (all) CK2(cudaMemsetAsync(g->marks, 1, T, st));
     else if (g->crit == NH_CRIT_HYDROSTATIC) CK2(cudaMemsetAsync(g->marks, 0, T, st));
-    else k2_marks<<<eg, 256, 0, st>>>(g->geos, P, g->q[nxt][0], g->q[nxt][1], g->q[nxt][2], g->q[nxt][3],
-                                     g->dn1, g->crit, g->knh, g->marks);
+    else k2_marks<TS><<<eg, 256, 0, st>>>(g->geos, P, sa2.oh, sa2.ohu, sa2.ohv, sa2.ohw, as<TS>(g->dn1), d0s,
+                                         g->crit, g->knh, g->marks);
     k2_dilate<<<eg, 256, 0, st>>>(g->geos, P, g->marks, all ? 0 : g->enlarge, g->act, tc);
     k2_count<<<dim3(g->nblk, g->nb), kCompact2, 0, st>>>(g->geos, P, g->act, g->nblk, g->bcnt);
     k2_scan<<<g->nb, 1024, 0, st>>>(g->bcnt, g->nblk, g->boff, g->nact[lnew], g->ms, tc);
@@ -225,11 +245,11 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     k_items<<<1, 1024, 0, st>>>(g->ms, g->nb, g->items, g->pitems, g->ctl);
     CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
 
-    Asm2Args aa;
+    Asm2Args<TS> aa;
     aa.geos = g->geos; aa.slides = g->slides; aa.kin = g->kin;
     aa.nb = g->nb; aa.pitch = g->pitch; aa.maxch = g->maxch;
-    aa.ht = g->q[nxt][0]; aa.hut = g->q[nxt][1]; aa.hvt = g->q[nxt][2]; aa.hwt = g->q[nxt][3];
-    aa.d0 = g->d0; aa.d1 = g->dn1; aa.dt = dt;
+    aa.ht = sa2.oh; aa.hut = sa2.ohu; aa.hvt = sa2.ohv; aa.hwt = sa2.ohw;
+    aa.d0 = g->d0; aa.d1 = as<TS>(g->dn1); aa.dt = dt;
     aa.list = g->list[lnew]; aa.inv = g->inv; aa.ms = g->ms;
     aa.diag = g->diag; aa.offl = g->offl; aa.offr = g->offr; aa.R = g->R;
     aa.nbl = g->nbl; aa.nbr = g->nbr;
@@ -237,12 +257,13 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     aa.c6 = g->c6; aa.cx = g->cx; aa.cy = g->cy; aa.phi = g->phi; aa.ddx = g->ddx; aa.ddy = g->ddy;
     aa.part = g->part; aa.cnt = g->cnt; aa.solver = NH_SOLVER_AUTO;
     aa.items = g->items; aa.ctl = g->ctl;
-    k2_assemble<<<g->items_grid, kChunk, 0, st>>>(aa);
-    k2_mass<<<dim3(g->nmass, g->nb), 256, 0, st>>>(g->geos, P, g->q[nxt][0], g->mass_part);
+    k2_assemble<TS><<<g->items_grid, kChunk, 0, st>>>(aa);
+    k2_mass<TS><<<dim3(g->nmass, g->nb), 256, 0, st>>>(g->geos, P, sa2.oh, g->d0, g->mass_part);
     return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }
 
 // The accepted step's tail: zero psi on the previous mask, correct on the new one.
+template <typename TS>
 nh_status enqueue_back(nh_grid2d* g, cudaStream_t st, int nxt, int lprev, int lnew, const TimeCtl* tc)
 {
     const size_t T = (size_t)g->nb * g->pitch;
@@ -250,14 +271,14 @@ nh_status enqueue_back(nh_grid2d* g, cudaStream_t st, int nxt, int lprev, int ln
     cl.nb = g->nb; cl.pitch = g->pitch; cl.maxlist = g->pitch;
     cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = tc;
     k_clear_prev<<<(int)std::min<size_t>((T + 255) / 256, (size_t)g->sms * 8), 256, 0, st>>>(cl);
-    Corr2Args co;
+    Corr2Args<TS> co;
     co.geos = g->geos; co.pitch = g->pitch; co.list = g->list[lnew];
     co.nbl = g->nbl; co.nbr = g->nbr; co.ext_k = g->ext_k; co.ext_stride = T;
     co.x = g->x; co.c6 = g->c6; co.cx = g->cx; co.cy = g->cy; co.phi = g->phi;
     co.ddx = g->ddx; co.ddy = g->ddy; co.ms = g->ms;
-    co.hu = g->q[nxt][1]; co.hv = g->q[nxt][2]; co.hw = g->q[nxt][3]; co.psi = g->psi;
+    co.hu = as<TS>(g->q[nxt][1]); co.hv = as<TS>(g->q[nxt][2]); co.hw = as<TS>(g->q[nxt][3]); co.psi = g->psi;
     co.items = g->items; co.ctl = g->ctl; co.tc = tc;
-    k2_correct<<<g->items_grid, kChunk, 0, st>>>(co);
+    k2_correct<TS><<<g->items_grid, kChunk, 0, st>>>(co);
     return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }
 
@@ -371,7 +392,8 @@ nh_status step2(nh_grid2d* g, double dt, nh_step_info* info)
     const double t_n1 = g->t_base + (double)(g->n_since + 1) * dt;
     const int cur = g->cur, nxt = cur ^ 1, lprev = g->lcur, lnew = lprev ^ 1;
     const bool all = g->crit == NH_CRIT_GLOBAL || (g->first_global && g->steps == 0);
-    nh_status rc = enqueue_front(g, st, cur, lnew, dt, t_n, t_n1, all, nullptr);
+    nh_status rc = g->prec == NH_FP64 ? enqueue_front<double>(g, st, cur, lnew, dt, t_n, t_n1, all, nullptr)
+                                      : enqueue_front<float>(g, st, cur, lnew, dt, t_n, t_n1, all, nullptr);
     if (rc != NH_OK) return rc;
     const double gscale = (g->guess == NH_GUESS_PREV && g->last_dt > 0.0) ? dt / g->last_dt : 0.0;
     SolveArgs<double> sa = solve_args2(g, lnew, gscale, nullptr);
@@ -384,7 +406,8 @@ nh_status step2(nh_grid2d* g, double dt, nh_step_info* info)
     CK2(cudaGetLastError());
     const nh_status status = (nh_status)S.status;
     if (status == NH_OK) {
-        rc = enqueue_back(g, st, nxt, lprev, lnew, nullptr);
+        rc = g->prec == NH_FP64 ? enqueue_back<double>(g, st, nxt, lprev, lnew, nullptr)
+                                : enqueue_back<float>(g, st, nxt, lprev, lnew, nullptr);
         if (rc != NH_OK) return rc;
         g->cur = nxt;
         g->lcur = lnew;
@@ -404,7 +427,9 @@ nh_status step2(nh_grid2d* g, double dt, nh_step_info* info)
 nh_status enqueue_graph_step(nh_grid2d* g, cudaStream_t st, int cur, int lprev, double dt)
 {
     const int nxt = cur ^ 1, lnew = lprev ^ 1;
-    nh_status rc = enqueue_front(g, st, cur, lnew, dt, 0.0, 0.0, g->crit == NH_CRIT_GLOBAL, g->tc);
+    const bool all = g->crit == NH_CRIT_GLOBAL;
+    nh_status rc = g->prec == NH_FP64 ? enqueue_front<double>(g, st, cur, lnew, dt, 0.0, 0.0, all, g->tc)
+                                      : enqueue_front<float>(g, st, cur, lnew, dt, 0.0, 0.0, all, g->tc);
     if (rc != NH_OK) return rc;
     SolveArgs<double> sa = solve_args2(g, lnew, g->guess == NH_GUESS_PREV ? 1.0 : 0.0, g->tc);
     CK2(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
@@ -417,7 +442,8 @@ nh_status enqueue_graph_step(nh_grid2d* g, cudaStream_t st, int cur, int lprev, 
     if (rc != NH_OK) return rc;
     k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->nmass, 1.0, g->summary, g->tc);
     k_commit<<<1, 32, 0, st>>>(g->summary, g->tc);
-    return enqueue_back(g, st, nxt, lprev, lnew, g->tc);
+    return g->prec == NH_FP64 ? enqueue_back<double>(g, st, nxt, lprev, lnew, g->tc)
+                              : enqueue_back<float>(g, st, nxt, lprev, lnew, g->tc);
 }
 
 bool graph_eligible(const nh_grid2d* g, double dt)
@@ -436,7 +462,7 @@ void graph_destroy(nh_grid2d* g)
 nh_status graph_prepare(nh_grid2d* g, double dt)
 {
     const double key[9] = {dt, (double)g->crit, g->knh, (double)g->enlarge, g->rtol, (double)g->max_iter,
-                           (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->first_global};
+                           (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->prec};
     if (g->graph_valid && std::memcmp(key, g->graph_key, sizeof(key)) == 0) return NH_OK;
     graph_destroy(g);
     for (int p = 0; p < 2; ++p) {
@@ -547,6 +573,7 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
     g->egx = std::max(1, std::min((g->pitch + 255) / 256, (g->sms * 8 + g->nb - 1) / g->nb));
     g->crit = NH_CRIT_GLOBAL; g->knh = 1e-3; g->enlarge = 1; g->first_global = 0;
     g->rtol = 1e-12; g->max_iter = 20000; g->guess = NH_GUESS_PREV;
+    g->prec = NH_FP64;
     g->has_state = false;
     g->t_base = 0.0; g->last_dt = 0.0; g->n_since = 0; g->steps = 0; g->cur = 0; g->lcur = 0;
     g->graph[0] = g->graph[1] = nullptr;
@@ -591,6 +618,11 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
                                 sizeof(double) * descs[b].nx * descs[b].ny, cudaMemcpyHostToDevice,
                                 st) != cudaSuccess)
                 rc = NH_ERR_CUDA;
+        if (rc == NH_OK) {
+            const size_t T = (size_t)n_members * g->pitch;
+            k2_to_f32<<<(int)std::min<size_t>((T + 255) / 256, (size_t)g->sms * 8), 256, 0, st>>>(T, g->d0, g->d0f);
+            if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
+        }
         // the host copies above are pageable: finish them before geo_h goes
         if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
     } while (0);
@@ -664,6 +696,18 @@ nh_status nh2d_set_graphs(nh_grid2d* g, int on)
     return NH_OK;
 }
 
+nh_status nh2d_set_precision(nh_grid2d* g, int precision)
+{
+    if (!g || (precision != NH_FP64 && precision != NH_MIXED_FP64_SOLVE)) return NH_ERR_ARG;
+    if (precision != g->prec) {
+        g->prec = precision;
+        graph_destroy(g);
+        std::fill(g->member_set.begin(), g->member_set.end(), 0);
+        g->has_state = false;
+    }
+    return NH_OK;
+}
+
 nh_status nh2d_set_member_state(nh_grid2d* g, int m, const double* h, const double* hu, const double* hv,
                                 const double* hw, double t)
 {
@@ -676,8 +720,19 @@ nh_status nh2d_set_member_state(nh_grid2d* g, int m, const double* h, const doub
     cudaStream_t st = g->stream;
     const size_t mo = (size_t)m * g->pitch;
     const double* src[4] = {h, hu, hv, hw};
-    for (int f = 0; f < 4; ++f)
-        CK2(cudaMemcpyAsync(g->q[g->cur][f] + mo, src[f], sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    if (g->prec == NH_FP64) {
+        for (int f = 0; f < 4; ++f)
+            CK2(cudaMemcpyAsync(g->q[g->cur][f] + mo, src[f], sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    } else {   // through the FP64 scratch of the stage buffers, then zeta = h - d0 etc. in FP32
+        for (int f = 0; f < 4; ++f)
+            CK2(cudaMemcpyAsync(g->qs[f] + mo, src[f], sizeof(double) * N, cudaMemcpyHostToDevice, st));
+        const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)g->sms * 8);
+        k2_store_f32<<<grid, 256, 0, st>>>((int)N, g->d0 + mo, g->qs[0] + mo, g->qs[1] + mo, g->qs[2] + mo,
+                                           g->qs[3] + mo, as<float>(g->q[g->cur][0]) + mo,
+                                           as<float>(g->q[g->cur][1]) + mo, as<float>(g->q[g->cur][2]) + mo,
+                                           as<float>(g->q[g->cur][3]) + mo);
+        CK2(cudaGetLastError());
+    }
     CK2(cudaMemsetAsync(g->psi + mo, 0, sizeof(double) * g->pitch, st));
     CK2(cudaMemsetAsync(g->nact[0] + m, 0, sizeof(int), st));
     CK2(cudaMemsetAsync(g->nact[1] + m, 0, sizeof(int), st));
@@ -703,13 +758,21 @@ nh_status nh2d_get_member_state(nh_grid2d* g, int m, double* h, double* hu, doub
     const size_t N = (size_t)g->d[m].nx * g->d[m].ny;
     const size_t mo = (size_t)m * g->pitch;
     double* dst[4] = {h, hu, hv, hw};
+    double* srcs[4] = {g->q[g->cur][0] + mo, g->q[g->cur][1] + mo, g->q[g->cur][2] + mo, g->q[g->cur][3] + mo};
+    if (g->prec != NH_FP64) {   // FP32 storage -> FP64 (h = zeta + d0) in the stage scratch
+        for (int f = 0; f < 4; ++f) srcs[f] = g->qs[f] + mo;
+        const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)g->sms * 8);
+        k2_load_f32<<<grid, 256, 0, st>>>((int)N, g->d0 + mo, as<float>(g->q[g->cur][0]) + mo,
+                                          as<float>(g->q[g->cur][1]) + mo, as<float>(g->q[g->cur][2]) + mo,
+                                          as<float>(g->q[g->cur][3]) + mo, srcs[0], srcs[1], srcs[2], srcs[3]);
+        CK2(cudaGetLastError());
+    }
     for (int f = 0; f < 4; ++f)
-        if (dst[f])
-            CK2(cudaMemcpyAsync(dst[f], g->q[g->cur][f] + mo, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        if (dst[f]) CK2(cudaMemcpyAsync(dst[f], srcs[f], sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     std::vector<double> hh, ps;
     if (p_nh) {
         hh.resize(N); ps.resize(N);
-        CK2(cudaMemcpyAsync(hh.data(), g->q[g->cur][0] + mo, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        CK2(cudaMemcpyAsync(hh.data(), srcs[0], sizeof(double) * N, cudaMemcpyDeviceToHost, st));
         CK2(cudaMemcpyAsync(ps.data(), g->psi + mo, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     }
     CK2(cudaStreamSynchronize(st));

@@ -1333,7 +1333,6 @@ __global__ void __launch_bounds__(kPcrThreads) k_pcr(SolveArgs<T> a, int mode)
     TP* sa = reinterpret_cast<TP*>(smem_raw);   // reduction ping-pong buffers
     TP* sd = sa + kPcrRows;
     __shared__ double red[96];
-    constexpr int RPT = kPcrRows / kPcrThreads;
     const int it = a.it;
     const T* rnew = (mode == PCR_PCG) ? a.r : ((it & 1) ? a.r1 : a.r);
     const T* rold = (it & 1) ? a.r : a.r1;

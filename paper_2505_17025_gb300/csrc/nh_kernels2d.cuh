@@ -1,6 +1,12 @@
-// nh_kernels2d.cuh -- kernels of the two-dimensional grid (FP64).
+// nh_kernels2d.cuh -- kernels of the two-dimensional grid.
 //
-//  k2_depth      bottom depth d = d0 - mound at one time               (a1)
+// State storage (template parameter TS): FP64 keeps h, hu, hv, hw and the
+// depth d; FP32 keeps zeta = h - d0, hu, hv, hw and the mound m = d0 - d, with
+// an FP32 copy of d0, so that eta = zeta + m keeps its digits in FP32 (the 1D
+// mixed path's representation).  Assembly, Krylov solve and the correction's
+// arithmetic stay FP64 in both.
+//
+//  k2_depth      bottom depth d = d0 - mound (FP64) or the mound (FP32)  (a1)
 //  k2_stage      one Heun stage of the hydrostatic predictor: x and y
 //                Rusanov fluxes of MUSCL states, well-balanced sources    (a2)
 //  k2_marks      criterion of Sec. 5.1 (2D form) on the predicted state  (a3)
@@ -154,10 +160,12 @@ __device__ __forceinline__ void bottom2(const Geo2& G, const double* __restrict_
     out[6] = d_t; out[7] = d_xt; out[8] = d_yt; out[9] = d_tt;
 }
 
-// Depth at t^n (which = 0) or t^{n+1} (which = 1).
+// Depth (FP64 storage) or mound (FP32 storage) at t^n (which = 0) or
+// t^{n+1} (which = 1).
+template <typename TS>
 static __global__ void k2_depth(const Geo2* __restrict__ geos, const Slide2* __restrict__ slides,
                                 const Kin2* __restrict__ kin, int which, size_t pitch,
-                                const double* __restrict__ d0, double* d, const TimeCtl* __restrict__ tc)
+                                const double* __restrict__ d0, TS* dm, const TimeCtl* __restrict__ tc)
 {
     if (tc && tc->abort) return;
     const int b = blockIdx.y;
@@ -166,38 +174,42 @@ static __global__ void k2_depth(const Geo2* __restrict__ geos, const Slide2* __r
     const double s = kin[2 * b + which].s;
     const size_t mo = (size_t)b * pitch;
     const int N = G.nx * G.ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
-        d[mo + c] = d0[mo + c] - mound2(G, S, c % G.nx, c / G.nx, s);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const double m = mound2(G, S, c % G.nx, c / G.nx, s);
+        if constexpr (sizeof(TS) == 8) dm[mo + c] = d0[mo + c] - m;
+        else dm[mo + c] = TS(m);
+    }
 }
 
-__device__ __forceinline__ double slope2(int lim, double vm, double v0, double vp)
+// h, eta and d of cell c from the stored state (see the head of this file).
+template <typename TS>
+__device__ __forceinline__ void cell_hed(const TS* __restrict__ hz, const TS* __restrict__ dm,
+                                         const TS* __restrict__ d0s, size_t c, TS& h, TS& eta, TS& d)
+{
+    if constexpr (sizeof(TS) == 8) {
+        h = hz[c]; d = dm[c]; eta = h - d;
+    } else {
+        const TS z = hz[c], m = dm[c], dz = d0s[c];
+        d = dz - m; eta = z + m; h = z + dz;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T slope2(int lim, T vm, T v0, T vp)
 {
     return limited_slope(lim, vm, v0, vp);
 }
 
-// Rusanov flux normal to a face of (hun, hun un + g h^2/2, hun ut, hun w) from
-// left / right (h, un, ut, w).
-__device__ __forceinline__ void rusanov2(double g, double hL, double nL, double tL, double wL,
-                                         double hR, double nR, double tR, double wR, double F[4])
-{
-    const double FL0 = hL * nL, FL1 = hL * nL * nL + 0.5 * g * hL * hL, FL2 = hL * nL * tL, FL3 = hL * nL * wL;
-    const double FR0 = hR * nR, FR1 = hR * nR * nR + 0.5 * g * hR * hR, FR2 = hR * nR * tR, FR3 = hR * nR * wR;
-    const double sL = fabs(nL) + sqrt(g * hL), sR = fabs(nR) + sqrt(g * hR);
-    const double s = (sL > sR) ? sL : sR;
-    F[0] = 0.5 * (FL0 + FR0) - 0.5 * s * (hR - hL);
-    F[1] = 0.5 * (FL1 + FR1) - 0.5 * s * (hR * nR - hL * nL);
-    F[2] = 0.5 * (FL2 + FR2) - 0.5 * s * (hR * tR - hL * tL);
-    F[3] = 0.5 * (FL3 + FR3) - 0.5 * s * (hR * wR - hL * wL);
-}
-
+template <typename TS>
 struct StageArgs {
     const Geo2* geos;
     size_t pitch;                          // member b's cells at b * pitch in every array
-    const double *h, *hu, *hv, *hw;        // state the rate is evaluated on
-    const double* d;                       // depth at that state's time
-    const double *h0, *hu0, *hv0, *hw0;    // Q^n
-    double *k1h, *k1u, *k1v, *k1w;         // stage-1 rates (written at stage 1, read at stage 2)
-    double *oh, *ohu, *ohv, *ohw;          // output: Q* (stage 1) or Q~ (stage 2)
+    const TS *h, *hu, *hv, *hw;            // state the rate is evaluated on (h or zeta first)
+    const TS* d;                           // depth (FP64) or mound (FP32) at that state's time
+    const TS* d0s;                         // FP32 copy of d0 (FP32 storage)
+    const TS *h0, *hu0, *hv0, *hw0;        // Q^n
+    TS *k1h, *k1u, *k1v, *k1w;             // stage-1 rates (written at stage 1, read at stage 2)
+    TS *oh, *ohu, *ohv, *ohw;              // output: Q* (stage 1) or Q~ (stage 2)
     double dt;
     int stage;
     const TimeCtl* tc;                     // captured runs: skip after an aborted step
@@ -208,41 +220,61 @@ struct StageArgs {
 //  1. every tile and halo cell (mirrored / wrapped by g2_cell, odd parity on
 //     the normal velocity) -> eta, u, v, w, d once (one reciprocal of h);
 //  2. every x-face and y-face of the tile -> limited slopes of its two cells
-//     and the Rusanov flux, once per face;
-//  3. every cell -> flux differences plus the bottom source
-//     g hbar (d_{+1/2} - d_{-1/2}) / ds per direction (depth continuous at
-//     faces, hbar from the cell's own face thicknesses), then the Heun stage.
+//     and the Rusanov flux, once per face, with the normal momentum flux split
+//     as F = A + (g/4)(hL^2 + hR^2) and the jump part G = (g/4)(hR + hL)(etaR - etaL);
+//  3. every cell -> per direction -(A_r - A_l + G_r + G_l + g hbar sigma_eta)/ds
+//     for the normal momentum (hbar = eta + (d_l + d_r)/2, the mean of its two
+//     face thicknesses; algebraically the flux difference plus the bottom
+//     source g hbar (d_r - d_l)/ds with the depth continuous at faces, and
+//     exact for a lake at rest in any precision), flux differences for the
+//     rest, then the Heun stage.
 constexpr int kTX = 32, kTY = 8;                 // 256 threads, one cell each
 constexpr int kHX = kTX + 4, kHY = kTY + 4;      // tile with halo
 constexpr int kFX = (kTX + 1) * kTY;             // x-faces of a tile
 constexpr int kFY = kTX * (kTY + 1);             // y-faces
 
-__device__ __forceinline__ void face_flux(double g, int lim, const double* e, const double* un, const double* ut,
-                                          const double* w, const double* d, int s, double F[4])
+// Face between cells L = -1 and R = 0 (e[k * s] is cell k's value): mass flux,
+// normal momentum A and G parts, tangential momentum and hw fluxes.
+template <typename T>
+__device__ __forceinline__ void face_flux(T g, int lim, const T* e, const T* un, const T* ut, const T* w,
+                                          const T* d, int s, T F[5])
 {
-    // cells L = -1, R = 0 relative to the face; e[k * s] is cell k's value
-    const double seL = slope2(lim, e[-2 * s], e[-s], e[0]), seR = slope2(lim, e[-s], e[0], e[s]);
-    const double snL = slope2(lim, un[-2 * s], un[-s], un[0]), snR = slope2(lim, un[-s], un[0], un[s]);
-    const double stL = slope2(lim, ut[-2 * s], ut[-s], ut[0]), stR = slope2(lim, ut[-s], ut[0], ut[s]);
-    const double swL = slope2(lim, w[-2 * s], w[-s], w[0]), swR = slope2(lim, w[-s], w[0], w[s]);
-    const double df = 0.5 * (d[-s] + d[0]);
-    rusanov2(g, e[-s] + 0.5 * seL + df, un[-s] + 0.5 * snL, ut[-s] + 0.5 * stL, w[-s] + 0.5 * swL,
-             e[0] - 0.5 * seR + df, un[0] - 0.5 * snR, ut[0] - 0.5 * stR, w[0] - 0.5 * swR, F);
+    const T h2 = T(0.5);
+    const T seL = slope2(lim, e[-2 * s], e[-s], e[0]), seR = slope2(lim, e[-s], e[0], e[s]);
+    const T snL = slope2(lim, un[-2 * s], un[-s], un[0]), snR = slope2(lim, un[-s], un[0], un[s]);
+    const T stL = slope2(lim, ut[-2 * s], ut[-s], ut[0]), stR = slope2(lim, ut[-s], ut[0], ut[s]);
+    const T swL = slope2(lim, w[-2 * s], w[-s], w[0]), swR = slope2(lim, w[-s], w[0], w[s]);
+    const T df = h2 * (d[-s] + d[0]);
+    const T eL = e[-s] + h2 * seL, eR = e[0] - h2 * seR;
+    const T uL = un[-s] + h2 * snL, uR = un[0] - h2 * snR;
+    const T tL = ut[-s] + h2 * stL, tR = ut[0] - h2 * stR;
+    const T wL = w[-s] + h2 * swL, wR = w[0] - h2 * swR;
+    const T hL = eL + df, hR = eR + df;
+    const T qL = hL * uL, qR = hR * uR;
+    const T aL = fabs(uL) + sqrt(g * hL), aR = fabs(uR) + sqrt(g * hR);
+    const T sp = aL > aR ? aL : aR;
+    const T de = eR - eL;
+    F[0] = h2 * (qL + qR) - h2 * sp * de;
+    F[1] = h2 * (qL * uL + qR * uR) - h2 * sp * (qR - qL);
+    F[2] = T(0.25) * g * (hR + hL) * de;
+    F[3] = h2 * (qL * tL + qR * tR) - h2 * sp * (hR * tR - hL * tL);
+    F[4] = h2 * (qL * wL + qR * wR) - h2 * sp * (hR * wR - hL * wL);
 }
 
-static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs a)
+template <typename TS>
+static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs<TS> a)
 {
     if (a.tc && a.tc->abort) return;
-    __shared__ double s_e[kHY][kHX], s_u[kHY][kHX], s_v[kHY][kHX], s_w[kHY][kHX], s_d[kHY][kHX];
-    __shared__ double s_fx[4][kTY][kTX + 1], s_fy[4][kTY + 1][kTX];
+    __shared__ TS s_e[kHY][kHX], s_u[kHY][kHX], s_v[kHY][kHX], s_w[kHY][kHX], s_d[kHY][kHX];
+    __shared__ TS s_fx[5][kTY][kTX + 1], s_fy[5][kTY + 1][kTX];
     const int b = blockIdx.y;
     const size_t mo = (size_t)b * a.pitch;
     const Geo2 G = a.geos[b];
     const int tiles_x = (G.nx + kTX - 1) / kTX, tiles = tiles_x * ((G.ny + kTY - 1) / kTY);
     const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
-    const double* h = a.h + mo; const double* hu = a.hu + mo; const double* hv = a.hv + mo;
-    const double* hw = a.hw + mo; const double* dd = a.d + mo;
-    const double idx = 1.0 / G.dx, idy = 1.0 / G.dy;
+    const TS* hz = a.h + mo; const TS* hu = a.hu + mo; const TS* hv = a.hv + mo;
+    const TS* hw = a.hw + mo; const TS* dm = a.d + mo; const TS* d0s = a.d0s ? a.d0s + mo : nullptr;
+    const TS g = TS(G.g), idx = TS(1.0 / G.dx), idy = TS(1.0 / G.dy), h2 = TS(0.5);
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int i0 = (tile % tiles_x) * kTX, j0 = (tile / tiles_x) * kTY;
         // 1. primitives of the tile and its cross-shaped halo
@@ -252,30 +284,33 @@ static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs a)
             if (!in_x && !in_y) continue;   // corners: no stencil reaches them
             double ox, oy;
             const int c = g2_cell(G, i0 + lx - 2, j0 + ly - 2, &ox, &oy);
-            const double hc = h[c], rh = 1.0 / hc, dc = dd[c];
-            s_e[ly][lx] = hc - dc;
+            TS hc, ec, dc;
+            cell_hed<TS>(hz, dm, d0s, c, hc, ec, dc);
+            const TS rh = TS(1) / hc;
+            s_e[ly][lx] = ec;
             s_d[ly][lx] = dc;
-            s_u[ly][lx] = ox * hu[c] * rh;
-            s_v[ly][lx] = oy * hv[c] * rh;
+            s_u[ly][lx] = TS(ox) * hu[c] * rh;
+            s_v[ly][lx] = TS(oy) * hv[c] * rh;
             s_w[ly][lx] = hw[c] * rh;
         }
         __syncthreads();
-        // 2. face fluxes: x-face (fx, ty) between cells fx-1 and fx of row ty;
-        //    y-face (tx, fy) between cells fy-1 and fy of column tx
+        // 2. face fluxes: x-face (fx, r) between cells fx-1 and fx of row r;
+        //    y-face (col, fy) between cells fy-1 and fy of column col
         for (int q = tid; q < kFX + kFY; q += kTX * kTY) {
-            double F[4];
+            TS F[5];
             if (q < kFX) {
                 const int fx = q % (kTX + 1), r = q / (kTX + 1);
                 const int ly = r + 2, lx = fx + 2;
-                face_flux(G.g, G.lim, &s_e[ly][lx], &s_u[ly][lx], &s_v[ly][lx], &s_w[ly][lx], &s_d[ly][lx], 1, F);
+                face_flux<TS>(g, G.lim, &s_e[ly][lx], &s_u[ly][lx], &s_v[ly][lx], &s_w[ly][lx], &s_d[ly][lx], 1, F);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) s_fx[k][r][fx] = F[k];
+                for (int k = 0; k < 5; ++k) s_fx[k][r][fx] = F[k];
             } else {
                 const int q2 = q - kFX, col = q2 % kTX, fy = q2 / kTX;
                 const int ly = fy + 2, lx = col + 2;
-                face_flux(G.g, G.lim, &s_e[ly][lx], &s_v[ly][lx], &s_u[ly][lx], &s_w[ly][lx], &s_d[ly][lx], kHX, F);
+                face_flux<TS>(g, G.lim, &s_e[ly][lx], &s_v[ly][lx], &s_u[ly][lx], &s_w[ly][lx], &s_d[ly][lx], kHX,
+                              F);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) s_fy[k][fy][col] = F[k];
+                for (int k = 0; k < 5; ++k) s_fy[k][fy][col] = F[k];
             }
         }
         __syncthreads();
@@ -283,36 +318,33 @@ static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs a)
         const int i = i0 + tx, j = j0 + ty;
         if (i < G.nx && j < G.ny) {
             const int lx = tx + 2, ly = ty + 2;
-            const double ec = s_e[ly][lx], dc = s_d[ly][lx];
-            // x: bottom source with the cell's face thicknesses
-            const double sex = slope2(G.lim, s_e[ly][lx - 1], ec, s_e[ly][lx + 1]);
-            const double dfw = 0.5 * (s_d[ly][lx - 1] + dc), dfe = 0.5 * (dc + s_d[ly][lx + 1]);
-            const double Sx = G.g * 0.5 * ((ec - 0.5 * sex + dfw) + (ec + 0.5 * sex + dfe)) * (dfe - dfw) * idx;
-            const double sey = slope2(G.lim, s_e[ly - 1][lx], ec, s_e[ly + 1][lx]);
-            const double dfs = 0.5 * (s_d[ly - 1][lx] + dc), dfn = 0.5 * (dc + s_d[ly + 1][lx]);
-            const double Sy = G.g * 0.5 * ((ec - 0.5 * sey + dfs) + (ec + 0.5 * sey + dfn)) * (dfn - dfs) * idy;
-            double rx[4], ry[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                rx[k] = -(s_fx[k][ty][tx + 1] - s_fx[k][ty][tx]) * idx;
-                ry[k] = -(s_fy[k][ty + 1][tx] - s_fy[k][ty][tx]) * idy;
-            }
-            const double rh = rx[0] + ry[0];
-            const double ru = (rx[1] + Sx) + ry[2];     // x-normal momentum, y-tangential
-            const double rv = rx[2] + (ry[1] + Sy);     // x-tangential, y-normal momentum
-            const double rw = rx[3] + ry[3];
+            const TS ec = s_e[ly][lx], dc = s_d[ly][lx];
+            const TS sex = slope2(G.lim, s_e[ly][lx - 1], ec, s_e[ly][lx + 1]);
+            const TS hbx = ec + h2 * (h2 * (s_d[ly][lx - 1] + dc) + h2 * (dc + s_d[ly][lx + 1]));
+            const TS sey = slope2(G.lim, s_e[ly - 1][lx], ec, s_e[ly + 1][lx]);
+            const TS hby = ec + h2 * (h2 * (s_d[ly - 1][lx] + dc) + h2 * (dc + s_d[ly + 1][lx]));
+            const TS rh = -(s_fx[0][ty][tx + 1] - s_fx[0][ty][tx]) * idx - (s_fy[0][ty + 1][tx] - s_fy[0][ty][tx]) * idy;
+            const TS ru = -((s_fx[1][ty][tx + 1] - s_fx[1][ty][tx]) + (s_fx[2][ty][tx + 1] + s_fx[2][ty][tx])
+                            + g * hbx * sex) * idx
+                          - (s_fy[3][ty + 1][tx] - s_fy[3][ty][tx]) * idy;
+            const TS rv = -(s_fx[3][ty][tx + 1] - s_fx[3][ty][tx]) * idx
+                          - ((s_fy[1][ty + 1][tx] - s_fy[1][ty][tx]) + (s_fy[2][ty + 1][tx] + s_fy[2][ty][tx])
+                             + g * hby * sey) * idy;
+            const TS rw = -(s_fx[4][ty][tx + 1] - s_fx[4][ty][tx]) * idx - (s_fy[4][ty + 1][tx] - s_fy[4][ty][tx]) * idy;
             const size_t c = mo + (size_t)j * G.nx + i;
+            const TS dt = TS(a.dt);
             if (a.stage == 1) {
                 a.k1h[c] = rh; a.k1u[c] = ru; a.k1v[c] = rv; a.k1w[c] = rw;
-                a.oh[c] = a.h0[c] + a.dt * rh;
-                a.ohu[c] = a.hu0[c] + a.dt * ru;
-                a.ohv[c] = a.hv0[c] + a.dt * rv;
-                a.ohw[c] = a.hw0[c] + a.dt * rw;
+                a.oh[c] = a.h0[c] + dt * rh;
+                a.ohu[c] = a.hu0[c] + dt * ru;
+                a.ohv[c] = a.hv0[c] + dt * rv;
+                a.ohw[c] = a.hw0[c] + dt * rw;
             } else {
-                a.oh[c] = a.h0[c] + 0.5 * a.dt * (a.k1h[c] + rh);
-                a.ohu[c] = a.hu0[c] + 0.5 * a.dt * (a.k1u[c] + ru);
-                a.ohv[c] = a.hv0[c] + 0.5 * a.dt * (a.k1v[c] + rv);
-                a.ohw[c] = a.hw0[c] + 0.5 * a.dt * (a.k1w[c] + rw);
+                const TS hdt = TS(0.5 * a.dt);
+                a.oh[c] = a.h0[c] + hdt * (a.k1h[c] + rh);
+                a.ohu[c] = a.hu0[c] + hdt * (a.k1u[c] + ru);
+                a.ohv[c] = a.hv0[c] + hdt * (a.k1v[c] + rv);
+                a.ohw[c] = a.hw0[c] + hdt * (a.k1w[c] + rw);
             }
         }
         __syncthreads();
@@ -320,55 +352,62 @@ static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs a)
 }
 
 // Criterion (Sec. 5.1, 2D form: |eta/d|, |grad eta|, |u|, |grad u|
-// (Frobenius), |w|, |grad w|; central differences), strict > k_nh.
-static __global__ void k2_marks(const Geo2* __restrict__ geos, size_t pitch, const double* __restrict__ h,
-                                const double* __restrict__ hu, const double* __restrict__ hv,
-                                const double* __restrict__ hw, const double* __restrict__ d, int crit, double knh,
-                                unsigned char* marks)
+// (Frobenius), |w|, |grad w|; central differences), strict > k_nh, in the
+// storage precision; only the selected criterion's quantities are formed.
+template <typename TS>
+static __global__ void k2_marks(const Geo2* __restrict__ geos, size_t pitch, const TS* __restrict__ hz,
+                                const TS* __restrict__ hu, const TS* __restrict__ hv,
+                                const TS* __restrict__ hw, const TS* __restrict__ dm, const TS* __restrict__ d0s,
+                                int crit, double knh, unsigned char* marks)
 {
     const int b = blockIdx.y;
     const Geo2 G = geos[b];
     const size_t mo = (size_t)b * pitch;
-    h += mo; hu += mo; hv += mo; hw += mo; d += mo; marks += mo;
+    hz += mo; hu += mo; hv += mo; hw += mo; dm += mo; marks += mo;
+    if (d0s) d0s += mo;
     const int N = G.nx * G.ny;
+    const TS two_dx = TS(2.0 * G.dx), two_dy = TS(2.0 * G.dy);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int i = c % G.nx, j = c / G.nx;
-        double val = 0.0;
+        TS val = TS(0);
+        TS h, eta, d;
         if (crit == NH_CRIT_ETA_D) {
-            const double dk = d[c];
-            val = fabs((h[c] - dk) / dk);
+            cell_hed<TS>(hz, dm, d0s, c, h, eta, d);
+            val = fabs(eta / d);
         } else if (crit == NH_CRIT_U) {
-            const double uk = hu[c] / h[c], vk = hv[c] / h[c];
+            cell_hed<TS>(hz, dm, d0s, c, h, eta, d);
+            const TS uk = hu[c] / h, vk = hv[c] / h;
             val = sqrt(uk * uk + vk * vk);
         } else if (crit == NH_CRIT_W) {
-            val = fabs(hw[c] / h[c]);
+            cell_hed<TS>(hz, dm, d0s, c, h, eta, d);
+            val = fabs(hw[c] / h);
         } else {   // the gradient criteria: central differences over the four neighbours
             double o[4][2];
             const int nb[4] = {g2_cell(G, i - 1, j, &o[0][0], &o[0][1]), g2_cell(G, i + 1, j, &o[1][0], &o[1][1]),
                                g2_cell(G, i, j - 1, &o[2][0], &o[2][1]), g2_cell(G, i, j + 1, &o[3][0], &o[3][1])};
+            TS hq[4], eq[4];
+            for (int q = 0; q < 4; ++q) cell_hed<TS>(hz, dm, d0s, nb[q], hq[q], eq[q], d);
             if (crit == NH_CRIT_ETA_X) {
-                double eta[4];
-                for (int q = 0; q < 4; ++q) eta[q] = h[nb[q]] - d[nb[q]];
-                const double ex = (eta[1] - eta[0]) / (2.0 * G.dx), ey = (eta[3] - eta[2]) / (2.0 * G.dy);
+                const TS ex = (eq[1] - eq[0]) / two_dx, ey = (eq[3] - eq[2]) / two_dy;
                 val = sqrt(ex * ex + ey * ey);
             } else if (crit == NH_CRIT_U_X) {
-                double u[4], v[4];
+                TS u[4], v[4];
                 for (int q = 0; q < 4; ++q) {
                     const int m = nb[q];
-                    u[q] = o[q][0] * hu[m] / h[m];
-                    v[q] = o[q][1] * hv[m] / h[m];
+                    u[q] = TS(o[q][0]) * hu[m] / hq[q];
+                    v[q] = TS(o[q][1]) * hv[m] / hq[q];
                 }
-                const double ux = (u[1] - u[0]) / (2.0 * G.dx), uy = (u[3] - u[2]) / (2.0 * G.dy);
-                const double vx = (v[1] - v[0]) / (2.0 * G.dx), vy = (v[3] - v[2]) / (2.0 * G.dy);
+                const TS ux = (u[1] - u[0]) / two_dx, uy = (u[3] - u[2]) / two_dy;
+                const TS vx = (v[1] - v[0]) / two_dx, vy = (v[3] - v[2]) / two_dy;
                 val = sqrt(ux * ux + uy * uy + vx * vx + vy * vy);
             } else if (crit == NH_CRIT_W_X) {
-                double w[4];
-                for (int q = 0; q < 4; ++q) w[q] = hw[nb[q]] / h[nb[q]];
-                const double wx = (w[1] - w[0]) / (2.0 * G.dx), wy = (w[3] - w[2]) / (2.0 * G.dy);
+                TS w[4];
+                for (int q = 0; q < 4; ++q) w[q] = hw[nb[q]] / hq[q];
+                const TS wx = (w[1] - w[0]) / two_dx, wy = (w[3] - w[2]) / two_dy;
                 val = sqrt(wx * wx + wy * wy);
             }
         }
-        marks[c] = val > knh ? 1 : 0;
+        marks[c] = val > TS(knh) ? 1 : 0;
     }
 }
 
@@ -519,13 +558,14 @@ struct CellQ2 {
     double h, Kxx, Kyy, Kxy, bx, by, Vx, Vy, U0, V0, phi, d_x, d_y, d_t, G, D;
 };
 
+template <typename TS>
 struct Asm2Args {
     const Geo2* geos; const Slide2* slides;
     const Kin2* kin;                       // kin[2b + 1]: bottom motion at t^{n+1}
     int nb, pitch, maxch;
-    const double *ht, *hut, *hvt, *hwt;    // Q~
+    const TS *ht, *hut, *hvt, *hwt;        // Q~ (h or zeta first)
     const double* d0;
-    const double* d1;                      // depth at t^{n+1}
+    const TS* d1;                          // depth (FP64) or mound (FP32) at t^{n+1}
     double dt;
     const int* list; const int* inv;
     MState* ms;
@@ -538,26 +578,40 @@ struct Asm2Args {
     const int2* items; const Ctl* ctl;
 };
 
-// One member's fields as seen by the assembly (pointers at the member's slice).
+// One member's fields as seen by the assembly (pointers at the member's
+// slice); h and eta in FP64 from either storage.
+template <typename TS>
 struct Mem2 {
     Geo2 G; Slide2 S; Kin2 K;
-    const double *ht, *hut, *hvt, *d0, *d1;
+    const TS *ht, *hut, *hvt, *d1;
+    const double* d0;
     double dt;
+    __device__ __forceinline__ double h_at(int k) const
+    {
+        if constexpr (sizeof(TS) == 8) return ht[k];
+        else return (double)ht[k] + d0[k];
+    }
+    __device__ __forceinline__ double eta_at(int k) const
+    {
+        if constexpr (sizeof(TS) == 8) return ht[k] - d1[k];
+        else return (double)ht[k] + (double)d1[k];
+    }
 };
 
-__device__ __forceinline__ CellQ2 cell_q2(const Mem2& a, int i, int j)
+template <typename TS>
+__device__ __forceinline__ CellQ2 cell_q2(const Mem2<TS>& a, int i, int j)
 {
     const Geo2& G = a.G;
     double b[10], o1, o2;
     bottom2(G, a.d0, a.S, a.K, i, j, b);
     const int kw = g2_cell(G, i - 1, j, &o1, &o2), ke = g2_cell(G, i + 1, j, &o1, &o2);
     const int ks = g2_cell(G, i, j - 1, &o1, &o2), kn = g2_cell(G, i, j + 1, &o1, &o2);
-    const double eta_x = ((a.ht[ke] - a.d1[ke]) - (a.ht[kw] - a.d1[kw])) / (2.0 * G.dx);
-    const double eta_y = ((a.ht[kn] - a.d1[kn]) - (a.ht[ks] - a.d1[ks])) / (2.0 * G.dy);
+    const double eta_x = (a.eta_at(ke) - a.eta_at(kw)) / (2.0 * G.dx);
+    const double eta_y = (a.eta_at(kn) - a.eta_at(ks)) / (2.0 * G.dy);
     const int k = j * G.nx + i;
     CellQ2 q;
-    q.h = a.ht[k];
-    const double u = a.hut[k] / q.h, v = a.hvt[k] / q.h;
+    q.h = a.h_at(k);
+    const double u = (double)a.hut[k] / q.h, v = (double)a.hvt[k] / q.h;
     q.d_x = b[1]; q.d_y = b[2]; q.d_t = b[6];
     const double d_xx = b[3], d_yy = b[4], d_xy = b[5], d_xt = b[7], d_yt = b[8], d_tt = b[9];
     q.G = q.d_x * q.d_x + q.d_y * q.d_y;
@@ -569,15 +623,16 @@ __device__ __forceinline__ CellQ2 cell_q2(const Mem2& a, int i, int j)
     q.Kxy = -1.0 / q.h * q.d_x * q.d_y / q.D;
     q.bx = 6.0 * q.d_x / (q.h * q.h * q.D);
     q.by = 6.0 * q.d_y / (q.h * q.h * q.D);
-    q.U0 = a.hut[k] + q.phi * q.d_x;
-    q.V0 = a.hvt[k] + q.phi * q.d_y;
+    q.U0 = (double)a.hut[k] + q.phi * q.d_x;
+    q.V0 = (double)a.hvt[k] + q.phi * q.d_y;
     q.Vx = q.U0 / q.h;
     q.Vy = q.V0 / q.h;
     return q;
 }
 
 // The same seen from a neighbour: mirrored cells flip their odd components.
-__device__ __forceinline__ CellQ2 cell_q2_at(const Mem2& a, int i, int j)
+template <typename TS>
+__device__ __forceinline__ CellQ2 cell_q2_at(const Mem2<TS>& a, int i, int j)
 {
     double ox, oy;
     const int c = g2_cell(a.G, i, j, &ox, &oy);
@@ -590,7 +645,8 @@ __device__ __forceinline__ CellQ2 cell_q2_at(const Mem2& a, int i, int j)
 
 // Rows of the 9-point operator on the active cells (work items of kChunk
 // list entries of one member) and each member's ||R||^2 and min gamma.
-static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args a)
+template <typename TS>
+static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args<TS> a)
 {
     __shared__ double red[64];
     const int n_items = a.ctl->n_items;
@@ -599,7 +655,7 @@ static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args a)
         const int b = itm.x, jj = itm.y;
         const int n = a.ms[b].n_active, nch = a.ms[b].nchunks, ioff = a.ms[b].ioff;
         const size_t mo = (size_t)b * a.pitch;
-        Mem2 m;
+        Mem2<TS> m;
         m.G = a.geos[b]; m.S = a.slides[b]; m.K = a.kin[2 * b + 1];
         m.ht = a.ht + mo; m.hut = a.hut + mo; m.hvt = a.hvt + mo; m.d0 = a.d0 + mo; m.d1 = a.d1 + mo;
         m.dt = a.dt;
@@ -621,7 +677,7 @@ static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args a)
             const double div_V = (E.Vx - W.Vx) / (2.0 * G.dx) + (N.Vy - S.Vy) / (2.0 * G.dy);
             const double h = q.h, h2 = h * h;
             const double gam = div_beta + 12.0 * (1.0 + q.G) / (h2 * h * q.D);
-            const double Rk = -(div_V + 2.0 * (q.d_x * q.U0 + q.d_y * q.V0) / h2 + 2.0 * a.hwt[mo + c] / h2
+            const double Rk = -(div_V + 2.0 * (q.d_x * q.U0 + q.d_y * q.V0) / h2 + 2.0 * (double)a.hwt[mo + c] / h2
                                 + 2.0 * q.phi / h2 + 2.0 * q.d_t / h);
             const double cW = -Kw * idx2, cE = -Ke * idx2, cS = -Ks * idy2, cN = -Kn * idy2;
             const double cNE = -(E.Kxy + N.Kxy) * ixy, cSW = -(W.Kxy + S.Kxy) * ixy;
@@ -673,6 +729,7 @@ static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args a)
     }
 }
 
+template <typename TS>
 struct Corr2Args {
     const Geo2* geos;
     int pitch;
@@ -681,7 +738,7 @@ struct Corr2Args {
     const double* x;             // psi on the active cells
     const double *c6, *cx, *cy, *phi, *ddx, *ddy;
     const MState* ms;
-    double *hu, *hv, *hw;        // Q~, corrected in place
+    TS *hu, *hv, *hw;            // Q~, corrected in place (FP64 arithmetic)
     double* psi;                 // dense psi (warm start, pressure output)
     const int2* items; const Ctl* ctl;
     const TimeCtl* tc;           // captured runs: skip unless the step was accepted
@@ -689,7 +746,8 @@ struct Corr2Args {
 
 // Eqs. 10-11 in 2D: with psi = a q, P = c6 psi + cx psi_x + cy psi_y + a phi;
 // U = U~ - grad psi + grad d P, hw = hw~ + P; psi = 0 off the mask.
-static __global__ void __launch_bounds__(kChunk) k2_correct(Corr2Args a)
+template <typename TS>
+static __global__ void __launch_bounds__(kChunk) k2_correct(Corr2Args<TS> a)
 {
     if (a.tc && a.tc->abort) return;
     const int n_items = a.ctl->n_items;
@@ -710,25 +768,64 @@ static __global__ void __launch_bounds__(kChunk) k2_correct(Corr2Args a)
         const double px = (pe - pw) / (2.0 * dx), py = (pn - pss) / (2.0 * dy);
         const double P = a.c6[o] * ps + a.cx[o] * px + a.cy[o] * py + a.phi[o];
         const size_t c = mo + a.list[o];
-        a.hu[c] = a.hu[c] + (-px + a.ddx[o] * P);
-        a.hv[c] = a.hv[c] + (-py + a.ddy[o] * P);
-        a.hw[c] = a.hw[c] + P;
+        a.hu[c] = TS((double)a.hu[c] + (-px + a.ddx[o] * P));
+        a.hv[c] = TS((double)a.hv[c] + (-py + a.ddy[o] * P));
+        a.hw[c] = TS((double)a.hw[c] + P);
         a.psi[c] = ps;
     }
 }
 
-// Block partial sums of h dx dy (FP64): part[b * gridDim.x + blockIdx.x].
+// Block partial sums of h dx dy (FP64; h = zeta + d0 for FP32 storage):
+// part[b * gridDim.x + blockIdx.x].
+template <typename TS>
 static __global__ void __launch_bounds__(256) k2_mass(const Geo2* __restrict__ geos, size_t pitch,
-                                                     const double* __restrict__ h, double* part)
+                                                     const TS* __restrict__ hz, const double* __restrict__ d0,
+                                                     double* part)
 {
     __shared__ double red[32];
     const int b = blockIdx.y;
     const int N = geos[b].nx * geos[b].ny;
-    h += (size_t)b * pitch;
+    hz += (size_t)b * pitch;
+    d0 += (size_t)b * pitch;
     double v[1] = {0.0};
-    for (int c = blockIdx.x * 256 + threadIdx.x; c < N; c += gridDim.x * 256) v[0] += h[c];
+    for (int c = blockIdx.x * 256 + threadIdx.x; c < N; c += gridDim.x * 256) {
+        if constexpr (sizeof(TS) == 8) v[0] += hz[c];
+        else v[0] += (double)hz[c] + d0[c];
+    }
     block_sum<1>(v, red);
     if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = v[0] * geos[b].dx * geos[b].dy;
+}
+
+// One member's state between FP64 (h, hu, hv, hw) and FP32 storage
+// (zeta = h - d0, hu, hv, hw); n cells.
+static __global__ void k2_store_f32(int n, const double* __restrict__ d0, const double* __restrict__ h,
+                                    const double* __restrict__ hu, const double* __restrict__ hv,
+                                    const double* __restrict__ hw, float* z, float* u, float* v, float* w)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        z[c] = (float)(h[c] - d0[c]);
+        u[c] = (float)hu[c];
+        v[c] = (float)hv[c];
+        w[c] = (float)hw[c];
+    }
+}
+
+static __global__ void k2_load_f32(int n, const double* __restrict__ d0, const float* __restrict__ z,
+                                   const float* __restrict__ u, const float* __restrict__ v,
+                                   const float* __restrict__ w, double* h, double* hu, double* hv, double* hw)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        h[c] = (double)z[c] + d0[c];
+        hu[c] = (double)u[c];
+        hv[c] = (double)v[c];
+        hw[c] = (double)w[c];
+    }
+}
+
+static __global__ void k2_to_f32(size_t n, const double* __restrict__ src, float* dst)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+        dst[c] = (float)src[c];
 }
 
 }  // namespace nh

@@ -42,7 +42,7 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh2d_set_solver", "nh2d_set_state", "nh2d_get_state", "nh2d_get_mask", "nh2d_step",
            "nh2d_run", "nh2d_destroy", "nh2d_ensemble_workspace_bytes", "nh2d_create_ensemble", "nh2d_members",
            "nh2d_set_member_bottom_motion", "nh2d_set_graphs", "nh2d_set_member_state", "nh2d_get_member_state",
-           "nh2d_get_member_mask", "nh2d_get_member_info", "nh2d_graph_runs")
+           "nh2d_get_member_mask", "nh2d_get_member_info", "nh2d_graph_runs", "nh2d_set_precision")
 NH_CNN_PARAMS = 9328
 NH_CNN_IN = 16
 NH_STATIC_MAX_CELLS = 262144
@@ -183,13 +183,14 @@ def load():
         L.nh2d_get_member_state.argtypes = [vp, C.c_int, _D, _D, _D, _D, _D]
         L.nh2d_get_member_mask.argtypes = [vp, C.c_int, C.POINTER(C.c_ubyte)]
         L.nh2d_get_member_info.argtypes = [vp, C.c_int, C.POINTER(nh_step_info)]
+        L.nh2d_set_precision.argtypes = [vp, C.c_int]
         L.nh2d_graph_runs.argtypes = [vp]
         L.nh2d_graph_runs.restype = C.c_longlong
         for f in ("nh2d_create", "nh2d_set_bottom_motion", "nh2d_set_criterion", "nh2d_set_solver",
                   "nh2d_set_state", "nh2d_get_state", "nh2d_get_mask", "nh2d_step", "nh2d_run",
                   "nh2d_create_ensemble", "nh2d_set_member_bottom_motion", "nh2d_set_graphs",
                   "nh2d_set_member_state", "nh2d_get_member_state", "nh2d_get_member_mask",
-                  "nh2d_get_member_info"):
+                  "nh2d_get_member_info", "nh2d_set_precision"):
             getattr(L, f).restype = C.c_int
         L.nh_status_string.argtypes = [C.c_int]
         L.nh_status_string.restype = C.c_char_p
@@ -589,6 +590,10 @@ class Grid2D:
 
     def set_graphs(self, on):
         _check(self.L.nh2d_set_graphs(self.h, int(bool(on))), "nh2d_set_graphs")
+
+    def set_precision(self, precision):
+        """NH_FP64 or NH_MIXED_FP64_SOLVE (FP32 state); clears every member's state."""
+        _check(self.L.nh2d_set_precision(self.h, int(precision)), "nh2d_set_precision")
 
     def set_state(self, h, hu, hv, hw, t=0.0, member=0):
         a = [self._f(v, member) for v in (h, hu, hv, hw)]
