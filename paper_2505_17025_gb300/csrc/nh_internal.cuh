@@ -132,6 +132,13 @@ __device__ __forceinline__ double texp(double v) { return exp(v); }
 __device__ __forceinline__ float texp(float v) { return expf(v); }
 __device__ __forceinline__ double tsqrt(double v) { return sqrt(v); }
 __device__ __forceinline__ float tsqrt(float v) { return sqrtf(v); }
+// Gravity-wave speed sqrt(g h) for the Rusanov dissipation coefficient
+// s = max(|u| + sqrt(g h)) over a face: s only scales the numerical
+// diffusion (the flux stays consistent and conservative for any s), so it is
+// taken in FP32 (relative error 6e-8) even on the FP64 path, sparing two
+// FP64 square roots per face on GB300's narrow FP64 pipe.
+__device__ __forceinline__ double wave_sqrt(double v) { return (double)sqrtf((float)v); }
+__device__ __forceinline__ float wave_sqrt(float v) { return sqrtf(v); }
 
 
 // Height of the moving mound at the centre of cell c (already resolved) at

@@ -103,7 +103,7 @@ __device__ __forceinline__ void rusanov(T g, T df, T eL, T uL, T wL, T eR, T uR,
 {
     const T hL = eL + df, hR = eR + df;
     const T qL = hL * uL, qR = hR * uR;
-    const T aL = tabs(uL) + tsqrt(g * hL), aR = tabs(uR) + tsqrt(g * hR);
+    const T aL = tabs(uL) + wave_sqrt(g * hL), aR = tabs(uR) + wave_sqrt(g * hR);
     const T s = aL > aR ? aL : aR;
     const T de = eR - eL;
     F0 = T(0.5) * (qL + qR) - T(0.5) * s * de;

@@ -251,7 +251,7 @@ __device__ __forceinline__ void face_flux(T g, int lim, const T* e, const T* un,
     const T wL = w[-s] + h2 * swL, wR = w[0] - h2 * swR;
     const T hL = eL + df, hR = eR + df;
     const T qL = hL * uL, qR = hR * uR;
-    const T aL = fabs(uL) + sqrt(g * hL), aR = fabs(uR) + sqrt(g * hR);
+    const T aL = fabs(uL) + wave_sqrt(g * hL), aR = fabs(uR) + wave_sqrt(g * hR);
     const T sp = aL > aR ? aL : aR;
     const T de = eR - eL;
     F[0] = h2 * (qL + qR) - h2 * sp * de;
