@@ -285,7 +285,7 @@ Geo geo(const nh_grid* g)
     Geo G;
     G.nx = g->nx; G.nb = g->nb; G.pitch = g->pitch; G.wpitch = g->wpitch; G.bc = g->d.bc;
     G.lim = g->d.limiter; G.ntiles = g->pitch / g->tile; G.maxch = g->maxch;
-    G.dx = g->d.dx; G.x0 = g->d.x0; G.g = g->d.g;
+    G.dx = g->d.dx; G.x0 = g->d.x0; G.g = g->d.g; G.idx = 1.0 / g->d.dx;
     G.nxv = g->uneven ? g->nxd : nullptr;
     return G;
 }

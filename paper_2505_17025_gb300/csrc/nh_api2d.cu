@@ -171,6 +171,7 @@ Geo2 geo2(const nh_grid2d_desc& d)
     Geo2 G;
     G.nx = d.nx; G.ny = d.ny; G.bcx = d.bc_x; G.bcy = d.bc_y; G.lim = d.limiter;
     G.dx = d.dx; G.dy = d.dy; G.x0 = d.x0; G.y0 = d.y0; G.g = d.g;
+    G.idx = 1.0 / d.dx; G.idy = 1.0 / d.dy;
     return G;
 }
 

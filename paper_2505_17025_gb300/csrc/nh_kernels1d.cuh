@@ -20,6 +20,7 @@ namespace nh {
 struct Geo {
     int nx, nb, pitch, wpitch, bc, lim, ntiles, maxch;
     double dx, x0, g;
+    double idx;          // 1 / dx
     const int* nxv;      // per-member cell counts (uneven ensembles), or null: all nx
 };
 
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
     T* const k1u = sm + 17 * NL;
     T* const k1w = sm + 18 * NL;
     T* const sdf = sm + 19 * NL;    // depth at face l of the current stage
-    __shared__ double red[32];
+    __shared__ double red_mass[TILE];
 
     const Geo& G = a.G;
     const int b = blockIdx.y, i0 = blockIdx.x * TILE, tid = threadIdx.x;
@@ -175,8 +176,6 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
     const T* __restrict__ D0 = a.d0 + mo;
     const Slide sl = a.slide[b];
     const Kin kn = a.kin[b];
-    const T g = T(G.g), dx = T(G.dx), dt = T(a.dt), half_dt = T(0.5) * T(a.dt);
-    const T idx = T(1.0 / G.dx);
     const int nxb = member_nx(G, b);
     if (i0 >= nxb) {   // tile beyond this member's cells (uneven ensemble)
         if (tid == 0) a.mass_part[(size_t)b * G.ntiles + blockIdx.x] = 0.0;
@@ -189,7 +188,9 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
     // s_mhi] (the cut-off of mound_at with a margin, one cell either side);
     // elsewhere the per-cell evaluation is skipped (it would return 0).
     __shared__ int s_mlo, s_mhi;
+    __shared__ T s_k[5];   // g, dt, dt/2, 1/dx, k_nh in T, converted once per CTA
     if (tid == 0) {
+        s_k[0] = T(G.g); s_k[1] = T(a.dt); s_k[2] = T(0.5) * T(a.dt); s_k[3] = T(G.idx); s_k[4] = T(a.knh);
         int lo = 1, hi = 0;
         if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
             const double r = sqrt(kMoundCut * 1.0001) * sl.L;
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
         s_mlo = lo; s_mhi = hi;
     }
     __syncthreads();
+    const T g = s_k[0], dt = s_k[1], half_dt = s_k[2], idx = s_k[3];
     for (int l = tid; l < NL; l += TILE) {
         const int j = i0 - H + l;
         T zv = T(0), huv = T(0), hwv = T(0), d0v = T(1), mn = T(0), mn1 = T(0);
@@ -314,14 +316,21 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
                 case NH_CRIT_W:     c = tabs(shw[l] / hc); break;
                 default:            c = tabs((shw[l + 1] / hp - shw[l - 1] / hm) * inv2dx); break;
                 }
-                mark = (double)c > a.knh;
+                mark = c > s_k[4];   // strict, in the state precision
             }
         }
         const uint32_t word = __ballot_sync(0xffffffffu, mark);
         if ((tid & 31) == 0) a.marks[(size_t)b * G.wpitch + (j >> 5)] = word;
-        double v[1] = {mass};
-        block_sum<1>(v, red);
-        if (tid == 0) a.mass_part[(size_t)b * G.ntiles + blockIdx.x] = v[0];
+        // the tile's FP64 mass: one warp adds the cells' values in a fixed
+        // order (fewer FP64 operations than a shuffle tree over every lane)
+        red_mass[tid] = mass;
+        __syncthreads();
+        if (tid < 32) {
+            double t = 0.0;
+            for (int q = tid; q < TILE; q += 32) t += red_mass[q];
+            t = warp_sum(t);
+            if (tid == 0) a.mass_part[(size_t)b * G.ntiles + blockIdx.x] = t;
+        }
     }
 }
 

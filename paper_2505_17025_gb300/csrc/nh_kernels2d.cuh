@@ -38,7 +38,12 @@ namespace nh {
 struct Geo2 {
     int nx, ny, bcx, bcy, lim;
     double dx, dy, x0, y0, g;
+    double idx, idy;   // 1 / dx, 1 / dy
 };
+
+// v with the sign of the parity o (+1 or -1): no floating-point multiply.
+template <typename T>
+__device__ __forceinline__ T flip(int o, T v) { return o < 0 ? -v : v; }
 
 // 2D slide: mound A exp(-xi^2 - zeta^2), xi = (x - xc0 - s)/Lx, zeta = (y - yc0)/Ly.
 // Its position s(t) = s0 ln cosh(t / t0) (Sec. 4.2).
@@ -78,18 +83,18 @@ static __global__ void k2_kin(const Slide2* __restrict__ slides, int nb, double 
     }
 }
 
-__device__ __forceinline__ int g2_index1(int bc, int n, int i, double* odd)
+__device__ __forceinline__ int g2_index1(int bc, int n, int i, int* odd)
 {
-    *odd = 1.0;
+    *odd = 1;
     if (i >= 0 && i < n) return i;
     if (bc == NH_BC_PERIODIC) return ((i % n) + n) % n;
-    *odd = -1.0;
+    *odd = -1;
     return (i < 0) ? (-1 - i) : (2 * n - 1 - i);
 }
 
 // Flat index of the in-domain (mirrored / wrapped) cell of (i, j) and the
 // parities of quantities odd in x and in y.
-__device__ __forceinline__ int g2_cell(const Geo2& G, int i, int j, double* ox, double* oy)
+__device__ __forceinline__ int g2_cell(const Geo2& G, int i, int j, int* ox, int* oy)
 {
     const int ci = g2_index1(G.bcx, G.nx, i, ox);
     const int cj = g2_index1(G.bcy, G.ny, j, oy);
@@ -128,7 +133,7 @@ __device__ __forceinline__ double mound2(const Geo2& G, const Slide2& S, int i, 
 __device__ __forceinline__ void bottom2(const Geo2& G, const double* __restrict__ d0, const Slide2& S,
                                         const Kin2& K, int i, int j, double out[10])
 {
-    double o1, o2;
+    int o1, o2;
     const double dx = G.dx, dy = G.dy;
     const double c = d0[j * G.nx + i];
     const double xm = d0[g2_cell(G, i - 1, j, &o1, &o2)], xp = d0[g2_cell(G, i + 1, j, &o1, &o2)];
@@ -161,7 +166,10 @@ __device__ __forceinline__ void bottom2(const Geo2& G, const double* __restrict_
 }
 
 // Depth (FP64 storage) or mound (FP32 storage) at t^n (which = 0) or
-// t^{n+1} (which = 1).
+// t^{n+1} (which = 1).  The FP32 mound measures the offset from the slide's
+// centre as an exact integer cell offset plus an FP32 fraction (computed once
+// per CTA in FP64), so xi and zeta keep FP32 relative precision however far
+// from the origin the slide is; same kMoundCut test as mound2.
 template <typename TS>
 static __global__ void k2_depth(const Geo2* __restrict__ geos, const Slide2* __restrict__ slides,
                                 const Kin2* __restrict__ kin, int which, size_t pitch,
@@ -174,10 +182,32 @@ static __global__ void k2_depth(const Geo2* __restrict__ geos, const Slide2* __r
     const double s = kin[2 * b + which].s;
     const size_t mo = (size_t)b * pitch;
     const int N = G.nx * G.ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const double m = mound2(G, S, c % G.nx, c / G.nx, s);
-        if constexpr (sizeof(TS) == 8) dm[mo + c] = d0[mo + c] - m;
-        else dm[mo + c] = TS(m);
+    if constexpr (sizeof(TS) == 8) {
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+            dm[mo + c] = d0[mo + c] - mound2(G, S, c % G.nx, c / G.nx, s);
+    } else {
+        __shared__ int s_ic[2];
+        __shared__ float s_f[5];   // fraction x, fraction y, dx / Lx, dy / Ly, A
+        if (threadIdx.x == 0) {
+            const double cx = (S.xc0 + s - G.x0) * G.idx - 0.5, cy = (S.yc0 - G.y0) * G.idy - 0.5;
+            const double fx = floor(cx), fy = floor(cy);
+            s_ic[0] = (int)fmax(fmin(fx, 1e9), -1e9); s_ic[1] = (int)fmax(fmin(fy, 1e9), -1e9);
+            s_f[0] = (float)(cx - fx); s_f[1] = (float)(cy - fy);
+            s_f[2] = (float)(G.dx * S.iLx); s_f[3] = (float)(G.dy * S.iLy); s_f[4] = (float)S.A;
+        }
+        __syncthreads();
+        const bool on = S.shape == NH_SLIDE_GAUSS_LNCOSH;
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+            float m = 0.0f;
+            if (on) {
+                const int i = c % G.nx, j = c / G.nx;
+                const float xi = ((float)(i - s_ic[0]) - s_f[0]) * s_f[2];
+                const float ze = ((float)(j - s_ic[1]) - s_f[1]) * s_f[3];
+                const float r2 = xi * xi + ze * ze;
+                if (r2 <= (float)kMoundCut) m = s_f[4] * expf(-r2);
+            }
+            dm[mo + c] = m;
+        }
     }
 }
 
@@ -274,7 +304,13 @@ static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs<TS> a)
     const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
     const TS* hz = a.h + mo; const TS* hu = a.hu + mo; const TS* hv = a.hv + mo;
     const TS* hw = a.hw + mo; const TS* dm = a.d + mo; const TS* d0s = a.d0s ? a.d0s + mo : nullptr;
-    const TS g = TS(G.g), idx = TS(1.0 / G.dx), idy = TS(1.0 / G.dy), h2 = TS(0.5);
+    // constants in the storage precision, converted once per CTA
+    __shared__ TS s_k[5];
+    if (tid == 0) {
+        s_k[0] = TS(G.g); s_k[1] = TS(G.idx); s_k[2] = TS(G.idy); s_k[3] = TS(a.dt); s_k[4] = TS(0.5 * a.dt);
+    }
+    __syncthreads();
+    const TS g = s_k[0], idx = s_k[1], idy = s_k[2], h2 = TS(0.5);
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int i0 = (tile % tiles_x) * kTX, j0 = (tile / tiles_x) * kTY;
         // 1. primitives of the tile and its cross-shaped halo
@@ -282,15 +318,15 @@ static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs<TS> a)
             const int lx = q % kHX, ly = q / kHX;
             const bool in_x = lx >= 2 && lx < kTX + 2, in_y = ly >= 2 && ly < kTY + 2;
             if (!in_x && !in_y) continue;   // corners: no stencil reaches them
-            double ox, oy;
+            int ox, oy;
             const int c = g2_cell(G, i0 + lx - 2, j0 + ly - 2, &ox, &oy);
             TS hc, ec, dc;
             cell_hed<TS>(hz, dm, d0s, c, hc, ec, dc);
             const TS rh = TS(1) / hc;
             s_e[ly][lx] = ec;
             s_d[ly][lx] = dc;
-            s_u[ly][lx] = TS(ox) * hu[c] * rh;
-            s_v[ly][lx] = TS(oy) * hv[c] * rh;
+            s_u[ly][lx] = flip(ox, hu[c] * rh);
+            s_v[ly][lx] = flip(oy, hv[c] * rh);
             s_w[ly][lx] = hw[c] * rh;
         }
         __syncthreads();
@@ -332,7 +368,7 @@ static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs<TS> a)
                              + g * hby * sey) * idy;
             const TS rw = -(s_fx[4][ty][tx + 1] - s_fx[4][ty][tx]) * idx - (s_fy[4][ty + 1][tx] - s_fy[4][ty][tx]) * idy;
             const size_t c = mo + (size_t)j * G.nx + i;
-            const TS dt = TS(a.dt);
+            const TS dt = s_k[3];
             if (a.stage == 1) {
                 a.k1h[c] = rh; a.k1u[c] = ru; a.k1v[c] = rv; a.k1w[c] = rw;
                 a.oh[c] = a.h0[c] + dt * rh;
@@ -340,7 +376,7 @@ static __global__ void __launch_bounds__(kTX * kTY) k2_stage(StageArgs<TS> a)
                 a.ohv[c] = a.hv0[c] + dt * rv;
                 a.ohw[c] = a.hw0[c] + dt * rw;
             } else {
-                const TS hdt = TS(0.5 * a.dt);
+                const TS hdt = s_k[4];
                 a.oh[c] = a.h0[c] + hdt * (a.k1h[c] + rh);
                 a.ohu[c] = a.hu0[c] + hdt * (a.k1u[c] + ru);
                 a.ohv[c] = a.hv0[c] + hdt * (a.k1v[c] + rv);
@@ -382,7 +418,7 @@ static __global__ void k2_marks(const Geo2* __restrict__ geos, size_t pitch, con
             cell_hed<TS>(hz, dm, d0s, c, h, eta, d);
             val = fabs(hw[c] / h);
         } else {   // the gradient criteria: central differences over the four neighbours
-            double o[4][2];
+            int o[4][2];
             const int nb[4] = {g2_cell(G, i - 1, j, &o[0][0], &o[0][1]), g2_cell(G, i + 1, j, &o[1][0], &o[1][1]),
                                g2_cell(G, i, j - 1, &o[2][0], &o[2][1]), g2_cell(G, i, j + 1, &o[3][0], &o[3][1])};
             TS hq[4], eq[4];
@@ -394,8 +430,8 @@ static __global__ void k2_marks(const Geo2* __restrict__ geos, size_t pitch, con
                 TS u[4], v[4];
                 for (int q = 0; q < 4; ++q) {
                     const int m = nb[q];
-                    u[q] = TS(o[q][0]) * hu[m] / hq[q];
-                    v[q] = TS(o[q][1]) * hv[m] / hq[q];
+                    u[q] = flip(o[q][0], hu[m]) / hq[q];
+                    v[q] = flip(o[q][1], hv[m]) / hq[q];
                 }
                 const TS ux = (u[1] - u[0]) / two_dx, uy = (u[3] - u[2]) / two_dy;
                 const TS vx = (v[1] - v[0]) / two_dx, vy = (v[3] - v[2]) / two_dy;
@@ -602,7 +638,8 @@ template <typename TS>
 __device__ __forceinline__ CellQ2 cell_q2(const Mem2<TS>& a, int i, int j)
 {
     const Geo2& G = a.G;
-    double b[10], o1, o2;
+    double b[10];
+    int o1, o2;
     bottom2(G, a.d0, a.S, a.K, i, j, b);
     const int kw = g2_cell(G, i - 1, j, &o1, &o2), ke = g2_cell(G, i + 1, j, &o1, &o2);
     const int ks = g2_cell(G, i, j - 1, &o1, &o2), kn = g2_cell(G, i, j + 1, &o1, &o2);
@@ -634,12 +671,12 @@ __device__ __forceinline__ CellQ2 cell_q2(const Mem2<TS>& a, int i, int j)
 template <typename TS>
 __device__ __forceinline__ CellQ2 cell_q2_at(const Mem2<TS>& a, int i, int j)
 {
-    double ox, oy;
+    int ox, oy;
     const int c = g2_cell(a.G, i, j, &ox, &oy);
     CellQ2 q = cell_q2(a, c % a.G.nx, c / a.G.nx);
-    q.Kxy *= ox * oy;
-    q.bx *= ox; q.by *= oy;
-    q.Vx *= ox; q.Vy *= oy;
+    q.Kxy = flip(ox * oy, q.Kxy);
+    q.bx = flip(ox, q.bx); q.by = flip(oy, q.by);
+    q.Vx = flip(ox, q.Vx); q.Vy = flip(oy, q.Vy);
     return q;
 }
 
