@@ -48,6 +48,7 @@ constexpr double kMoundCut = 40.0;
 // Per-member slide parameters (device copy of nh_slide_desc, FP64).
 struct Slide {
     double A, L, xc0, s0, t0;
+    double iL;    // 1 / L (set on the host with L)
     int shape;
     int pad;
 };
@@ -149,7 +150,7 @@ __device__ __forceinline__ T mound_at(int c, double x0, double dx, const Slide& 
 {
     if (sl.shape != NH_SLIDE_GAUSS_LNCOSH) return T(0);
     const double xc = x0 + (c + 0.5) * dx;
-    const T xi = T((xc - sl.xc0 - s) * (1.0 / sl.L));
+    const T xi = T((xc - sl.xc0 - s) * sl.iL);
     if (xi * xi > T(kMoundCut)) return T(0);
     return T(sl.A) * texp(-xi * xi);
 }
@@ -185,7 +186,7 @@ __device__ __forceinline__ Bottom<T> bottom_full(const T* __restrict__ d0m, int 
     if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
         const T L = T(sl.L);
         double xc = x0 + (i + 0.5) * dx;
-        T xi = T((xc - sl.xc0 - k.s_n1) * (1.0 / sl.L));   // as in mound_at: B.m == mound_at
+        T xi = T((xc - sl.xc0 - k.s_n1) * sl.iL);   // as in mound_at: B.m == mound_at
         T m = xi * xi > T(kMoundCut) ? T(0) : T(sl.A) * texp(-xi * xi);
         T sd = T(k.sd_n1), sdd = T(k.sdd_n1);
         T two_xi2m1 = T(2) * xi * xi - T(1);
