@@ -64,11 +64,14 @@ BYTES_PER_UNIT_MIXED = {
 # FLOP/s against the FP64 peak.  FP64 FLOPs per cell and launch, from ncu's
 # executed-instruction counters (dadd + dmul + 2 dfma) on the 64 x 50000
 # batch ("profiles/k_predict_fp64_slide64x50k.md"); they include the two
-# stages' square roots and reciprocals and the tile halo.
-FLOPS_PER_CELL_FP64_PREDICT = 313.7
+# stages' reciprocals and the tile halo.
+FLOPS_PER_CELL_FP64_PREDICT = 234.0
+# FP64 instructions per cell (dadd + dmul + dfma), same counters: the
+# issue-rate fraction (the pipe issues 2 FP64 instructions per clock per SM).
+INSTS_PER_CELL_FP64_PREDICT = 169.5
 # DRAM bytes per launch of that kernel from the same capture (null once the
 # kernel changes).
-TRAFFIC_FP64_PREDICT = 142112.5e3
+TRAFFIC_FP64_PREDICT = 138246.7e3
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x
 # 2 FLOP x 2.07 GHz (the nominal 1.25 TFLOP/s).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
@@ -380,10 +383,13 @@ def run_2d(args):
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
     clocks.start()
+    # profiler range = the timed steps (ncu --profile-from-start off)
+    torch.cuda.profiler.start()
     e0.record(G.stream)
     st, info = G.run(dt, args.steps)
     e1.record(G.stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     graph_runs = G.graph_runs
@@ -500,6 +506,8 @@ def run_ours(args):
                     "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 pipe)",
                     "flops_per_launch": flops, "bytes_per_launch": bytes_per_launch,
                     "hbm_frac": bytes_per_launch / t_launch / 1e9 / peaks["hbm_gbs"],
+                    "fp64_issue_frac": INSTS_PER_CELL_FP64_PREDICT * cells / t_launch
+                    / (FP64_PEAK_GFLOPS / 2 * 1e9),
                     "launches_per_step": dn / args.steps, "avg_launch_us": 1e6 * t_launch}
         else:
             achieved = bytes_per_launch / t_launch / 1e9
