@@ -286,6 +286,7 @@ Geo geo(const nh_grid* g)
     G.nx = g->nx; G.nb = g->nb; G.pitch = g->pitch; G.wpitch = g->wpitch; G.bc = g->d.bc;
     G.lim = g->d.limiter; G.ntiles = g->pitch / g->tile; G.maxch = g->maxch;
     G.dx = g->d.dx; G.x0 = g->d.x0; G.g = g->d.g; G.idx = 1.0 / g->d.dx;
+    G.i2dx = 1.0 / (2.0 * g->d.dx); G.idx2 = 1.0 / (g->d.dx * g->d.dx);
     G.nxv = g->uneven ? g->nxd : nullptr;
     return G;
 }

@@ -182,6 +182,7 @@ __device__ __forceinline__ Bottom<T> bottom_full(const T* __restrict__ d0m, int 
     B.d = c;
     B.d_x = (e - a) / (T(2) * dxT);
     B.d_xx = (e - T(2) * c + a) / (dxT * dxT);
+    const T iL = T(sl.iL), iL2 = iL * iL;
     B.d_t = T(0); B.d_xt = T(0); B.d_tt = T(0); B.m = T(0);
     if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
         const T L = T(sl.L);
@@ -190,11 +191,11 @@ __device__ __forceinline__ Bottom<T> bottom_full(const T* __restrict__ d0m, int 
         T m = xi * xi > T(kMoundCut) ? T(0) : T(sl.A) * texp(-xi * xi);
         T sd = T(k.sd_n1), sdd = T(k.sdd_n1);
         T two_xi2m1 = T(2) * xi * xi - T(1);
-        T m_x = m * (T(-2) * xi / L);
-        T m_xx = m * (T(4) * xi * xi - T(2)) / (L * L);
-        T m_t = m * (T(2) * xi / L) * sd;
-        T m_xt = -m * (T(2) / (L * L)) * two_xi2m1 * sd;
-        T m_tt = m * (T(2) / (L * L)) * (two_xi2m1 * sd * sd + xi * L * sdd);
+        T m_x = m * (T(-2) * xi * iL);
+        T m_xx = m * (T(4) * xi * xi - T(2)) * iL2;
+        T m_t = m * (T(2) * xi * iL) * sd;
+        T m_xt = -m * (T(2) * iL2) * two_xi2m1 * sd;
+        T m_tt = m * (T(2) * iL2) * (two_xi2m1 * sd * sd + xi * L * sdd);
         B.d -= m; B.d_x -= m_x; B.d_xx -= m_xx; B.m = m;
         B.d_t = -m_t; B.d_xt = -m_xt; B.d_tt = -m_tt;
     }

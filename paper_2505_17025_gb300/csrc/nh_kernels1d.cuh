@@ -21,6 +21,7 @@ struct Geo {
     int nx, nb, pitch, wpitch, bc, lim, ntiles, maxch;
     double dx, x0, g;
     double idx;          // 1 / dx
+    double i2dx, idx2;   // 1 / (2 dx), 1 / dx^2
     const int* nxv;      // per-member cell counts (uneven ensembles), or null: all nx
 };
 
@@ -559,6 +560,7 @@ struct AsmArgs {
 
 struct CellQ {
     double h, K, beta, U0, V, phi, d_x, D, d_t;
+    double rh, rD;   // 1 / h, 1 / D
 };
 
 // Per-cell quantities of the elliptic equation at an in-domain cell c, in FP64
@@ -570,18 +572,20 @@ __device__ __forceinline__ CellQ cell_q_from(const AsmArgs<TS>& a, const TS* __r
                                              int c, const Bottom<double>& B, double etam, double etap)
 {
     const Geo& G = a.G;
-    const double eta_x = (etap - etam) / (2.0 * G.dx);
+    const double eta_x = (etap - etam) * G.i2dx;
     CellQ q;
     q.h = (double)zt[c] + D0[c];
-    const double u = (double)hut[c] / q.h;
+    q.rh = 1.0 / q.h;   // the two reciprocals of the cell: every quotient below multiplies
+    const double u = (double)hut[c] * q.rh;
     q.d_x = B.d_x;
     q.d_t = B.d_t;
     q.D = 4.0 + B.d_x * B.d_x;
-    q.phi = a.dt * q.h / q.D * (G.g * B.d_x * eta_x - B.d_tt - 2.0 * u * B.d_xt - u * u * B.d_xx);
-    q.K = 4.0 / (q.h * q.D);
-    q.beta = 6.0 * B.d_x / (q.h * q.h * q.D);
+    q.rD = 1.0 / q.D;
+    q.phi = a.dt * q.h * q.rD * (G.g * B.d_x * eta_x - B.d_tt - 2.0 * u * B.d_xt - u * u * B.d_xx);
+    q.K = 4.0 * q.rh * q.rD;
+    q.beta = 6.0 * B.d_x * (q.rh * q.rh) * q.rD;
     q.U0 = (double)hut[c] + q.phi * B.d_x;
-    q.V = q.U0 / q.h;
+    q.V = q.U0 * q.rh;
     return q;
 }
 
@@ -665,14 +669,14 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
             else qm = cell_q(a, zt, hut, D0, cm, nxb, sl, kn);
             if (right_here) { qp.K = s_K[tid + 1]; qp.beta = s_beta[tid + 1]; qp.V = s_V[tid + 1]; }
             else qp = cell_q(a, zt, hut, D0, cp, nxb, sl, kn);
-            const double idx2 = 1.0 / (G.dx * G.dx);
+            const double idx2 = G.idx2;
             const double Kl = 0.5 * (qm.K + qi.K), Kr = 0.5 * (qi.K + qp.K);
             const double bm = sgm > 0 ? qm.beta : -qm.beta, bp = sgp > 0 ? qp.beta : -qp.beta;
             const double Vm = sgm > 0 ? qm.V : -qm.V, Vp = sgp > 0 ? qp.V : -qp.V;
-            const double h = qi.h, h2 = h * h;
-            const double gam = (bp - bm) / (2.0 * G.dx) + 12.0 * (1.0 + qi.d_x * qi.d_x) / (h2 * h * qi.D);
-            const double Rk = -((Vp - Vm) / (2.0 * G.dx) + 2.0 * qi.d_x * qi.U0 / h2 + 2.0 * (double)hwt[i] / h2
-                                + 2.0 * qi.phi / h2 + 2.0 * qi.d_t / h);
+            const double rh = qi.rh, rh2 = rh * rh;
+            const double gam = (bp - bm) * G.i2dx + 12.0 * (1.0 + qi.d_x * qi.d_x) * (rh2 * rh * qi.rD);
+            const double Rk = -((Vp - Vm) * G.i2dx + 2.0 * qi.d_x * qi.U0 * rh2 + 2.0 * (double)hwt[i] * rh2
+                                + 2.0 * qi.phi * rh2 + 2.0 * qi.d_t * rh);
             // neighbours inside the active set (zero Dirichlet data outside)
             bool hasl, hasr;
             int kl = -1, kr = -1;
@@ -701,8 +705,8 @@ __global__ void __launch_bounds__(kChunk) k_assemble(AsmArgs<TS> a)
             }
             a.nbl[mo + k] = kl;
             a.nbr[mo + k] = kr;
-            a.c6[mo + k] = TS(6.0 / (h * qi.D));
-            a.cx[mo + k] = TS(qi.d_x / qi.D);
+            a.c6[mo + k] = TS(6.0 * rh * qi.rD);
+            a.cx[mo + k] = TS(qi.d_x * qi.rD);
             a.phi[mo + k] = TS(qi.phi);
             a.ddx[mo + k] = TS(qi.d_x);
             r2 = Rk * Rk;

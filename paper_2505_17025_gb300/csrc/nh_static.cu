@@ -127,6 +127,7 @@ extern "C" nh_status nh_predict_static(const double* h, const double* hu, const 
     pa.G.nx = nx; pa.G.nb = 1; pa.G.pitch = ntiles * kPredTile; pa.G.wpitch = ntiles * kPredTile / 32;
     pa.G.bc = bc; pa.G.lim = limiter; pa.G.ntiles = ntiles; pa.G.maxch = 1;
     pa.G.dx = dx; pa.G.x0 = x0; pa.G.g = g; pa.G.idx = 1.0 / dx;
+    pa.G.i2dx = 1.0 / (2.0 * dx); pa.G.idx2 = 1.0 / (dx * dx);
     pa.z = z; pa.hu = hu; pa.hw = hw;
     pa.zt = h_out; pa.hut = hu_out; pa.hwt = hw_out;
     pa.d0 = d0; pa.slide = slide_dev; pa.kin = kin_dev;
