@@ -231,6 +231,14 @@ nh_status nh_set_tile(nh_grid* g, int tile, int* chosen);
    step-by-step path.  use_graphs == 0: always step by step. */
 nh_status nh_set_run_mode(nh_grid* g, int use_graphs);
 
+/* Spin limit of the persistent solver's grid-wide barrier, in SM clock
+   cycles (0: the default, about one second of the device clock).  A barrier
+   whose partners do not arrive within the limit makes every CTA of the solve
+   return; the step reports NH_ERR_TIMEOUT, is not taken (the state stays at
+   the last accepted step) and the handle stays usable.  Drops the captured
+   graphs.  Errors: NH_ERR_ARG (cycles < 0). */
+nh_status nh_set_wait_budget(nh_grid* g, long long cycles);
+
 /* Kernel classes timed by the profiler (index into nh_get_profile arrays). */
 enum { NH_K_KINEMATICS = 0, NH_K_PREDICT = 1, NH_K_COMPACT = 2, NH_K_ASSEMBLE = 3,
        NH_K_SOLVE_INIT = 4, NH_K_PRECOND = 5, NH_K_PCG_A = 6, NH_K_PCG_B = 7,

@@ -105,6 +105,11 @@ nh_status nh2d_set_precision(nh_grid2d* g, int precision);
    0: every step is enqueued from the host. */
 nh_status nh2d_set_graphs(nh_grid2d* g, int on);
 
+/* As nh_set_wait_budget: spin limit (SM clock cycles, 0 = about one second)
+   of the persistent solver's grid barrier; on expiry the step reports
+   NH_ERR_TIMEOUT and is not taken. */
+nh_status nh2d_set_wait_budget(nh_grid2d* g, long long cycles);
+
 /* h > 0 (m), hu, hv, hw (m^2/s) of member m; sets the whole ensemble's time
    to t and clears member m's warm start.  Steps need every member set. */
 nh_status nh2d_set_state(nh_grid2d* g, const double* h, const double* hu, const double* hv,

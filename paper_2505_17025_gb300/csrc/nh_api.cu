@@ -28,6 +28,7 @@ struct nh_grid {
     int tile;                    // predictor tile (cells per CTA), chosen by the autotuner
     bool tuned;
     long long barrier_budget;    // clock cycles a grid barrier may spin
+    long long barrier_budget_default;
     size_t es;                   // element size of the Krylov vectors
     bool mixed;                  // FP32 state and predictor (NH_MIXED, NH_MIXED_FP64_SOLVE)
     bool ir_mode;                // FP32 Krylov inside FP64 refinement (NH_MIXED)
@@ -1077,6 +1078,7 @@ static nh_status finish_create(nh_grid* g, const double* d0_host, int dev, int s
             int clk_khz = 0;
             cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
             g->barrier_budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL;   // about one second
+            g->barrier_budget_default = g->barrier_budget;
         }
         if (cudaFuncSetAttribute(k_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(uint32_t) * ((g->nx + 31) / 32))) != cudaSuccess) {
@@ -1180,6 +1182,14 @@ nh_status nh_set_run_mode(nh_grid* g, int use_graphs)
 {
     if (!g) return NH_ERR_ARG;
     g->use_graphs = use_graphs != 0;
+    return NH_OK;
+}
+
+nh_status nh_set_wait_budget(nh_grid* g, long long cycles)
+{
+    if (!g || cycles < 0) return NH_ERR_ARG;
+    g->barrier_budget = cycles > 0 ? cycles : g->barrier_budget_default;
+    graph_destroy(g);
     return NH_OK;
 }
 

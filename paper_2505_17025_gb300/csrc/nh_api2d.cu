@@ -31,7 +31,7 @@ struct nh_grid2d {
     std::vector<char> member_set;
     cudaStream_t stream, cap_stream;
     int maxch, maxpb, nblk, nmass, sms, items_grid, pcr_grid, egx, coop_grid;
-    long long barrier_budget;
+    long long barrier_budget, barrier_budget_default;
     int crit, enlarge, first_global;
     double knh;
     double rtol;
@@ -602,6 +602,7 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
         int clk_khz = 0;
         cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
         g->barrier_budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL;   // about one second
+        g->barrier_budget_default = g->barrier_budget;
         if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
             g->cap_stream = nullptr; rc = NH_ERR_CUDA; break;
         }
@@ -694,6 +695,14 @@ nh_status nh2d_set_graphs(nh_grid2d* g, int on)
     if (!g) return NH_ERR_ARG;
     g->use_graphs = on != 0;
     if (!g->use_graphs) graph_destroy(g);
+    return NH_OK;
+}
+
+nh_status nh2d_set_wait_budget(nh_grid2d* g, long long cycles)
+{
+    if (!g || cycles < 0) return NH_ERR_ARG;
+    g->barrier_budget = cycles > 0 ? cycles : g->barrier_budget_default;
+    graph_destroy(g);
     return NH_OK;
 }
 

@@ -35,14 +35,15 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh_set_solver", "nh_set_preconditioner", "nh_set_state", "nh_put_state", "nh_get_state",
            "nh_get_mask", "nh_step", "nh_run", "nh_set_profiling", "nh_get_profile", "nh_destroy",
            "nh_status_string", "nh_predict_static", "nh_workspace_bytes_ensemble", "nh_create_ensemble",
-           "nh_set_run_mode", "nh_set_tile", "nh_cnn_forward", "nh_cnn_workspace_bytes",
+           "nh_set_run_mode", "nh_set_tile", "nh_set_wait_budget", "nh_cnn_forward", "nh_cnn_workspace_bytes",
            "nh_cnn_loss_grad", "nh_cnn_adam", "nh_cnn_attach_bytes", "nh_cnn_attach",
            "nh_cnn_set_params", "nh_cnn_record", "nh_cnn_harvest", "nh_cnn_choices",
            "nh2d_workspace_bytes", "nh2d_create", "nh2d_set_bottom_motion", "nh2d_set_criterion",
            "nh2d_set_solver", "nh2d_set_state", "nh2d_get_state", "nh2d_get_mask", "nh2d_step",
            "nh2d_run", "nh2d_destroy", "nh2d_ensemble_workspace_bytes", "nh2d_create_ensemble", "nh2d_members",
            "nh2d_set_member_bottom_motion", "nh2d_set_graphs", "nh2d_set_member_state", "nh2d_get_member_state",
-           "nh2d_get_member_mask", "nh2d_get_member_info", "nh2d_graph_runs", "nh2d_set_precision")
+           "nh2d_get_member_mask", "nh2d_get_member_info", "nh2d_graph_runs", "nh2d_set_precision",
+           "nh2d_set_wait_budget")
 NH_CNN_PARAMS = 9328
 NH_CNN_IN = 16
 NH_STATIC_MAX_CELLS = 262144
@@ -133,6 +134,8 @@ def load():
         L.nh_put_state.argtypes = [C.c_void_p, _D, _D, _D]
         L.nh_set_profiling.argtypes = [C.c_void_p, C.c_int]
         L.nh_set_run_mode.argtypes = [C.c_void_p, C.c_int]
+        L.nh_set_wait_budget.argtypes = [C.c_void_p, C.c_longlong]
+        L.nh2d_set_wait_budget.argtypes = [C.c_void_p, C.c_longlong]
         L.nh_set_tile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
         L.nh_get_profile.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
         L.nh_get_mask.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), C.POINTER(C.c_int), _D]
@@ -196,7 +199,7 @@ def load():
         L.nh_status_string.restype = C.c_char_p
         for f in ("nh_create_grid", "nh_create_ensemble", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
                   "nh_set_preconditioner", "nh_put_state", "nh_set_profiling", "nh_get_profile",
-                  "nh_set_run_mode", "nh_set_tile",
+                  "nh_set_run_mode", "nh_set_tile", "nh_set_wait_budget", "nh2d_set_wait_budget",
                   "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run",
                   "nh_cnn_forward", "nh_cnn_loss_grad", "nh_cnn_adam", "nh_cnn_attach",
                   "nh_cnn_set_params", "nh_cnn_record", "nh_cnn_harvest", "nh_cnn_choices"):
@@ -336,6 +339,10 @@ class Grid:
 
     def set_run_mode(self, use_graphs=True):
         _check(self.L.nh_set_run_mode(self.h, int(bool(use_graphs))), "nh_set_run_mode")
+
+    def set_wait_budget(self, cycles=0):
+        """Spin limit of the solver's grid barrier in SM clock cycles (0: about one second)."""
+        _check(self.L.nh_set_wait_budget(self.h, int(cycles)), "nh_set_wait_budget")
 
     def set_profiling(self, enable=True):
         _check(self.L.nh_set_profiling(self.h, int(bool(enable))), "nh_set_profiling")
@@ -590,6 +597,10 @@ class Grid2D:
 
     def set_graphs(self, on):
         _check(self.L.nh2d_set_graphs(self.h, int(bool(on))), "nh2d_set_graphs")
+
+    def set_wait_budget(self, cycles=0):
+        """Spin limit of the solver's grid barrier in SM clock cycles (0: about one second)."""
+        _check(self.L.nh2d_set_wait_budget(self.h, int(cycles)), "nh2d_set_wait_budget")
 
     def set_precision(self, precision):
         """NH_FP64 or NH_MIXED_FP64_SOLVE (FP32 state); clears every member's state."""
