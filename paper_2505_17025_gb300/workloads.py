@@ -16,6 +16,11 @@ measured on; the paper's own runs are quoted where they are used):
   with a Gaussian mound of height A and width L moving down-slope as
   s(t) = s0 ln cosh(t / t0); per-member A, L, s0 drawn from a seeded uniform
   +-30 % band around the nominal values.
+* ``ensemble_1d`` -- uneven 1D slide members with drawn sizes and parameters.
+* ``line_soliton_2d`` -- the solitary wave in x, uniform in y, periodic.
+* ``landslide_2d`` -- an elliptic Gaussian slide on a plane slope, walls.
+* ``landslide_ensemble_2d`` -- uneven 2D landslide grids with drawn sizes,
+  slopes and slide parameters, one time step for all.
 """
 from __future__ import annotations
 
