@@ -1272,13 +1272,14 @@ nh_status nh_run(nh_grid* g, double dt, long long n_steps, nh_run_info* info)
             return rc;
         }
         // a step failed inside the captured run: redo it step by step (this
-        // also gives AUTO members their BiCGStab fallback) and continue there
+        // also gives AUTO members their BiCGStab fallback) and continue there;
+        // R keeps the steps the replay accepted
         n_steps -= R.steps;
-        std::memset(&R, 0, sizeof(R));
         rc = NH_OK;
     }
     for (long long k = 0; k < n_steps; ++k) {
         nh_step_info si;
+        std::memset(&si, 0, sizeof(si));
         rc = do_step(g, dt, &si);
         R.last = si;
         if (rc != NH_OK) break;

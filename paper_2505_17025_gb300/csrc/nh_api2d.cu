@@ -853,6 +853,7 @@ nh_status nh2d_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* info
     // a first step that is global by request runs on its own
     if (n_steps > 0 && g->first_global && g->steps == 0) {
         nh_step_info si;
+        std::memset(&si, 0, sizeof(si));
         rc = step2(g, dt, &si);
         R.last = si;
         if (rc != NH_OK) {
@@ -879,6 +880,7 @@ nh_status nh2d_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* info
     }
     for (long long k = 0; k < n_steps; ++k) {
         nh_step_info si;
+        std::memset(&si, 0, sizeof(si));
         rc = step2(g, dt, &si);
         R.last = si;
         if (rc != NH_OK) break;
