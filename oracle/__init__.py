@@ -27,7 +27,7 @@ _LIB = None
 # enums (mirror nh_oracle.h)
 BC_WALL, BC_PERIODIC = 0, 1
 LIM_NONE, LIM_CENTRAL, LIM_MINMOD, LIM_MC = 0, 1, 2, 3
-SLIDE_NONE, SLIDE_GAUSS_LNCOSH = 0, 1
+SLIDE_NONE, SLIDE_GAUSS_LNCOSH, SLIDE_PLATE_EXP, SLIDE_QUARTIC = 0, 1, 2, 3
 CRIT_GLOBAL, CRIT_HYDROSTATIC, CRIT_ETA_D, CRIT_ETA_X, CRIT_U, CRIT_U_X, CRIT_W, CRIT_W_X = range(8)
 SOLVER_AUTO, SOLVER_CG, SOLVER_BICGSTAB, SOLVER_DENSE = 0, 1, 2, 3
 GUESS_ZERO, GUESS_PREV = 0, 1
@@ -61,7 +61,7 @@ class _Params(C.Structure):
         ("nx", C.c_int), ("bc", C.c_int), ("dx", C.c_double), ("xl", C.c_double),
         ("g", C.c_double), ("rho", C.c_double), ("limiter", C.c_int),
         ("slide", C.c_int), ("A", C.c_double), ("L", C.c_double), ("xc0", C.c_double),
-        ("s0", C.c_double), ("t0", C.c_double),
+        ("s0", C.c_double), ("t0", C.c_double), ("t2", C.c_double),
         ("crit", C.c_int), ("knh", C.c_double), ("enlarge", C.c_int),
         ("first_step_global", C.c_int),
         ("solver", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
@@ -92,6 +92,7 @@ class Params:
     xc0: float = 0.0
     s0: float = 0.0
     t0: float = 1.0
+    t2: float = 0.0
     crit: int = CRIT_GLOBAL
     knh: float = 1e-3
     enlarge: int = 1

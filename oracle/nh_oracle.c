@@ -76,9 +76,33 @@ static void slide_law(const or_params* P, double t, double* s, double* sd, doubl
     *sdd = (P->s0 / (P->t0 * P->t0)) / (cosh(z) * cosh(z));
 }
 
-/* d(x,t) = d0(x) - m(x,t), m = A exp(-xi^2), xi = (x - xc0 - s(t)) / L.
-   The derivatives of m follow from the chain rule with dxi/dx = 1/L and
-   dxi/dt = -s'(t)/L. */
+/* The sliding block's position S(t) (Sec. 4.3): S = a0 t^2 / 2 up to t1,
+   then S(t1) + ut (t - t1) up to t2, then that minus a0 (t - t2)^2 / 2 up to
+   t3, constant after; ut = a0 t1 and t3 = t2 + t1 make S' continuous and
+   zero from t3 on.  S(t) = 0 before t = 0. */
+static void block_law(const or_params* P, double t, double* S, double* Sd, double* Sdd)
+{
+    double a0 = P->s0, t1 = P->t0, t2 = P->t2, t3 = t2 + t1, ut = a0 * t1;
+    double S1 = 0.5 * a0 * t1 * t1;
+    if (t <= 0.0) { *S = 0.0; *Sd = 0.0; *Sdd = 0.0; }
+    else if (t <= t1) { *S = 0.5 * a0 * t * t; *Sd = a0 * t; *Sdd = a0; }
+    else if (t <= t2) { *S = S1 + ut * (t - t1); *Sd = ut; *Sdd = 0.0; }
+    else if (t <= t3) {
+        *S = S1 + ut * (t - t1) - 0.5 * a0 * (t - t2) * (t - t2);
+        *Sd = ut - a0 * (t - t2);
+        *Sdd = -a0;
+    } else {
+        *S = S1 + ut * (t3 - t1) - 0.5 * a0 * (t3 - t2) * (t3 - t2);
+        *Sd = 0.0; *Sdd = 0.0;
+    }
+}
+
+/* d(x,t) = d0(x) - m(x,t) for the motions listed in nh_oracle.h.  For the
+   mound, xi = (x - xc0 - s(t)) / L and the derivatives of m follow from the
+   chain rule with dxi/dx = 1/L and dxi/dt = -s'(t)/L; for the block,
+   xi = 2 (x - xc0 - S(t)) / L with dxi/dx = 2/L and dxi/dt = -2 S'(t)/L; the
+   plate moves vertically only, and its edges (a jump of the depth) reach the
+   method through the depth at cell centres and faces. */
 void or_bottom(const or_params* P, const double* d0, int i, double t, double out[6])
 {
     double odd;
@@ -102,6 +126,31 @@ void or_bottom(const or_params* P, const double* d0, int i, double t, double out
         double m_tt = m * (2.0 / (L * L)) * ((2.0 * xi * xi - 1.0) * sd * sd + xi * L * sdd);
         d -= m; d_x -= m_x; d_xx -= m_xx;
         d_t = -m_t; d_xt = -m_xt; d_tt = -m_tt;
+    } else if (P->slide == OR_SLIDE_PLATE_EXP) {
+        double x = P->xl + (i + 0.5) * dx;
+        if (fabs(x - P->xc0) < P->L) {
+            double e = exp(-t / P->t0);
+            d -= P->A * (1.0 - e);
+            d_t = -P->A * e / P->t0;
+            d_tt = P->A * e / (P->t0 * P->t0);
+        }
+    } else if (P->slide == OR_SLIDE_QUARTIC) {
+        double S, Sd, Sdd;
+        block_law(P, t, &S, &Sd, &Sdd);
+        double x = P->xl + (i + 0.5) * dx;
+        double L = P->L;
+        double xi = 2.0 * (x - P->xc0 - S) / L;
+        if (fabs(xi) < 1.0) {
+            double A = P->A, xi2 = xi * xi, xi3 = xi2 * xi;
+            double m = A * (1.0 - xi2 * xi2);
+            double m_x = -8.0 * A * xi3 / L;
+            double m_xx = -48.0 * A * xi2 / (L * L);
+            double m_t = 8.0 * A * xi3 * Sd / L;
+            double m_xt = 48.0 * A * xi2 * Sd / (L * L);
+            double m_tt = (8.0 * A / L) * (-6.0 * xi2 * Sd * Sd / L + xi3 * Sdd);
+            d -= m; d_x -= m_x; d_xx -= m_xx;
+            d_t = -m_t; d_xt = -m_xt; d_tt = -m_tt;
+        }
     }
     out[0] = d; out[1] = d_x; out[2] = d_xx; out[3] = d_t; out[4] = d_xt; out[5] = d_tt;
 }

@@ -32,7 +32,18 @@ extern "C" {
 
 enum { OR_BC_WALL = 0, OR_BC_PERIODIC = 1 };
 enum { OR_LIM_NONE = 0, OR_LIM_CENTRAL = 1, OR_LIM_MINMOD = 2, OR_LIM_MC = 3 };
-enum { OR_SLIDE_NONE = 0, OR_SLIDE_GAUSS_LNCOSH = 1 };
+/* Bottom motions d(x,t) = d0(x) - m(x,t):
+   OR_SLIDE_GAUSS_LNCOSH  m = A exp(-((x - xc0 - s)/L)^2), s = s0 ln cosh(t/t0)
+                          (the moving-mound workloads);
+   OR_SLIDE_PLATE_EXP     m = A (1 - exp(-t/t0)) for |x - xc0| < L, else 0
+                          (the impulsive plate of Sec. 4.2: zeta0 = A, b = L,
+                          alpha = 1/t0);
+   OR_SLIDE_QUARTIC       m = A (1 - xi^4) for |xi| < 1, xi = 2 (x - xc0 - S(t))/L,
+                          else 0, with the piecewise-quadratic law S(t) of the
+                          sliding block of Sec. 4.3: acceleration a0 = s0 up to
+                          t1 = t0, glide at ut = a0 t1 up to t2, deceleration
+                          -a0 up to t3 = t2 + t1, at rest after. */
+enum { OR_SLIDE_NONE = 0, OR_SLIDE_GAUSS_LNCOSH = 1, OR_SLIDE_PLATE_EXP = 2, OR_SLIDE_QUARTIC = 3 };
 /* Sec. 5.1 criteria; GLOBAL = whole domain (Sec. 4), HYDROSTATIC = no cell */
 enum { OR_CRIT_GLOBAL = 0, OR_CRIT_HYDROSTATIC = 1, OR_CRIT_ETA_D = 2,
        OR_CRIT_ETA_X = 3, OR_CRIT_U = 4, OR_CRIT_U_X = 5, OR_CRIT_W = 6,
@@ -50,10 +61,10 @@ typedef struct {
     double g;         /* gravity                                            */
     double rho;       /* density                                            */
     int    limiter;   /* OR_LIM_*                                           */
-    /* bottom motion d(x,t) = d0(x) - A exp(-((x - xc0 - s(t))/L)^2),
-       s(t) = s0 ln cosh(t/t0)                                              */
+    /* bottom motion (OR_SLIDE_*, see above)                                */
     int    slide;
     double A, L, xc0, s0, t0;
+    double t2;        /* OR_SLIDE_QUARTIC: end of the glide (t2 >= t0)       */
     /* adaptivity */
     int    crit;
     double knh;
