@@ -80,7 +80,7 @@ enum { NH_GUESS_ZERO = 0, NH_GUESS_PREV = 1, NH_GUESS_CNN = 2 };
    that fits in one block), inside a flexible (Polak-Ribiere) PCG whose
    vectors, dots and stopping test stay in the handle's precision. */
 enum { NH_PRECOND_NONE = 0, NH_PRECOND_LINE = 1 };
-enum { NH_SLIDE_NONE = 0, NH_SLIDE_GAUSS_LNCOSH = 1 };
+enum { NH_SLIDE_NONE = 0, NH_SLIDE_GAUSS_LNCOSH = 1, NH_SLIDE_PLATE_EXP = 2, NH_SLIDE_QUARTIC = 3 };
 
 typedef struct {
     int    dim;        /* 1                                                 */
@@ -95,14 +95,25 @@ typedef struct {
     double rho;        /* density (kg/m^3), > 0; scales p^nh only           */
 } nh_grid_desc;
 
-/* Moving bottom of one member: d(x,t) = d0(x) - A exp(-((x - xc0 - s(t))/L)^2)
-   with s(t) = s0 ln cosh(t / t0) (a Gaussian mound sliding down-slope).  The
-   static part d0 is sampled per cell; its x-derivatives are central
-   differences; the mound's value and derivatives are analytic. */
+/* Moving bottom of one member, d(x,t) = d0(x) - m(x,t):
+   NH_SLIDE_GAUSS_LNCOSH  m = A exp(-((x - xc0 - s(t))/L)^2), s(t) = s0 ln cosh(t/t0)
+                          (a Gaussian mound sliding down-slope);
+   NH_SLIDE_PLATE_EXP     m = A (1 - exp(-t/t0)) on |x - xc0| < L, else 0: the
+                          impulsively moved plate of Sec. 4.2 (A = zeta0, L = b,
+                          t0 = 1/alpha); the plate's edges are a jump of the depth;
+   NH_SLIDE_QUARTIC       m = A (1 - xi^4) on |xi| < 1, xi = 2 (x - xc0 - S(t))/L,
+                          else 0: the sliding block of Sec. 4.3 (A = H_s, L = L_s)
+                          with S = s0 t^2/2 up to t0, then a glide at s0 t0 up to t2,
+                          then deceleration -s0 up to t2 + t0, at rest after.
+   The static part d0 is sampled per cell; its x-derivatives are central
+   differences; the moving part's value and derivatives are analytic. */
 typedef struct {
-    int    shape;      /* NH_SLIDE_NONE or NH_SLIDE_GAUSS_LNCOSH            */
-    double A, L, xc0;  /* height (m), width (m, > 0), start position (m)    */
-    double s0, t0;     /* travel scale (m), time scale (s, > 0)             */
+    int    shape;      /* NH_SLIDE_*                                        */
+    double A, L, xc0;  /* height (m), width (m, > 0), position (m)          */
+    double s0, t0;     /* GAUSS: travel scale (m), time scale (s, > 0);
+                          PLATE: s0 unused, t0 = 1/alpha (s, > 0);
+                          QUARTIC: acceleration a0 (m/s^2), its duration t1 (s, > 0) */
+    double t2;         /* QUARTIC: end of the glide (s, >= t0); else unused  */
 } nh_slide_desc;
 
 typedef struct {
@@ -153,9 +164,9 @@ size_t nh_workspace_bytes_ensemble(const nh_grid_desc* desc, const int* nx_per_m
 nh_status nh_create_ensemble(const nh_grid_desc* desc, const int* nx_per_member, const double* d0_host,
                              void* ws, size_t ws_bytes, void* stream, nh_grid** out);
 
-/* Bottom motion per member (Sec. 4.2-4.3 describe the paper's own moving
-   bottoms; this library moves a Gaussian mound, see nh_slide_desc).
-   slides: nbatch entries, or NULL for a static bottom.  Errors: NH_ERR_ARG. */
+/* Bottom motion per member (nh_slide_desc: the Gaussian mound, and the
+   paper's own moving bottoms of Sec. 4.2-4.3).  slides: nbatch entries, or
+   NULL for a static bottom.  Errors: NH_ERR_ARG. */
 nh_status nh_set_bottom_motion(nh_grid* g, const nh_slide_desc* slides);
 
 /* Adaptivity (Sec. 5.1, 5.2): cells whose criterion value on the predicted

@@ -1038,7 +1038,9 @@ static nh_status finish_create(nh_grid* g, const double* d0_host, int dev, int s
         for (long long q = 0; q < g->ncells; ++q) m0 += d0_host[q];
         g->mass0 = m0 * g->d.dx;
         std::vector<Slide> sl(g->nb);
-        for (auto& s : sl) { s.A = 0; s.L = 1; s.iL = 1; s.xc0 = 0; s.s0 = 0; s.t0 = 1; s.shape = NH_SLIDE_NONE; s.pad = 0; }
+        for (auto& s : sl) {
+            s.A = 0; s.L = 1; s.iL = 1; s.xc0 = 0; s.s0 = 0; s.t0 = 1; s.t2 = 0; s.shape = NH_SLIDE_NONE; s.pad = 0;
+        }
         if (cudaMemcpyAsync(g->slide, sl.data(), sizeof(Slide) * g->nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
             rc = NH_ERR_CUDA; break;
         }
@@ -1093,15 +1095,18 @@ nh_status nh_set_bottom_motion(nh_grid* g, const nh_slide_desc* slides)
     if (!g) return NH_ERR_ARG;
     std::vector<Slide> sl(g->nb);
     for (int b = 0; b < g->nb; ++b) {
-        Slide s{0.0, 1.0, 0.0, 0.0, 1.0, 1.0, NH_SLIDE_NONE, 0};
+        Slide s{0.0, 1.0, 0.0, 0.0, 1.0, 1.0, 0.0, NH_SLIDE_NONE, 0};
         if (slides) {
             const nh_slide_desc& q = slides[b];
-            if (q.shape != NH_SLIDE_NONE && q.shape != NH_SLIDE_GAUSS_LNCOSH) return NH_ERR_ARG;
-            if (q.shape == NH_SLIDE_GAUSS_LNCOSH) {
+            if (q.shape < NH_SLIDE_NONE || q.shape > NH_SLIDE_QUARTIC) return NH_ERR_ARG;
+            if (q.shape != NH_SLIDE_NONE) {
                 if (!(q.L > 0.0) || !(q.t0 > 0.0) || !std::isfinite(q.A) || !std::isfinite(q.xc0) ||
                     !std::isfinite(q.s0))
                     return NH_ERR_ARG;
-                s.A = q.A; s.L = q.L; s.iL = 1.0 / q.L; s.xc0 = q.xc0; s.s0 = q.s0; s.t0 = q.t0; s.shape = q.shape;
+                if (q.shape == NH_SLIDE_QUARTIC && !(q.t2 >= q.t0 && std::isfinite(q.t2))) return NH_ERR_ARG;
+                s.A = q.A; s.L = q.L; s.iL = 1.0 / q.L; s.xc0 = q.xc0; s.s0 = q.s0; s.t0 = q.t0;
+                s.t2 = q.shape == NH_SLIDE_QUARTIC ? q.t2 : 0.0;
+                s.shape = q.shape;
             }
         }
         sl[b] = s;

@@ -46,12 +46,51 @@ static_assert((1 << kPcrLevels) == kPcrRows, "kPcrLevels = log2(kPcrRows)");
 constexpr double kMoundCut = 40.0;
 
 // Per-member slide parameters (device copy of nh_slide_desc, FP64).
+// Shapes (NH_SLIDE_*): GAUSS_LNCOSH m = A exp(-((x - xc0 - s)/L)^2) with
+// s = s0 ln cosh(t/t0); PLATE_EXP m = A s on |x - xc0| < L with the time
+// factor s = 1 - exp(-t/t0) (Sec. 4.2); QUARTIC m = A (1 - xi^4) on |xi| < 1,
+// xi = 2 (x - xc0 - s)/L, s = S(t) the sliding block's position (Sec. 4.3:
+// acceleration s0 up to t0, glide at s0 t0 up to t2, deceleration up to
+// t2 + t0, at rest after).
 struct Slide {
     double A, L, xc0, s0, t0;
     double iL;    // 1 / L (set on the host with L)
+    double t2;    // QUARTIC: end of the glide
     int shape;
     int pad;
 };
+
+// s(t), s'(t), s''(t) of a slide (the mound's displacement, the plate's time
+// factor or the block's position, see Slide).
+__host__ __device__ __forceinline__ void slide_law(const Slide& sl, double t, double* s, double* sd, double* sdd)
+{
+    *s = 0.0; *sd = 0.0; *sdd = 0.0;
+    if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
+        const double z = t / sl.t0, c = cosh(z);
+        *s = sl.s0 * log(c);
+        *sd = (sl.s0 / sl.t0) * tanh(z);
+        *sdd = (sl.s0 / (sl.t0 * sl.t0)) / (c * c);
+    } else if (sl.shape == NH_SLIDE_PLATE_EXP) {
+        const double e = exp(-t / sl.t0);
+        *s = 1.0 - e;
+        *sd = e / sl.t0;
+        *sdd = -e / (sl.t0 * sl.t0);
+    } else if (sl.shape == NH_SLIDE_QUARTIC) {
+        const double a0 = sl.s0, t1 = sl.t0, t2 = sl.t2, t3 = t2 + t1, ut = a0 * t1;
+        const double S1 = 0.5 * a0 * t1 * t1;
+        if (t <= 0.0) {
+        } else if (t <= t1) {
+            *s = 0.5 * a0 * t * t; *sd = a0 * t; *sdd = a0;
+        } else if (t <= t2) {
+            *s = S1 + ut * (t - t1); *sd = ut;
+        } else if (t <= t3) {
+            *s = S1 + ut * (t - t1) - 0.5 * a0 * (t - t2) * (t - t2);
+            *sd = ut - a0 * (t - t2); *sdd = -a0;
+        } else {
+            *s = S1 + ut * (t3 - t1) - 0.5 * a0 * (t3 - t2) * (t3 - t2);
+        }
+    }
+}
 
 // Per-member slide kinematics at t^n and t^{n+1}: position s and, at t^{n+1},
 // its first and second time derivatives.
@@ -148,11 +187,24 @@ __device__ __forceinline__ float wave_sqrt(float v) { return sqrtf(v); }
 template <typename T>
 __device__ __forceinline__ T mound_at(int c, double x0, double dx, const Slide& sl, double s)
 {
-    if (sl.shape != NH_SLIDE_GAUSS_LNCOSH) return T(0);
-    const double xc = x0 + (c + 0.5) * dx;
-    const T xi = T((xc - sl.xc0 - s) * sl.iL);
-    if (xi * xi > T(kMoundCut)) return T(0);
-    return T(sl.A) * texp(-xi * xi);
+    if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
+        const double xc = x0 + (c + 0.5) * dx;
+        const T xi = T((xc - sl.xc0 - s) * sl.iL);
+        if (xi * xi > T(kMoundCut)) return T(0);
+        return T(sl.A) * texp(-xi * xi);
+    }
+    if (sl.shape == NH_SLIDE_PLATE_EXP) {
+        const double xc = x0 + (c + 0.5) * dx;
+        return fabs(xc - sl.xc0) < sl.L ? T(sl.A * s) : T(0);
+    }
+    if (sl.shape == NH_SLIDE_QUARTIC) {
+        const double xc = x0 + (c + 0.5) * dx;
+        const double xi = 2.0 * (xc - sl.xc0 - s) / sl.L;
+        if (!(fabs(xi) < 1.0)) return T(0);
+        const double xi2 = xi * xi;
+        return T(sl.A * (1.0 - xi2 * xi2));
+    }
+    return T(0);
 }
 
 template <typename T>
@@ -198,6 +250,30 @@ __device__ __forceinline__ Bottom<T> bottom_full(const T* __restrict__ d0m, int 
         T m_tt = m * (T(2) * iL2) * (two_xi2m1 * sd * sd + xi * L * sdd);
         B.d -= m; B.d_x -= m_x; B.d_xx -= m_xx; B.m = m;
         B.d_t = -m_t; B.d_xt = -m_xt; B.d_tt = -m_tt;
+    } else if (sl.shape == NH_SLIDE_PLATE_EXP) {
+        // vertical motion only; the plate's edges are a jump of the depth
+        const double xc = x0 + (i + 0.5) * dx;
+        if (fabs(xc - sl.xc0) < sl.L) {
+            const T m = T(sl.A * k.s_n1);
+            B.d -= m; B.m = m;
+            B.d_t = T(-sl.A * k.sd_n1);
+            B.d_tt = T(-sl.A * k.sdd_n1);
+        }
+    } else if (sl.shape == NH_SLIDE_QUARTIC) {
+        const double xc = x0 + (i + 0.5) * dx;
+        const double xi = 2.0 * (xc - sl.xc0 - k.s_n1) / sl.L;   // as in mound_at
+        if (fabs(xi) < 1.0) {
+            const double L = sl.L, A = sl.A, Sd = k.sd_n1, Sdd = k.sdd_n1;
+            const double xi2 = xi * xi, xi3 = xi2 * xi;
+            const double m = A * (1.0 - xi2 * xi2);
+            const double m_x = -8.0 * A * xi3 / L;
+            const double m_xx = -48.0 * A * xi2 / (L * L);
+            const double m_t = 8.0 * A * xi3 * Sd / L;
+            const double m_xt = 48.0 * A * xi2 * Sd / (L * L);
+            const double m_tt = (8.0 * A / L) * (-6.0 * xi2 * Sd * Sd / L + xi3 * Sdd);
+            B.d -= T(m); B.d_x -= T(m_x); B.d_xx -= T(m_xx); B.m = T(m);
+            B.d_t = T(-m_t); B.d_xt = T(-m_xt); B.d_tt = T(-m_tt);
+        }
     }
     return B;
 }

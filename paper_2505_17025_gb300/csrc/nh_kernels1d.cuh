@@ -34,17 +34,11 @@ static __global__ void k_kinematics(const Slide* __restrict__ sl, Kin* __restric
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
-    Slide s = sl[b];
+    const Slide s = sl[b];
     Kin k{0.0, 0.0, 0.0, 0.0};
-    if (s.shape == NH_SLIDE_GAUSS_LNCOSH) {
-        // s(t) = s0 ln cosh(t/t0);  s' = (s0/t0) tanh(t/t0);  s'' = (s0/t0^2) / cosh^2(t/t0)
-        double zn = t_n / s.t0, z1 = t_n1 / s.t0;
-        k.s_n = s.s0 * log(cosh(zn));
-        k.s_n1 = s.s0 * log(cosh(z1));
-        k.sd_n1 = (s.s0 / s.t0) * tanh(z1);
-        double c1 = cosh(z1);
-        k.sdd_n1 = (s.s0 / (s.t0 * s.t0)) / (c1 * c1);
-    }
+    double sd_n, sdd_n;
+    slide_law(s, t_n, &k.s_n, &sd_n, &sdd_n);
+    slide_law(s, t_n1, &k.s_n1, &k.sd_n1, &k.sdd_n1);
     kin[b] = k;
 }
 
@@ -56,16 +50,11 @@ static __global__ void k_kinematics_dev(const Slide* __restrict__ sl, Kin* __res
     if (b >= nb || tc->abort) return;
     const double t_n = tc->t_base + (double)tc->n * tc->dt;
     const double t_n1 = tc->t_base + (double)(tc->n + 1) * tc->dt;
-    Slide s = sl[b];
+    const Slide s = sl[b];
     Kin k{0.0, 0.0, 0.0, 0.0};
-    if (s.shape == NH_SLIDE_GAUSS_LNCOSH) {
-        double zn = t_n / s.t0, z1 = t_n1 / s.t0;
-        k.s_n = s.s0 * log(cosh(zn));
-        k.s_n1 = s.s0 * log(cosh(z1));
-        k.sd_n1 = (s.s0 / s.t0) * tanh(z1);
-        double c1 = cosh(z1);
-        k.sdd_n1 = (s.s0 / (s.t0 * s.t0)) / (c1 * c1);
-    }
+    double sd_n, sdd_n;
+    slide_law(s, t_n, &k.s_n, &sd_n, &sdd_n);
+    slide_law(s, t_n1, &k.s_n1, &k.sd_n1, &k.sdd_n1);
     kin[b] = k;
 }
 
@@ -193,10 +182,17 @@ __global__ void __launch_bounds__(TILE) k_predict(PredArgs<T> a)
     if (tid == 0) {
         s_k[0] = T(G.g); s_k[1] = T(a.dt); s_k[2] = T(0.5) * T(a.dt); s_k[3] = T(G.idx); s_k[4] = T(a.knh);
         int lo = 1, hi = 0;
-        if (sl.shape == NH_SLIDE_GAUSS_LNCOSH) {
-            const double r = sqrt(kMoundCut * 1.0001) * sl.L;
-            const double ca = (sl.xc0 + fmin(kn.s_n, kn.s_n1) - r - G.x0) / G.dx - 0.5;
-            const double cb = (sl.xc0 + fmax(kn.s_n, kn.s_n1) + r - G.x0) / G.dx - 0.5;
+        if (sl.shape == NH_SLIDE_GAUSS_LNCOSH || sl.shape == NH_SLIDE_PLATE_EXP || sl.shape == NH_SLIDE_QUARTIC) {
+            // support of the mound at t^n and t^{n+1}, with a margin
+            double lo_x, hi_x;
+            if (sl.shape == NH_SLIDE_PLATE_EXP) {
+                lo_x = sl.xc0 - 1.0001 * sl.L; hi_x = sl.xc0 + 1.0001 * sl.L;
+            } else {
+                const double r = sl.shape == NH_SLIDE_QUARTIC ? 0.5001 * sl.L : sqrt(kMoundCut * 1.0001) * sl.L;
+                lo_x = sl.xc0 + fmin(kn.s_n, kn.s_n1) - r; hi_x = sl.xc0 + fmax(kn.s_n, kn.s_n1) + r;
+            }
+            const double ca = (lo_x - G.x0) / G.dx - 0.5;
+            const double cb = (hi_x - G.x0) / G.dx - 0.5;
             lo = (int)fmax(floor(ca) - 1.0, -1073741824.0);
             hi = (int)fmin(ceil(cb) + 1.0, 1073741824.0);
         }

@@ -101,11 +101,13 @@ extern "C" nh_status nh_predict_static(const double* h, const double* hu, const 
     if (!(dx > 0.0) || !(g > 0.0) || !(dt > 0.0) || !std::isfinite(t) || !std::isfinite(x0)) return NH_ERR_ARG;
     if (bc != NH_BC_WALL && bc != NH_BC_PERIODIC) return NH_ERR_ARG;
     if (limiter < NH_LIM_NONE || limiter > NH_LIM_MC) return NH_ERR_ARG;
-    Slide s{0.0, 1.0, 0.0, 0.0, 1.0, 1.0, NH_SLIDE_NONE, 0};
-    if (slide && slide->shape == NH_SLIDE_GAUSS_LNCOSH) {
+    Slide s{0.0, 1.0, 0.0, 0.0, 1.0, 1.0, 0.0, NH_SLIDE_NONE, 0};
+    if (slide && slide->shape >= NH_SLIDE_GAUSS_LNCOSH && slide->shape <= NH_SLIDE_QUARTIC) {
         if (!(slide->L > 0.0) || !(slide->t0 > 0.0)) return NH_ERR_ARG;
+        if (slide->shape == NH_SLIDE_QUARTIC && !(slide->t2 >= slide->t0)) return NH_ERR_ARG;
         s.A = slide->A; s.L = slide->L; s.iL = 1.0 / slide->L; s.xc0 = slide->xc0; s.s0 = slide->s0; s.t0 = slide->t0;
-        s.shape = NH_SLIDE_GAUSS_LNCOSH;
+        s.t2 = slide->shape == NH_SLIDE_QUARTIC ? slide->t2 : 0.0;
+        s.shape = slide->shape;
     } else if (slide && slide->shape != NH_SLIDE_NONE) {
         return NH_ERR_ARG;
     }

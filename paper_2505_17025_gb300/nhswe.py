@@ -28,7 +28,7 @@ NH_LIM_NONE, NH_LIM_CENTRAL, NH_LIM_MINMOD, NH_LIM_MC = range(4)
 NH_SOLVER_AUTO, NH_SOLVER_CG, NH_SOLVER_BICGSTAB = range(3)
 NH_GUESS_ZERO, NH_GUESS_PREV, NH_GUESS_CNN = 0, 1, 2
 NH_PRECOND_NONE, NH_PRECOND_LINE = 0, 1
-NH_SLIDE_NONE, NH_SLIDE_GAUSS_LNCOSH = 0, 1
+NH_SLIDE_NONE, NH_SLIDE_GAUSS_LNCOSH, NH_SLIDE_PLATE_EXP, NH_SLIDE_QUARTIC = 0, 1, 2, 3
 
 # every exported symbol of the ABI (checked by the CPU test suite)
 EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_set_criterion",
@@ -60,7 +60,7 @@ class nh_grid_desc(C.Structure):
 
 class nh_slide_desc(C.Structure):
     _fields_ = [("shape", C.c_int), ("A", C.c_double), ("L", C.c_double), ("xc0", C.c_double),
-                ("s0", C.c_double), ("t0", C.c_double)]
+                ("s0", C.c_double), ("t0", C.c_double), ("t2", C.c_double)]
 
 
 class nh_step_info(C.Structure):
@@ -294,14 +294,15 @@ class Grid:
 
     # -- configuration
     def set_bottom_motion(self, slides):
-        """slides: list of dicts (shape, A, L, xc0, s0, t0) per member, or None."""
+        """slides: list of dicts (shape, A, L, xc0, s0, t0[, t2]) per member, or None."""
         if slides is None:
             _check(self.L.nh_set_bottom_motion(self.h, None), "nh_set_bottom_motion")
             return
         arr = (nh_slide_desc * self.nb)()
         for b, s in enumerate(slides):
             arr[b] = nh_slide_desc(int(s.get("shape", NH_SLIDE_GAUSS_LNCOSH)), float(s["A"]),
-                                   float(s["L"]), float(s["xc0"]), float(s["s0"]), float(s["t0"]))
+                                   float(s["L"]), float(s["xc0"]), float(s["s0"]), float(s["t0"]),
+                                   float(s.get("t2", 0.0)))
         _check(self.L.nh_set_bottom_motion(self.h, arr), "nh_set_bottom_motion")
 
     def set_criterion(self, kind, k_nh=1e-3, enlarge=1, first_step_global=False):
@@ -670,6 +671,7 @@ def grid_from_workload(wl, precision=NH_FP64, limiter=NH_LIM_CENTRAL, bc=None, *
     G = Grid(nx, m0.dx, [m.d0 for m in ms], nbatch=len(ms), x0=m0.xl,
              bc=wl.bc if bc is None else bc, precision=precision, limiter=limiter, **kw)
     if any(m.slide for m in ms):
-        G.set_bottom_motion([dict(shape=m.slide, A=m.A, L=m.L, xc0=m.xc0, s0=m.s0, t0=m.t0) for m in ms])
+        G.set_bottom_motion([dict(shape=m.slide, A=m.A, L=m.L, xc0=m.xc0, s0=m.s0, t0=m.t0, t2=m.t2)
+                             for m in ms])
     G.set_state([m.h for m in ms], [m.hu for m in ms], [m.hw for m in ms])
     return G

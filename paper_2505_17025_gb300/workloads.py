@@ -71,12 +71,13 @@ class Member1D:
     h: np.ndarray
     hu: np.ndarray
     hw: np.ndarray
-    slide: int = 0           # 0 static bottom, 1 Gaussian mound, s0 ln cosh(t/t0)
+    slide: int = 0           # 0 static, 1 Gaussian mound, 2 impulsive plate, 3 sliding block
     A: float = 0.0
     L: float = 1.0
     xc0: float = 0.0
     s0: float = 0.0
     t0: float = 1.0
+    t2: float = 0.0          # sliding block: end of the glide
 
     @property
     def x(self):
@@ -138,6 +139,51 @@ def slide_1d(n_members=64, nx=50000, length=40.0, h_min=0.05, h_max=1.0, slope=0
     return Workload1D("slide_1d", members, dt, n, T, amplitude=A,
                       meta={"h_min": h_min, "h_max": h_max, "slope": slope, "A": A, "L": L,
                             "s0": s0, "t0": t0, "xc0": xc0, "spread": spread, "seed0": seed0})
+
+
+# The paper's sliding-block table (Sec. 4.3), one row per Froude number
+# 0.125, 0.25, 0.375: acceleration a0 (m/s^2), t1, t2 (s); the glide speed
+# is a0 t1 and the block stops at t2 + t1 (the table's ut and t3 to rounding).
+BLOCK_TABLE = ((1.5, 0.109, 2.109), (1.5, 0.218, 2.218), (1.5, 0.327, 2.327))
+
+
+def plate_1d(up=True, nx=1200, dx=0.025, h0=0.05, zeta0=0.005, b=0.61, T=2.0, cfl=None, dt=0.01, g=G):
+    """The impulsively moved plate of Sec. 4.2 on a flat bottom h0 = 0.05 m:
+    d = h0 - zeta0 (1 - exp(-alpha t)) on 0 <= x < b next to the wall at x = 0
+    (mirror of |x| < b), b = 0.61 m, |zeta0| = 0.005 m (positive: the plate
+    rises), alpha = 1.11 / t_c with t_c sqrt(g h0) / b = 0.148 (up) or 0.093
+    (down); the paper's dx = 0.025 m and dt = 0.01 s; still water, walls (the
+    far wall stands in for the paper's absorbing end)."""
+    ratio = 0.148 if up else 0.093
+    tc = ratio * b / math.sqrt(g * h0)
+    z0 = zeta0 if up else -zeta0
+    d0 = np.full(nx, h0)
+    m = Member1D(nx=nx, dx=dx, xl=0.0, d0=d0, h=d0.copy(), hu=np.zeros(nx), hw=np.zeros(nx), slide=2,
+                 A=z0, L=b, xc0=0.0, s0=0.0, t0=tc / 1.11)
+    n = int(math.ceil(T / dt))
+    return Workload1D("plate_1d", [m], T / n, n, T, amplitude=abs(z0),
+                      meta={"up": up, "t_c": tc, "alpha": 1.11 / tc})
+
+
+def block_1d(row=1, nx=400, length=10.0, h0=0.175, Hs=0.026, Ls=0.5, xc0=2.0, T=3.0, dt=0.005):
+    """The sliding block of Sec. 4.3 over a flat bottom h0 = 0.175 m: the
+    bump H_s (1 - (2 (x - S)/L_s)^4), H_s = 0.026 m, L_s = 0.5 m, centred at
+    xc0 + S(t) with S(t) from BLOCK_TABLE[row]; still water over it, walls;
+    the paper's dt = 0.005 s and dx = 0.025 m (a third of the paper's).  The
+    bump's edges are kinks of the depth: at spacings far below the paper's
+    the reaction term gamma turns negative next to them and the elliptic
+    problem loses definiteness (seen at dx = 5 mm)."""
+    a0, t1, t2 = BLOCK_TABLE[row]
+    dx = length / nx
+    x = (np.arange(nx) + 0.5) * dx
+    d0 = np.full(nx, h0)
+    xi = 2.0 * (x - xc0) / Ls
+    mound = np.where(np.abs(xi) < 1.0, Hs * (1.0 - xi ** 4), 0.0)
+    m = Member1D(nx=nx, dx=dx, xl=0.0, d0=d0, h=d0 - mound, hu=np.zeros(nx), hw=np.zeros(nx), slide=3,
+                 A=Hs, L=Ls, xc0=xc0, s0=a0, t0=t1, t2=t2)
+    n = int(math.ceil(T / dt))
+    return Workload1D("block_1d", [m], T / n, n, T, amplitude=Hs,
+                      meta={"a0": a0, "t1": t1, "t2": t2, "travel": a0 * t1 * t2})
 
 
 def ensemble_1d(n_members=32, nx_min=16384, nx_max=131072, dx=0.002, h_min=0.1, h_max=2.0,

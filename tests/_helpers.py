@@ -9,7 +9,7 @@ from paper_2505_17025_gb300 import nhswe as N
 def oracle_params(m, crit, knh=1e-3, enlarge=1, first=0, solver=O.SOLVER_AUTO, rtol=1e-12,
                   max_iter=20000, guess=O.GUESS_PREV, bc=O.BC_WALL, limiter=O.LIM_CENTRAL):
     return O.Params(nx=m.nx, dx=m.dx, xl=m.xl, bc=bc, limiter=limiter, slide=m.slide, A=m.A, L=m.L,
-                    xc0=m.xc0, s0=m.s0, t0=m.t0, crit=crit, knh=knh, enlarge=enlarge,
+                    xc0=m.xc0, s0=m.s0, t0=m.t0, t2=m.t2, crit=crit, knh=knh, enlarge=enlarge,
                     first_step_global=first, solver=solver, rtol=rtol, max_iter=max_iter, guess=guess)
 
 
