@@ -442,3 +442,65 @@ def test_mask_criteria_and_enlargement():
     p.crit = O.CRIT_HYDROSTATIC
     p.first_step_global = 0
     assert O.mask(p, d0, 0.0, 3, h, hu, hw).sum() == 0
+
+
+# ------------------------------------------------- structural properties
+
+def test_reflection_symmetry_of_the_rates():
+    """Mirroring a walled problem in x (h(x) -> h(L - x), hu -> -hu(L - x),
+    hw -> hw(L - x), d0 likewise) mirrors the hydrostatic rates: a sign or
+    index slip in the fluxes, the slopes or the bottom source breaks it."""
+    nx, dx = 64, 0.05
+    x = (np.arange(nx) + 0.5) * dx
+    d0 = 0.4 + 0.1 * np.sin(2.1 * x) + 0.05 * x
+    h = d0 + 0.02 * np.exp(-((x - 1.1) / 0.3) ** 2)
+    hu = 0.03 * np.sin(3.0 * x) * h
+    hw = 0.004 * np.cos(1.7 * x)
+    for lim in (O.LIM_CENTRAL, O.LIM_MINMOD, O.LIM_MC):
+        p = O.Params(nx=nx, dx=dx, limiter=lim)
+        r = O.rhs(p, d0, 0.0, h, hu, hw)
+        rm = O.rhs(p, d0[::-1].copy(), 0.0, h[::-1].copy(), -hu[::-1].copy(), hw[::-1].copy())
+        scale = max(np.max(np.abs(v)) for v in r)
+        assert np.max(np.abs(rm[0][::-1] - r[0])) <= 1e-12 * scale
+        assert np.max(np.abs(-rm[1][::-1] - r[1])) <= 1e-12 * scale
+        assert np.max(np.abs(rm[2][::-1] - r[2])) <= 1e-12 * scale
+
+
+def test_correction_leaves_h_untouched():
+    """Sec. 3.2: the projection corrects the momenta, not the thickness."""
+    wl = W.slide_1d(n_members=1, nx=600, length=4.0, xc0=1.0, T=0.2, seed0=2)
+    m = wl.members[0]
+    p = _params(m, crit=O.CRIT_GLOBAL)
+    ht, hut, hwt = O.predict(p, m.d0, 0.1, wl.dt, m.h, m.hu, m.hw)
+    mk = np.ones(m.nx, dtype=np.uint8)
+    Kf, gam, R = O.assemble(p, m.d0, 0.1 + wl.dt, wl.dt, ht, hut, hwt)
+    q, st, _ = O.solve(p, mk, Kf, gam, R)
+    assert st == O.OK and np.max(np.abs(q)) > 0.0
+    h1, hu1, hw1 = O.correct(p, m.d0, 0.1 + wl.dt, wl.dt, mk, q, ht, hut, hwt)
+    assert np.array_equal(h1, ht)
+    assert np.max(np.abs(hu1 - hut)) > 0.0
+
+
+def test_auto_solver_follows_the_sign_of_gamma():
+    """AUTO takes CG when gamma > 0 on every active cell (a sufficient
+    condition for a positive-definite operator) and BiCGStab otherwise; both
+    give the dense solution."""
+    wl = W.solitary_1d(nx=400, length=40.0, a=0.1, T=1.0)   # flat bottom: gamma = 12 a / (4 h^3) > 0
+    m = wl.members[0]
+    p = _params(m, crit=O.CRIT_GLOBAL, rtol=1e-13)
+    ht, hut, hwt = O.predict(p, m.d0, 0.0, wl.dt, m.h, m.hu, m.hw)
+    mk = np.ones(m.nx, dtype=np.uint8)
+    Kf, gam, R = O.assemble(p, m.d0, wl.dt, wl.dt, ht, hut, hwt)
+    assert np.all(gam > 0)
+    q_cg, st, info = O.solve(p, mk, Kf, gam, R)
+    assert st == O.OK and info["solver_used"] == O.SOLVER_CG
+    gneg = gam.copy()
+    gneg[m.nx // 2] = -0.5 * abs(gam[m.nx // 2])      # one negative reaction term
+    q_bi, st, info = O.solve(p, mk, Kf, gneg, R)
+    assert st == O.OK and info["solver_used"] == O.SOLVER_BICGSTAB
+    pd = _params(m, crit=O.CRIT_GLOBAL, solver=O.SOLVER_DENSE)
+    q_d, st, _ = O.solve(pd, mk, Kf, gneg, R)
+    assert st == O.OK
+    assert np.max(np.abs(q_bi - q_d)) <= 1e-9 * np.max(np.abs(q_d))
+    q_d2, st, _ = O.solve(pd, mk, Kf, gam, R)
+    assert np.max(np.abs(q_cg - q_d2)) <= 1e-9 * np.max(np.abs(q_d2))
