@@ -305,3 +305,43 @@ def test_mask_moore_enlargement():
     m = O2.mask(p, d0, 0.0, 3, h, z, z, z)
     expect = {(j, i) for j in range(2, 5) for i in range(3, 6)} | {(0, 7), (0, 8), (1, 7), (1, 8)}
     assert set(zip(*np.nonzero(m))) == expect
+
+
+def test_nine_point_operator_second_order_manufactured():
+    """Manufactured solution of -div(K grad q) + gamma q = R on a periodic
+    square with a full tensor K (Kxx = 1 + 0.3 cos 2 pi x, Kyy = 1 + 0.2 sin 2 pi y,
+    Kxy = 0.1), q = sin 2 pi x sin 4 pi y, gamma = 2, R from sympy.  The rows
+    are built here from the textbook conservative 5-point part (K at the faces)
+    and the central cross term -2 Kxy q_xy on the diagonals; the oracle's
+    9-point apply and solve must then converge at second order, which fails if
+    a neighbour slot is mapped to the wrong cell."""
+    sympy = pytest.importorskip("sympy")
+    X, Y = sympy.symbols("x y")
+    q_e = sympy.sin(2 * sympy.pi * X) * sympy.sin(4 * sympy.pi * Y)
+    kxx = 1 + sympy.Rational(3, 10) * sympy.cos(2 * sympy.pi * X)
+    kyy = 1 + sympy.Rational(1, 5) * sympy.sin(2 * sympy.pi * Y)
+    kxy = sympy.Rational(1, 10)
+    qx, qy = sympy.diff(q_e, X), sympy.diff(q_e, Y)
+    R_e = -(sympy.diff(kxx * qx + kxy * qy, X) + sympy.diff(kxy * qx + kyy * qy, Y)) + 2 * q_e
+    qf, kxxf, kyyf, Rf = (sympy.lambdify((X, Y), e, "numpy") for e in (q_e, kxx, kyy, R_e))
+    errs = []
+    for n in (24, 48, 96):
+        d = 1.0 / n
+        xc = (np.arange(n) + 0.5) * d
+        Xc, Yc = np.meshgrid(xc, xc)
+        kw = kxxf(Xc - 0.5 * d, Yc); ke = kxxf(Xc + 0.5 * d, Yc)
+        ks = kyyf(Xc, Yc - 0.5 * d); kn = kyyf(Xc, Yc + 0.5 * d)
+        c = np.zeros((O2.NCOEF, n, n))
+        c[1], c[2] = -kw / d ** 2, -ke / d ** 2          # W, E
+        c[3], c[4] = -ks / d ** 2, -kn / d ** 2          # S, N
+        cross = 0.1 * 2.0 / (4.0 * d * d)
+        c[5], c[6], c[7], c[8] = -cross, cross, cross, -cross   # SW, SE, NW, NE
+        gam = np.full((n, n), 2.0)
+        c[0] = (kw + ke) / d ** 2 + (ks + kn) / d ** 2 + gam
+        p = O2.Params2D(nx=n, ny=n, dx=d, dy=d, bcx=O.BC_PERIODIC, bcy=O.BC_PERIODIC, solver=O.SOLVER_CG,
+                        rtol=1e-14, max_iter=100000)
+        mk = np.ones((n, n), dtype=np.uint8)
+        q, st, _ = O2.solve(p, mk, c, gam, Rf(Xc, Yc))
+        assert st == O.OK
+        errs.append(float(np.max(np.abs(q - qf(Xc, Yc)))))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
