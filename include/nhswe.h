@@ -135,7 +135,7 @@ typedef struct {
     long long steps;         /* steps completed                                */
     long long iters_total;   /* sum over steps of nh_step_info.iters           */
     long long active_total;  /* sum over steps of nh_step_info.n_active        */
-    nh_step_info last;       /* the last completed step                        */
+    nh_step_info last;       /* the last step: completed, or the failing one   */
 } nh_run_info;
 
 /* Bytes of device workspace nh_create_grid needs for `desc` (0 if invalid). */
@@ -216,8 +216,9 @@ nh_status nh_get_state(nh_grid* g, double* h, double* hu, double* hw, double* p_
 nh_status nh_get_mask(nh_grid* g, unsigned char* mask, int* iters, double* rel_res);
 
 /* One step of size dt > 0: predictor, criterion and mask, elliptic solve on
-   the mask, correction.  On NH_ERR_NOT_CONVERGED or NH_ERR_NONFINITE the
-   state is left as it was before the step.  info may be NULL. */
+   the mask, correction.  On NH_ERR_NOT_CONVERGED, NH_ERR_NONFINITE or
+   NH_ERR_TIMEOUT the state is left as it was before the step.  info may be
+   NULL. */
 nh_status nh_step(nh_grid* g, double dt, nh_step_info* info);
 
 /* n_steps steps of size dt; stops at the first failing step (whose status is
