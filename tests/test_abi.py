@@ -5,6 +5,9 @@ import ctypes
 import os
 import re
 
+import numpy as np
+import pytest
+
 from paper_2505_17025_gb300 import build as B
 from paper_2505_17025_gb300 import nhswe
 
@@ -79,3 +82,18 @@ def test_ensemble_workspace_2d_needs_no_gpu():
     assert lib.nh2d_ensemble_workspace_bytes(0, arr) == 0
     arr[2] = D(40, 2, 1, 0, 2, 0.05, 0.04, 0.0, 0.0, 9.81, 1000.0)   # ny < 3
     assert lib.nh2d_ensemble_workspace_bytes(3, arr) == 0
+
+
+def test_product_path_fails_loudly_without_a_gpu():
+    """No CPU fallback: on a machine without CUDA every product entry point
+    raises instead of computing anything (the oracle is never consulted)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2505_17025_gb300 import workloads as W
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        nhswe.load()
+    with pytest.raises(RuntimeError):
+        nhswe.grid_from_workload(W.slide_1d(n_members=1, nx=64, length=1.0, T=0.01))
+    with pytest.raises(RuntimeError):
+        nhswe.Grid2D(8, 8, 0.1, 0.1, np.ones((8, 8)))
