@@ -29,7 +29,7 @@ BC_WALL, BC_PERIODIC = 0, 1
 LIM_NONE, LIM_CENTRAL, LIM_MINMOD, LIM_MC = 0, 1, 2, 3
 SLIDE_NONE, SLIDE_GAUSS_LNCOSH, SLIDE_PLATE_EXP, SLIDE_QUARTIC = 0, 1, 2, 3
 CRIT_GLOBAL, CRIT_HYDROSTATIC, CRIT_ETA_D, CRIT_ETA_X, CRIT_U, CRIT_U_X, CRIT_W, CRIT_W_X = range(8)
-SOLVER_AUTO, SOLVER_CG, SOLVER_BICGSTAB, SOLVER_DENSE = 0, 1, 2, 3
+SOLVER_AUTO, SOLVER_CG, SOLVER_BICGSTAB, SOLVER_DENSE, SOLVER_BANDED = 0, 1, 2, 3, 4
 GUESS_ZERO, GUESS_PREV = 0, 1
 OK, NOT_CONVERGED, BAD_ARG, SINGULAR = 0, 1, 2, 3
 

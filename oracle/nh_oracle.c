@@ -581,6 +581,83 @@ static int solve_dense(const or_params* P, const unsigned char* mask, const doub
     return status;
 }
 
+/* Direct solve of the tridiagonal active block: Gaussian elimination with
+   partial pivoting in band form (a row interchange gives U a second
+   superdiagonal; Golub & Van Loan, band Gaussian elimination with pivoting).
+   The three diagonals are read off the operator itself: or_apply on the
+   vector that is 1 on every third cell (offset s = 0, 1, 2) gives, in row i,
+   the entry of the one column of that colour among i-1, i, i+1.  Inactive
+   rows become identity rows (zero right-hand side).  Walls, or a periodic
+   grid whose two end cells are not both active (no coupling across the
+   wrap); OR_BAD_ARG otherwise. */
+static int solve_banded(const or_params* P, const unsigned char* mask, const double* Kf,
+                        const double* gam, const double* R, double* x, or_step_info* info)
+{
+    int n = P->nx;
+    if (P->bc == OR_BC_PERIODIC && mask[0] && mask[n - 1]) return OR_BAD_ARG;
+    double* lo = calloc(n, sizeof(double));
+    double* di = calloc(n, sizeof(double));
+    double* up = calloc(n, sizeof(double));
+    double* up2 = calloc(n, sizeof(double));
+    double* b = calloc(n, sizeof(double));
+    double* e = calloc(n, sizeof(double));
+    double* y = calloc(n, sizeof(double));
+    for (int s = 0; s < 3; ++s) {
+        for (int i = 0; i < n; ++i) e[i] = (i % 3 == s) ? 1.0 : 0.0;
+        or_apply(P, mask, Kf, gam, e, y);
+        for (int i = 0; i < n; ++i) {
+            if (!mask[i]) continue;
+            if (i % 3 == s) di[i] = y[i];
+            else if (i - 1 >= 0 && (i - 1) % 3 == s) lo[i] = y[i];
+            else if (i + 1 < n && (i + 1) % 3 == s) up[i] = y[i];
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        if (mask[i]) b[i] = R[i];
+        else { lo[i] = 0.0; di[i] = 1.0; up[i] = 0.0; b[i] = 0.0; }
+    }
+    int status = OR_OK;
+    for (int c = 0; c < n; ++c) {
+        /* row c holds columns c, c+1, c+2 in di, up, up2; row c+1 holds
+           columns c, c+1, c+2 in lo, di, up */
+        if (c + 1 < n && fabs(lo[c + 1]) > fabs(di[c])) {
+            double r0 = di[c], r1 = up[c];
+            di[c] = lo[c + 1]; up[c] = di[c + 1]; up2[c] = up[c + 1];
+            lo[c + 1] = r0; di[c + 1] = r1; up[c + 1] = 0.0;
+            double tb = b[c]; b[c] = b[c + 1]; b[c + 1] = tb;
+        }
+        if (di[c] == 0.0) { status = OR_SINGULAR; break; }
+        if (c + 1 < n) {
+            double f = lo[c + 1] / di[c];
+            di[c + 1] -= f * up[c];
+            up[c + 1] -= f * up2[c];
+            b[c + 1] -= f * b[c];
+            lo[c + 1] = 0.0;
+        }
+    }
+    if (status == OR_OK) {
+        for (int c = n - 1; c >= 0; --c) {
+            double s = b[c];
+            if (c + 1 < n) s -= up[c] * x[c + 1];
+            if (c + 2 < n) s -= up2[c] * x[c + 2];
+            x[c] = s / di[c];
+        }
+        for (int i = 0; i < n; ++i) if (!mask[i]) x[i] = 0.0;
+        or_apply(P, mask, Kf, gam, x, y);
+        double rr = 0.0, bb = 0.0;
+        for (int i = 0; i < n; ++i)
+            if (mask[i]) { rr += (R[i] - y[i]) * (R[i] - y[i]); bb += R[i] * R[i]; }
+        info->rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    } else {
+        for (int i = 0; i < n; ++i) x[i] = 0.0;
+        info->rel_res = 0.0;
+    }
+    info->iters = 1;
+    info->solver_used = OR_SOLVER_BANDED;
+    free(lo); free(di); free(up); free(up2); free(b); free(e); free(y);
+    return status;
+}
+
 int or_solve(const or_params* P, const unsigned char* mask,
              const double* Kf, const double* gam, const double* R,
              double* q, or_step_info* info)
@@ -601,6 +678,7 @@ int or_solve(const or_params* P, const unsigned char* mask,
     if (kind == OR_SOLVER_CG) return solve_cg(P, mask, Kf, gam, R, q, info);
     if (kind == OR_SOLVER_BICGSTAB) return solve_bicgstab(P, mask, Kf, gam, R, q, info);
     if (kind == OR_SOLVER_DENSE) return solve_dense(P, mask, Kf, gam, R, q, info);
+    if (kind == OR_SOLVER_BANDED) return solve_banded(P, mask, Kf, gam, R, q, info);
     return OR_BAD_ARG;
 }
 

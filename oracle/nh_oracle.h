@@ -48,8 +48,11 @@ enum { OR_SLIDE_NONE = 0, OR_SLIDE_GAUSS_LNCOSH = 1, OR_SLIDE_PLATE_EXP = 2, OR_
 enum { OR_CRIT_GLOBAL = 0, OR_CRIT_HYDROSTATIC = 1, OR_CRIT_ETA_D = 2,
        OR_CRIT_ETA_X = 3, OR_CRIT_U = 4, OR_CRIT_U_X = 5, OR_CRIT_W = 6,
        OR_CRIT_W_X = 7 };
+/* DENSE: Gaussian elimination with partial pivoting on the dense active
+   block (tiny grids); BANDED: the same elimination in tridiagonal band form
+   (any size; walls, or periodic without an active pair across the wrap). */
 enum { OR_SOLVER_AUTO = 0, OR_SOLVER_CG = 1, OR_SOLVER_BICGSTAB = 2,
-       OR_SOLVER_DENSE = 3 };
+       OR_SOLVER_DENSE = 3, OR_SOLVER_BANDED = 4 };
 enum { OR_GUESS_ZERO = 0, OR_GUESS_PREV = 1 };
 enum { OR_OK = 0, OR_NOT_CONVERGED = 1, OR_BAD_ARG = 2, OR_SINGULAR = 3 };
 

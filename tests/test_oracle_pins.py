@@ -296,6 +296,70 @@ def test_krylov_matches_dense_lu(bc):
             assert np.max(np.abs(q - ref)) <= 1e-11 * scale, kind
 
 
+def test_banded_direct_solve_matches_dense_and_numpy():
+    """The banded elimination equals the dense elimination and numpy's solve
+    on random masks of tiny grids (walls; periodic without an active pair
+    across the wrap), including a pivoting case (a negative reaction term
+    that makes a diagonal small), and refuses a periodic wrap coupling."""
+    for bc in (O.BC_WALL, O.BC_PERIODIC):
+        p, d0, st, (Kf, gam, R), rng = _random_problem(nx=48, bc=bc)
+        for trial in range(6):
+            m = (rng.random(p.nx) < 0.7).astype(np.uint8)
+            if bc == O.BC_PERIODIC:
+                m[0] = 0
+            g2 = gam.copy()
+            if trial >= 3:
+                act = np.flatnonzero(m)
+                g2[act[len(act) // 2]] = -2.0 * abs(g2[act[len(act) // 2]]) - 2.0 * Kf[act[len(act) // 2]] / p.dx ** 2
+            idx = np.flatnonzero(m)
+            A = np.zeros((len(idx), len(idx)))
+            for l, j in enumerate(idx):
+                e = np.zeros(p.nx); e[j] = 1.0
+                A[:, l] = O.apply(p, m, Kf, g2, e)[idx]
+            ref = np.linalg.solve(A, R[idx])
+            p.solver = O.SOLVER_DENSE
+            qd, sd, _ = O.solve(p, m, Kf, g2, R)
+            p.solver = O.SOLVER_BANDED
+            qb, sb, info = O.solve(p, m, Kf, g2, R)
+            assert sd == O.OK and sb == O.OK and info["solver_used"] == O.SOLVER_BANDED
+            assert np.all(qb[m == 0] == 0)
+            scale = np.max(np.abs(ref))
+            assert np.max(np.abs(qb[idx] - ref)) <= 1e-11 * scale
+            assert np.max(np.abs(qb - qd)) <= 1e-11 * scale
+        m = np.ones(p.nx, dtype=np.uint8)
+        p.solver = O.SOLVER_BANDED
+        _, sb, _ = O.solve(p, m, Kf, gam, R)
+        assert sb == (O.BAD_ARG if bc == O.BC_PERIODIC else O.OK)
+
+
+def test_banded_solve_on_the_benchmark_member():
+    """On a full 50 000-cell slide member (global mask, condition number near
+    1e6) the banded elimination is backward stable to a few ulps per row
+    and CG started from its solution stops at once."""
+    wl = W.slide_1d(n_members=1)
+    m = wl.members[0]
+    p = _params(m, crit=O.CRIT_GLOBAL, solver=O.SOLVER_BANDED)
+    ht, hut, hwt = O.predict(p, m.d0, 0.0, wl.dt, m.h, m.hu, m.hw)
+    Kf, gam, R = O.assemble(p, m.d0, wl.dt, wl.dt, ht, hut, hwt)
+    mk = np.ones(m.nx, dtype=np.uint8)
+    q, st, info = O.solve(p, mk, Kf, gam, R)
+    assert st == O.OK
+    r = R - O.apply(p, mk, Kf, gam, q)
+    # componentwise backward error |r| <= c eps |A| |q| (Oettli-Prager), with
+    # |A| |q| from the three-point rows: (K_l + K_r)/dx^2 + |gamma| on the
+    # diagonal, K_l/dx^2 and K_r/dx^2 off it (K > 0)
+    aq = ((Kf[:-1] + Kf[1:]) / m.dx ** 2 + np.abs(gam)) * np.abs(q)
+    aq[1:] += Kf[1:-1] / m.dx ** 2 * np.abs(q[:-1])
+    aq[:-1] += Kf[1:-1] / m.dx ** 2 * np.abs(q[1:])
+    assert np.max(np.abs(r) / aq) <= 64 * np.finfo(float).eps
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(R)
+    assert abs(info["rel_res"] - np.linalg.norm(r) / np.linalg.norm(R)) <= 1e-3 * info["rel_res"]
+    p.solver = O.SOLVER_CG
+    p.rtol = 1e-10
+    q2, st, info = O.solve(p, mk, Kf, gam, R, q0=q)
+    assert st == O.OK and info["iters"] == 0
+
+
 def test_flat_bottom_reduction():
     """Flat static bottom: the elliptic equation reduces to
     -(q_x / h)_x + 3 q / h^3 = (rho/dt)(-u_x - 2 hw / h^2) (Eqs. 12-13 with
