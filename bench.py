@@ -1,19 +1,22 @@
 """Benchmark: cell-updates/s of the adaptive non-hydrostatic step, including the
-elliptic solve, on the 1D moving-bottom slide batch (64 members x 50 000
-cells, plane slope tan = 0.25 from 0.05 m to 1 m, Gaussian mound moving as
-s0 ln cosh(t/t0), per-member A, L, s0 drawn +-30 %).
+elliptic solve, at a measured error against the FP64 oracle.
 
-One "step" is one time step of the whole batch: predictor, criterion and mask,
-assembly, preconditioned Krylov solve on the active cells, correction.  The
-state is first advanced (untimed) to --t-start so the timed steps see a
-developed wave field; then --warmup steps, then --steps timed steps bracketed
-by a barrier and stream synchronisation, timed with CUDA events on the
-library's stream.  The per-step state (~154 MB in FP64) exceeds the 129 MB L2,
-so no L2 flush is done between steps.
+Default workload: the ensemble of 32 uneven 2D landslide runs (grids of
+256^2 to 1024^2 cells, 1.58e7 cells in all; plane slopes, elliptic Gaussian
+slides moving as s0 ln cosh(t/t0), parameters drawn per member), adaptive
+|eta/d| > 1e-3 with the Moore enlargement, FP32 state with the FP64
+multigrid-preconditioned solve.  One "step" is one time step of every
+member: bottom, two Heun stages, criterion and mask, compaction, assembly,
+Krylov solve on the active cells, correction.  The state is advanced
+(untimed) --spin-steps steps from still water at t = 0.3 s, then --warmup
+steps, then --steps timed steps bracketed by a barrier and stream
+synchronisation and timed with CUDA events on the handle's stream (the
+state, 4 fields per cell, exceeds the 129 MB L2, so no flush is needed).
+--workload slide_1d runs the 1D slide batch (64 members x 50 000 cells).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun each rank runs its own 64-member batch (seeds offset by rank):
-weak scaling, no collective on the data path.
+Under torchrun each rank runs its own ensemble (weak scaling, no collective
+on the data path).
 """
 from __future__ import annotations
 
@@ -21,6 +24,7 @@ import argparse
 import json
 import math
 import os
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -334,56 +338,186 @@ def _landslide_h(wl, t):
     return wl.d0 - sl["A"] * np.exp(-((X - sl["xc0"] - s) / sl["Lx"]) ** 2 - ((Y - sl["yc0"]) / sl["Ly"]) ** 2)
 
 
-def run_2d(args):
-    """The 2D workloads (not the default line): --workload line_soliton_2d
-    (1024^2 line soliton, periodic, a/h = 0.2), landslide_2d (2048^2 slide on
-    a 0.2 slope, walls) or landslide_ensemble_2d (32 uneven landslide runs of
-    256^2 to 1024^2 cells with drawn slope, A, L, s0, one handle), adaptive
-    |eta/d| > k (or --mode global), FP64, cell-updates/s over --steps timed
-    steps (captured-graph replays) after --warmup; a second pass of the same
-    steps enqueued step by step from the host is reported beside it."""
-    import torch
-    from paper_2505_17025_gb300 import nhswe as N
+def _workload_2d(args):
+    """(members, dt, description, k_nh, t_start) of a 2D workload."""
     from paper_2505_17025_gb300 import workloads as W
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
+    knh = args.knh or 1e-3
     if args.workload == "line_soliton_2d":
-        wls = [W.line_soliton_2d()]
-        dt = wls[0].dt
-        knh, t_start = 1e-3, 0.0
-        name = f"line_soliton_2d {wls[0].nx}x{wls[0].ny}, dx {wls[0].dx}"
-    elif args.workload == "landslide_2d":
-        wls = [W.landslide_2d()]
-        dt = wls[0].dt
-        knh, t_start = 1e-4, 0.3
-        name = f"landslide_2d {wls[0].nx}x{wls[0].ny}, dx {wls[0].dx}"
-    else:
-        wls, dt = W.landslide_ensemble_2d()
-        knh, t_start = 1e-4, 0.3
-        name = (f"landslide_ensemble_2d: {len(wls)} runs, nx, ny drawn from 256..1024 (step 64), dx 0.02 m, "
-                f"tan(theta) U(0.1,0.3), A U(0.05,0.15), Lx U(0.5,1.5), s0 U(1,3); member m seeded with m")
+        w = W.line_soliton_2d()
+        return [w], w.dt, f"line_soliton_2d {w.nx}x{w.ny}, dx {w.dx} m, periodic, a/h 0.2", knh, 0.0
+    if args.workload == "landslide_2d":
+        w = W.landslide_2d()
+        return [w], w.dt, f"landslide_2d {w.nx}x{w.ny}, dx {w.dx} m, slope 0.2, walls", knh, 0.3
+    _, rank, _ = _dist()
+    wls, dt = W.landslide_ensemble_2d(seed0=rank_seed0(32, rank))
+    return (wls, dt, f"landslide_ensemble_2d: {len(wls)} runs, nx, ny drawn from 256..1024 (step 64), dx 0.02 m, "
+            f"tan(theta) U(0.1,0.3), A U(0.05,0.15), Lx U(0.5,1.5), s0 U(1,3); member m seeded with m "
+            f"(+ 32 x rank)",
+            knh, 0.3)
+
+
+def _initial_2d(w, t_start):
+    """Member's state at t_start: the workload's own, or still water over the slide."""
+    return (_landslide_h(w, t_start) if w.slide else w.h), w.hu, w.hv, w.hw
+
+
+def _save_member(path, w, fields):
+    sl = w.slide or {}
+    np.savez(path, h=fields[0], hu=fields[1], hv=fields[2], hw=fields[3], d0=w.d0,
+             geo=np.array([w.nx, w.ny, w.bc_x, w.bc_y], dtype=np.int64), sp=np.array([w.dx, w.dy]),
+             slide=np.array([1.0 if w.slide else 0.0] + [float(sl.get(k, 0.0)) for k in
+                                                         ("A", "Lx", "Ly", "xc0", "yc0", "s0", "t0")]),
+             amp=np.array([w.amplitude]))
+
+
+def _oracle2d_job(job):
+    """Worker (a spawned process): the FP64 2D oracle on one member from a
+    handed-over state saved by _save_member.  job = (path, crit, k_nh, t0,
+    step0, dt, n_steps, checkpoints); returns (path, {step: (h, hu, hv, hw,
+    mask)}, seconds, cells x steps, iterations)."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import oracle as O
+    import oracle.oracle2d as O2
+    path, crit, knh, t0, step0, dt, n, checks = job[:8]
+    write_back = len(job) > 8 and job[8]
+    z = np.load(path)
+    nx, ny, bcx, bcy = (int(v) for v in z["geo"])
+    p = O2.Params2D(nx=nx, ny=ny, dx=float(z["sp"][0]), dy=float(z["sp"][1]), bcx=bcx, bcy=bcy, crit=crit,
+                    knh=knh, enlarge=1, rtol=1e-13)
+    sl = z["slide"]
+    if sl[0] > 0:
+        p.slide = O.SLIDE_GAUSS_LNCOSH
+        p.A, p.Lx, p.Ly, p.xc0, p.yc0, p.s0, p.t0 = (float(v) for v in sl[1:])
+    d0 = z["d0"]
+    s = O2.State2D(z["h"], z["hu"], z["hv"], z["hw"], z["q"] if "q" in z.files else None)
+    out, iters = {}, 0
+    t_begin = time.perf_counter()
+    for k in range(n):
+        st, info, mk = O2.step(p, d0, t0 + k * dt, step0 + k, dt, s, want_mask=True)
+        if st != O.OK:
+            raise RuntimeError(f"oracle {path} step {k}: status {st}")
+        iters += info["iters"]
+        if k + 1 in checks:
+            out[k + 1] = tuple(a.reshape(ny, nx).copy() for a in (s.h, s.hu, s.hv, s.hw)) + (mk.copy(),)
+    el = time.perf_counter() - t_begin
+    if write_back:
+        np.savez(path, h=s.h, hu=s.hu, hv=s.hv, hw=s.hw, q=s.q, d0=d0, geo=z["geo"], sp=z["sp"], slide=z["slide"],
+                 amp=z["amp"])
+    return path, out, el, nx * ny * n, iters
+
+
+def _pool(n):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(processes=n)
+
+
+def _ncores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _errors_2d(w, got, ref):
+    """max |d eta| / a and the momenta / (a sqrt(g h_max)) between two
+    (h, hu, hv, hw[, mask]) tuples of one member, and the mask cells that differ."""
+    a = w.amplitude
+    qs = a * math.sqrt(9.81 * float(np.max(w.d0)))
+    e = [float(np.max(np.abs(got[0] - ref[0]))) / a]
+    e += [float(np.max(np.abs(got[q] - ref[q]))) / qs for q in (1, 2, 3)]
+    return e
+
+
+def _grid_2d(N, wls, precision, crit, knh, precond, t, states):
     G = N.Grid2D.ensemble([dict(nx=w.nx, ny=w.ny, dx=w.dx, dy=w.dy, d0=w.d0, bc_x=w.bc_x, bc_y=w.bc_y)
                            for w in wls])
-    if args.precision == "mixed":
-        raise SystemExit("2D grids: --precision fp64 or mixed64 (FP32 state, FP64 solve)")
-    if args.precision == "mixed64":
+    if precision == "mixed64":
         G.set_precision(N.NH_MIXED_FP64_SOLVE)
     for i, w in enumerate(wls):
-        h = w.h
         if w.slide:
             G.set_bottom_motion(w.slide, member=i)
-            h = _landslide_h(w, t_start)
-        G.set_state(h, w.hu, w.hv, w.hw, t=t_start, member=i)
-    G.set_criterion(N.NH_CRIT_GLOBAL if args.mode == "global" else N.NH_CRIT_ETA_D, knh, 1)
+        G.set_state(*states[i][:4], t=t, member=i)
+    G.set_criterion(crit, knh, 1)
     G.set_solver(1e-12, 20000, N.NH_GUESS_PREV)
+    G.set_preconditioner(precond)
+    return G
+
+
+# Algorithmic bytes of the 2D kernel classes.  Predictor: the fused minimum
+# of a Heun step is to read Q^n and write Q~ once (4 fields each: 64 B per
+# cell in FP64, 32 B with FP32 state); the two stage launches of a step share
+# it, so one launch is credited half.  Krylov solve: per active cell and
+# iteration the fused CG minimum, 24 B in FP32, 48 B with FP64 vectors.  The
+# bottom (k2_depth) is in-register work in the minimum (0 B).
+BYTES_2D_STAGE = {"fp64": 32.0, "mixed64": 16.0}
+SOLVE_BYTES_PER_ITER = 48.0
+# FP64 FLOPs per cell of one stage, counted from the algorithm (central
+# slopes, each face once, no halo recompute): primitives 5, two faces of 82
+# (slopes 16, reconstruction 18, depths and discharges 6, wave speeds 9,
+# five flux components 33), cell update 55 (slopes and face thicknesses 18,
+# four rates 32, the stage 5 to 10).
+FLOPS_2D_STAGE_FP64 = 229.0
+
+
+def run_2d(args):
+    """The 2D workloads: --workload landslide_ensemble_2d (default; 32
+    uneven landslide runs of 256^2 to 1024^2 cells), landslide_2d (2048^2)
+    or line_soliton_2d (1024^2, periodic).  The state is advanced --spin-steps
+    untimed steps from t_start (still water over the slide at t = 0.3 s) so
+    the timed window sees a developed wave field, then --warmup steps, then
+    --steps timed steps replayed from the captured graph (CUDA events on the
+    handle's stream, nvidia-smi clocks sampled meanwhile).  Around the window:
+    the error against the FP64 oracle run from the same hand-off on sampled
+    members; a second, event-profiled pass for per-kernel times and the
+    roofline; an end-to-end pass through the C ABI with pinned host buffers;
+    the method's forms from the window's start (global FP64, adaptive FP64,
+    adaptive FP32 state, the line-preconditioned solve) with their own errors;
+    and the oracle timed on one host thread and on all host cores."""
+    import torch
+    from paper_2505_17025_gb300 import nhswe as N
+    import oracle as O
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    wls, dt, name, knh, t_start = _workload_2d(args)
+    crit = N.NH_CRIT_GLOBAL if args.mode == "global" else N.NH_CRIT_ETA_D
+    ocrit = O.CRIT_GLOBAL if args.mode == "global" else O.CRIT_ETA_D
+    precond = N.NH_PRECOND_LINE if args.precond == "line" else N.NH_PRECOND_MG
+    if args.precision == "mixed":
+        raise SystemExit("2D grids: --precision fp64 or mixed64 (FP32 state, FP64 solve)")
+    init = [_initial_2d(w, t_start) for w in wls]
+    G = _grid_2d(N, wls, args.precision, crit, knh, precond, t_start, init)
+    cells = sum(w.nx * w.ny for w in wls)
+    t_spin0 = time.perf_counter()
+    if args.spin_steps:
+        G.run(dt, args.spin_steps)
+    torch.cuda.synchronize()
+    t_spin = time.perf_counter() - t_spin0
     warm = max(3, args.warmup)
     G.run(dt, warm)
+    n_before = args.spin_steps + warm
+    t0 = t_start + n_before * dt
+    # hand-off at the window's start: every member's FP64 state
+    handoff = [G.get_state(i)[:4] for i in range(len(wls))]
+    order = sorted(range(len(wls)), key=lambda i: wls[i].nx * wls[i].ny)
+    sample = order[:max(1, min(args.err_members, len(wls)))]
+    tmpdir = tempfile.mkdtemp(prefix="nhbench")
+    paths = {}
+    for i in range(len(wls)):
+        paths[i] = os.path.join(tmpdir, f"m{i}.npz")
+        _save_member(paths[i], wls[i], handoff[i])
+
+    # ---- timed window
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    # profiler range = the timed steps (ncu --profile-from-start off)
     torch.cuda.profiler.start()
     e0.record(G.stream)
     st, info = G.run(dt, args.steps)
@@ -391,33 +525,259 @@ def run_2d(args):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
     graph_runs = G.graph_runs
-    # the same number of further steps enqueued from the host, for comparison
-    G.set_graphs(False)
-    torch.cuda.synchronize()
-    e0.record(G.stream)
+    final = {i: G.get_state(i)[:4] + (G.get_mask(i),) for i in sample}
+    value = ws * cells * args.steps / (ms * 1e-3)
+
+    # ---- the oracle from the same hand-off (sampled members), in worker processes
+    n_form = max(1, args.form_steps)
+    checks = sorted({args.steps, n_form})
+    jobs = [(paths[i], ocrit, knh, t0, n_before, dt, max(checks), set(checks)) for i in sample]
+    pool = _pool(min(len(jobs) + 1, _ncores()))
+    err_async = pool.map_async(_oracle2d_job, jobs)
+    jobs_g = [(paths[sample[0]], O.CRIT_GLOBAL, knh, t0, n_before, dt, n_form, {n_form})] if args.form_steps else []
+    err_g_async = pool.map_async(_oracle2d_job, jobs_g) if jobs_g else None
+
+    # ---- profiled pass: per-kernel device times (events on the handle's stream)
+    G.set_profiling(True)
     st2, info2 = G.run(dt, args.steps)
-    e1.record(G.stream)
-    torch.cuda.synchronize()
-    ms_host = e0.elapsed_time(e1)
-    cells = sum(w.nx * w.ny for w in wls)
-    out = {"metric": METRIC, "value": cells * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-           "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == "fp64" else "f32 state, f64 solve", "data": "synthetic",
-           "config": {"workload": name, "cells": cells, "members": len(wls), "mode": args.mode,
-                      "precision": args.precision,
-                      "k_nh": knh, "t_start": t_start, "dt": dt,
-                      "mean_active_cells_per_step": info["active_total"] / max(1, args.steps),
-                      "mean_krylov_iters_per_step": info["iters_total"] / max(1, args.steps),
-                      "l2": "state (4 x 8 B per cell) and solver arrays exceed the 129 MB L2; no flush"},
-           "clocks": clk,
-           "timed_region": f"nh2d_run: captured-graph replays ({graph_runs} graph run(s) so far)",
-           "host_enqueued": {"ms_per_step": ms_host / args.steps,
-                             "mean_krylov_iters_per_step": info2["iters_total"] / max(1, args.steps)}}
-    print(json.dumps(out))
+    prof = G.get_profile()
+    G.set_profiling(False)
+    iters_prof = info2["iters_total"] / max(1, args.steps)
+    act_prof = info2["active_total"] / max(1, args.steps)
+
+    # ---- end to end through the C ABI: pinned host state in, step, state out
+    e2e = None
+    if args.e2e_steps > 0:
+        hb = [[torch.empty(w.nx * w.ny, dtype=torch.float64, pin_memory=True) for _ in range(4)] for w in wls]
+        for i in range(len(wls)):
+            G.get_state_ptr(i, *(b.data_ptr() for b in hb[i]))
+        torch.cuda.synchronize()
+        tt0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            for i in range(len(wls)):
+                G.put_state_ptr(i, *(b.data_ptr() for b in hb[i]))
+            G.run(dt, 1)
+            for i in range(len(wls)):
+                G.get_state_ptr(i, *(b.data_ptr() for b in hb[i]))
+        el = time.perf_counter() - tt0
+        nbytes = 4 * 8 * cells
+        e2e = {"value": ws * cells * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
+               "path": "nh2d_put_member_state (pinned host, all members) + nh2d_run(1) + nh2d_get_member_state"}
     G.close()
+
+    # ---- the method's forms from the window's start (timed on the device)
+    forms = {}
+    if args.form_steps > 0:
+        flist = [("adaptive_fp64_mg", "fp64", crit, N.NH_PRECOND_MG),
+                 ("adaptive_fp32state_mg", "mixed64", crit, N.NH_PRECOND_MG),
+                 ("adaptive_fp64_line", "fp64", crit, N.NH_PRECOND_LINE),
+                 ("global_fp64_mg", "fp64", N.NH_CRIT_GLOBAL, N.NH_PRECOND_MG)]
+        for fname, prec, fcrit, fpc in flist:
+            F = _grid_2d(N, wls, prec, fcrit, knh, fpc, t0, handoff)
+            fe0 = torch.cuda.Event(enable_timing=True)
+            fe1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            fe0.record(F.stream)
+            _, finfo = F.run(dt, n_form)
+            fe1.record(F.stream)
+            torch.cuda.synchronize()
+            fms = fe0.elapsed_time(fe1) / n_form
+            forms[fname] = {"ms_per_step": fms, "cell_updates_per_s": cells / (fms * 1e-3),
+                            "krylov_iters_per_step": finfo["iters_total"] / n_form,
+                            "active_cells_per_step": finfo["active_total"] / n_form,
+                            "precision": "f64" if prec == "fp64" else "f32 state, f64 solve",
+                            "preconditioner": "multigrid" if fpc == N.NH_PRECOND_MG else "x-line",
+                            "steps": n_form, "first_solve_from_zero": True}
+            forms[fname]["_state"] = {i: F.get_state(i)[:4] + (F.get_mask(i),) for i in sample}
+            F.close()
+
+    # ---- errors against the oracle
+    ref = {}
+    for path, out, el, cu, it in err_async.get():
+        ref[path] = out
+    worst = [0.0] * 4
+    mask_diff = 0
+    per_member = {}
+    for i in sample:
+        r = ref[paths[i]][args.steps]
+        e = _errors_2d(wls[i], final[i], r)
+        d = int(np.sum(final[i][4] != r[4]))
+        mask_diff += d
+        worst = [max(u, v) for u, v in zip(worst, e)]
+        per_member[str(i)] = {"cells": wls[i].nx * wls[i].ny, "max_d_eta_over_a": e[0], "mask_cells_differ": d}
+    bound = 1e-9 if args.precision == "fp64" else 1e-4
+    error = {"max_d_eta_over_a": worst[0], "max_d_momentum_over_a_sqrt_gh": max(worst[1:]),
+             "bound": bound, "meets_bound": max(worst) <= bound, "mask_cells_differ": mask_diff,
+             "members": per_member, "steps": args.steps,
+             "how": (f"the FP64 2D oracle run from the GPU state handed over at the window's start "
+                     f"(t = {t0:.4f} s, step {n_before}) on the {len(sample)} smallest members, "
+                     f"the same {args.steps} steps; states compared cell for cell")}
+    if forms:
+        ref_g = {p: o for p, o, *_ in err_g_async.get()} if err_g_async else {}
+        for fname, rec in forms.items():
+            fstate = rec.pop("_state")
+            glob = fname.startswith("global")
+            ew, dm = 0.0, 0
+            for i in sample:
+                if glob:
+                    if i != sample[0]:
+                        continue
+                    r = ref_g[paths[i]][n_form]
+                else:
+                    r = ref[paths[i]][n_form]
+                e = _errors_2d(wls[i], fstate[i], r)
+                ew = max(ew, max(e))
+                dm += int(np.sum(fstate[i][4] != r[4]))
+            b = 1e-9 if rec["precision"] == "f64" else 1e-4
+            rec.update({"max_error_over_a": ew, "bound": b, "meets_bound": ew <= b, "mask_cells_differ": dm})
+        base = forms["global_fp64_mg"]["ms_per_step"]
+        speed = {k: base / v["ms_per_step"] for k, v in forms.items()}
+    pool.close()
+    pool.join()
+
+    # ---- roofline of the kernel class with the largest device time
+    peaks, peak_kind = _load_peaks()
+    mg = precond == N.NH_PRECOND_MG
+    name_k, (dms, dn) = max(((k, v) for k, v in prof.items() if v[1] > 0), key=lambda kv: kv[1][0])
+    t_launch = dms * 1e-3 / dn
+    kernel_name = {"solve": "k2_mg_pcg" if mg else "k_pcg_persistent", "stage": "k2_stage"}.get(name_k,
+                                                                                            f"k2_{name_k}")
+    if name_k == "stage" and args.precision == "fp64":
+        flops = FLOPS_2D_STAGE_FP64 * cells
+        ach = flops / t_launch / 1e12
+        pk = FP64_PEAK_GFLOPS / 1e3
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
+                "kernel": kernel_name, "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 pipe)",
+                "flops_per_launch": flops,
+                "hbm_frac": BYTES_2D_STAGE["fp64"] * cells / t_launch / 1e9 / peaks["hbm_gbs"]}
+    else:
+        if name_k == "stage":
+            bpl = BYTES_2D_STAGE[args.precision] * cells
+        elif name_k == "solve":
+            bpl = SOLVE_BYTES_PER_ITER * act_prof * iters_prof
+        else:
+            bpl = None
+        ach = bpl / t_launch / 1e9 if bpl else None
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": None, "kernel": kernel_name,
+                "peak_kind": peak_kind, "bytes_per_launch": bpl}
+    roof.update({"launches_per_step": dn / args.steps, "avg_launch_us": 1e6 * t_launch,
+                 "share_of_device_time": dms / max(1e-12, sum(v[0] for v in prof.values()))})
+    solve_ms = prof["solve"][0]
+    solve_info = {"ms_per_step": solve_ms / max(1, args.steps), "krylov_iters_per_step": iters_prof,
+                  "active_cells_per_step": act_prof,
+                  "bytes_per_active_cell_and_iteration": SOLVE_BYTES_PER_ITER,
+                  "achieved_gbs": (SOLVE_BYTES_PER_ITER * act_prof * iters_prof * args.steps
+                                   / max(solve_ms * 1e-3, 1e-12) / 1e9)}
+    stage_ms, stage_n = prof["stage"]
+    stage_info = {"ms_per_launch": stage_ms / max(1, stage_n),
+                  "achieved_gbs": BYTES_2D_STAGE[args.precision] * cells / max(stage_ms * 1e-3 / max(1, stage_n),
+                                                                               1e-12) / 1e9}
+
+    # ---- the oracle on the host cores, on the same window (hand-off at t0)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline_2d(wls, paths, order, ocrit, knh, t0, n_before, dt, args)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": warm, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 state, f64 solve",
+               "data": "synthetic",
+               "config": {"workload": name, "cells": cells, "members": len(wls), "mode": args.mode,
+                          "precision": args.precision,
+                          "preconditioner": "multigrid" if precond == N.NH_PRECOND_MG else "x-line",
+                          "k_nh": knh, "t_start": t_start, "spin_up_steps": args.spin_steps,
+                          "spin_up_s": t_spin, "window_t0": t0, "dt": dt,
+                          "mean_active_cells_per_step": info["active_total"] / max(1, args.steps),
+                          "mean_krylov_iters_per_step": info["iters_total"] / max(1, args.steps),
+                          "l2": "inputs larger than the 129 MB L2 (state 4 x 8 B x cells); no flush"},
+               "error_vs_oracle": error,
+               "roofline": roof, "solve": solve_info, "stage": stage_info, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": sum(n for _, n in prof.values()) + (2 * prof["solve"][1] if mg else 0),
+               "timed_region": f"nh2d_run replaying the captured step graph ({graph_runs} graph run(s))",
+               "clocks": clk,
+               "kernel_ms": {k: v[0] for k, v in prof.items() if v[1] > 0},
+               "kernel_launches": {k: v[1] for k, v in prof.items() if v[1] > 0}}
+        if forms:
+            out["forms"] = {"t0": t0, "forms": forms, "speedup_vs_global_fp64_mg": speed,
+                            "note": "each form from the FP64 state at the window's start; first solve from "
+                                    "a zero guess; errors against the oracle over the same steps"}
+        print(json.dumps(out))
+    shutil.rmtree(tmpdir, ignore_errors=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _cpu_baseline_2d(wls, paths, order, ocrit, knh, t0, step0, dt, args):
+    """The oracle as it stands on the window's hand-off: one host thread on
+    the smallest member, and every member at once on all host cores (one
+    process per member, up to the core count)."""
+    one = _oracle2d_job((paths[order[0]], ocrit, knh, t0, step0, dt, args.cpu_steps, set()))
+    v1 = one[3] / one[2]
+    nc = _ncores()
+    pool = _pool(min(nc, len(wls)))
+    t_begin = time.perf_counter()
+    res = pool.map(_oracle2d_job, [(paths[i], ocrit, knh, t0, step0, dt, 1, set()) for i in range(len(wls))])
+    el = time.perf_counter() - t_begin
+    pool.close()
+    pool.join()
+    cu = sum(r[3] for r in res)
+    return {"value": cu / el, "unit": UNIT, "cores": min(nc, len(wls)), "kind": "oracle",
+            "one_thread": {"value": v1, "cores": 1,
+                           "sample": f"member {order[0]} ({wls[order[0]].nx}x{wls[order[0]].ny}), "
+                                     f"{args.cpu_steps} steps from the window's start"},
+            "sample": (f"all {len(wls)} members, one time step from the window's hand-off (t = {t0:.4f} s), "
+                       f"one spawned process per member on {min(nc, len(wls))} of {nc} host cores; "
+                       f"FP64 C oracle as it stands")}
+
+
+def run_reference_2d(args):
+    """The oracle arm on the 2D workload: every member from the workload's own
+    start (t = 0.3 s, still water over each slide; the GPU arm's spin-up is
+    out of reach of the oracle in minutes), one process per member on the
+    host cores; --warmup untimed steps, then --steps timed steps (one step =
+    one time step of every member)."""
+    import oracle as O
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    wls, dt, name, knh, t_start = _workload_2d(args)
+    ocrit = O.CRIT_GLOBAL if args.mode == "global" else O.CRIT_ETA_D
+    tmpdir = tempfile.mkdtemp(prefix="nhref")
+    paths = []
+    for i, w in enumerate(wls):
+        paths.append(os.path.join(tmpdir, f"m{i}.npz"))
+        _save_member(paths[-1], w, _initial_2d(w, t_start))
+    nc = _ncores()
+    pool = _pool(min(nc, len(wls)))
+    if args.warmup:
+        pool.map(_oracle2d_job, [(p, ocrit, knh, t_start, 0, dt, args.warmup, set(), True) for p in paths])
+    t1 = t_start + args.warmup * dt
+    tb = time.perf_counter()
+    res = pool.map(_oracle2d_job, [(p, ocrit, knh, t1, args.warmup, dt, args.steps, set(), True) for p in paths])
+    el = time.perf_counter() - tb
+    pool.close()
+    pool.join()
+    shutil.rmtree(tmpdir, ignore_errors=True)
+    cells = sum(w.nx * w.ny for w in wls)
+    v = cells * args.steps / el
+    sample = (f"all {len(wls)} members, steps {args.warmup}..{args.warmup + args.steps - 1} from t = {t_start} s "
+              f"(still water over each slide), one spawned process per member on {min(nc, len(wls))} of {nc} "
+              f"host cores, FP64 C oracle as it stands")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name + " (oracle)", "cells": cells, "members": len(wls), "k_nh": knh,
+                   "t_start": t_start},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": min(nc, len(wls)), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
 def run_ours(args):
@@ -585,28 +945,46 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed64"])
+    ap.add_argument("--workload", default="landslide_ensemble_2d",
+                    choices=["landslide_ensemble_2d", "landslide_2d", "line_soliton_2d", "slide_1d"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed64"],
+                    help="fp64; mixed64 = FP32 state with the FP64 solve; mixed = FP32 Krylov in FP64 "
+                         "refinement (1D only).  Default: fp64 (1D), mixed64 (2D)")
     ap.add_argument("--mode", default="adaptive", choices=["adaptive", "global"])
-    ap.add_argument("--precond", default="line", choices=["line", "none"])
-    ap.add_argument("--t-start", type=float, default=0.5)
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--precond", default=None, choices=["line", "none", "mg"],
+                    help="1D: line (default) or none; 2D: mg (default) or line")
+    ap.add_argument("--t-start", type=float, default=0.5, help="1D: spin-up to this time (s)")
+    ap.add_argument("--spin-steps", type=int, default=200, help="2D: untimed steps before the warm-up")
+    ap.add_argument("--knh", type=float, default=None, help="criterion threshold of the 2D workloads (default 1e-3)")
+    ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=400)
+    ap.add_argument("--cpu-steps", type=int, default=None)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--members", type=int, default=64)
-    ap.add_argument("--workload", default="slide_1d", choices=["slide_1d", "line_soliton_2d", "landslide_2d", "landslide_ensemble_2d"])
-    ap.add_argument("--form-steps", type=int, default=30, help="timed steps per form (0: skip the comparison)")
+    ap.add_argument("--members", type=int, default=64, help="1D: members per GPU")
+    ap.add_argument("--err-members", type=int, default=2, help="2D: members checked against the oracle")
+    ap.add_argument("--form-steps", type=int, default=None, help="timed steps per form (0: skip the comparison)")
     ap.add_argument("--form-harvest", type=int, default=20)
     ap.add_argument("--form-train", type=int, default=200)
     args = ap.parse_args()
+    two_d = args.workload != "slide_1d"
+    if args.precision is None:
+        args.precision = "mixed64" if two_d else "fp64"
+    if args.precond is None:
+        args.precond = "mg" if two_d else "line"
+    if args.e2e_steps is None:
+        args.e2e_steps = 5 if two_d else 20
+    if args.cpu_steps is None:
+        args.cpu_steps = 2 if two_d else 400
+    if args.form_steps is None:
+        args.form_steps = 10 if two_d else 30
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
-        run_reference(args)
-    elif args.workload != "slide_1d":
+        run_reference_2d(args) if two_d else run_reference(args)
+    elif two_d:
         run_2d(args)
     else:
         run_ours(args)

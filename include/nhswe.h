@@ -79,7 +79,9 @@ enum { NH_GUESS_ZERO = 0, NH_GUESS_PREV = 1, NH_GUESS_CNN = 2 };
    cyclic reduction in FP32 (exact up to FP32 rounding on any active segment
    that fits in one block), inside a flexible (Polak-Ribiere) PCG whose
    vectors, dots and stopping test stay in the handle's precision. */
-enum { NH_PRECOND_NONE = 0, NH_PRECOND_LINE = 1 };
+/* NH_PRECOND_MG (2D grids only, nhswe2d.h): an aggregation multigrid V-cycle
+   in FP32 inside the same flexible PCG. */
+enum { NH_PRECOND_NONE = 0, NH_PRECOND_LINE = 1, NH_PRECOND_MG = 2 };
 enum { NH_SLIDE_NONE = 0, NH_SLIDE_GAUSS_LNCOSH = 1, NH_SLIDE_PLATE_EXP = 2, NH_SLIDE_QUARTIC = 3 };
 
 typedef struct {
@@ -288,14 +290,19 @@ nh_status nh_get_profile(nh_grid* g, double* ms, long long* launches);
    correction); each output must not alias its input.  slide: host pointer to
    the member's bottom motion, or NULL for a static bottom.  mass: host
    pointer receiving sum(h_out) dx, or NULL; when non-NULL the call
-   synchronises `stream`.  Geometry arguments as in nh_grid_desc (one member).
+   synchronises `stream`, so mass must be NULL while `stream` is being
+   captured (NH_ERR_ARG otherwise).  Geometry arguments as in nh_grid_desc
+   (one member); slide values must be finite.
    Limits: 8 <= nx <= NH_STATIC_MAX_CELLS, else NH_ERR_ARG.
    The scratch array (about 2.2 MB) is held by every GPU that loads the
    library until the process exits.  The first call on a device looks up the
    array's device address (cudaGetSymbolAddress) with that device current;
    make that first call before any stream capture.  All calls share the
    array, so calls that overlap on the GPU race; issue them on one stream.
-   Errors: NH_ERR_ARG, NH_ERR_CUDA. */
+   Errors: NH_ERR_ARG, NH_ERR_CUDA (also returned, with nothing launched,
+   when a CUDA error from earlier work is still pending).  With mass == NULL
+   the call reports launch errors only; a fault inside its kernels surfaces
+   at the caller's next synchronisation of `stream`. */
 #define NH_STATIC_MAX_CELLS 262144
 nh_status nh_predict_static(const double* h, const double* hu, const double* hw,
                             const double* d0, double* h_out, double* hu_out, double* hw_out,

@@ -11,9 +11,9 @@
  *     -div(K grad q) + gamma q = R,  K = (dt/rho)/h (I - grad d grad d^T / D),
  *     D = 4 + |grad d|^2, q = h p,
  * on the marked cells (q = 0 elsewhere and outside walled sides), discretised
- * with a symmetric 9-point stencil and solved by CG preconditioned with exact
- * x-line (tridiagonal) solves.  A problem that does not depend on y gives the
- * 1D method's result.
+ * with a symmetric 9-point stencil and solved by CG preconditioned with an
+ * aggregation multigrid V-cycle (or with exact x-line tridiagonal solves).
+ * A problem that does not depend on y gives the 1D method's result.
  *
  * Ensembles: one handle may hold n_members grids, each with its own size,
  * spacing, sides, static depth and slide (the drawn-parameter landslide runs
@@ -93,6 +93,19 @@ nh_status nh2d_set_criterion(nh_grid2d* g, int kind, double k_nh, int enlarge, i
    operator) is solved again by unpreconditioned BiCGStab. */
 nh_status nh2d_set_solver(nh_grid2d* g, double rtol, int max_iter, int guess);
 
+/* Preconditioner of the CG solve: NH_PRECOND_MG (default) or
+   NH_PRECOND_LINE.  MG: aggregation multigrid over the bounding box of each
+   member's active cells -- coarse cell (I, J) at level l gathers the fine
+   cells (i >> l, j >> l) = (I, J), Galerkin coarse operators (sums of the
+   children's 9-point rows), one damped-Jacobi sweep (omega 0.7) before and
+   after the coarse correction, 7 sweeps on the coarsest level (at most 16
+   cells), all in FP32 -- applied once per iteration of the FP64 flexible PCG.
+   LINE: exact x-line (tridiagonal) solves by cyclic reduction in FP32.  The
+   converged answer is the same (the preconditioner changes the iteration,
+   not the solution); members that fall back to BiCGStab (an indefinite
+   operator) use the line preconditioner.  Errors: NH_ERR_ARG. */
+nh_status nh2d_set_preconditioner(nh_grid2d* g, int kind);
+
 /* NH_FP64 (default) or NH_MIXED_FP64_SOLVE: the state is stored in FP32 as
    zeta = h - d0, hu, hv, hw (so eta = zeta + mound keeps its digits), the
    predictor and the criterion run in FP32, the assembly, the Krylov solve,
@@ -117,6 +130,18 @@ nh_status nh2d_set_state(nh_grid2d* g, const double* h, const double* hu, const 
 nh_status nh2d_set_member_state(nh_grid2d* g, int member, const double* h, const double* hu,
                                 const double* hv, const double* hw, double t);
 
+/* Replace member m's state with host values (same layout and units as
+   nh2d_set_member_state) and keep the time, the step count and the warm
+   start: the state a caller hands in between steps.  The copies are ordered
+   on the handle's stream and the call does not synchronise it, so the host
+   arrays must stay untouched until the next synchronising call (pinned
+   memory makes the copies asynchronous).  Values are not checked on the
+   host: a non-positive or non-finite thickness fails the next step
+   (NH_ERR_NONFINITE).  Errors: NH_ERR_ARG, NH_ERR_STATE (no state set yet),
+   NH_ERR_CUDA. */
+nh_status nh2d_put_member_state(nh_grid2d* g, int member, const double* h, const double* hu, const double* hv,
+                                const double* hw);
+
 /* Any pointer may be NULL.  p_nh: non-hydrostatic pressure of the last step
    (Pa; 0 on cells that were hydrostatic). */
 nh_status nh2d_get_state(nh_grid2d* g, double* h, double* hu, double* hv, double* hw, double* p_nh);
@@ -135,6 +160,21 @@ nh_status nh2d_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* info
 /* Member m's figures of the last step (n_active, iters, rel_res, min_gamma,
    solver, status) and the mass sum(h) dx dy of its new state. */
 nh_status nh2d_get_member_info(nh_grid2d* g, int member, nh_step_info* info);
+
+/* Kernel classes of nh2d_get_profile. */
+enum { NH2_K_KIN = 0, NH2_K_DEPTH, NH2_K_STAGE, NH2_K_MARKS, NH2_K_DILATE, NH2_K_COMPACT, NH2_K_ASSEMBLE,
+       NH2_K_MASS, NH2_K_SOLVE_INIT, NH2_K_SOLVE, NH2_K_SUMMARY, NH2_K_CLEAR, NH2_K_CORRECT, NH2_K_COUNT };
+
+/* 1: later steps are enqueued from the host (no graph replay) with a CUDA
+   event pair on the handle's stream around every launch, summed per kernel
+   class (NH2_K_SOLVE: the whole Krylov solve of a step, NH2_K_COMPACT: the
+   four compaction launches); 0: off.  Either call resets the totals. */
+nh_status nh2d_set_profiling(nh_grid2d* g, int enable);
+
+/* ms[NH2_K_COUNT]: device milliseconds per class since the last
+   nh2d_set_profiling; launches[NH2_K_COUNT]: launches (event pairs) per
+   class.  Errors: NH_ERR_ARG. */
+nh_status nh2d_get_profile(nh_grid2d* g, double* ms, long long* launches);
 
 /* Number of captured-graph runs nh2d_run has made (-1 for NULL). */
 long long nh2d_graph_runs(const nh_grid2d* g);

@@ -19,7 +19,7 @@
 #include <new>
 #include <vector>
 
-#include "nh_kernels2d.cuh"
+#include "nh_mg2d.cuh"
 #include "nhswe2d.h"
 
 using namespace nh;
@@ -66,14 +66,73 @@ struct nh_grid2d {
     Slide2* slides;
     Kin2* kin;
     TimeCtl* tc;
+    // multigrid preconditioner (nh_mg2d.cuh)
+    int precond;                                    // NH_PRECOND_LINE or NH_PRECOND_MG
+    int cpitch, mg_grid;
+    MgPlan* mg_plan;
+    MgJob* mg_jobs;
+    int* mg_njobs;
+    unsigned* mg_gbar;
+    double* mg_gpart;
+    float *mg_cf, *mg_z0, *mg_t0, *mg_cc, *mg_cb, *mg_cza, *mg_czb, *mg_ct;
+    // profiling (nh2d_set_profiling): event pairs around each launch on the
+    // handle's stream, folded into per-class totals at synchronisations
+    bool prof_on;
+    double prof_ms[NH2_K_COUNT];
+    long long prof_launches[NH2_K_COUNT];
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<int> prof_kind;
+    size_t prof_used;
     // captured step: graph[p] starts from state buffer p
     cudaGraphExec_t graph[2];
     bool graph_valid, use_graphs;
-    double graph_key[9];
+    double graph_key[10];
     long long graph_runs;
 };
 
 namespace {
+
+// Events around one launch of class `kind` when profiling and enqueuing on the
+// handle's own stream (never inside a capture).
+void prof2_pre(nh_grid2d* g, cudaStream_t st, int kind)
+{
+    if (!g->prof_on || st != g->stream) return;
+    g->prof_launches[kind] += 1;
+    const size_t need = 2 * (g->prof_used + 1);
+    while (g->prof_pool.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { g->prof_on = false; return; }
+        g->prof_pool.push_back(e);
+    }
+    if (g->prof_kind.size() < g->prof_used + 1) g->prof_kind.resize(g->prof_used + 1);
+    g->prof_kind[g->prof_used] = kind;
+    cudaEventRecord(g->prof_pool[2 * g->prof_used], st);
+}
+
+void prof2_post(nh_grid2d* g, cudaStream_t st)
+{
+    if (!g->prof_on || st != g->stream || g->prof_pool.size() < 2 * (g->prof_used + 1)) return;
+    cudaEventRecord(g->prof_pool[2 * g->prof_used + 1], st);
+    g->prof_used += 1;
+}
+
+// After a synchronisation of the handle's stream.
+void prof2_fold(nh_grid2d* g)
+{
+    for (size_t q = 0; q < g->prof_used; ++q) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g->prof_pool[2 * q], g->prof_pool[2 * q + 1]) == cudaSuccess)
+            g->prof_ms[g->prof_kind[q]] += ms;
+    }
+    g->prof_used = 0;
+}
+
+#define P2(kind, launch)          \
+    do {                          \
+        prof2_pre(g, st, kind);   \
+        launch;                   \
+        prof2_post(g, st);        \
+    } while (0)
 
 constexpr size_t kAlign2 = 256;
 constexpr int kPitchQuantum = 256;   // cells; keeps every member's slice 256-byte aligned
@@ -121,7 +180,23 @@ long long ens_pitch(int nb, const nh_grid2d_desc* descs)
 // Mass partial sums per member: about 4096 cells per 256-thread block.
 int mass_blocks(int pitch) { return std::max(1, std::min((pitch + 4095) / 4096, 512)); }
 
-size_t carve2(int nb, int pitch, nh_grid2d* g, char* base)
+// Coarse cells per member slot of the multigrid levels: the sum over levels
+// l = 1..kMgLevels of the member's grid coarsened l times, the largest member.
+int mg_cpitch(int nb, const nh_grid2d_desc* descs)
+{
+    long long mx = 0;
+    for (int b = 0; b < nb; ++b) {
+        long long t = 0;
+        for (int l = 1; l <= kMgLevels; ++l)
+            t += (long long)(((descs[b].nx - 1) >> l) + 1) * (((descs[b].ny - 1) >> l) + 1);
+        mx = std::max(mx, t);
+    }
+    return (int)((mx + kPitchQuantum - 1) / kPitchQuantum * kPitchQuantum);
+}
+
+constexpr int kMgMaxGrid = 4096;   // CTAs of the multigrid solve at most
+
+size_t carve2(int nb, int pitch, int cpitch, nh_grid2d* g, char* base)
 {
     const size_t T = (size_t)nb * pitch;
     const int maxch = (pitch + kChunk - 1) / kChunk;
@@ -157,7 +232,18 @@ size_t carve2(int nb, int pitch, nh_grid2d* g, char* base)
     G->mass_part = c.take<double>((size_t)nb * nmass); G->summary = c.take<Summary>(1);
     G->geos = c.take<Geo2>(nb); G->slides = c.take<Slide2>(nb); G->kin = c.take<Kin2>(2 * (size_t)nb);
     G->tc = c.take<TimeCtl>(1);
-    if (g) { g->maxch = maxch; g->maxpb = maxpb; g->nblk = nblk; g->nmass = nmass; }
+    const size_t CT = (size_t)nb * cpitch;
+    G->mg_plan = c.take<MgPlan>(nb);
+    G->mg_jobs = c.take<MgJob>((size_t)std::max(nb, kMgMaxGrid));
+    G->mg_njobs = c.take<int>(1);
+    G->mg_gbar = c.take<unsigned>(2 * (size_t)nb);
+    G->mg_gpart = c.take<double>(8 * (size_t)kMgMaxGrid);
+    G->mg_cf = c.take<float>(10 * T);
+    G->mg_z0 = c.take<float>(T); G->mg_t0 = c.take<float>(T);
+    G->mg_cc = c.take<float>(10 * CT);
+    G->mg_cb = c.take<float>(CT); G->mg_cza = c.take<float>(CT); G->mg_czb = c.take<float>(CT);
+    G->mg_ct = c.take<float>(CT);
+    if (g) { g->maxch = maxch; g->maxpb = maxpb; g->nblk = nblk; g->nmass = nmass; g->cpitch = cpitch; }
     return (c.off + kAlign2 - 1) / kAlign2 * kAlign2;
 }
 
@@ -214,10 +300,10 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     const size_t T = (size_t)g->nb * g->pitch;
     const size_t P = (size_t)g->pitch;
     const dim3 eg(g->egx, g->nb);
-    k2_kin<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slides, g->nb, t_n, t_n1, tc, g->kin);
+    P2(NH2_K_KIN, (k2_kin<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slides, g->nb, t_n, t_n1, tc, g->kin)));
     const TS* d0s = d0_storage<TS>(g);
-    k2_depth<TS><<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 0, P, g->d0, as<TS>(g->dn), tc);
-    k2_depth<TS><<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 1, P, g->d0, as<TS>(g->dn1), tc);
+    P2(NH2_K_DEPTH, (k2_depth<TS><<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 0, P, g->d0, as<TS>(g->dn), tc)));
+    P2(NH2_K_DEPTH, (k2_depth<TS><<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 1, P, g->d0, as<TS>(g->dn1), tc)));
     StageArgs<TS> sa1;
     sa1.geos = g->geos; sa1.pitch = P; sa1.d0s = d0s;
     sa1.h = as<TS>(g->q[cur][0]); sa1.hu = as<TS>(g->q[cur][1]); sa1.hv = as<TS>(g->q[cur][2]);
@@ -226,24 +312,24 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     sa1.k1h = as<TS>(g->k1[0]); sa1.k1u = as<TS>(g->k1[1]); sa1.k1v = as<TS>(g->k1[2]); sa1.k1w = as<TS>(g->k1[3]);
     sa1.oh = as<TS>(g->qs[0]); sa1.ohu = as<TS>(g->qs[1]); sa1.ohv = as<TS>(g->qs[2]); sa1.ohw = as<TS>(g->qs[3]);
     sa1.dt = dt; sa1.stage = 1; sa1.tc = tc;
-    k2_stage<TS><<<eg, kTX * kTY, 0, st>>>(sa1);
+    P2(NH2_K_STAGE, (k2_stage<TS><<<eg, kTX * kTY, 0, st>>>(sa1)));
     StageArgs<TS> sa2 = sa1;
     sa2.h = sa1.oh; sa2.hu = sa1.ohu; sa2.hv = sa1.ohv; sa2.hw = sa1.ohw; sa2.d = as<TS>(g->dn1);
     sa2.oh = as<TS>(g->q[nxt][0]); sa2.ohu = as<TS>(g->q[nxt][1]); sa2.ohv = as<TS>(g->q[nxt][2]);
     sa2.ohw = as<TS>(g->q[nxt][3]);
     sa2.stage = 2;
-    k2_stage<TS><<<eg, kTX * kTY, 0, st>>>(sa2);
+    P2(NH2_K_STAGE, (k2_stage<TS><<<eg, kTX * kTY, 0, st>>>(sa2)));
 
     if (all) CK2(cudaMemsetAsync(g->marks, 1, T, st));
     else if (g->crit == NH_CRIT_HYDROSTATIC) CK2(cudaMemsetAsync(g->marks, 0, T, st));
-    else k2_marks<TS><<<eg, 256, 0, st>>>(g->geos, P, sa2.oh, sa2.ohu, sa2.ohv, sa2.ohw, as<TS>(g->dn1), d0s,
-                                         g->crit, g->knh, g->marks);
-    k2_dilate<<<eg, 256, 0, st>>>(g->geos, P, g->marks, all ? 0 : g->enlarge, g->act, tc);
-    k2_count<<<dim3(g->nblk, g->nb), kCompact2, 0, st>>>(g->geos, P, g->act, g->nblk, g->bcnt);
-    k2_scan<<<g->nb, 1024, 0, st>>>(g->bcnt, g->nblk, g->boff, g->nact[lnew], g->ms, tc);
-    k2_emit<<<dim3(g->nblk, g->nb), kCompact2, 0, st>>>(g->geos, P, g->act, g->nblk, g->boff, g->list[lnew],
-                                                          g->inv, tc);
-    k_items<<<1, 1024, 0, st>>>(g->ms, g->nb, g->items, g->pitems, g->ctl);
+    else P2(NH2_K_MARKS, (k2_marks<TS><<<eg, 256, 0, st>>>(g->geos, P, sa2.oh, sa2.ohu, sa2.ohv, sa2.ohw,
+                                                           as<TS>(g->dn1), d0s, g->crit, g->knh, g->marks)));
+    P2(NH2_K_DILATE, (k2_dilate<<<eg, 256, 0, st>>>(g->geos, P, g->marks, all ? 0 : g->enlarge, g->act, tc)));
+    P2(NH2_K_COMPACT, (k2_count<<<dim3(g->nblk, g->nb), kCompact2, 0, st>>>(g->geos, P, g->act, g->nblk, g->bcnt)));
+    P2(NH2_K_COMPACT, (k2_scan<<<g->nb, 1024, 0, st>>>(g->bcnt, g->nblk, g->boff, g->nact[lnew], g->ms, tc)));
+    P2(NH2_K_COMPACT, (k2_emit<<<dim3(g->nblk, g->nb), kCompact2, 0, st>>>(g->geos, P, g->act, g->nblk, g->boff,
+                                                                             g->list[lnew], g->inv, tc)));
+    P2(NH2_K_COMPACT, (k_items<<<1, 1024, 0, st>>>(g->ms, g->nb, g->items, g->pitems, g->ctl)));
     CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
 
     Asm2Args<TS> aa;
@@ -258,8 +344,8 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     aa.c6 = g->c6; aa.cx = g->cx; aa.cy = g->cy; aa.phi = g->phi; aa.ddx = g->ddx; aa.ddy = g->ddy;
     aa.part = g->part; aa.cnt = g->cnt; aa.solver = NH_SOLVER_AUTO;
     aa.items = g->items; aa.ctl = g->ctl;
-    k2_assemble<TS><<<g->items_grid, kChunk, 0, st>>>(aa);
-    k2_mass<TS><<<dim3(g->nmass, g->nb), 256, 0, st>>>(g->geos, P, sa2.oh, g->d0, g->mass_part);
+    P2(NH2_K_ASSEMBLE, (k2_assemble<TS><<<g->items_grid, kChunk, 0, st>>>(aa)));
+    P2(NH2_K_MASS, (k2_mass<TS><<<dim3(g->nmass, g->nb), 256, 0, st>>>(g->geos, P, sa2.oh, g->d0, g->mass_part)));
     return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }
 
@@ -271,7 +357,7 @@ nh_status enqueue_back(nh_grid2d* g, cudaStream_t st, int nxt, int lprev, int ln
     ClearArgs cl;
     cl.nb = g->nb; cl.pitch = g->pitch; cl.maxlist = g->pitch;
     cl.list_prev = g->list[lprev]; cl.nact_prev = g->nact[lprev]; cl.psi = g->psi; cl.tc = tc;
-    k_clear_prev<<<(int)std::min<size_t>((T + 255) / 256, (size_t)g->sms * 8), 256, 0, st>>>(cl);
+    P2(NH2_K_CLEAR, (k_clear_prev<<<(int)std::min<size_t>((T + 255) / 256, (size_t)g->sms * 8), 256, 0, st>>>(cl)));
     Corr2Args<TS> co;
     co.geos = g->geos; co.pitch = g->pitch; co.list = g->list[lnew];
     co.nbl = g->nbl; co.nbr = g->nbr; co.ext_k = g->ext_k; co.ext_stride = T;
@@ -279,7 +365,7 @@ nh_status enqueue_back(nh_grid2d* g, cudaStream_t st, int nxt, int lprev, int ln
     co.ddx = g->ddx; co.ddy = g->ddy; co.ms = g->ms;
     co.hu = as<TS>(g->q[nxt][1]); co.hv = as<TS>(g->q[nxt][2]); co.hw = as<TS>(g->q[nxt][3]); co.psi = g->psi;
     co.items = g->items; co.ctl = g->ctl; co.tc = tc;
-    k2_correct<TS><<<g->items_grid, kChunk, 0, st>>>(co);
+    P2(NH2_K_CORRECT, (k2_correct<TS><<<g->items_grid, kChunk, 0, st>>>(co)));
     return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }
 
@@ -296,9 +382,45 @@ nh_status launch_persistent(nh_grid2d* g, SolveArgs<double>& sa, cudaStream_t st
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     long long budget = g->barrier_budget;
+    prof2_pre(g, st, NH2_K_SOLVE);
     CK2(cudaLaunchKernelEx(&cfg, k_pcg_persistent<double, float>, sa, budget));
+    prof2_post(g, st);
     return NH_OK;
 }
+
+// Multigrid-preconditioned CG of every member solving with CG (after
+// k_solve_init): plan the levels, split the members over the cooperative
+// grid, then the persistent solve.
+nh_status launch_mg(nh_grid2d* g, const SolveArgs<double>& sa, cudaStream_t st)
+{
+    prof2_pre(g, st, NH2_K_SOLVE);
+    k2_mg_box<<<g->nb, 1024, 0, st>>>(g->geos, g->ms, sa.list, g->pitch, g->mg_plan);
+    k2_mg_assign<<<1, 1024, 0, st>>>(g->ms, g->nb, g->mg_grid, g->mg_jobs, g->mg_njobs);
+    CK2(cudaMemsetAsync(g->mg_gbar, 0, 2 * sizeof(unsigned) * g->nb, st));
+    MgArgs m;
+    m.s = sa;
+    m.geos = g->geos; m.inv = g->inv; m.plan = g->mg_plan; m.jobs = g->mg_jobs; m.njobs = g->mg_njobs;
+    m.gbar = g->mg_gbar; m.gpart = g->mg_gpart;
+    m.cf = g->mg_cf; m.z0 = g->mg_z0; m.t0 = g->mg_t0;
+    m.cc = g->mg_cc; m.cb = g->mg_cb; m.cza = g->mg_cza; m.czb = g->mg_czb; m.ct = g->mg_ct;
+    m.T = (size_t)g->nb * g->pitch; m.CT = (size_t)g->nb * g->cpitch; m.cpitch = g->cpitch;
+    m.budget = g->barrier_budget;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g->mg_grid);
+    cfg.blockDim = dim3(kMgThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK2(cudaLaunchKernelEx(&cfg, k2_mg_pcg, m));
+    prof2_post(g, st);
+    return NH_OK;
+}
+
+bool use_mg(const nh_grid2d* g) { return g->precond == NH_PRECOND_MG && g->mg_grid > 0; }
 
 // One Krylov pass: set-up, then preconditioned CG in one cooperative launch,
 // and preconditioned BiCGStab driven from the host for members that need it.
@@ -307,19 +429,31 @@ nh_status krylov2_pass(nh_grid2d* g, SolveArgs<double>& sa)
     cudaStream_t st = g->stream;
     CK2(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
     CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
-    k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa);
+    P2(NH2_K_SOLVE_INIT, (k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa)));
     Ctl h;
     CK2(cudaMemcpyAsync(&h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK2(cudaStreamSynchronize(st));
+    prof2_fold(g);
     const size_t pcr_smem = 2 * sizeof(float) * (size_t)kPcrRows;
-    if (h.n_cg > 0 || h.n_bicg > 0)
-        k_pcr_factor<double, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa);
-    if (h.n_cg > 0) {
+    const bool mg = use_mg(g);
+    if ((h.n_cg > 0 && !mg) || h.n_bicg > 0)
+        P2(NH2_K_SOLVE, (k_pcr_factor<double, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa)));
+    if (h.n_cg > 0 && !mg) {
         sa.it = 0;
-        k_pcr<double, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG);
+        P2(NH2_K_SOLVE, (k_pcr<double, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG)));
     }
     if (h.not_done <= 0) return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
-    const bool coop_cg = h.n_cg > 0 && g->coop_grid > 0;
+    if (h.n_cg > 0 && mg) {
+        CK2(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
+        nh_status rc = launch_mg(g, sa, st);
+        if (rc != NH_OK) return rc;
+        int to = 0;
+        CK2(cudaMemcpyAsync(&to, &g->ctl->timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK2(cudaStreamSynchronize(st));
+        if (to) return NH_ERR_TIMEOUT;
+        if (h.n_bicg == 0) return NH_OK;
+    }
+    const bool coop_cg = h.n_cg > 0 && g->coop_grid > 0 && !mg;
     if (coop_cg) {
         CK2(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
         nh_status rc = launch_persistent(g, sa, st);
@@ -332,7 +466,7 @@ nh_status krylov2_pass(nh_grid2d* g, SolveArgs<double>& sa)
     }
     for (int it = 1; it <= g->max_iter; ++it) {
         sa.it = it;
-        if (h.n_cg > 0 && !coop_cg) {
+        if (h.n_cg > 0 && !coop_cg && !mg) {
             k_pcg_a<double><<<g->items_grid, kChunk, 0, st>>>(sa);
             k_pcr<double, float><<<g->pcr_grid, kPcrThreads, pcr_smem, st>>>(sa, PCR_PCG_STEP);
         }
@@ -400,10 +534,12 @@ nh_status step2(nh_grid2d* g, double dt, nh_step_info* info)
     SolveArgs<double> sa = solve_args2(g, lnew, gscale, nullptr);
     rc = krylov2(g, sa);
     if (rc != NH_OK) return rc;
-    k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->nmass, 1.0, g->summary, nullptr);
+    P2(NH2_K_SUMMARY, (k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->nmass, 1.0, g->summary,
+                                                  nullptr)));
     Summary S;
     CK2(cudaMemcpyAsync(&S, g->summary, sizeof(Summary), cudaMemcpyDeviceToHost, st));
     CK2(cudaStreamSynchronize(st));
+    prof2_fold(g);
     CK2(cudaGetLastError());
     const nh_status status = (nh_status)S.status;
     if (status == NH_OK) {
@@ -415,6 +551,10 @@ nh_status step2(nh_grid2d* g, double dt, nh_step_info* info)
         g->n_since += 1;
         g->steps += 1;
         g->last_dt = dt;
+        if (g->prof_on) {
+            CK2(cudaStreamSynchronize(st));
+            prof2_fold(g);
+        }
     }
     if (info) fill_info(g, S, status, status == NH_OK ? t_n1 : t_n, info);
     return status;
@@ -436,10 +576,15 @@ nh_status enqueue_graph_step(nh_grid2d* g, cudaStream_t st, int cur, int lprev, 
     CK2(cudaMemsetAsync(g->ctl, 0, 3 * sizeof(int), st));
     CK2(cudaMemsetAsync(g->cnt, 0, sizeof(int) * g->nb, st));
     k_solve_init<double><<<g->items_grid, kChunk, 0, st>>>(sa);
-    k_pcr_factor<double, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa);
-    k_pcr<double, float><<<g->pcr_grid, kPcrThreads, 2 * sizeof(float) * kPcrRows, st>>>(sa, PCR_PCG);
-    CK2(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
-    rc = launch_persistent(g, sa, st);
+    if (use_mg(g)) {
+        CK2(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
+        rc = launch_mg(g, sa, st);
+    } else {
+        k_pcr_factor<double, float><<<g->pcr_grid, kPcrThreads, 3 * sizeof(float) * kPcrRows, st>>>(sa);
+        k_pcr<double, float><<<g->pcr_grid, kPcrThreads, 2 * sizeof(float) * kPcrRows, st>>>(sa, PCR_PCG);
+        CK2(cudaMemsetAsync(&g->ctl->timeout, 0, 3 * sizeof(int), st));
+        rc = launch_persistent(g, sa, st);
+    }
     if (rc != NH_OK) return rc;
     k_summary<<<1, 256, 0, st>>>(g->ms, g->nb, g->mass_part, g->nb * g->nmass, 1.0, g->summary, g->tc);
     k_commit<<<1, 32, 0, st>>>(g->summary, g->tc);
@@ -449,7 +594,7 @@ nh_status enqueue_graph_step(nh_grid2d* g, cudaStream_t st, int cur, int lprev, 
 
 bool graph_eligible(const nh_grid2d* g, double dt)
 {
-    return g->use_graphs && g->coop_grid > 0 && g->cap_stream != nullptr &&
+    return g->use_graphs && !g->prof_on && g->coop_grid > 0 && g->cap_stream != nullptr &&
            !(g->first_global && g->steps == 0) && (g->last_dt == 0.0 || g->last_dt == dt);
 }
 
@@ -462,8 +607,8 @@ void graph_destroy(nh_grid2d* g)
 
 nh_status graph_prepare(nh_grid2d* g, double dt)
 {
-    const double key[9] = {dt, (double)g->crit, g->knh, (double)g->enlarge, g->rtol, (double)g->max_iter,
-                           (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->prec};
+    const double key[10] = {dt, (double)g->crit, g->knh, (double)g->enlarge, g->rtol, (double)g->max_iter,
+                            (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->prec, (double)g->precond};
     if (g->graph_valid && std::memcmp(key, g->graph_key, sizeof(key)) == 0) return NH_OK;
     graph_destroy(g);
     for (int p = 0; p < 2; ++p) {
@@ -534,7 +679,7 @@ size_t nh2d_ensemble_workspace_bytes(int n_members, const nh_grid2d_desc* descs)
 {
     const long long pitch = ens_pitch(n_members, descs);
     if (pitch == 0) return 0;
-    return carve2(n_members, (int)pitch, nullptr, nullptr);
+    return carve2(n_members, (int)pitch, mg_cpitch(n_members, descs), nullptr, nullptr);
 }
 
 size_t nh2d_workspace_bytes(const nh_grid2d_desc* desc) { return nh2d_ensemble_workspace_bytes(1, desc); }
@@ -546,7 +691,8 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
     *out = nullptr;
     const long long pitch = ens_pitch(n_members, descs);
     if (pitch == 0 || !d0_host || !ws) return NH_ERR_ARG;
-    const size_t need = carve2(n_members, (int)pitch, nullptr, nullptr);
+    const int cpitch = mg_cpitch(n_members, descs);
+    const size_t need = carve2(n_members, (int)pitch, cpitch, nullptr, nullptr);
     if (ws_bytes < need || ((uintptr_t)ws % kAlign2) != 0) return NH_ERR_ARG;
     for (int b = 0; b < n_members; ++b) {
         if (!d0_host[b]) return NH_ERR_ARG;
@@ -563,7 +709,9 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
     g->member_set.assign(n_members, 0);
     g->stream = static_cast<cudaStream_t>(stream);
     g->cap_stream = nullptr;
-    carve2(n_members, (int)pitch, g, static_cast<char*>(ws));
+    carve2(n_members, (int)pitch, cpitch, g, static_cast<char*>(ws));
+    g->precond = NH_PRECOND_MG;
+    g->mg_grid = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     g->sms = 1;
@@ -579,6 +727,8 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
     g->t_base = 0.0; g->last_dt = 0.0; g->n_since = 0; g->steps = 0; g->cur = 0; g->lcur = 0;
     g->graph[0] = g->graph[1] = nullptr;
     g->graph_valid = false; g->use_graphs = true; g->graph_runs = 0;
+    g->prof_on = false; g->prof_used = 0;
+    for (int k = 0; k < NH2_K_COUNT; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
     std::memset(g->graph_key, 0, sizeof(g->graph_key));
     nh_status rc = NH_OK;
     cudaStream_t st = g->stream;
@@ -599,6 +749,10 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
                                                                   kPcrThreads, pcr_smem) == cudaSuccess &&
             per_sm > 0)
             g->coop_grid = per_sm * g->sms;
+        per_sm = 0;
+        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_mg_pcg, kMgThreads, 0) == cudaSuccess &&
+            per_sm > 0)
+            g->mg_grid = std::min(per_sm * g->sms, kMgMaxGrid);
         int clk_khz = 0;
         cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
         g->barrier_budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL;   // about one second
@@ -698,6 +852,33 @@ nh_status nh2d_set_graphs(nh_grid2d* g, int on)
     return NH_OK;
 }
 
+nh_status nh2d_set_profiling(nh_grid2d* g, int enable)
+{
+    if (!g) return NH_ERR_ARG;
+    CK2(cudaStreamSynchronize(g->stream));
+    g->prof_used = 0;
+    g->prof_on = enable != 0;
+    for (int k = 0; k < NH2_K_COUNT; ++k) { g->prof_ms[k] = 0.0; g->prof_launches[k] = 0; }
+    return NH_OK;
+}
+
+nh_status nh2d_get_profile(nh_grid2d* g, double* ms, long long* launches)
+{
+    if (!g || !ms || !launches) return NH_ERR_ARG;
+    CK2(cudaStreamSynchronize(g->stream));
+    prof2_fold(g);
+    for (int k = 0; k < NH2_K_COUNT; ++k) { ms[k] = g->prof_ms[k]; launches[k] = g->prof_launches[k]; }
+    return NH_OK;
+}
+
+nh_status nh2d_set_preconditioner(nh_grid2d* g, int kind)
+{
+    if (!g || (kind != NH_PRECOND_LINE && kind != NH_PRECOND_MG)) return NH_ERR_ARG;
+    g->precond = kind;
+    graph_destroy(g);
+    return NH_OK;
+}
+
 nh_status nh2d_set_wait_budget(nh_grid2d* g, long long cycles)
 {
     if (!g || cycles < 0) return NH_ERR_ARG;
@@ -751,6 +932,31 @@ nh_status nh2d_set_member_state(nh_grid2d* g, int m, const double* h, const doub
     g->member_set[m] = 1;
     g->has_state = std::all_of(g->member_set.begin(), g->member_set.end(), [](char c) { return c != 0; });
     g->t_base = t; g->n_since = 0; g->steps = 0; g->last_dt = 0.0;
+    return NH_OK;
+}
+
+nh_status nh2d_put_member_state(nh_grid2d* g, int m, const double* h, const double* hu, const double* hv,
+                                const double* hw)
+{
+    if (!member_ok(g, m) || !h || !hu || !hv || !hw) return NH_ERR_ARG;
+    if (!g->has_state) return NH_ERR_STATE;
+    cudaStream_t st = g->stream;
+    const size_t N = (size_t)g->d[m].nx * g->d[m].ny;
+    const size_t mo = (size_t)m * g->pitch;
+    const double* src[4] = {h, hu, hv, hw};
+    if (g->prec == NH_FP64) {
+        for (int f = 0; f < 4; ++f)
+            CK2(cudaMemcpyAsync(g->q[g->cur][f] + mo, src[f], sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    } else {
+        for (int f = 0; f < 4; ++f)
+            CK2(cudaMemcpyAsync(g->qs[f] + mo, src[f], sizeof(double) * N, cudaMemcpyHostToDevice, st));
+        const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)g->sms * 8);
+        k2_store_f32<<<grid, 256, 0, st>>>((int)N, g->d0 + mo, g->qs[0] + mo, g->qs[1] + mo, g->qs[2] + mo,
+                                           g->qs[3] + mo, as<float>(g->q[g->cur][0]) + mo,
+                                           as<float>(g->q[g->cur][1]) + mo, as<float>(g->q[g->cur][2]) + mo,
+                                           as<float>(g->q[g->cur][3]) + mo);
+        CK2(cudaGetLastError());
+    }
     return NH_OK;
 }
 
@@ -899,6 +1105,7 @@ void nh2d_destroy(nh_grid2d* g)
     if (!g) return;
     cudaStreamSynchronize(g->stream);
     graph_destroy(g);
+    for (cudaEvent_t e : g->prof_pool) cudaEventDestroy(e);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
 }

@@ -103,14 +103,25 @@ extern "C" nh_status nh_predict_static(const double* h, const double* hu, const 
     if (limiter < NH_LIM_NONE || limiter > NH_LIM_MC) return NH_ERR_ARG;
     Slide s{0.0, 1.0, 0.0, 0.0, 1.0, 1.0, 0.0, NH_SLIDE_NONE, 0};
     if (slide && slide->shape >= NH_SLIDE_GAUSS_LNCOSH && slide->shape <= NH_SLIDE_QUARTIC) {
-        if (!(slide->L > 0.0) || !(slide->t0 > 0.0)) return NH_ERR_ARG;
-        if (slide->shape == NH_SLIDE_QUARTIC && !(slide->t2 >= slide->t0)) return NH_ERR_ARG;
+        if (!(slide->L > 0.0) || !(slide->t0 > 0.0) || !std::isfinite(slide->L) || !std::isfinite(slide->t0))
+            return NH_ERR_ARG;
+        if (!std::isfinite(slide->A) || !std::isfinite(slide->xc0) || !std::isfinite(slide->s0)) return NH_ERR_ARG;
+        if (slide->shape == NH_SLIDE_QUARTIC && !(slide->t2 >= slide->t0 && std::isfinite(slide->t2)))
+            return NH_ERR_ARG;
         s.A = slide->A; s.L = slide->L; s.iL = 1.0 / slide->L; s.xc0 = slide->xc0; s.s0 = slide->s0; s.t0 = slide->t0;
         s.t2 = slide->shape == NH_SLIDE_QUARTIC ? slide->t2 : 0.0;
         s.shape = slide->shape;
     } else if (slide && slide->shape != NH_SLIDE_NONE) {
         return NH_ERR_ARG;
     }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // reading the mass synchronises the stream, which a stream capture forbids
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return NH_ERR_CUDA;
+    if (mass && cap != cudaStreamCaptureStatusNone) return NH_ERR_ARG;
+    // an error left pending by earlier CUDA work is not this call's: refuse
+    // to launch rather than report (and clear) it as ours
+    if (cudaPeekAtLastError() != cudaSuccess) return NH_ERR_CUDA;
     unsigned char* base = nullptr;
     nh_status rc = scratch_base(&base);
     if (rc != NH_OK) return rc;
@@ -120,7 +131,6 @@ extern "C" nh_status nh_predict_static(const double* h, const double* hu, const 
     Slide* slide_dev = reinterpret_cast<Slide*>(base + kOffSlide);
     Kin* kin_dev = reinterpret_cast<Kin*>(base + kOffKin);
     double* sum_dev = reinterpret_cast<double*>(base + kOffSum);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     k_static_prepare<<<(nx + 255) / 256, 256, 0, st>>>(s, slide_dev, h, d0, z, nx);
     k_kinematics<<<1, 32, 0, st>>>(slide_dev, kin_dev, 1, t, t + dt);

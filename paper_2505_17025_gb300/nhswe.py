@@ -27,7 +27,7 @@ NH_LIM_NONE, NH_LIM_CENTRAL, NH_LIM_MINMOD, NH_LIM_MC = range(4)
  NH_CRIT_W, NH_CRIT_W_X) = range(8)
 NH_SOLVER_AUTO, NH_SOLVER_CG, NH_SOLVER_BICGSTAB = range(3)
 NH_GUESS_ZERO, NH_GUESS_PREV, NH_GUESS_CNN = 0, 1, 2
-NH_PRECOND_NONE, NH_PRECOND_LINE = 0, 1
+NH_PRECOND_NONE, NH_PRECOND_LINE, NH_PRECOND_MG = 0, 1, 2
 NH_SLIDE_NONE, NH_SLIDE_GAUSS_LNCOSH, NH_SLIDE_PLATE_EXP, NH_SLIDE_QUARTIC = 0, 1, 2, 3
 
 # every exported symbol of the ABI (checked by the CPU test suite)
@@ -43,10 +43,13 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh2d_run", "nh2d_destroy", "nh2d_ensemble_workspace_bytes", "nh2d_create_ensemble", "nh2d_members",
            "nh2d_set_member_bottom_motion", "nh2d_set_graphs", "nh2d_set_member_state", "nh2d_get_member_state",
            "nh2d_get_member_mask", "nh2d_get_member_info", "nh2d_graph_runs", "nh2d_set_precision",
-           "nh2d_set_wait_budget")
+           "nh2d_set_wait_budget", "nh2d_set_preconditioner", "nh2d_set_profiling", "nh2d_get_profile",
+           "nh2d_put_member_state")
 NH_CNN_PARAMS = 9328
 NH_CNN_IN = 16
 NH_STATIC_MAX_CELLS = 262144
+KERNEL_CLASSES_2D = ("kin", "depth", "stage", "marks", "dilate", "compact", "assemble", "mass", "solve_init",
+                     "solve", "summary", "clear", "correct")
 KERNEL_CLASSES = ("kinematics", "predict", "compact", "assemble", "solve_init", "precond", "pcg_a",
                   "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct",
                   "pcg_loop", "cnn")
@@ -136,6 +139,11 @@ def load():
         L.nh_set_run_mode.argtypes = [C.c_void_p, C.c_int]
         L.nh_set_wait_budget.argtypes = [C.c_void_p, C.c_longlong]
         L.nh2d_set_wait_budget.argtypes = [C.c_void_p, C.c_longlong]
+        L.nh2d_set_preconditioner.argtypes = [C.c_void_p, C.c_int]
+        L.nh2d_set_profiling.argtypes = [C.c_void_p, C.c_int]
+        L.nh2d_put_member_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.nh2d_put_member_state.restype = C.c_int
+        L.nh2d_get_profile.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
         L.nh_set_tile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
         L.nh_get_profile.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
         L.nh_get_mask.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), C.POINTER(C.c_int), _D]
@@ -200,7 +208,7 @@ def load():
         for f in ("nh_create_grid", "nh_create_ensemble", "nh_set_bottom_motion", "nh_set_criterion", "nh_set_solver",
                   "nh_set_preconditioner", "nh_put_state", "nh_set_profiling", "nh_get_profile",
                   "nh_set_run_mode", "nh_set_tile", "nh_set_wait_budget", "nh2d_set_wait_budget",
-                  "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run",
+                  "nh2d_set_preconditioner", "nh2d_set_profiling", "nh2d_get_profile", "nh_set_state", "nh_get_state", "nh_get_mask", "nh_step", "nh_run",
                   "nh_cnn_forward", "nh_cnn_loss_grad", "nh_cnn_adam", "nh_cnn_attach",
                   "nh_cnn_set_params", "nh_cnn_record", "nh_cnn_harvest", "nh_cnn_choices"):
             getattr(L, f).restype = C.c_int
@@ -603,6 +611,22 @@ class Grid2D:
         """Spin limit of the solver's grid barrier in SM clock cycles (0: about one second)."""
         _check(self.L.nh2d_set_wait_budget(self.h, int(cycles)), "nh2d_set_wait_budget")
 
+    def set_preconditioner(self, kind=NH_PRECOND_MG):
+        """NH_PRECOND_MG (default) or NH_PRECOND_LINE for the CG solve."""
+        _check(self.L.nh2d_set_preconditioner(self.h, int(kind)), "nh2d_set_preconditioner")
+
+    def set_profiling(self, enable=True):
+        """Event pairs around every launch of later (host-enqueued) steps."""
+        _check(self.L.nh2d_set_profiling(self.h, int(bool(enable))), "nh2d_set_profiling")
+
+    def get_profile(self):
+        """{class: (device ms, launches)} since the last set_profiling."""
+        ms = np.zeros(len(KERNEL_CLASSES_2D))
+        n = np.zeros(len(KERNEL_CLASSES_2D), dtype=np.int64)
+        _check(self.L.nh2d_get_profile(self.h, _dptr(ms), n.ctypes.data_as(C.POINTER(C.c_longlong))),
+               "nh2d_get_profile")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES_2D)}
+
     def set_precision(self, precision):
         """NH_FP64 or NH_MIXED_FP64_SOLVE (FP32 state); clears every member's state."""
         _check(self.L.nh2d_set_precision(self.h, int(precision)), "nh2d_set_precision")
@@ -617,6 +641,17 @@ class Grid2D:
         out = [np.empty(nx * ny) for _ in range(5)]
         _check(self.L.nh2d_get_member_state(self.h, int(member), *[_dptr(v) for v in out]), "nh2d_get_member_state")
         return [v.reshape(ny, nx) for v in out]
+
+    def put_state_ptr(self, member, h_ptr, hu_ptr, hv_ptr, hw_ptr):
+        """Member state from raw host addresses (e.g. pinned tensors), keeping time and warm start."""
+        _check(self.L.nh2d_put_member_state(self.h, int(member), C.c_void_p(h_ptr), C.c_void_p(hu_ptr),
+                                            C.c_void_p(hv_ptr), C.c_void_p(hw_ptr)), "nh2d_put_member_state")
+
+    def get_state_ptr(self, member, h_ptr, hu_ptr=0, hv_ptr=0, hw_ptr=0):
+        """Member state into raw host addresses (0 skips a field)."""
+        cast = lambda p: C.cast(C.c_void_p(p), _D) if p else None
+        _check(self.L.nh2d_get_member_state(self.h, int(member), cast(h_ptr), cast(hu_ptr), cast(hv_ptr),
+                                            cast(hw_ptr), None), "nh2d_get_member_state")
 
     def get_mask(self, member=0):
         ny, nx = self._shape(member)

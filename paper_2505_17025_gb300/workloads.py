@@ -290,17 +290,18 @@ def landslide_2d(n=2048, dx=0.02, h_min=0.1, h_max=2.0, slope=0.2, A=0.1, Lx=1.0
 
 def landslide_ensemble_2d(n_members=32, sizes=tuple(range(256, 1025, 64)), dx=0.02, h_min=0.1, h_max=2.0,
                           slope=(0.1, 0.3), A=(0.05, 0.15), L=(0.5, 1.5), s0=(1.0, 3.0), t0=1.0,
-                          d_start=0.6, x_frac_max=0.3, cfl=0.5, g=G):
+                          d_start=0.6, x_frac_max=0.3, cfl=0.5, g=G, seed0=0):
     """Ensemble of uneven 2D landslide runs: member m draws, from
     numpy.random.default_rng(m), nx and ny independently from `sizes`, the
     plane slope tan(theta), the mound amplitude A, its length Lx (Ly = Lx / 2)
     and run-out s0 uniformly from the given ranges; d0 = min(h_min + slope x,
     h_max) at spacing dx in x and y; the slide starts where d0 = d_start (at
     most x_frac_max of the basin length), centred in y; still water, walls.
-    One dt for all members: CFL cfl at depth h_max.  Returns (members, dt)."""
+    One dt for all members: CFL cfl at depth h_max.  Member m is drawn from
+    default_rng(seed0 + m).  Returns (members, dt)."""
     out = []
     for m in range(n_members):
-        rng = np.random.default_rng(m)
+        rng = np.random.default_rng(seed0 + m)
         nx = int(rng.choice(sizes))
         ny = int(rng.choice(sizes))
         sl_m = float(rng.uniform(*slope))
@@ -315,7 +316,7 @@ def landslide_ensemble_2d(n_members=32, sizes=tuple(range(256, 1025, 64)), dx=0.
         X, Y = np.meshgrid(x, y)
         h = d0 - A_m * np.exp(-((X - xc0) / Lx) ** 2 - ((Y - yc0) / (Lx / 2.0)) ** 2)
         z = np.zeros((ny, nx))
-        out.append(Workload2D(f"landslide_ens_{m}", nx, ny, dx, dx, d0, h, z, z.copy(), z.copy(), 0.0,
+        out.append(Workload2D(f"landslide_ens_{seed0 + m}", nx, ny, dx, dx, d0, h, z, z.copy(), z.copy(), 0.0,
                               amplitude=A_m,
                               slide=dict(A=A_m, Lx=Lx, Ly=Lx / 2.0, xc0=xc0, yc0=yc0, s0=s0_m, t0=t0),
                               meta={"h_min": h_min, "h_max": h_max, "slope": sl_m}))
