@@ -349,10 +349,10 @@ def _workload_2d(args):
         w = W.landslide_2d()
         return [w], w.dt, f"landslide_2d {w.nx}x{w.ny}, dx {w.dx} m, slope 0.2, walls", knh, 0.3
     _, rank, _ = _dist()
-    wls, dt = W.landslide_ensemble_2d(seed0=rank_seed0(32, rank))
+    wls, dt = W.landslide_ensemble_2d(n_members=args.ens_members, seed0=rank_seed0(args.ens_members, rank))
     return (wls, dt, f"landslide_ensemble_2d: {len(wls)} runs, nx, ny drawn from 256..1024 (step 64), dx 0.02 m, "
             f"tan(theta) U(0.1,0.3), A U(0.05,0.15), Lx U(0.5,1.5), s0 U(1,3); member m seeded with m "
-            f"(+ 32 x rank)",
+            f"(+ {args.ens_members} x rank)",
             knh, 0.3)
 
 
@@ -501,7 +501,7 @@ def run_2d(args):
     n_before = args.spin_steps + warm
     t0 = t_start + n_before * dt
     # hand-off at the window's start: every member's FP64 state
-    handoff = [G.get_state(i)[:4] for i in range(len(wls))]
+    handoff = [tuple(G.get_state(i)[:4]) for i in range(len(wls))]
     order = sorted(range(len(wls)), key=lambda i: wls[i].nx * wls[i].ny)
     sample = order[:max(1, min(args.err_members, len(wls)))]
     tmpdir = tempfile.mkdtemp(prefix="nhbench")
@@ -529,7 +529,7 @@ def run_2d(args):
         torch.distributed.barrier()
     ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
     graph_runs = G.graph_runs
-    final = {i: G.get_state(i)[:4] + (G.get_mask(i),) for i in sample}
+    final = {i: tuple(G.get_state(i)[:4]) + (G.get_mask(i),) for i in sample}
     value = ws * cells * args.steps / (ms * 1e-3)
 
     # ---- the oracle from the same hand-off (sampled members), in worker processes
@@ -593,8 +593,9 @@ def run_2d(args):
                             "precision": "f64" if prec == "fp64" else "f32 state, f64 solve",
                             "preconditioner": "multigrid" if fpc == N.NH_PRECOND_MG else "x-line",
                             "steps": n_form, "first_solve_from_zero": True}
-            forms[fname]["_state"] = {i: F.get_state(i)[:4] + (F.get_mask(i),) for i in sample}
+            forms[fname]["_state"] = {i: tuple(F.get_state(i)[:4]) + (F.get_mask(i),) for i in sample}
             F.close()
+            del F
 
     # ---- errors against the oracle
     ref = {}
@@ -780,6 +781,78 @@ def run_reference_2d(args):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def _ratio_cases():
+    """The paper's 1D cases with their own dx, dt and duration: the solitary
+    wave of Sec. 4.1 (a = 2 m, d = 10 m, 800 m, 200 cells, dt 0.1 s, 30 s),
+    the plate moved up and down (Sec. 4.2) and the sliding block at the three
+    Froude numbers (Sec. 4.3)."""
+    from paper_2505_17025_gb300 import workloads as W
+    sol = W.solitary_1d(nx=200, length=800.0, depth=10.0, a=2.0, T=30.0)
+    cases = [("solitary", sol, 0.1, 300), ("plate_up", W.plate_1d(up=True), None, None),
+             ("plate_down", W.plate_1d(up=False), None, None)]
+    for r, fr in enumerate(("0.125", "0.25", "0.375")):
+        cases.append((f"block_fr{fr}", W.block_1d(row=r), None, None))
+    return cases
+
+
+def run_paper_ratios(args):
+    """GPU wall time of the adaptive runs relative to the global run
+    (t_local / t_global) for the six criteria of Sec. 5.1, plain and enlarged
+    by one cell (Sec. 5.2), on the paper's 1D cases, beside the paper's
+    printed ratios.  Each run: the whole simulation from t = 0, replayed from
+    captured graphs, timed with CUDA events after one untimed capture run;
+    one member alone (latency-bound: about 1 000 cells), and a batch of
+    --members copies of it in one handle (the GPU loaded)."""
+    import copy
+    import torch
+    from paper_2505_17025_gb300 import nhswe as N
+    with open(os.path.join(ROOT, "tests", "golden", "paper_time_ratios.json")) as f:
+        paper = json.load(f)
+    crits = [("eta_d", N.NH_CRIT_ETA_D), ("eta_x", N.NH_CRIT_ETA_X), ("u", N.NH_CRIT_U),
+             ("u_x", N.NH_CRIT_U_X), ("w", N.NH_CRIT_W), ("w_x", N.NH_CRIT_W_X)]
+    out = {}
+    for name, wl, dt, n in _ratio_cases():
+        dt = dt or wl.dt
+        n = n or wl.n_steps
+        m0 = wl.members[0]
+        res = {}
+        for batch in (1, args.members):
+            wlb = copy.copy(wl)
+            wlb.members = [m0] * batch
+
+            def timed(crit, enlarge, first):
+                G = N.grid_from_workload(wlb)
+                G.set_criterion(crit, 1e-3, enlarge, first)
+                G.set_solver(N.NH_SOLVER_AUTO, 1e-12, 20000, N.NH_GUESS_PREV)
+                G.run(dt, 3)
+                G.set_state([m0.h] * batch, [m0.hu] * batch, [m0.hw] * batch, 0.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(G.stream)
+                st, info = G.run(dt, n)
+                e1.record(G.stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                share = info["active_total"] / float(m0.nx * batch * n)
+                G.close()
+                return ms, share
+
+            tg, _ = timed(N.NH_CRIT_GLOBAL, 1, False)
+            rec = {"global_ms": tg}
+            for key, enl in (("plain", 0), ("enlarged", 1)):
+                rows = {}
+                for ci, (cn, ck) in enumerate(crits):
+                    t, share = timed(ck, enl, cn in ("w", "w_x"))
+                    rows[cn] = {"gpu": t / tg, "active_share": share, "paper": paper[key][name][ci]}
+                rec[key] = rows
+            res[f"batch_{batch}"] = rec
+        out[name] = {"cells": m0.nx, "steps": n, "dt": dt, "runs": res}
+    print(json.dumps({"paper_time_ratios": out, "k_nh": 1e-3,
+                      "note": "t_local / t_global of whole runs on one GB300; the paper's ratios are "
+                              "from its own DG implementation on unstated hardware (context only)"}))
+
+
 def run_ours(args):
     import torch
     from paper_2505_17025_gb300 import nhswe as N
@@ -949,7 +1022,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="landslide_ensemble_2d",
-                    choices=["landslide_ensemble_2d", "landslide_2d", "line_soliton_2d", "slide_1d"])
+                    choices=["landslide_ensemble_2d", "landslide_2d", "line_soliton_2d", "slide_1d",
+                             "paper_ratios"])
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed64"],
                     help="fp64; mixed64 = FP32 state with the FP64 solve; mixed = FP32 Krylov in FP64 "
                          "refinement (1D only).  Default: fp64 (1D), mixed64 (2D)")
@@ -965,11 +1039,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--members", type=int, default=64, help="1D: members per GPU")
     ap.add_argument("--err-members", type=int, default=2, help="2D: members checked against the oracle")
+    ap.add_argument("--ens-members", type=int, default=32, help="2D ensemble: members (32 in the workload)")
     ap.add_argument("--form-steps", type=int, default=None, help="timed steps per form (0: skip the comparison)")
     ap.add_argument("--form-harvest", type=int, default=20)
     ap.add_argument("--form-train", type=int, default=200)
     args = ap.parse_args()
-    two_d = args.workload != "slide_1d"
+    two_d = args.workload not in ("slide_1d", "paper_ratios")
     if args.precision is None:
         args.precision = "mixed64" if two_d else "fp64"
     if args.precond is None:
@@ -982,7 +1057,9 @@ def main():
         args.form_steps = 10 if two_d else 30
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.workload == "paper_ratios":
+        run_paper_ratios(args)
+    elif args.impl == "reference":
         run_reference_2d(args) if two_d else run_reference(args)
     elif two_d:
         run_2d(args)
