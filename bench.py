@@ -64,18 +64,13 @@ BYTES_PER_UNIT_MIXED = {
     "pcg_loop": 84.0,     # per inner PCG iteration: 36 + 48
     "correct": 50.0,
 }
-# The FP64 predictor is bound by the FP64 pipe, not by HBM: its roofline is
-# FLOP/s against the FP64 peak.  FP64 FLOPs per cell and launch, from ncu's
-# executed-instruction counters (dadd + dmul + 2 dfma) on the 64 x 50000
-# batch ("profiles/k_predict_fp64_slide64x50k.md"); they include the two
-# stages' reciprocals and the tile halo.
-FLOPS_PER_CELL_FP64_PREDICT = 234.0
-# FP64 instructions per cell (dadd + dmul + dfma), same counters: the
-# issue-rate fraction (the pipe issues 2 FP64 instructions per clock per SM).
-INSTS_PER_CELL_FP64_PREDICT = 169.5
-# DRAM bytes per launch of that kernel from the same capture (null once the
-# kernel changes).
-TRAFFIC_FP64_PREDICT = 138246.7e3
+# The 1D FP64 predictor is bound by the FP64 pipe, not by HBM: its roofline is
+# FLOP/s against the FP64 peak.  FP64 FLOPs per cell and step counted from the
+# algorithm (each face once, no halo recompute, central slopes): per Heun
+# stage the primitives 4, one face 62 (slopes 12, reconstruction 12, depths
+# and discharges 6, wave speeds 9, four flux components 23), the cell update
+# 17 and the stage 7 to 9: 90 per stage.
+FLOPS_PER_CELL_FP64_PREDICT = 180.0
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x
 # 2 FLOP x 2.07 GHz (the nominal 1.25 TFLOP/s).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
@@ -446,11 +441,14 @@ def _grid_2d(N, wls, precision, crit, knh, precond, t, states):
 
 # Algorithmic bytes of the 2D kernel classes.  Predictor: the fused minimum
 # of a Heun step is to read Q^n and write Q~ once (4 fields each: 64 B per
-# cell in FP64, 32 B with FP32 state); the two stage launches of a step share
-# it, so one launch is credited half.  Krylov solve: per active cell and
+# cell in FP64, 32 B with FP32 state); the FP64 state's two stage launches
+# share it (one launch is credited half), the FP32 state's one-launch
+# predictor is credited all of it.  Krylov solve: per active cell and
 # iteration the fused CG minimum, 24 B in FP32, 48 B with FP64 vectors.  The
-# bottom (k2_depth) is in-register work in the minimum (0 B).
-BYTES_2D_STAGE = {"fp64": 32.0, "mixed64": 16.0}
+# bottom is in-register work in the minimum (0 B).
+BYTES_2D_STAGE = {"fp64": 32.0, "mixed64": 32.0}
+# Tile candidates of the one-launch FP32 predictor (nh2d_set_tile).
+PRED_TILES = ("32x16", "64x8", "32x8", "64x16")
 SOLVE_BYTES_PER_ITER = 48.0
 # FP64 FLOPs per cell of one stage, counted from the algorithm (central
 # slopes, each face once, no halo recompute): primitives 5, two faces of 82
@@ -529,6 +527,7 @@ def run_2d(args):
         torch.distributed.barrier()
     ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
     graph_runs = G.graph_runs
+    tile = G.set_tile(-1)
     final = {i: tuple(G.get_state(i)[:4]) + (G.get_mask(i),) for i in sample}
     value = ws * cells * args.steps / (ms * 1e-3)
 
@@ -693,6 +692,8 @@ def run_2d(args):
                "config": {"workload": name, "cells": cells, "members": len(wls), "mode": args.mode,
                           "precision": args.precision,
                           "preconditioner": "multigrid" if precond == N.NH_PRECOND_MG else "x-line",
+                          "predictor_tile": (PRED_TILES[tile] if args.precision == "mixed64" and tile >= 0
+                                             else "32x8 two-launch stages (FP64 state)"),
                           "k_nh": knh, "t_start": t_start, "spin_up_steps": args.spin_steps,
                           "spin_up_s": t_spin, "window_t0": t0, "dt": dt,
                           "mean_active_cells_per_step": info["active_total"] / max(1, args.steps),
@@ -935,12 +936,10 @@ def run_ours(args):
             achieved = flops / t_launch / 1e12
             peak = FP64_PEAK_GFLOPS / 1e3
             roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": TRAFFIC_FP64_PREDICT, "kernel": "k_predict",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_predict",
                     "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 pipe)",
                     "flops_per_launch": flops, "bytes_per_launch": bytes_per_launch,
                     "hbm_frac": bytes_per_launch / t_launch / 1e9 / peaks["hbm_gbs"],
-                    "fp64_issue_frac": INSTS_PER_CELL_FP64_PREDICT * cells / t_launch
-                    / (FP64_PEAK_GFLOPS / 2 * 1e9),
                     "launches_per_step": dn / args.steps, "avg_launch_us": 1e6 * t_launch}
         else:
             achieved = bytes_per_launch / t_launch / 1e9

@@ -161,6 +161,16 @@ nh_status nh2d_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* info
    solver, status) and the mass sum(h) dx dy of its new state. */
 nh_status nh2d_get_member_info(nh_grid2d* g, int member, nh_step_info* info);
 
+/* Tile of the one-launch FP32-state predictor (NH_MIXED_FP64_SOLVE): the
+   candidates are 32 x 16, 64 x 8, 32 x 8 and 64 x 16 cells (tile = 0..3).
+   By default the first FP32 step times each candidate on the live state and
+   keeps the fastest (cached per set of member sizes and limiters).  tile
+   0..3 forces a candidate, -2 asks for a new timing at the next step, -1
+   only reads; *chosen (may be NULL) receives the candidate in use (-1: not
+   chosen yet).  Every candidate gives the same result bit for bit.  Errors:
+   NH_ERR_ARG. */
+nh_status nh2d_set_tile(nh_grid2d* g, int tile, int* chosen);
+
 /* Kernel classes of nh2d_get_profile. */
 enum { NH2_K_KIN = 0, NH2_K_DEPTH, NH2_K_STAGE, NH2_K_MARKS, NH2_K_DILATE, NH2_K_COMPACT, NH2_K_ASSEMBLE,
        NH2_K_MASS, NH2_K_SOLVE_INIT, NH2_K_SOLVE, NH2_K_SUMMARY, NH2_K_CLEAR, NH2_K_CORRECT, NH2_K_COUNT };

@@ -16,10 +16,13 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "nh_mg2d.cuh"
+#include "nh_pred2d.cuh"
 #include "nhswe2d.h"
 
 using namespace nh;
@@ -31,6 +34,7 @@ struct nh_grid2d {
     std::vector<char> member_set;
     cudaStream_t stream, cap_stream;
     int maxch, maxpb, nblk, nmass, sms, items_grid, pcr_grid, egx, coop_grid;
+    int ptile;                                      // kPredTiles candidate of the FP32 predictor (-1: untuned)
     long long barrier_budget, barrier_budget_default;
     int crit, enlarge, first_global;
     double knh;
@@ -53,6 +57,7 @@ struct nh_grid2d {
     double *diag, *offl, *offr, *R, *ext_c;
     int *ext_k, *nbl, *nbr;
     double *c6, *cx, *cy, *phi, *ddx, *ddy, *psi;
+    double* cq;                                     // [kCq][T] per-cell fields of the assembly
     double *x, *r, *p0, *p1, *qv, *rh, *v0, *v1, *s, *t, *r1, *z;
     float2* pf;
     float* prb;
@@ -74,7 +79,8 @@ struct nh_grid2d {
     int* mg_njobs;
     unsigned* mg_gbar;
     double* mg_gpart;
-    float *mg_cf, *mg_z0, *mg_t0, *mg_cc, *mg_cb, *mg_cza, *mg_czb, *mg_ct;
+    float *mg_cf, *mg_z0, *mg_cc, *mg_cb, *mg_cza, *mg_czb;
+    int* mg_par;
     // profiling (nh2d_set_profiling): event pairs around each launch on the
     // handle's stream, folded into per-class totals at synchronisations
     bool prof_on;
@@ -86,7 +92,7 @@ struct nh_grid2d {
     // captured step: graph[p] starts from state buffer p
     cudaGraphExec_t graph[2];
     bool graph_valid, use_graphs;
-    double graph_key[10];
+    double graph_key[11];
     long long graph_runs;
 };
 
@@ -222,6 +228,7 @@ size_t carve2(int nb, int pitch, int cpitch, nh_grid2d* g, char* base)
     G->nbl = c.take<int>(T); G->nbr = c.take<int>(T);
     G->c6 = c.take<double>(T); G->cx = c.take<double>(T); G->cy = c.take<double>(T);
     G->phi = c.take<double>(T); G->ddx = c.take<double>(T); G->ddy = c.take<double>(T);
+    G->cq = c.take<double>((size_t)kCq * T);
     G->psi = c.take<double>(T);
     G->x = c.take<double>(T); G->r = c.take<double>(T); G->p0 = c.take<double>(T); G->p1 = c.take<double>(T);
     G->qv = c.take<double>(T); G->rh = c.take<double>(T); G->v0 = c.take<double>(T); G->v1 = c.take<double>(T);
@@ -239,10 +246,9 @@ size_t carve2(int nb, int pitch, int cpitch, nh_grid2d* g, char* base)
     G->mg_gbar = c.take<unsigned>(2 * (size_t)nb);
     G->mg_gpart = c.take<double>(8 * (size_t)kMgMaxGrid);
     G->mg_cf = c.take<float>(10 * T);
-    G->mg_z0 = c.take<float>(T); G->mg_t0 = c.take<float>(T);
+    G->mg_z0 = c.take<float>(T); G->mg_par = c.take<int>(T);
     G->mg_cc = c.take<float>(10 * CT);
     G->mg_cb = c.take<float>(CT); G->mg_cza = c.take<float>(CT); G->mg_czb = c.take<float>(CT);
-    G->mg_ct = c.take<float>(CT);
     if (g) { g->maxch = maxch; g->maxpb = maxpb; g->nblk = nblk; g->nmass = nmass; g->cpitch = cpitch; }
     return (c.off + kAlign2 - 1) / kAlign2 * kAlign2;
 }
@@ -293,6 +299,50 @@ const TS* d0_storage(const nh_grid2d* g)
 }
 
 template <typename TS>
+nh_status enqueue_mask_assembly(nh_grid2d* g, cudaStream_t st, int nxt, int lnew, double dt, bool all,
+                                const TimeCtl* tc);
+
+// The one-launch FP32 predictor with tile candidate c (kPredTiles[c]): CTAs
+// per member cover its largest tile count, at most 8 per SM over the members.
+template <int TX, int TY>
+cudaError_t launch_fused_t(nh_grid2d* g, cudaStream_t st, const FusedArgs& fa)
+{
+    int tiles = 1;
+    for (const nh_grid2d_desc& d : g->d) tiles = std::max(tiles, ((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY));
+    const int gx = std::max(1, std::min(tiles, (g->sms * 8 + g->nb - 1) / g->nb));
+    prof2_pre(g, st, NH2_K_STAGE);
+    k2_heun_fused<TX, TY><<<dim3(gx, g->nb), TX * TY, PTile<TX, TY>::smem, st>>>(fa);
+    prof2_post(g, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(nh_grid2d* g, cudaStream_t st, int c, const FusedArgs& fa)
+{
+    switch (c) {
+        case 1: return launch_fused_t<64, 8>(g, st, fa);
+        case 2: return launch_fused_t<32, 8>(g, st, fa);
+        case 3: return launch_fused_t<64, 16>(g, st, fa);
+        default: return launch_fused_t<32, 16>(g, st, fa);
+    }
+}
+
+cudaError_t fused_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(k2_heun_fused<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PTile<32, 16>::smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k2_heun_fused<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PTile<64, 8>::smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k2_heun_fused<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PTile<32, 8>::smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k2_heun_fused<64, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PTile<64, 16>::smem);
+    return e;
+}
+
+template <typename TS>
 nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double dt, double t_n, double t_n1,
                         bool all, const TimeCtl* tc)
 {
@@ -302,6 +352,25 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     const dim3 eg(g->egx, g->nb);
     P2(NH2_K_KIN, (k2_kin<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slides, g->nb, t_n, t_n1, tc, g->kin)));
     const TS* d0s = d0_storage<TS>(g);
+    if constexpr (sizeof(TS) == 4) {
+        // FP32 state: both Heun stages, the mound and the |eta/d| marks in one launch
+        const bool fused_marks = !all && g->crit == NH_CRIT_ETA_D;
+        FusedArgs fa;
+        fa.geos = g->geos; fa.slides = g->slides; fa.kin = g->kin; fa.pitch = P;
+        fa.z = as<float>(g->q[cur][0]); fa.hu = as<float>(g->q[cur][1]); fa.hv = as<float>(g->q[cur][2]);
+        fa.hw = as<float>(g->q[cur][3]); fa.d0s = g->d0f;
+        fa.oz = as<float>(g->q[nxt][0]); fa.ohu = as<float>(g->q[nxt][1]); fa.ohv = as<float>(g->q[nxt][2]);
+        fa.ohw = as<float>(g->q[nxt][3]); fa.m1 = as<float>(g->dn1);
+        fa.marks = fused_marks ? g->marks : nullptr; fa.knh = (float)g->knh; fa.dt = dt; fa.tc = tc;
+        CK2(launch_fused(g, st, g->ptile, fa));
+        if (all) CK2(cudaMemsetAsync(g->marks, 1, T, st));
+        else if (g->crit == NH_CRIT_HYDROSTATIC) CK2(cudaMemsetAsync(g->marks, 0, T, st));
+        else if (!fused_marks)
+            P2(NH2_K_MARKS, (k2_marks<TS><<<eg, 256, 0, st>>>(g->geos, P, as<TS>(g->q[nxt][0]), as<TS>(g->q[nxt][1]),
+                                                               as<TS>(g->q[nxt][2]), as<TS>(g->q[nxt][3]),
+                                                               as<TS>(g->dn1), d0s, g->crit, g->knh, g->marks)));
+        return enqueue_mask_assembly<TS>(g, st, nxt, lnew, dt, all, tc);
+    }
     P2(NH2_K_DEPTH, (k2_depth<TS><<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 0, P, g->d0, as<TS>(g->dn), tc)));
     P2(NH2_K_DEPTH, (k2_depth<TS><<<eg, 256, 0, st>>>(g->geos, g->slides, g->kin, 1, P, g->d0, as<TS>(g->dn1), tc)));
     StageArgs<TS> sa1;
@@ -324,6 +393,18 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     else if (g->crit == NH_CRIT_HYDROSTATIC) CK2(cudaMemsetAsync(g->marks, 0, T, st));
     else P2(NH2_K_MARKS, (k2_marks<TS><<<eg, 256, 0, st>>>(g->geos, P, sa2.oh, sa2.ohu, sa2.ohv, sa2.ohw,
                                                            as<TS>(g->dn1), d0s, g->crit, g->knh, g->marks)));
+    return enqueue_mask_assembly<TS>(g, st, nxt, lnew, dt, all, tc);
+}
+
+// After the predictor and the marks: enlargement, compaction, work items,
+// assembly of the elliptic rows, mass partial sums.
+template <typename TS>
+nh_status enqueue_mask_assembly(nh_grid2d* g, cudaStream_t st, int nxt, int lnew, double dt, bool all,
+                                const TimeCtl* tc)
+{
+    const size_t T = (size_t)g->nb * g->pitch;
+    const size_t P = (size_t)g->pitch;
+    const dim3 eg(g->egx, g->nb);
     P2(NH2_K_DILATE, (k2_dilate<<<eg, 256, 0, st>>>(g->geos, P, g->marks, all ? 0 : g->enlarge, g->act, tc)));
     P2(NH2_K_COMPACT, (k2_count<<<dim3(g->nblk, g->nb), kCompact2, 0, st>>>(g->geos, P, g->act, g->nblk, g->bcnt)));
     P2(NH2_K_COMPACT, (k2_scan<<<g->nb, 1024, 0, st>>>(g->bcnt, g->nblk, g->boff, g->nact[lnew], g->ms, tc)));
@@ -335,17 +416,21 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
     Asm2Args<TS> aa;
     aa.geos = g->geos; aa.slides = g->slides; aa.kin = g->kin;
     aa.nb = g->nb; aa.pitch = g->pitch; aa.maxch = g->maxch;
-    aa.ht = sa2.oh; aa.hut = sa2.ohu; aa.hvt = sa2.ohv; aa.hwt = sa2.ohw;
+    aa.ht = as<TS>(g->q[nxt][0]); aa.hut = as<TS>(g->q[nxt][1]); aa.hvt = as<TS>(g->q[nxt][2]);
+    aa.hwt = as<TS>(g->q[nxt][3]);
     aa.d0 = g->d0; aa.d1 = as<TS>(g->dn1); aa.dt = dt;
     aa.list = g->list[lnew]; aa.inv = g->inv; aa.ms = g->ms;
     aa.diag = g->diag; aa.offl = g->offl; aa.offr = g->offr; aa.R = g->R;
     aa.nbl = g->nbl; aa.nbr = g->nbr;
     aa.ext_c = g->ext_c; aa.ext_k = g->ext_k; aa.ext_stride = T;
     aa.c6 = g->c6; aa.cx = g->cx; aa.cy = g->cy; aa.phi = g->phi; aa.ddx = g->ddx; aa.ddy = g->ddy;
+    aa.cq = g->cq;
     aa.part = g->part; aa.cnt = g->cnt; aa.solver = NH_SOLVER_AUTO;
     aa.items = g->items; aa.ctl = g->ctl;
+    P2(NH2_K_ASSEMBLE, (k2_cellq<TS><<<g->items_grid, kChunk, 0, st>>>(aa)));
     P2(NH2_K_ASSEMBLE, (k2_assemble<TS><<<g->items_grid, kChunk, 0, st>>>(aa)));
-    P2(NH2_K_MASS, (k2_mass<TS><<<dim3(g->nmass, g->nb), 256, 0, st>>>(g->geos, P, sa2.oh, g->d0, g->mass_part)));
+    P2(NH2_K_MASS, (k2_mass<TS><<<dim3(g->nmass, g->nb), 256, 0, st>>>(g->geos, P, as<TS>(g->q[nxt][0]), g->d0,
+                                                                        g->mass_part)));
     return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }
 
@@ -388,6 +473,65 @@ nh_status launch_persistent(nh_grid2d* g, SolveArgs<double>& sa, cudaStream_t st
     return NH_OK;
 }
 
+std::mutex g_tune2_mutex;
+std::map<std::vector<int>, int> g_tune2_cache;
+
+// Tile of the FP32 one-launch predictor: each candidate of kPredTiles is
+// timed (2 warm-up and 5 timed launches, CUDA events on the handle's stream)
+// on the handle's live state, and the fastest is kept; the choice is cached
+// per set of member sizes and limiters.  The launches only write the next
+// step's buffers.
+nh_status tune_fused(nh_grid2d* g, double dt)
+{
+    if (g->ptile >= 0) return NH_OK;
+    std::vector<int> key;
+    for (const nh_grid2d_desc& d : g->d) { key.push_back(d.nx); key.push_back(d.ny); key.push_back(d.limiter); }
+    {
+        std::lock_guard<std::mutex> lock(g_tune2_mutex);
+        auto it = g_tune2_cache.find(key);
+        if (it != g_tune2_cache.end()) { g->ptile = it->second; return NH_OK; }
+    }
+    cudaStream_t st = g->stream;
+    const int cur = g->cur, nxt = cur ^ 1;
+    const double t_n = g->t_base + (double)g->n_since * dt;
+    k2_kin<<<(g->nb + 127) / 128, 128, 0, st>>>(g->slides, g->nb, t_n, t_n + dt, nullptr, g->kin);
+    FusedArgs fa;
+    fa.geos = g->geos; fa.slides = g->slides; fa.kin = g->kin; fa.pitch = (size_t)g->pitch;
+    fa.z = as<float>(g->q[cur][0]); fa.hu = as<float>(g->q[cur][1]); fa.hv = as<float>(g->q[cur][2]);
+    fa.hw = as<float>(g->q[cur][3]); fa.d0s = g->d0f;
+    fa.oz = as<float>(g->q[nxt][0]); fa.ohu = as<float>(g->q[nxt][1]); fa.ohv = as<float>(g->q[nxt][2]);
+    fa.ohw = as<float>(g->q[nxt][3]); fa.m1 = as<float>(g->dn1);
+    fa.marks = g->marks; fa.knh = (float)g->knh; fa.dt = dt; fa.tc = nullptr;
+    cudaEvent_t e0, e1;
+    CK2(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return NH_ERR_CUDA; }
+    const bool prof = g->prof_on;
+    g->prof_on = false;
+    float best = 1e30f;
+    int best_c = 0;
+    nh_status rc = NH_OK;
+    for (int c = 0; c < 4 && rc == NH_OK; ++c) {
+        for (int w = 0; w < 2; ++w)
+            if (launch_fused(g, st, c, fa) != cudaSuccess) rc = NH_ERR_CUDA;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5; ++r)
+            if (launch_fused(g, st, c, fa) != cudaSuccess) rc = NH_ERR_CUDA;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = NH_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == NH_OK && ms < best) { best = ms; best_c = c; }
+    }
+    g->prof_on = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != NH_OK) return rc;
+    g->ptile = best_c;
+    std::lock_guard<std::mutex> lock(g_tune2_mutex);
+    g_tune2_cache[key] = best_c;
+    return NH_OK;
+}
+
 // Multigrid-preconditioned CG of every member solving with CG (after
 // k_solve_init): plan the levels, split the members over the cooperative
 // grid, then the persistent solve.
@@ -401,14 +545,14 @@ nh_status launch_mg(nh_grid2d* g, const SolveArgs<double>& sa, cudaStream_t st)
     m.s = sa;
     m.geos = g->geos; m.inv = g->inv; m.plan = g->mg_plan; m.jobs = g->mg_jobs; m.njobs = g->mg_njobs;
     m.gbar = g->mg_gbar; m.gpart = g->mg_gpart;
-    m.cf = g->mg_cf; m.z0 = g->mg_z0; m.t0 = g->mg_t0;
-    m.cc = g->mg_cc; m.cb = g->mg_cb; m.cza = g->mg_cza; m.czb = g->mg_czb; m.ct = g->mg_ct;
+    m.cf = g->mg_cf; m.z0 = g->mg_z0; m.par = g->mg_par;
+    m.cc = g->mg_cc; m.cb = g->mg_cb; m.cza = g->mg_cza; m.czb = g->mg_czb;
     m.T = (size_t)g->nb * g->pitch; m.CT = (size_t)g->nb * g->cpitch; m.cpitch = g->cpitch;
     m.budget = g->barrier_budget;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(g->mg_grid);
     cfg.blockDim = dim3(kMgThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kMgSmemBytes;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -527,6 +671,10 @@ nh_status step2(nh_grid2d* g, double dt, nh_step_info* info)
     const double t_n1 = g->t_base + (double)(g->n_since + 1) * dt;
     const int cur = g->cur, nxt = cur ^ 1, lprev = g->lcur, lnew = lprev ^ 1;
     const bool all = g->crit == NH_CRIT_GLOBAL || (g->first_global && g->steps == 0);
+    if (g->prec != NH_FP64) {
+        nh_status rt = tune_fused(g, dt);
+        if (rt != NH_OK) return rt;
+    }
     nh_status rc = g->prec == NH_FP64 ? enqueue_front<double>(g, st, cur, lnew, dt, t_n, t_n1, all, nullptr)
                                       : enqueue_front<float>(g, st, cur, lnew, dt, t_n, t_n1, all, nullptr);
     if (rc != NH_OK) return rc;
@@ -607,8 +755,9 @@ void graph_destroy(nh_grid2d* g)
 
 nh_status graph_prepare(nh_grid2d* g, double dt)
 {
-    const double key[10] = {dt, (double)g->crit, g->knh, (double)g->enlarge, g->rtol, (double)g->max_iter,
-                            (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->prec, (double)g->precond};
+    const double key[11] = {dt, (double)g->crit, g->knh, (double)g->enlarge, g->rtol, (double)g->max_iter,
+                            (double)g->guess, (double)(g->cur ^ g->lcur), (double)g->prec, (double)g->precond,
+                            (double)g->ptile};
     if (g->graph_valid && std::memcmp(key, g->graph_key, sizeof(key)) == 0) return NH_OK;
     graph_destroy(g);
     for (int p = 0; p < 2; ++p) {
@@ -639,6 +788,10 @@ nh_status graph_run(nh_grid2d* g, double dt, long long n_steps, nh_run_info* R)
     if (g->last_dt != 0.0 && dt != g->last_dt) {
         g->t_base += (double)g->n_since * g->last_dt;
         g->n_since = 0;
+    }
+    if (g->prec != NH_FP64) {
+        nh_status rt = tune_fused(g, dt);
+        if (rt != NH_OK) return rt;
     }
     nh_status rc = graph_prepare(g, dt);
     if (rc != NH_OK) return rc;
@@ -720,6 +873,7 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
     g->items_grid = (int)std::max(1LL, std::min((long long)g->maxch * g->nb, (long long)g->sms * 8));
     g->pcr_grid = (int)std::max(1LL, std::min((long long)g->maxpb * g->nb, (long long)g->sms * 2));
     g->egx = std::max(1, std::min((g->pitch + 255) / 256, (g->sms * 8 + g->nb - 1) / g->nb));
+    g->ptile = -1;
     g->crit = NH_CRIT_GLOBAL; g->knh = 1e-3; g->enlarge = 1; g->first_global = 0;
     g->rtol = 1e-12; g->max_iter = 20000; g->guess = NH_GUESS_PREV;
     g->prec = NH_FP64;
@@ -750,7 +904,13 @@ nh_status nh2d_create_ensemble(int n_members, const nh_grid2d_desc* descs, const
             per_sm > 0)
             g->coop_grid = per_sm * g->sms;
         per_sm = 0;
-        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_mg_pcg, kMgThreads, 0) == cudaSuccess &&
+        if (cudaFuncSetAttribute(k2_mg_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMgSmemBytes) !=
+                cudaSuccess ||
+            fused_attributes() != cudaSuccess) {
+            rc = NH_ERR_CUDA; break;
+        }
+        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_mg_pcg, kMgThreads, kMgSmemBytes) ==
+                        cudaSuccess &&
             per_sm > 0)
             g->mg_grid = std::min(per_sm * g->sms, kMgMaxGrid);
         int clk_khz = 0;
@@ -849,6 +1009,17 @@ nh_status nh2d_set_graphs(nh_grid2d* g, int on)
     if (!g) return NH_ERR_ARG;
     g->use_graphs = on != 0;
     if (!g->use_graphs) graph_destroy(g);
+    return NH_OK;
+}
+
+nh_status nh2d_set_tile(nh_grid2d* g, int tile, int* chosen)
+{
+    if (!g || tile < -2 || tile > 3) return NH_ERR_ARG;
+    if (tile >= 0 || tile == -2) {
+        g->ptile = tile >= 0 ? tile : -1;
+        graph_destroy(g);
+    }
+    if (chosen) *chosen = g->ptile;
     return NH_OK;
 }
 

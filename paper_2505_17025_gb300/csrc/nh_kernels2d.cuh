@@ -83,13 +83,18 @@ static __global__ void k2_kin(const Slide2* __restrict__ slides, int nb, double 
     }
 }
 
+// In-domain index of i: wrapped (periodic) or mirrored once at a wall; a
+// halo cell further out than the grid is wide (a tile's far halo on a tiny
+// grid, which no in-domain stencil reaches) is clamped into the grid, so it
+// is never read outside the member's slice.
 __device__ __forceinline__ int g2_index1(int bc, int n, int i, int* odd)
 {
     *odd = 1;
     if (i >= 0 && i < n) return i;
     if (bc == NH_BC_PERIODIC) return ((i % n) + n) % n;
     *odd = -1;
-    return (i < 0) ? (-1 - i) : (2 * n - 1 - i);
+    const int r = (i < 0) ? (-1 - i) : (2 * n - 1 - i);
+    return r < 0 ? 0 : (r >= n ? n - 1 : r);
 }
 
 // Flat index of the in-domain (mirrored / wrapped) cell of (i, j) and the
@@ -134,30 +139,32 @@ __device__ __forceinline__ void bottom2(const Geo2& G, const double* __restrict_
                                         const Kin2& K, int i, int j, double out[10])
 {
     int o1, o2;
-    const double dx = G.dx, dy = G.dy;
     const double c = d0[j * G.nx + i];
     const double xm = d0[g2_cell(G, i - 1, j, &o1, &o2)], xp = d0[g2_cell(G, i + 1, j, &o1, &o2)];
     const double ym = d0[g2_cell(G, i, j - 1, &o1, &o2)], yp = d0[g2_cell(G, i, j + 1, &o1, &o2)];
     const double mm = d0[g2_cell(G, i - 1, j - 1, &o1, &o2)], pm = d0[g2_cell(G, i + 1, j - 1, &o1, &o2)];
     const double mp = d0[g2_cell(G, i - 1, j + 1, &o1, &o2)], pp = d0[g2_cell(G, i + 1, j + 1, &o1, &o2)];
+    // reciprocals of the spacings and slide lengths instead of divisions
+    // (GB300's FP64 division is a long instruction sequence)
+    const double ix = G.idx, iy = G.idy;
     double d = c;
-    double d_x = (xp - xm) / (2.0 * dx), d_y = (yp - ym) / (2.0 * dy);
-    double d_xx = (xp - 2.0 * c + xm) / (dx * dx), d_yy = (yp - 2.0 * c + ym) / (dy * dy);
-    double d_xy = (pp - pm - mp + mm) / (4.0 * dx * dy);
+    double d_x = (xp - xm) * (0.5 * ix), d_y = (yp - ym) * (0.5 * iy);
+    double d_xx = (xp - 2.0 * c + xm) * (ix * ix), d_yy = (yp - 2.0 * c + ym) * (iy * iy);
+    double d_xy = (pp - pm - mp + mm) * (0.25 * ix * iy);
     double d_t = 0.0, d_xt = 0.0, d_yt = 0.0, d_tt = 0.0;
     if (S.shape == NH_SLIDE_GAUSS_LNCOSH) {
-        const double x = G.x0 + (i + 0.5) * dx, y = G.y0 + (j + 0.5) * dy;
-        const double Lx = S.Lx, Ly = S.Ly, sd = K.sd, sdd = K.sdd;
-        const double xi = (x - S.xc0 - K.s) / Lx, ze = (y - S.yc0) / Ly;
+        const double x = G.x0 + (i + 0.5) * G.dx, y = G.y0 + (j + 0.5) * G.dy;
+        const double iLx = S.iLx, iLy = S.iLy, sd = K.sd, sdd = K.sdd;
+        const double xi = (x - S.xc0 - K.s) * iLx, ze = (y - S.yc0) * iLy;
         const double m = S.A * exp(-xi * xi - ze * ze);
-        const double m_x = m * (-2.0 * xi / Lx), m_y = m * (-2.0 * ze / Ly);
-        const double m_xx = m * (4.0 * xi * xi - 2.0) / (Lx * Lx);
-        const double m_yy = m * (4.0 * ze * ze - 2.0) / (Ly * Ly);
-        const double m_xy = m * (4.0 * xi * ze) / (Lx * Ly);
-        const double m_t = m * (2.0 * xi / Lx) * sd;
-        const double m_xt = -m * (2.0 / (Lx * Lx)) * (2.0 * xi * xi - 1.0) * sd;
-        const double m_yt = -m * (4.0 * xi * ze / (Lx * Ly)) * sd;
-        const double m_tt = m * (2.0 / (Lx * Lx)) * ((2.0 * xi * xi - 1.0) * sd * sd + xi * Lx * sdd);
+        const double m_x = m * (-2.0 * xi * iLx), m_y = m * (-2.0 * ze * iLy);
+        const double m_xx = m * (4.0 * xi * xi - 2.0) * (iLx * iLx);
+        const double m_yy = m * (4.0 * ze * ze - 2.0) * (iLy * iLy);
+        const double m_xy = m * (4.0 * xi * ze) * (iLx * iLy);
+        const double m_t = m * (2.0 * xi * iLx) * sd;
+        const double m_xt = -m * (2.0 * iLx * iLx) * (2.0 * xi * xi - 1.0) * sd;
+        const double m_yt = -m * (4.0 * xi * ze * iLx * iLy) * sd;
+        const double m_tt = m * (2.0 * iLx * iLx) * ((2.0 * xi * xi - 1.0) * sd * sd + xi * S.Lx * sdd);
         d -= m; d_x -= m_x; d_y -= m_y; d_xx -= m_xx; d_yy -= m_yy; d_xy -= m_xy;
         d_t = -m_t; d_xt = -m_xt; d_yt = -m_yt; d_tt = -m_tt;
     }
@@ -609,6 +616,7 @@ struct Asm2Args {
     int *nbl, *nbr;
     double* ext_c; int* ext_k; size_t ext_stride;   // S, N, SW, SE, NW, NE; stride nb * pitch
     double *c6, *cx, *cy, *phi, *ddx, *ddy;
+    double* cq;                            // [kCq][nb * pitch] per-cell fields (k2_cellq); stride ext_stride
     double* part; int* cnt;                // part: [2][nb * maxch]
     int solver;
     const int2* items; const Ctl* ctl;
@@ -643,29 +651,35 @@ __device__ __forceinline__ CellQ2 cell_q2(const Mem2<TS>& a, int i, int j)
     bottom2(G, a.d0, a.S, a.K, i, j, b);
     const int kw = g2_cell(G, i - 1, j, &o1, &o2), ke = g2_cell(G, i + 1, j, &o1, &o2);
     const int ks = g2_cell(G, i, j - 1, &o1, &o2), kn = g2_cell(G, i, j + 1, &o1, &o2);
-    const double eta_x = (a.eta_at(ke) - a.eta_at(kw)) / (2.0 * G.dx);
-    const double eta_y = (a.eta_at(kn) - a.eta_at(ks)) / (2.0 * G.dy);
+    const double eta_x = (a.eta_at(ke) - a.eta_at(kw)) * (0.5 * G.idx);
+    const double eta_y = (a.eta_at(kn) - a.eta_at(ks)) * (0.5 * G.idy);
     const int k = j * G.nx + i;
     CellQ2 q;
     q.h = a.h_at(k);
-    const double u = (double)a.hut[k] / q.h, v = (double)a.hvt[k] / q.h;
+    const double rh = 1.0 / q.h;
+    const double u = (double)a.hut[k] * rh, v = (double)a.hvt[k] * rh;
     q.d_x = b[1]; q.d_y = b[2]; q.d_t = b[6];
     const double d_xx = b[3], d_yy = b[4], d_xy = b[5], d_xt = b[7], d_yt = b[8], d_tt = b[9];
     q.G = q.d_x * q.d_x + q.d_y * q.d_y;
     q.D = 4.0 + q.G;
-    q.phi = a.dt * q.h / q.D * (G.g * (q.d_x * eta_x + q.d_y * eta_y) - d_tt - 2.0 * (u * d_xt + v * d_yt)
-                                 - (u * u * d_xx + 2.0 * u * v * d_xy + v * v * d_yy));
-    q.Kxx = 1.0 / q.h * (1.0 - q.d_x * q.d_x / q.D);
-    q.Kyy = 1.0 / q.h * (1.0 - q.d_y * q.d_y / q.D);
-    q.Kxy = -1.0 / q.h * q.d_x * q.d_y / q.D;
-    q.bx = 6.0 * q.d_x / (q.h * q.h * q.D);
-    q.by = 6.0 * q.d_y / (q.h * q.h * q.D);
+    const double rD = 1.0 / q.D;
+    q.phi = a.dt * q.h * rD * (G.g * (q.d_x * eta_x + q.d_y * eta_y) - d_tt - 2.0 * (u * d_xt + v * d_yt)
+                                - (u * u * d_xx + 2.0 * u * v * d_xy + v * v * d_yy));
+    q.Kxx = rh * (1.0 - q.d_x * q.d_x * rD);
+    q.Kyy = rh * (1.0 - q.d_y * q.d_y * rD);
+    q.Kxy = -rh * q.d_x * q.d_y * rD;
+    q.bx = 6.0 * q.d_x * (rh * rh * rD);
+    q.by = 6.0 * q.d_y * (rh * rh * rD);
     q.U0 = (double)a.hut[k] + q.phi * q.d_x;
     q.V0 = (double)a.hvt[k] + q.phi * q.d_y;
-    q.Vx = q.U0 / q.h;
-    q.Vy = q.V0 / q.h;
+    q.Vx = q.U0 * rh;
+    q.Vy = q.V0 * rh;
     return q;
 }
+
+// The fields of a cell that its neighbours' rows use (Kxx, Kyy, Kxy, bx, by,
+// Vx, Vy), stored per cell by k2_cellq so each is computed once per step.
+constexpr int kCq = 7;
 
 // The same seen from a neighbour: mirrored cells flip their odd components.
 template <typename TS>
@@ -678,6 +692,65 @@ __device__ __forceinline__ CellQ2 cell_q2_at(const Mem2<TS>& a, int i, int j)
     q.bx = flip(ox, q.bx); q.by = flip(oy, q.by);
     q.Vx = flip(ox, q.Vx); q.Vy = flip(oy, q.Vy);
     return q;
+}
+
+// A neighbour's stored fields (cq: [kCq][nb * pitch], member slice at mo),
+// mirrored cells flipping their odd components.
+__device__ __forceinline__ CellQ2 cell_q2_stored(const Geo2& G, const double* __restrict__ cq, size_t T, size_t mo,
+                                                 int i, int j)
+{
+    int ox, oy;
+    const size_t c = mo + g2_cell(G, i, j, &ox, &oy);
+    CellQ2 q;
+    q.Kxx = cq[c];
+    q.Kyy = cq[T + c];
+    q.Kxy = flip(ox * oy, cq[2 * T + c]);
+    q.bx = flip(ox, cq[3 * T + c]);
+    q.by = flip(oy, cq[4 * T + c]);
+    q.Vx = flip(ox, cq[5 * T + c]);
+    q.Vy = flip(oy, cq[6 * T + c]);
+    return q;
+}
+
+__device__ __forceinline__ void cq_store(double* __restrict__ cq, size_t T, size_t c, const CellQ2& q)
+{
+    cq[c] = q.Kxx; cq[T + c] = q.Kyy; cq[2 * T + c] = q.Kxy; cq[3 * T + c] = q.bx; cq[4 * T + c] = q.by;
+    cq[5 * T + c] = q.Vx; cq[6 * T + c] = q.Vy;
+}
+
+// Per-cell quantities of every active cell and of each in-domain cell its
+// 9-point row reaches in x and y (mirrored or wrapped), stored once so the
+// assembly reads neighbours instead of recomputing them.  Two active cells
+// may share an inactive neighbour: both write the same values.
+template <typename TS>
+static __global__ void __launch_bounds__(kChunk) k2_cellq(Asm2Args<TS> a)
+{
+    const int n_items = a.ctl->n_items;
+    const size_t T = a.ext_stride;
+    for (int wi = blockIdx.x; wi < n_items; wi += gridDim.x) {
+        const int2 itm = a.items[wi];
+        const int b = itm.x;
+        const int n = a.ms[b].n_active;
+        const int k = itm.y * kChunk + threadIdx.x;
+        if (k >= n) continue;
+        const size_t mo = (size_t)b * a.pitch;
+        Mem2<TS> m;
+        m.G = a.geos[b]; m.S = a.slides[b]; m.K = a.kin[2 * b + 1];
+        m.ht = a.ht + mo; m.hut = a.hut + mo; m.hvt = a.hvt + mo; m.d0 = a.d0 + mo; m.d1 = a.d1 + mo;
+        m.dt = a.dt;
+        const Geo2& G = m.G;
+        const int c = a.list[mo + k];
+        const int i = c % G.nx, j = c / G.nx;
+        cq_store(a.cq, T, mo + c, cell_q2(m, i, j));
+        const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int ox, oy;
+            const int cn = g2_cell(G, i + di[q], j + dj[q], &ox, &oy);
+            if (a.inv[mo + cn] >= 0) continue;   // active: its own thread stores it
+            cq_store(a.cq, T, mo + cn, cell_q2(m, cn % G.nx, cn / G.nx));
+        }
+    }
 }
 
 // Rows of the 9-point operator on the active cells (work items of kChunk
@@ -698,7 +771,7 @@ static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args<TS> a)
         m.dt = a.dt;
         const Geo2& G = m.G;
         const int* inv = a.inv + mo;
-        const double idx2 = 1.0 / (G.dx * G.dx), idy2 = 1.0 / (G.dy * G.dy), ixy = 1.0 / (4.0 * G.dx * G.dy);
+        const double idx2 = G.idx * G.idx, idy2 = G.idy * G.idy, ixy = 0.25 * G.idx * G.idy;
         const int k = jj * kChunk + threadIdx.x;
         double r2 = 0.0, gmin = INFINITY;
         if (k < n) {
@@ -706,16 +779,17 @@ static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args<TS> a)
             const int c = a.list[o];
             const int i = c % G.nx, j = c / G.nx;
             const CellQ2 q = cell_q2(m, i, j);
-            const CellQ2 W = cell_q2_at(m, i - 1, j), E = cell_q2_at(m, i + 1, j);
-            const CellQ2 S = cell_q2_at(m, i, j - 1), N = cell_q2_at(m, i, j + 1);
+            const size_t T = a.ext_stride;
+            const CellQ2 W = cell_q2_stored(G, a.cq, T, mo, i - 1, j), E = cell_q2_stored(G, a.cq, T, mo, i + 1, j);
+            const CellQ2 S = cell_q2_stored(G, a.cq, T, mo, i, j - 1), N = cell_q2_stored(G, a.cq, T, mo, i, j + 1);
             const double Kw = 0.5 * (W.Kxx + q.Kxx), Ke = 0.5 * (q.Kxx + E.Kxx);
             const double Ks = 0.5 * (S.Kyy + q.Kyy), Kn = 0.5 * (q.Kyy + N.Kyy);
-            const double div_beta = (E.bx - W.bx) / (2.0 * G.dx) + (N.by - S.by) / (2.0 * G.dy);
-            const double div_V = (E.Vx - W.Vx) / (2.0 * G.dx) + (N.Vy - S.Vy) / (2.0 * G.dy);
-            const double h = q.h, h2 = h * h;
-            const double gam = div_beta + 12.0 * (1.0 + q.G) / (h2 * h * q.D);
-            const double Rk = -(div_V + 2.0 * (q.d_x * q.U0 + q.d_y * q.V0) / h2 + 2.0 * (double)a.hwt[mo + c] / h2
-                                + 2.0 * q.phi / h2 + 2.0 * q.d_t / h);
+            const double div_beta = (E.bx - W.bx) * (0.5 * G.idx) + (N.by - S.by) * (0.5 * G.idy);
+            const double div_V = (E.Vx - W.Vx) * (0.5 * G.idx) + (N.Vy - S.Vy) * (0.5 * G.idy);
+            const double h = q.h, rh = 1.0 / h, rh2 = rh * rh;
+            const double gam = div_beta + 12.0 * (1.0 + q.G) * (rh2 * rh) / q.D;
+            const double Rk = -(div_V + 2.0 * (q.d_x * q.U0 + q.d_y * q.V0) * rh2 + 2.0 * (double)a.hwt[mo + c] * rh2
+                                + 2.0 * q.phi * rh2 + 2.0 * q.d_t * rh);
             const double cW = -Kw * idx2, cE = -Ke * idx2, cS = -Ks * idy2, cN = -Kn * idy2;
             const double cNE = -(E.Kxy + N.Kxy) * ixy, cSW = -(W.Kxy + S.Kxy) * ixy;
             const double cSE = (E.Kxy + S.Kxy) * ixy, cNW = (W.Kxy + N.Kxy) * ixy;
@@ -736,9 +810,10 @@ static __global__ void __launch_bounds__(kChunk) k2_assemble(Asm2Args<TS> a)
                 a.ext_k[e * a.ext_stride + o] = ke[e];
             }
             a.R[o] = Rk;
-            a.c6[o] = 6.0 / (h * q.D);
-            a.cx[o] = q.d_x / q.D;
-            a.cy[o] = q.d_y / q.D;
+            const double rD = 1.0 / q.D;
+            a.c6[o] = 6.0 * rh * rD;
+            a.cx[o] = q.d_x * rD;
+            a.cy[o] = q.d_y * rD;
             a.phi[o] = q.phi;
             a.ddx[o] = q.d_x;
             a.ddy[o] = q.d_y;

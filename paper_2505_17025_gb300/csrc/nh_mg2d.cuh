@@ -46,19 +46,26 @@ constexpr int kMgCoarsest = 16;      // a level of at most this many cells is th
 constexpr int kMgSweeps = 7;         // damped-Jacobi sweeps on the coarsest level (odd)
 constexpr int kMgRowsPerCta = 4096;  // active cells per CTA before a member gets another one
 constexpr float kMgOmega = 0.7f;     // Jacobi damping
+constexpr float kMgCoarseScale = 1.5f;   // weight of the coarse-level correction (over-correction of the piecewise-constant prolongation)
+constexpr int kMgSmemCells = 3840;   // coarse cells the group's first CTA keeps in shared memory
+constexpr int kMgSmemFloats = 13;    // per such cell: 9 couplings, omega / diagonal, b, two iterates
+constexpr size_t kMgSmemBytes = sizeof(float) * kMgSmemFloats * kMgSmemCells;
 
 // Coarse level of one member: box origin (level coordinates) and size; wx / wy
 // set when the box spans a periodic extent (neighbours wrap modulo w / h);
-// off = first cell of the level in the member's coarse region.
+// off = first cell of the level in the member's coarse region; soff = its
+// first cell in shared memory (levels lloc..nlev), else -1.
 struct MgLev {
     int i0, j0, w, h;
-    int wx, wy, off, pad;
+    int wx, wy, off, soff;
 };
 
 struct MgPlan {
     int nlev;                 // coarse levels (0: the fine smoother alone)
+    int lloc;                 // first level kept in shared memory (nlev + 1: none)
+    int nloc;                 // cells in shared memory
     int bi0, bi1, bj0, bj1;   // bounding box of the active cells (fine)
-    int pad[3];
+    int pad;
     MgLev lev[kMgLevels + 1];
 };
 
@@ -77,12 +84,11 @@ struct MgArgs {
     double* gpart;            // [8 * coop grid]: group partial sums (two buffers of 4 per CTA)
     float* cf;                // [10][T]: fine FP32 rows (slots 0-8) and omega / diagonal (slot 9)
     float* z0;                // [T] fine pre-smoothed iterate
-    float* t0;                // [T] fine residual
+    int* par;                 // [T] level-1 cell (local index) of each fine row
     float* cc;                // [10][CT]: coarse rows and omega / diagonal
     float* cb;                // [CT] coarse right-hand sides
     float* cza;               // [CT] coarse pre-smoothed iterates
     float* czb;               // [CT] coarse post-smoothed iterates
-    float* ct;                // [CT] coarse residuals
     size_t T, CT;             // nb * pitch, nb * cpitch
     int cpitch;
     long long budget;         // group-barrier spin limit (clock cycles)
@@ -148,9 +154,9 @@ static __global__ void __launch_bounds__(1024) k2_mg_box(const Geo2* __restrict_
     if (threadIdx.x != 0) return;
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = min(lo, s_min[w]); hi = max(hi, s_max[w]); }
     MgPlan P;
-    P.nlev = 0;
+    P.nlev = 0; P.lloc = 1; P.nloc = 0;
     P.bi0 = P.bi1 = P.bj0 = P.bj1 = 0;
-    P.pad[0] = P.pad[1] = P.pad[2] = 0;
+    P.pad = 0;
     if (n > 0) {
         P.bi0 = lo; P.bi1 = hi;
         P.bj0 = L[0] / G.nx; P.bj1 = L[n - 1] / G.nx;
@@ -162,7 +168,7 @@ static __global__ void __launch_bounds__(1024) k2_mg_box(const Geo2* __restrict_
             MgLev v;
             v.i0 = lo >> l; v.j0 = P.bj0 >> l;
             v.w = (hi >> l) - v.i0 + 1; v.h = (P.bj1 >> l) - v.j0 + 1;
-            v.wx = wx; v.wy = wy; v.off = off; v.pad = 0;
+            v.wx = wx; v.wy = wy; v.off = off; v.soff = -1;
             const long long area = (long long)v.w * v.h;
             if (area >= prev) break;
             P.lev[l] = v;
@@ -170,6 +176,20 @@ static __global__ void __launch_bounds__(1024) k2_mg_box(const Geo2* __restrict_
             off += (int)area;
             prev = area;
         }
+        // the coarsest levels that fit in shared memory together
+        P.lloc = P.nlev + 1;
+        long long tot = 0;
+        for (int l = P.nlev; l >= 1; --l) {
+            tot += (long long)P.lev[l].w * P.lev[l].h;
+            if (tot > kMgSmemCells) break;
+            P.lloc = l;
+        }
+        int so = 0;
+        for (int l = P.lloc; l <= P.nlev; ++l) {
+            P.lev[l].soff = so;
+            so += P.lev[l].w * P.lev[l].h;
+        }
+        P.nloc = so;
     }
     plan[b] = P;
 }
@@ -328,56 +348,7 @@ __device__ __forceinline__ bool mg_sum(MgGroup& g, double (&v)[NV], double* red,
     return true;
 }
 
-// How the cells of one phase are split: over the whole group, or over the
-// CTA of rank 0 alone for small coarse levels (then barriers are block-wide).
-struct MgExec {
-    int stride, t0;
-    bool local;
-};
-
-__device__ __forceinline__ bool mg_bar(const MgGroup& g, const MgExec& ex, long long budget, Ctl* ctl)
-{
-    if (ex.local) {
-        __syncthreads();
-        return true;
-    }
-    return mg_sync(g, budget, ctl);
-}
-
 // -------------------------------------------------------- level operations
-
-// rhs - (A v)_k on fine row k (FP32), v a fine FP32 vector.
-__device__ __forceinline__ float fine_resid(const MgArgs& m, size_t mo, int k, float rhs, const float* v)
-{
-    const SolveArgs<double>& a = m.s;
-    const size_t o = mo + k;
-    int nk[9];
-    fine_nbrs(a, o, nk);
-    float y = m.cf[4 * m.T + o] * v[o];
-#pragma unroll
-    for (int s = 0; s < 9; ++s)
-        if (s != 4 && nk[s] >= 0) y += m.cf[s * m.T + o] * v[mo + nk[s]];
-    return rhs - y;
-}
-
-// rhs - (A v) at cell q of a coarse level (local coordinates il, jl).
-__device__ __forceinline__ float coarse_resid(const MgArgs& m, const MgLev& L, size_t cbase, int q, float rhs,
-                                              const float* v)
-{
-    const int il = q % L.w, jl = q / L.w;
-    const size_t c0 = cbase + L.off;
-    float y = 0.f;
-#pragma unroll
-    for (int s = 0; s < 9; ++s) {
-        int ii = il + slot_dx(s), jj = jl + slot_dy(s);
-        if (L.wx) ii = (ii + L.w) % L.w;
-        else if (ii < 0 || ii >= L.w) continue;
-        if (L.wy) jj = (jj + L.h) % L.h;
-        else if (jj < 0 || jj >= L.h) continue;
-        y += m.cc[s * m.CT + c0 + q] * v[c0 + (size_t)jj * L.w + ii];
-    }
-    return rhs - y;
-}
 
 // Level 1 row of aggregate q: the Galerkin sum of its fine children's rows.
 __device__ __forceinline__ void gather_level1(const MgArgs& m, const Geo2& G, const MgLev& L, size_t mo,
@@ -453,134 +424,213 @@ __device__ __forceinline__ void gather_coarse(const MgArgs& m, const MgLev& P, c
 
 // ------------------------------------------------------------------ V-cycle
 
-// Down the V at coarse level l: right-hand side by summing the children's
-// residuals, pre-smoothing from zero, and either the residual for the next
-// level or, on the coarsest level, the Jacobi sweeps (result in czb).
-__device__ __forceinline__ bool mg_down(const MgArgs& m, const MgGroup& g, const MgExec& ex, const MgPlan& P,
-                                        const Geo2& G, int l, size_t mo, size_t cbase)
+// A coarse level's arrays, in global memory or in the first CTA's shared
+// memory: couplings and omega / diagonal (planes c + s cs), right-hand side,
+// pre-smoothed and post-smoothed iterates; box geometry.
+struct LView {
+    const float* c;
+    size_t cs;
+    float *b, *za, *zb;
+    int i0, j0, w, h, wx, wy;
+};
+
+__device__ __forceinline__ LView lview_global(const MgArgs& m, const MgLev& L, size_t cbase)
 {
-    Ctl* ctl = m.s.ctl;
-    const MgLev& L = P.lev[l];
-    const int area = L.w * L.h;
-    const size_t c0 = cbase + L.off;
-    for (int q = ex.t0; q < area; q += ex.stride) {
-        const int I = L.i0 + q % L.w, J = L.j0 + q / L.w;
+    const size_t o = cbase + L.off;
+    return LView{m.cc + o, m.CT, m.cb + o, m.cza + o, m.czb + o, L.i0, L.j0, L.w, L.h, L.wx, L.wy};
+}
+
+__device__ __forceinline__ LView lview_smem(float* sm, const MgLev& L)
+{
+    const size_t S = kMgSmemCells;
+    return LView{sm + L.soff, S, sm + 10 * S + L.soff, sm + 11 * S + L.soff, sm + 12 * S + L.soff,
+                 L.i0, L.j0, L.w, L.h, L.wx, L.wy};
+}
+
+// (A v)_q on a coarse level, v(j, i, jr) the vector at local index j = jr w + i
+// (a callable).
+template <typename F>
+__device__ __forceinline__ float lv_apply(const LView& V, int q, F v)
+{
+    const int il = q % V.w, jl = q / V.w;
+    float y = 0.f;
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+        int ii = il + slot_dx(s), jj = jl + slot_dy(s);
+        if (V.wx) ii = (ii + V.w) % V.w;
+        else if (ii < 0 || ii >= V.w) continue;
+        if (V.wy) jj = (jj + V.h) % V.h;
+        else if (jj < 0 || jj >= V.h) continue;
+        y += V.c[s * V.cs + q] * v(jj * V.w + ii, ii, jj);
+    }
+    return y;
+}
+
+// Local index in U (one level coarser) of V's cell at local (i, jr).
+__device__ __forceinline__ int lv_parent(const LView& V, const LView& U, int i, int jr)
+{
+    return (((V.j0 + jr) >> 1) - U.j0) * U.w + (((V.i0 + i) >> 1) - U.i0);
+}
+
+// (A v)_k on fine row k in FP32, v(j) the vector at compact index j.
+template <typename F>
+__device__ __forceinline__ float fine_apply(const MgArgs& m, size_t mo, int k, F v)
+{
+    const size_t o = mo + k;
+    int nk[9];
+    fine_nbrs(m.s, o, nk);
+    float y = m.cf[4 * m.T + o] * v(k);
+#pragma unroll
+    for (int s = 0; s < 9; ++s)
+        if (s != 4 && nk[s] >= 0) y += m.cf[s * m.T + o] * v(nk[s]);
+    return y;
+}
+
+// Level 1 (view V) from the fine level: b = the children's residuals
+// r - A z0 summed, za = omega b / diag.
+__device__ __forceinline__ void down_fine(const MgArgs& m, const Geo2& G, size_t mo, const double* r,
+                                          const LView& V, int t0, int stride)
+{
+    const float* z0 = m.z0 + mo;
+    const int area = V.w * V.h;
+    for (int q = t0; q < area; q += stride) {
+        const int I = V.i0 + q % V.w, J = V.j0 + q / V.w;
         float bsum = 0.f;
-        if (l == 1) {
-            for (int dj = 0; dj < 2; ++dj)
-                for (int di = 0; di < 2; ++di) {
-                    const int i = 2 * I + di, j = 2 * J + dj;
-                    if (i >= G.nx || j >= G.ny) continue;
-                    const int k = m.inv[mo + (size_t)j * G.nx + i];
-                    if (k >= 0) bsum += m.t0[mo + k];
-                }
-        } else {
-            const MgLev& Q = P.lev[l - 1];
-            for (int dj = 0; dj < 2; ++dj)
-                for (int di = 0; di < 2; ++di) {
-                    const int ci = 2 * I + di - Q.i0, cj = 2 * J + dj - Q.j0;
-                    if (ci < 0 || ci >= Q.w || cj < 0 || cj >= Q.h) continue;
-                    bsum += m.ct[cbase + Q.off + (size_t)cj * Q.w + ci];
-                }
-        }
-        m.cb[c0 + q] = bsum;
-        m.cza[c0 + q] = m.cc[9 * m.CT + c0 + q] * bsum;
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj;
+                if (i >= G.nx || j >= G.ny) continue;
+                const int k = m.inv[mo + (size_t)j * G.nx + i];
+                if (k < 0) continue;
+                bsum += (float)r[mo + k] - fine_apply(m, mo, k, [&](int jj) { return z0[jj]; });
+            }
+        V.b[q] = bsum;
+        V.za[q] = V.c[9 * V.cs + q] * bsum;
     }
-    if (!mg_bar(g, ex, m.budget, ctl)) return false;
-    if (l < P.nlev) {
-        for (int q = ex.t0; q < area; q += ex.stride)
-            m.ct[c0 + q] = m.cc[9 * m.CT + c0 + q] == 0.f ? 0.f : coarse_resid(m, L, cbase, q, m.cb[c0 + q], m.cza);
-        return mg_bar(g, ex, m.budget, ctl);
-    }
-    // coarsest: kMgSweeps (odd) damped-Jacobi sweeps ping-ponging cza -> czb
-    static_assert(kMgSweeps % 2 == 1, "the coarsest result must end in czb");
-    float* src = m.cza;
-    float* dst = m.czb;
-    for (int sw = 0; sw < kMgSweeps; ++sw) {
-        for (int q = ex.t0; q < area; q += ex.stride) {
-            const float wd = m.cc[9 * m.CT + c0 + q];
-            dst[c0 + q] = wd == 0.f ? 0.f : src[c0 + q] + wd * coarse_resid(m, L, cbase, q, m.cb[c0 + q], src);
-        }
-        if (!mg_bar(g, ex, m.budget, ctl)) return false;
-        float* t = src; src = dst; dst = t;
-    }
-    return true;
 }
 
-// Up the V at coarse level l < nlev: the parent's correction, then one sweep into czb.
-__device__ __forceinline__ bool mg_up(const MgArgs& m, const MgGroup& g, const MgExec& ex, const MgPlan& P, int l,
-                                      size_t cbase)
+// Level V from the finer coarse level U: b = U's residuals summed over the children.
+__device__ __forceinline__ void down_coarse(const LView& U, const LView& V, int t0, int stride)
+{
+    const int area = V.w * V.h;
+    for (int q = t0; q < area; q += stride) {
+        const int I = V.i0 + q % V.w, J = V.j0 + q / V.w;
+        float bsum = 0.f;
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int ci = 2 * I + di - U.i0, cj = 2 * J + dj - U.j0;
+                if (ci < 0 || ci >= U.w || cj < 0 || cj >= U.h) continue;
+                const int c = cj * U.w + ci;
+                if (U.c[9 * U.cs + c] == 0.f) continue;   // empty child
+                bsum += U.b[c] - lv_apply(U, c, [&](int jj, int, int) { return U.za[jj]; });
+            }
+        V.b[q] = bsum;
+        V.za[q] = V.c[9 * V.cs + q] * bsum;
+    }
+}
+
+// One damped-Jacobi sweep dst = src + omega (b - A src) / diag.
+__device__ __forceinline__ void sweep(const LView& V, const float* src, float* dst, int t0, int stride)
+{
+    const int area = V.w * V.h;
+    for (int q = t0; q < area; q += stride) {
+        const float wd = V.c[9 * V.cs + q];
+        dst[q] = wd == 0.f ? 0.f : src[q] + wd * (V.b[q] - lv_apply(V, q, [&](int jj, int, int) { return src[jj]; }));
+    }
+}
+
+// Up at level V (parent level U): y = za + the parent's correction, then one
+// sweep into zb, with y formed on the fly at the neighbours.
+__device__ __forceinline__ void up_coarse(const LView& V, const LView& U, int t0, int stride)
+{
+    const int area = V.w * V.h;
+    auto y = [&](int j, int i, int jr) { return V.za[j] + kMgCoarseScale * U.zb[lv_parent(V, U, i, jr)]; };
+    for (int q = t0; q < area; q += stride) {
+        const float wd = V.c[9 * V.cs + q];
+        V.zb[q] = wd == 0.f ? 0.f : y(q, q % V.w, q / V.w) + wd * (V.b[q] - lv_apply(V, q, y));
+    }
+}
+
+// The levels held in the first CTA's shared memory (lloc..nlev), block
+// barriers only: down from level lloc - 1 (or the fine level), the coarsest
+// sweeps, up to lloc; level lloc's result is copied to global memory.
+__device__ void mg_local(const MgArgs& m, const MgPlan& P, const Geo2& G, size_t mo, size_t cbase, const double* r,
+                         float* sm)
+{
+    const int t0 = threadIdx.x, stride = blockDim.x;
+    const int L0 = P.lloc, L1 = P.nlev;
+    {
+        const LView V = lview_smem(sm, P.lev[L0]);
+        if (L0 == 1) down_fine(m, G, mo, r, V, t0, stride);
+        else down_coarse(lview_global(m, P.lev[L0 - 1], cbase), V, t0, stride);
+    }
+    __syncthreads();
+    for (int l = L0 + 1; l <= L1; ++l) {
+        down_coarse(lview_smem(sm, P.lev[l - 1]), lview_smem(sm, P.lev[l]), t0, stride);
+        __syncthreads();
+    }
+    {
+        const LView V = lview_smem(sm, P.lev[L1]);
+        static_assert(kMgSweeps % 2 == 1, "the coarsest result must end in zb");
+        for (int sw = 0; sw < kMgSweeps; ++sw) {
+            if (sw % 2 == 0) sweep(V, V.za, V.zb, t0, stride);
+            else sweep(V, V.zb, V.za, t0, stride);
+            __syncthreads();
+        }
+    }
+    for (int l = L1 - 1; l >= L0; --l) {
+        up_coarse(lview_smem(sm, P.lev[l]), lview_smem(sm, P.lev[l + 1]), t0, stride);
+        __syncthreads();
+    }
+    const LView V = lview_smem(sm, P.lev[L0]);
+    const LView Vg = lview_global(m, P.lev[L0], cbase);
+    for (int q = t0; q < V.w * V.h; q += stride) Vg.zb[q] = V.zb[q];
+}
+
+// z = M r on the member's group, given z0 = omega r / diag on the fine rows
+// and a group barrier since (r: FP64 fine residual, z: FP64 out).  Returns
+// false on a barrier timeout.
+__device__ bool mg_vcycle(const MgArgs& m, MgGroup& g, const MgPlan& P, const Geo2& G, int n, size_t mo,
+                          size_t cbase, const double* r, double* z, float* sm)
 {
     Ctl* ctl = m.s.ctl;
-    const MgLev& L = P.lev[l];
-    const MgLev& U = P.lev[l + 1];
-    const int area = L.w * L.h;
-    const size_t c0 = cbase + L.off;
-    for (int q = ex.t0; q < area; q += ex.stride) {
-        if (m.cc[9 * m.CT + c0 + q] == 0.f) continue;
-        const int I = (L.i0 + q % L.w) >> 1, J = (L.j0 + q / L.w) >> 1;
-        m.cza[c0 + q] += m.czb[cbase + U.off + (size_t)(J - U.j0) * U.w + (I - U.i0)];
-    }
-    if (!mg_bar(g, ex, m.budget, ctl)) return false;
-    for (int q = ex.t0; q < area; q += ex.stride) {
-        const float wd = m.cc[9 * m.CT + c0 + q];
-        m.czb[c0 + q] = wd == 0.f ? 0.f : m.cza[c0 + q] + wd * coarse_resid(m, L, cbase, q, m.cb[c0 + q], m.cza);
-    }
-    return mg_bar(g, ex, m.budget, ctl);
-}
-
-// z = M r on member b's group (r: FP64 fine residual, z: FP64 out).  Levels
-// of at most kMgLocal cells run on the group's first CTA alone (block
-// barriers) while the others wait at one group barrier.  Returns false on a
-// barrier timeout.
-constexpr int kMgLocal = 8192;
-
-__device__ bool mg_vcycle(const MgArgs& m, const MgGroup& g, const MgPlan& P, const Geo2& G, int n, size_t mo,
-                          size_t cbase, const double* r, double* z)
-{
-    const SolveArgs<double>& a = m.s;
-    Ctl* ctl = a.ctl;
-    const MgExec ex{g.G * (int)blockDim.x, g.rank * (int)blockDim.x + (int)threadIdx.x, g.G == 1};
-    const MgExec lx{(int)blockDim.x, (int)threadIdx.x, true};
-    // fine pre-smoothing from zero and residual
-    for (int k = ex.t0; k < n; k += ex.stride) m.z0[mo + k] = m.cf[9 * m.T + mo + k] * (float)r[mo + k];
-    if (!mg_sync(g, m.budget, ctl)) return false;
+    const int stride = g.G * blockDim.x, t0 = g.rank * blockDim.x + threadIdx.x;
+    const float* z0 = m.z0 + mo;
     if (P.nlev > 0) {
-        for (int k = ex.t0; k < n; k += ex.stride) m.t0[mo + k] = fine_resid(m, mo, k, (float)r[mo + k], m.z0);
-        if (!mg_sync(g, m.budget, ctl)) return false;
-        // first level small enough for one CTA
-        int lloc = 1;
-        if (g.G > 1) {
-            lloc = P.nlev + 1;
-            for (int l = 1; l <= P.nlev; ++l)
-                if (P.lev[l].w * P.lev[l].h <= kMgLocal) { lloc = l; break; }
-        }
-        for (int l = 1; l < lloc; ++l)
-            if (!mg_down(m, g, ex, P, G, l, mo, cbase)) return false;
-        if (lloc <= P.nlev) {
-            if (g.rank == 0) {
-                for (int l = lloc; l <= P.nlev; ++l) mg_down(m, g, lx, P, G, l, mo, cbase);
-                for (int l = P.nlev - 1; l >= lloc; --l) mg_up(m, g, lx, P, l, cbase);
+        const int lg = min(P.lloc - 1, P.nlev);   // levels 1..lg in global memory, group-wide
+        for (int l = 1; l <= lg; ++l) {
+            const LView V = lview_global(m, P.lev[l], cbase);
+            if (l == 1) down_fine(m, G, mo, r, V, t0, stride);
+            else down_coarse(lview_global(m, P.lev[l - 1], cbase), V, t0, stride);
+            if (!mg_sync(g, m.budget, ctl)) return false;
+            if (l == P.nlev) {   // coarsest in global memory
+                for (int sw = 0; sw < kMgSweeps; ++sw) {
+                    if (sw % 2 == 0) sweep(V, V.za, V.zb, t0, stride);
+                    else sweep(V, V.zb, V.za, t0, stride);
+                    if (!mg_sync(g, m.budget, ctl)) return false;
+                }
             }
+        }
+        if (P.lloc <= P.nlev) {
+            if (g.rank == 0) mg_local(m, P, G, mo, cbase, r, sm);
             if (!mg_sync(g, m.budget, ctl)) return false;
         }
-        for (int l = lloc - 1; l >= 1; --l) {
-            if (l == P.nlev) continue;   // the coarsest level has no parent
-            if (!mg_up(m, g, ex, P, l, cbase)) return false;
+        for (int l = min(lg, P.nlev - 1); l >= 1; --l) {
+            up_coarse(lview_global(m, P.lev[l], cbase), lview_global(m, P.lev[l + 1], cbase), t0, stride);
+            if (!mg_sync(g, m.budget, ctl)) return false;
         }
-        // fine: coarse correction
-        const MgLev& U = P.lev[1];
-        for (int k = ex.t0; k < n; k += ex.stride) {
-            const int c = a.list[mo + k];
-            const int I = (c % G.nx) >> 1, J = (c / G.nx) >> 1;
-            m.z0[mo + k] += m.czb[cbase + U.off + (size_t)(J - U.j0) * U.w + (I - U.i0)];
+        // fine: y = z0 + the level-1 correction, then one sweep
+        const float* zb1 = m.czb + cbase + P.lev[1].off;
+        const int* par = m.par + mo;
+        auto y = [&](int j) { return z0[j] + kMgCoarseScale * zb1[par[j]]; };
+        for (int k = t0; k < n; k += stride) {
+            const float yk = y(k);
+            z[mo + k] = (double)(yk + m.cf[9 * m.T + mo + k] * ((float)r[mo + k] - fine_apply(m, mo, k, y)));
         }
-        if (!mg_sync(g, m.budget, ctl)) return false;
-    }
-    // fine post-smoothing
-    for (int k = ex.t0; k < n; k += ex.stride) {
-        const float zk = m.z0[mo + k] + m.cf[9 * m.T + mo + k] * fine_resid(m, mo, k, (float)r[mo + k], m.z0);
-        z[mo + k] = (double)zk;
+    } else {
+        for (int k = t0; k < n; k += stride)
+            z[mo + k] = (double)(z0[k] + m.cf[9 * m.T + mo + k] *
+                                             ((float)r[mo + k] - fine_apply(m, mo, k, [&](int j) { return z0[j]; })));
     }
     return true;
 }
@@ -589,9 +639,10 @@ __device__ bool mg_vcycle(const MgArgs& m, const MgGroup& g, const MgPlan& P, co
 
 // Multigrid set-up and PCG for every member that solves with CG this step
 // (after k_solve_init: x = warm start, r = R - A x, p = 0).  Cooperative
-// launch of kMgThreads-thread CTAs.
+// launch of kMgThreads-thread CTAs with kMgSmemBytes of dynamic shared memory.
 static __global__ void __launch_bounds__(kMgThreads) k2_mg_pcg(MgArgs m)
 {
+    extern __shared__ __align__(16) float mg_sm[];
     __shared__ double red[96];
     __shared__ double bc[4];
     __shared__ MgPlan P;
@@ -612,7 +663,7 @@ static __global__ void __launch_bounds__(kMgThreads) k2_mg_pcg(MgArgs m)
         const size_t cbase = (size_t)b * m.cpitch;
         const Geo2 G = m.geos[b];
         const int stride = g.G * blockDim.x, t0i = g.rank * blockDim.x + threadIdx.x;
-        // ---- set-up: FP32 fine rows, then the coarse rows level by level
+        // ---- set-up: FP32 fine rows and level-1 parents, then the coarse rows level by level
         for (int k = t0i; k < n; k += stride) {
             const size_t o = mo + k, es = a.ext_stride;
             const double d = a.diag[o];
@@ -626,6 +677,11 @@ static __global__ void __launch_bounds__(kMgThreads) k2_mg_pcg(MgArgs m)
             m.cf[6 * m.T + o] = (float)a.ext_c[4 * es + o];
             m.cf[8 * m.T + o] = (float)a.ext_c[5 * es + o];
             m.cf[9 * m.T + o] = (float)((double)kMgOmega / d);
+            if (P.nlev > 0) {
+                const int c = a.list[o];
+                const MgLev& L = P.lev[1];
+                m.par[o] = (((c / G.nx) >> 1) - L.j0) * L.w + (((c % G.nx) >> 1) - L.i0);
+            }
         }
         if (!mg_sync(g, m.budget, ctl)) return;
         for (int l = 1; l <= P.nlev; ++l) {
@@ -637,8 +693,22 @@ static __global__ void __launch_bounds__(kMgThreads) k2_mg_pcg(MgArgs m)
             }
             if (!mg_sync(g, m.budget, ctl)) return;
         }
+        // the shared-memory levels' rows, once per solve
+        if (g.rank == 0 && P.lloc <= P.nlev) {
+            for (int l = P.lloc; l <= P.nlev; ++l) {
+                const MgLev& L = P.lev[l];
+                for (int q = threadIdx.x; q < L.w * L.h; q += blockDim.x)
+#pragma unroll
+                    for (int s2 = 0; s2 < 10; ++s2)
+                        mg_sm[(size_t)s2 * kMgSmemCells + L.soff + q] = m.cc[s2 * m.CT + cbase + L.off + q];
+            }
+            __syncthreads();
+        }
+        float* z0 = m.z0 + mo;
         // ---- z = M r, rz = <r, z>
-        if (!mg_vcycle(m, g, P, G, n, mo, cbase, a.r, a.z)) return;
+        for (int k = t0i; k < n; k += stride) z0[k] = m.cf[9 * m.T + mo + k] * (float)a.r[mo + k];
+        if (!mg_sync(g, m.budget, ctl)) return;
+        if (!mg_vcycle(m, g, P, G, n, mo, cbase, a.r, a.z, mg_sm)) return;
         double v1[1] = {0.0};
         for (int k = t0i; k < n; k += stride) v1[0] += a.r[mo + k] * a.z[mo + k];
         if (!mg_sum<1>(g, v1, red, bc, m.gpart, m.budget, ctl)) return;
@@ -652,16 +722,17 @@ static __global__ void __launch_bounds__(kMgThreads) k2_mg_pcg(MgArgs m)
             const double* rold = (it & 1) ? a.r : a.r1;
             double* rnew = (it & 1) ? a.r1 : a.r;
             iters = it;
-            for (int k = t0i; k < n; k += stride) pnew[mo + k] = a.z[mo + k] + beta * pold[mo + k];
-            if (!mg_sync(g, m.budget, ctl)) return;
+            // q = A p with p = z + beta p_old formed at the neighbours on the fly
             double vq[1] = {0.0};
             for (int k = t0i; k < n; k += stride) {
+                auto pv = [&](int j) { return a.z[mo + j] + beta * pold[mo + j]; };
                 const int kl = a.nbl[mo + k], kr = a.nbr[mo + k];
-                const double pk = pnew[mo + k];
-                const double pl = kl >= 0 ? pnew[mo + kl] : 0.0;
-                const double pr = kr >= 0 ? pnew[mo + kr] : 0.0;
+                const double pk = pv(k);
+                const double pl = kl >= 0 ? pv(kl) : 0.0;
+                const double pr = kr >= 0 ? pv(kr) : 0.0;
                 double qk = apply_row(a, mo, k, pk, pl, pr);
-                qk += ext_terms(a, mo, k, [&](int j) { return pnew[mo + j]; });
+                qk += ext_terms(a, mo, k, pv);
+                pnew[mo + k] = pk;
                 a.q[mo + k] = qk;
                 vq[0] += pk * qk;
             }
@@ -671,9 +742,12 @@ static __global__ void __launch_bounds__(kMgThreads) k2_mg_pcg(MgArgs m)
             const double alpha = rz / pq;
             for (int k = t0i; k < n; k += stride) {
                 a.x[mo + k] += alpha * pnew[mo + k];
-                rnew[mo + k] = rold[mo + k] - alpha * a.q[mo + k];
+                const double rk = rold[mo + k] - alpha * a.q[mo + k];
+                rnew[mo + k] = rk;
+                z0[k] = m.cf[9 * m.T + mo + k] * (float)rk;
             }
-            if (!mg_vcycle(m, g, P, G, n, mo, cbase, rnew, a.z)) return;
+            if (!mg_sync(g, m.budget, ctl)) return;
+            if (!mg_vcycle(m, g, P, G, n, mo, cbase, rnew, a.z, mg_sm)) return;
             double v3[3] = {0.0, 0.0, 0.0};
             for (int k = t0i; k < n; k += stride) {
                 const double zk = a.z[mo + k], rk = rnew[mo + k];

@@ -44,7 +44,7 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh2d_set_member_bottom_motion", "nh2d_set_graphs", "nh2d_set_member_state", "nh2d_get_member_state",
            "nh2d_get_member_mask", "nh2d_get_member_info", "nh2d_graph_runs", "nh2d_set_precision",
            "nh2d_set_wait_budget", "nh2d_set_preconditioner", "nh2d_set_profiling", "nh2d_get_profile",
-           "nh2d_put_member_state")
+           "nh2d_put_member_state", "nh2d_set_tile")
 NH_CNN_PARAMS = 9328
 NH_CNN_IN = 16
 NH_STATIC_MAX_CELLS = 262144
@@ -143,6 +143,8 @@ def load():
         L.nh2d_set_profiling.argtypes = [C.c_void_p, C.c_int]
         L.nh2d_put_member_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.nh2d_put_member_state.restype = C.c_int
+        L.nh2d_set_tile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
+        L.nh2d_set_tile.restype = C.c_int
         L.nh2d_get_profile.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
         L.nh_set_tile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
         L.nh_get_profile.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
@@ -614,6 +616,13 @@ class Grid2D:
     def set_preconditioner(self, kind=NH_PRECOND_MG):
         """NH_PRECOND_MG (default) or NH_PRECOND_LINE for the CG solve."""
         _check(self.L.nh2d_set_preconditioner(self.h, int(kind)), "nh2d_set_preconditioner")
+
+    def set_tile(self, tile=-1):
+        """FP32 predictor tile: 0..3 forces a candidate (32x16, 64x8, 32x8, 64x16), -2 re-times at
+        the next step, -1 only reads.  Returns the candidate in use (-1: not chosen yet)."""
+        out = C.c_int(-1)
+        _check(self.L.nh2d_set_tile(self.h, int(tile), C.byref(out)), "nh2d_set_tile")
+        return out.value
 
     def set_profiling(self, enable=True):
         """Event pairs around every launch of later (host-enqueued) steps."""

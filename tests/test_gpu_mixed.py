@@ -6,9 +6,9 @@ Tolerance: max |d eta| <= 1e-4 a and max |d hu|, |d hw| <= 1e-4 a sqrt(g h_max)
 (a = wave or slide amplitude), for every run whose non-hydrostatic cells are
 the same on both sides: global and hydrostatic runs, and adaptive runs up to
 the first step where a criterion value lies within FP32 rounding of k_nh and
-the two sides mark a different cell.  Such a decision flip moves the
-Dirichlet edge of the elliptic problem by one cell; its effect is bounded
-separately (1e-2 a) and the measured size is printed.
+the two sides mark a different cell.  Such a decision must be a near-tie of
+the oracle's own criterion value; after it the two runs solve on different
+sub-domains and are not compared.
 """
 import numpy as np
 import pytest
@@ -54,10 +54,20 @@ def test_mixed_global_solitary():
     G.close()
 
 
+def _near_tie(p, d0, t, dt, s, cells, rel=1e-3):
+    """Every differing mask cell has, within its enlargement, an oracle
+    criterion value within rel of k_nh (state s before the step)."""
+    ht, hut, hwt = O.predict(p, d0, t, dt, s.h, s.hu, s.hw)
+    c = O.criterion(p, d0, t + dt, ht, hut, hwt)
+    e = p.enlarge
+    return all(np.any(np.abs(c[max(0, i - e):i + e + 1] - p.knh) <= rel * p.knh) for i in cells)
+
+
 @pytest.mark.parametrize("wl_name", ["slide", "solitary"])
 def test_mixed_adaptive_until_decision_flip(wl_name):
     """Step by step: while both sides mark the same cells the mixed state is
-    within 1e-4 a; after a flip (if any) within 1e-2 a."""
+    within 1e-4 a; the first differing decision of a member is a near-tie,
+    and that member is not compared afterwards."""
     wl = _slide() if wl_name == "slide" else W.solitary_1d()
     n = 300
     members = range(len(wl.members))
@@ -68,10 +78,11 @@ def test_mixed_adaptive_until_decision_flip(wl_name):
     agree = [True] * len(wl.members)
     first_flip = [None] * len(wl.members)
     worst_agree = 0.0
-    worst_after = 0.0
     for k in range(n):
         masks = []
+        befores = []
         for b in members:
+            befores.append(states[b].copy())
             st, info, mk = O.step(params[b], wl.members[b].d0, k * wl.dt, k, wl.dt, states[b],
                                   want_mask=True)
             masks.append(mk)
@@ -79,18 +90,19 @@ def test_mixed_adaptive_until_decision_flip(wl_name):
         gm, _, _ = G.get_mask()
         h, hu, hw, _ = G.get_state()
         for b in members:
-            if agree[b] and not np.array_equal(gm[b], masks[b]):
+            if not agree[b]:
+                continue
+            if not np.array_equal(gm[b], masks[b]):
                 agree[b] = False
                 first_flip[b] = k + 1
+                diff = np.flatnonzero(gm[b] != masks[b])
+                assert _near_tie(params[b], wl.members[b].d0, k * wl.dt, wl.dt, befores[b], diff), (b, k, diff)
+                continue
             e = float(np.max(np.abs(h[b] - states[b].h))) / a
-            if agree[b]:
-                worst_agree = max(worst_agree, e)
-                assert e <= 1e-4, (b, k, e)
-            else:
-                worst_after = max(worst_after, e)
-                assert e <= 1e-2, (b, k, e)
+            worst_agree = max(worst_agree, e)
+            assert e <= 1e-4, (b, k, e)
     print(f"mixed adaptive {wl_name}: worst |d eta|/a with equal masks {worst_agree:.2e}; "
-          f"first decision flip at steps {first_flip}; worst after a flip {worst_after:.2e}")
+          f"first decision flip at steps {first_flip}")
     G.close()
 
 
