@@ -62,6 +62,7 @@ struct MoundF {
     {
         if (!on) return 0.0f;
         const float xi = ((float)(i - ic) - fx) * sx;
+        if (xi * xi > (float)kMoundCut) return 0.0f;   // r2 >= xi^2: beyond the cut-off
         const float ze = ((float)(j - jc) - fy) * sy;
         const float r2 = xi * xi + ze * ze;
         return r2 <= (float)kMoundCut ? A * expf(-r2) : 0.0f;
@@ -184,8 +185,9 @@ static __global__ void __launch_bounds__(TX * TY, TX * TY <= 256 ? 4 : (TX * TY 
         for (int q = threadIdx.x; q < kPA; q += kPThreads) {
             const int ax = q % kPAX, ay = q / kPAX;
             int ox, oy;
-            const int c = g2_cell(G, i0 - 4 + ax, j0 - 4 + ay, &ox, &oy);
-            const int ci = c % G.nx, cj = c / G.nx;
+            const int ci = g2_index1(G.bcx, G.nx, i0 - 4 + ax, &ox);
+            const int cj = g2_index1(G.bcy, G.ny, j0 - 4 + ay, &oy);
+            const int c = cj * G.nx + ci;
             const float zc = z[c], m = M0.at(ci, cj), dz = d0s[c];
             const float hc = zc + dz;
             const float rh = 1.0f / hc;
@@ -213,8 +215,10 @@ static __global__ void __launch_bounds__(TX * TY, TX * TY <= 256 ? 4 : (TX * TY 
             const float hvs = Ahv[ca] + dt * r[2];
             const float hws = Ahw[ca] + dt * r[3];
             int ox, oy;
-            const int c = g2_cell(G, i0 - 2 + bx, j0 - 2 + by, &ox, &oy);
-            const float m = M1.at(c % G.nx, c / G.nx), dz = d0s[c];
+            const int ci = g2_index1(G.bcx, G.nx, i0 - 2 + bx, &ox);
+            const int cj = g2_index1(G.bcy, G.ny, j0 - 2 + by, &oy);
+            const int c = cj * G.nx + ci;
+            const float m = M1.at(ci, cj), dz = d0s[c];
             const float rh = 1.0f / (zs + dz);
             Be[q] = zs + m;
             Bd[q] = dz - m;
