@@ -41,10 +41,11 @@ def build(force: bool = False) -> str:
     both x86 and Arm hosts, so results do not depend on FMA contraction.
     """
     os.makedirs(_BUILD, exist_ok=True)
-    src = [os.path.join(_HERE, "nh_oracle.c"), os.path.join(_HERE, "nh_oracle2d.c")]
+    src = [os.path.join(_HERE, f) for f in ("nh_oracle.c", "nh_oracle2d.c", "nh_oracle_dg.c")]
     src = [s for s in src if os.path.exists(s)]
     out = os.path.join(_BUILD, "libnh_oracle.so")
-    hdrs = [os.path.join(_HERE, h) for h in ("nh_oracle.h", "nh_oracle2d.h") if os.path.exists(os.path.join(_HERE, h))]
+    hdrs = [os.path.join(_HERE, h) for h in ("nh_oracle.h", "nh_oracle2d.h", "nh_oracle_dg.h")
+            if os.path.exists(os.path.join(_HERE, h))]
     newest = max(os.path.getmtime(s) for s in src + hdrs)
     if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
         tmp = out + f".tmp{os.getpid()}"
@@ -137,6 +138,9 @@ def lib():
             if hasattr(L, "or2_step"):
                 from . import oracle2d  # noqa: F401  (binds the 2D entry points)
                 oracle2d._bind(L)
+            if hasattr(L, "or_dg_step"):
+                from . import oracle_dg  # noqa: F401  (binds the DG / LDG entry points)
+                oracle_dg._bind(L)
             _LIB = L
     return _LIB
 
