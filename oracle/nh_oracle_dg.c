@@ -346,10 +346,10 @@ void or_dg_assemble(const or_dg_params* P, double t1, double dt, const double* h
    n = 4 ne unknowns, lower bandwidth KL = 7 and upper bandwidth KU = 7 of the
    block-tridiagonal matrix; pivoting widens the upper band by KL.  Row r of
    the band holds columns r - KL .. r + KL + KU at index c - r + KL. */
-int or_dg_solve(const or_dg_params* P, const double* blk, const double* rhs, double* x, double* rel_res)
+static int band_solve(int ne, const double* blk, const double* rhs, double* x)
 {
     enum { KL = 7, KU = 7, W = 2 * KL + KU + 1 };
-    int ne = P->ne, n = 4 * ne;
+    int n = 4 * ne;
     double* A = calloc((size_t)n * W, sizeof(double));
     double* b = malloc(sizeof(double) * n);
 #define AB(r, c) A[(size_t)(r) * W + ((c) - (r) + KL)]
@@ -393,23 +393,55 @@ int or_dg_solve(const or_dg_params* P, const double* blk, const double* rhs, dou
             for (int j = r + 1; j <= jmax; ++j) s -= AB(r, j) * x[j];
             x[r] = s / AB(r, r);
         }
-        /* relative residual of the original system */
-        double rr = 0.0, bb = 0.0;
-        for (int i = 0; i < ne; ++i)
-            for (int a = 0; a < 4; ++a) {
-                double s = rhs[4 * i + a];
-                for (int q = 0; q < 3; ++q) {
-                    int e = i + q - 1;
-                    if (e < 0 || e >= ne) continue;
-                    for (int c = 0; c < 4; ++c) s -= blk[48 * i + 16 * q + 4 * a + c] * x[4 * e + c];
-                }
-                rr += s * s;
-                bb += rhs[4 * i + a] * rhs[4 * i + a];
-            }
-        if (rel_res) *rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     }
 #undef AB
     free(A); free(b);
+    return status;
+}
+
+/* r = rhs - A x of the block-tridiagonal system; returns ||rhs||^2 in *bb. */
+static double dg_residual(int ne, const double* blk, const double* rhs, const double* x, double* r, double* bb)
+{
+    double rr = 0.0, b2 = 0.0;
+    for (int i = 0; i < ne; ++i)
+        for (int a = 0; a < 4; ++a) {
+            double s = rhs[4 * i + a];
+            for (int q = 0; q < 3; ++q) {
+                int e = i + q - 1;
+                if (e < 0 || e >= ne) continue;
+                for (int c = 0; c < 4; ++c) s -= blk[48 * i + 16 * q + 4 * a + c] * x[4 * e + c];
+            }
+            r[4 * i + a] = s;
+            rr += s * s;
+            b2 += rhs[4 * i + a] * rhs[4 * i + a];
+        }
+    *bb = b2;
+    return rr;
+}
+
+/* The banded elimination, then two steps of iterative refinement (the
+   residual in FP64, the correction by the same elimination): the system's
+   conditioning amplifies the elimination's rounding (the unscaled penalty c11
+   dominates the p-rows over the physical terms), and refinement brings the
+   solution back to the accuracy that conditioning allows. */
+int or_dg_solve(const or_dg_params* P, const double* blk, const double* rhs, double* x, double* rel_res)
+{
+    int ne = P->ne, n = 4 * ne;
+    int status = band_solve(ne, blk, rhs, x);
+    double* r = malloc(sizeof(double) * n);
+    double* dx = malloc(sizeof(double) * n);
+    double bb = 0.0;
+    for (int it = 0; it < 2 && status == OR_OK; ++it) {
+        dg_residual(ne, blk, rhs, x, r, &bb);
+        status = band_solve(ne, blk, r, dx);
+        if (status == OR_OK)
+            for (int k = 0; k < n; ++k) x[k] += dx[k];
+    }
+    if (status == OR_OK && rel_res) {
+        double rr = dg_residual(ne, blk, rhs, x, r, &bb);
+        *rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+    free(r); free(dx);
     return status;
 }
 

@@ -87,7 +87,8 @@ void or_dg_assemble(const or_dg_params* P, double t1, double dt, const double* h
                     const double* hwt, const unsigned char* mask, double* blk, double* rhs);
 
 /* Solve the block-tridiagonal system by banded Gaussian elimination with
-   partial pivoting; x: 4 ne unknowns. */
+   partial pivoting and two steps of iterative refinement; x: 4 ne unknowns;
+   rel_res (nullable): ||rhs - A x|| / ||rhs||. */
 int or_dg_solve(const or_dg_params* P, const double* blk, const double* rhs, double* x, double* rel_res);
 
 /* Correction (Eqs. 10-11 through the LDG unknowns): h = h~, hu = the LDG hu,
