@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libnhswe.so")
 
-SOURCES = ["nh_api.cu", "nh_static.cu", "nh_cnn.cu", "nh_api2d.cu"]
+SOURCES = ["nh_api.cu", "nh_static.cu", "nh_cnn.cu", "nh_api2d.cu", "nh_dg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

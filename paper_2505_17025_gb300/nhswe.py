@@ -44,12 +44,17 @@ EXPORTS = ("nh_workspace_bytes", "nh_create_grid", "nh_set_bottom_motion", "nh_s
            "nh2d_set_member_bottom_motion", "nh2d_set_graphs", "nh2d_set_member_state", "nh2d_get_member_state",
            "nh2d_get_member_mask", "nh2d_get_member_info", "nh2d_graph_runs", "nh2d_set_precision",
            "nh2d_set_wait_budget", "nh2d_set_preconditioner", "nh2d_set_profiling", "nh2d_get_profile",
-           "nh2d_put_member_state", "nh2d_set_tile")
+           "nh2d_put_member_state", "nh2d_set_tile",
+           "nh_dg_workspace_bytes", "nh_dg_create", "nh_dg_set_bottom_motion", "nh_dg_set_criterion",
+           "nh_dg_set_check", "nh_dg_set_state", "nh_dg_get_state", "nh_dg_get_mask", "nh_dg_step",
+           "nh_dg_run", "nh_dg_set_profiling", "nh_dg_get_profile", "nh_dg_destroy")
 NH_CNN_PARAMS = 9328
 NH_CNN_IN = 16
 NH_STATIC_MAX_CELLS = 262144
 KERNEL_CLASSES_2D = ("kin", "depth", "stage", "marks", "dilate", "compact", "assemble", "mass", "solve_init",
                      "solve", "summary", "clear", "correct")
+KERNEL_CLASSES_DG = ("kinematics", "predict", "mark", "compact", "local", "form", "reduce", "back", "correct",
+                     "finish")
 KERNEL_CLASSES = ("kinematics", "predict", "compact", "assemble", "solve_init", "precond", "pcg_a",
                   "pcg_b", "cg_a", "cg_b", "bi_1", "bi_2", "bi_3", "summary", "clear", "correct",
                   "pcg_loop", "cnn")
@@ -85,6 +90,11 @@ class nh_grid2d_desc(C.Structure):
 class nh_slide2d_desc(C.Structure):
     _fields_ = [("shape", C.c_int), ("A", C.c_double), ("Lx", C.c_double), ("Ly", C.c_double),
                 ("xc0", C.c_double), ("yc0", C.c_double), ("s0", C.c_double), ("t0", C.c_double)]
+
+
+class nh_dg_desc(C.Structure):
+    _fields_ = [("ne", C.c_int), ("nbatch", C.c_int), ("dx", C.c_double), ("x0", C.c_double),
+                ("g", C.c_double), ("rho", C.c_double), ("c11", C.c_double)]
 
 
 class nh_run_info(C.Structure):
@@ -204,6 +214,25 @@ def load():
                   "nh2d_create_ensemble", "nh2d_set_member_bottom_motion", "nh2d_set_graphs",
                   "nh2d_set_member_state", "nh2d_get_member_state", "nh2d_get_member_mask",
                   "nh2d_get_member_info", "nh2d_set_precision"):
+            getattr(L, f).restype = C.c_int
+        L.nh_dg_workspace_bytes.argtypes = [C.POINTER(nh_dg_desc)]
+        L.nh_dg_workspace_bytes.restype = sz
+        L.nh_dg_create.argtypes = [C.POINTER(nh_dg_desc), _D, vp, sz, vp, C.POINTER(C.c_void_p)]
+        L.nh_dg_set_bottom_motion.argtypes = [vp, C.POINTER(nh_slide_desc)]
+        L.nh_dg_set_criterion.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int]
+        L.nh_dg_set_check.argtypes = [vp, C.c_int]
+        L.nh_dg_set_state.argtypes = [vp, _D, _D, _D, C.c_double]
+        L.nh_dg_get_state.argtypes = [vp, _D, _D, _D, _D]
+        L.nh_dg_get_mask.argtypes = [vp, C.POINTER(C.c_ubyte), _D]
+        L.nh_dg_step.argtypes = [vp, C.c_double, C.POINTER(nh_step_info)]
+        L.nh_dg_run.argtypes = [vp, C.c_double, C.c_longlong, C.POINTER(nh_run_info)]
+        L.nh_dg_set_profiling.argtypes = [vp, C.c_int]
+        L.nh_dg_get_profile.argtypes = [vp, _D, C.POINTER(C.c_longlong)]
+        L.nh_dg_destroy.argtypes = [vp]
+        L.nh_dg_destroy.restype = None
+        for f in ("nh_dg_create", "nh_dg_set_bottom_motion", "nh_dg_set_criterion", "nh_dg_set_check",
+                  "nh_dg_set_state", "nh_dg_get_state", "nh_dg_get_mask", "nh_dg_step", "nh_dg_run",
+                  "nh_dg_set_profiling", "nh_dg_get_profile"):
             getattr(L, f).restype = C.c_int
         L.nh_status_string.argtypes = [C.c_int]
         L.nh_status_string.restype = C.c_char_p
@@ -719,3 +748,112 @@ def grid_from_workload(wl, precision=NH_FP64, limiter=NH_LIM_CENTRAL, bc=None, *
                              for m in ms])
     G.set_state([m.h for m in ms], [m.hu for m in ms], [m.hw for m in ms])
     return G
+
+
+class GridDG:
+    """A batch of 1D members in the paper's DG-P1 / LDG discretisation
+    (``include/nhswe_dg.h``), stepping through the C ABI.
+
+    Per-node arrays are (nbatch, 2 ne): node 2i is element i's left end, node
+    2i+1 its right end.  ``d0`` holds the static nodal depths.  Workspace and
+    stream come from PyTorch as for ``Grid``.
+    """
+
+    def __init__(self, ne, dx, d0, nbatch=1, x0=0.0, g=9.81, rho=1000.0, c11=0.5, stream=None):
+        import torch
+        self.L = load()
+        self.ne, self.nb = int(ne), int(nbatch)
+        self.nn = 2 * self.ne
+        self.dx = float(dx)
+        self.desc = nh_dg_desc(self.ne, self.nb, float(dx), float(x0), float(g), float(rho), float(c11))
+        nbytes = self.L.nh_dg_workspace_bytes(C.byref(self.desc))
+        if nbytes == 0:
+            raise NHError(NH_ERR_ARG, "nh_dg_workspace_bytes")
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        self._ws_ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d0c = self._nodes(d0)
+        h = C.c_void_p()
+        _check(self.L.nh_dg_create(C.byref(self.desc), _dptr(d0c), C.c_void_p(self._ws_ptr), C.c_size_t(nbytes),
+                                   C.c_void_p(self.stream.cuda_stream), C.byref(h)), "nh_dg_create")
+        self.h = h
+        self.workspace_bytes = nbytes
+
+    def _nodes(self, a):
+        arr = np.asarray(a, dtype=np.float64)
+        if arr.ndim == 1 and arr.size == self.nn:
+            arr = np.broadcast_to(arr, (self.nb, self.nn))
+        return _f64(np.ascontiguousarray(arr), self.nb * self.nn)
+
+    def nodes(self):
+        """Node positions (2 ne) of every member."""
+        i = np.arange(self.ne)
+        x = np.empty(self.nn)
+        x[0::2] = self.desc.x0 + i * self.dx
+        x[1::2] = self.desc.x0 + (i + 1) * self.dx
+        return x
+
+    def set_bottom_motion(self, slides):
+        if slides is None:
+            _check(self.L.nh_dg_set_bottom_motion(self.h, None), "nh_dg_set_bottom_motion")
+            return
+        arr = (nh_slide_desc * self.nb)()
+        for b, s in enumerate(slides):
+            arr[b] = nh_slide_desc(int(s.get("shape", NH_SLIDE_GAUSS_LNCOSH)), float(s.get("A", 0.0)),
+                                   float(s.get("L", 1.0)), float(s.get("xc0", 0.0)), float(s.get("s0", 0.0)),
+                                   float(s.get("t0", 1.0)), float(s.get("t2", 0.0)))
+        _check(self.L.nh_dg_set_bottom_motion(self.h, arr), "nh_dg_set_bottom_motion")
+
+    def set_criterion(self, kind, k_nh=1e-3, enlarge=1, first_step_global=False):
+        _check(self.L.nh_dg_set_criterion(self.h, int(kind), float(k_nh), int(enlarge),
+                                          int(bool(first_step_global))), "nh_dg_set_criterion")
+
+    def set_check(self, check=True):
+        _check(self.L.nh_dg_set_check(self.h, int(bool(check))), "nh_dg_set_check")
+
+    def set_state(self, h, hu, hw, t=0.0):
+        h, hu, hw = self._nodes(h), self._nodes(hu), self._nodes(hw)
+        _check(self.L.nh_dg_set_state(self.h, _dptr(h), _dptr(hu), _dptr(hw), float(t)), "nh_dg_set_state")
+
+    def get_state(self):
+        n = self.nb * self.nn
+        h, hu, hw, p = (np.empty(n) for _ in range(4))
+        _check(self.L.nh_dg_get_state(self.h, _dptr(h), _dptr(hu), _dptr(hw), _dptr(p)), "nh_dg_get_state")
+        return tuple(a.reshape(self.nb, self.nn) for a in (h, hu, hw, p))
+
+    def get_mask(self):
+        m = np.empty(self.nb * self.ne, dtype=np.uint8)
+        rr = np.empty(self.nb)
+        _check(self.L.nh_dg_get_mask(self.h, m.ctypes.data_as(C.POINTER(C.c_ubyte)), _dptr(rr)), "nh_dg_get_mask")
+        return m.reshape(self.nb, self.ne), rr
+
+    def step(self, dt):
+        info = nh_step_info()
+        st = self.L.nh_dg_step(self.h, float(dt), C.byref(info))
+        return st, info.as_dict()
+
+    def run(self, dt, n_steps):
+        info = nh_run_info()
+        st = self.L.nh_dg_run(self.h, float(dt), int(n_steps), C.byref(info))
+        return st, {"steps": info.steps, "active_total": info.active_total, "last": info.last.as_dict()}
+
+    def set_profiling(self, enable=True):
+        _check(self.L.nh_dg_set_profiling(self.h, int(bool(enable))), "nh_dg_set_profiling")
+
+    def get_profile(self):
+        ms = np.zeros(len(KERNEL_CLASSES_DG))
+        n = np.zeros(len(KERNEL_CLASSES_DG), dtype=np.int64)
+        _check(self.L.nh_dg_get_profile(self.h, _dptr(ms), n.ctypes.data_as(C.POINTER(C.c_longlong))),
+               "nh_dg_get_profile")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES_DG)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.nh_dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -97,3 +97,18 @@ def test_product_path_fails_loudly_without_a_gpu():
         nhswe.grid_from_workload(W.slide_1d(n_members=1, nx=64, length=1.0, T=0.01))
     with pytest.raises(RuntimeError):
         nhswe.Grid2D(8, 8, 0.1, 0.1, np.ones((8, 8)))
+
+
+def test_workspace_size_dg_needs_no_gpu():
+    """The DG handle's workspace grows with members x elements; invalid
+    descriptors (ne < 2, dx <= 0, negative c11) give 0."""
+    lib = ctypes.CDLL(B.build())
+    lib.nh_dg_workspace_bytes.argtypes = [ctypes.POINTER(nhswe.nh_dg_desc)]
+    lib.nh_dg_workspace_bytes.restype = ctypes.c_size_t
+    D = nhswe.nh_dg_desc
+    small = lib.nh_dg_workspace_bytes(ctypes.byref(D(200, 1, 4.0, 0.0, 9.81, 1000.0, 0.5)))
+    big = lib.nh_dg_workspace_bytes(ctypes.byref(D(50000, 64, 1e-3, 0.0, 9.81, 1000.0, 0.5)))
+    assert small > 200 * 8 * 30 and big > 64 * 50000 * 8 * 60
+    for bad in (D(1, 1, 4.0, 0.0, 9.81, 1000.0, 0.5), D(200, 1, 0.0, 0.0, 9.81, 1000.0, 0.5),
+                D(200, 1, 4.0, 0.0, 9.81, 1000.0, -0.5), D(200, 0, 4.0, 0.0, 9.81, 1000.0, 0.5)):
+        assert lib.nh_dg_workspace_bytes(ctypes.byref(bad)) == 0
