@@ -1014,6 +1014,217 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# DG-P1 / LDG path (nhswe_dg.h): algorithmic bytes per unit (FP64).  Units:
+# elements of the batch for the predictor and the compaction, marked elements
+# for the rest (the cyclic reduction's and back-substitution's bytes are
+# summed over their levels by _dg_cr_bytes).
+BYTES_PER_UNIT_DG = {
+    "predict": 129.0,   # read h, hu, hw, d0 at both nodes (64); write h~, hu~, hw~, p = 0 (64); the mark
+    "compact": 6.0,     # read the mark, write the mask byte and the int32 list entry
+    "local": 272.0,     # read list (8), h~, hu~, hw~, d0 at both nodes (64), outside hu (8); write hu(p) map,
+                        # correction factors (14 doubles) and the row's own blocks (10 doubles)
+    "form": 104.0,      # read list (8), left neighbour's hu_R map (32), D00, r0 (16); write L, D00, r0 (48)
+    "correct": 368.0,   # read list, x (own + next), 14 local doubles, h~, hw~ (176); write hu, hw, p (48);
+                        # residual check: the row (112) and both neighbours' x (32)
+}
+
+
+# The DG predictor is bound by the FP64 pipe: FP64 operations per element and
+# step counted from the algorithm (a node: 1/h, u, three flux components and
+# the wave speed, 11; an interface: the Rusanov flux, 19; an element: volume
+# and interface terms through the inverse mass matrix and the nodal source,
+# 39, the static slope 2; stage updates 12 and 18; two nodes and one
+# interface per element and stage; criterion and mass 11): 205.
+FLOPS_PER_ELEMENT_DG_PREDICT = 205.0
+
+
+def _dg_cr_bytes(n0, ne, small_rows=512):
+    """Algorithmic bytes of the block cyclic reduction of one member with n0
+    marked elements (rows of 14 doubles, x of 2): (reduce incl. the
+    shared-memory levels, back-substitution of the global levels)."""
+    lev = 0
+    while -(-ne // (1 << lev)) > small_rows:
+        lev += 1
+    red = back = 0.0
+    n = n0
+    for _ in range(lev):
+        n1 = -(-n // 2)
+        red += 112.0 * n + 112.0 * n1          # read every row of the level, write the even ones
+        back += 112.0 * (n - n1) + 16.0 * n1 + 16.0 * n   # odd rows and x of the level above in, x out
+        n = n1
+    red += 112.0 * n + 16.0 * n                # k_cr_small: rows in, x out
+    return red, back
+
+
+def run_dg(args):
+    """--workload dg_1d: the paper's own discretisation (DG-P1 predictor, LDG
+    mixed solve) on a batch of 1D slides, 64 members x 50 000 elements
+    (1e5 nodes each), adaptive |eta/d| > 1e-3 with one enlarging element,
+    FP64; timed after a spin-up to --t-start."""
+    import torch
+    from paper_2505_17025_gb300 import nhswe as N
+    from paper_2505_17025_gb300 import workloads as W
+    import oracle as O
+    import oracle.oracle_dg as D
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    wl = W.slide_dg_1d(n_members=args.members, seed0=rank_seed0(args.members, rank))
+    ms_ = wl.members
+    m0 = ms_[0]
+    ne, nb = m0.ne, len(ms_)
+    G = N.GridDG(ne, m0.dx, np.stack([m.d0() for m in ms_]), nbatch=nb, x0=m0.xl)
+    G.set_bottom_motion([dict(shape=m.slide, A=m.A, L=m.L, xc0=m.xc0, s0=m.s0, t0=m.t0) for m in ms_])
+    crit = N.NH_CRIT_GLOBAL if args.mode == "global" else N.NH_CRIT_ETA_D
+    G.set_criterion(crit, 1e-3, 1, False)
+    G.set_state(np.stack([m.h for m in ms_]), np.stack([m.hu for m in ms_]), np.stack([m.hw for m in ms_]), 0.0)
+    elements = ne * nb
+    dt = wl.dt
+
+    n_spin = int(round(args.t_start / dt))
+    t_spin0 = time.perf_counter()
+    if n_spin:
+        st, _ = G.run(dt, n_spin)
+        assert st == N.NH_OK, st
+    t_spin = time.perf_counter() - t_spin0
+    st, _ = G.run(dt, args.warmup)
+    assert st == N.NH_OK, st
+    # the timed window's start, handed to the oracle afterwards
+    h0, hu0, hw0, _ = G.get_state()
+    t_win = (n_spin + args.warmup) * dt
+
+    stream = G.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    torch.cuda.profiler.start()
+    e0.record(stream)
+    st, info = G.run(dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    clk = clocks.stop()
+    assert st == N.NH_OK, st
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    h1, hu1, hw1, _ = G.get_state()
+    ms = max_over_ranks(ms, ws, "cuda")
+    value = ws * elements * args.steps / (ms * 1e-3)
+    act_mean = info["active_total"] / max(args.steps, 1)
+
+    G.set_profiling(True)
+    st2, info2 = G.run(dt, args.steps)
+    prof = G.get_profile()
+    G.set_profiling(False)
+    launches = sum(n for _, n in prof.values())
+
+    # roofline of the dominant kernel class (bytes per launch / mean launch time)
+    name, (dms, dn) = max(prof.items(), key=lambda kv: kv[1][0])
+    peaks, peak_kind = _load_peaks()
+    act_member = act_mean / nb
+    red_b, back_b = _dg_cr_bytes(int(round(act_member)), ne)
+    per_step = {"predict": BYTES_PER_UNIT_DG["predict"] * elements, "compact": BYTES_PER_UNIT_DG["compact"] * elements,
+                "local": BYTES_PER_UNIT_DG["local"] * act_mean, "form": BYTES_PER_UNIT_DG["form"] * act_mean,
+                "correct": BYTES_PER_UNIT_DG["correct"] * act_mean, "reduce": red_b * nb, "back": back_b * nb}
+    roof = None
+    if dn > 0 and name in per_step:
+        launches_per_step = dn / args.steps
+        bytes_per_launch = per_step[name] / launches_per_step
+        t_launch = dms * 1e-3 / dn
+        if name == "predict":
+            flops = FLOPS_PER_ELEMENT_DG_PREDICT * elements
+            achieved = flops / t_launch / 1e12
+            peak = FP64_PEAK_GFLOPS / 1e3
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_dg_predict",
+                    "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 pipe)",
+                    "flops_per_launch": flops, "bytes_per_launch": bytes_per_launch,
+                    "hbm_frac": bytes_per_launch / t_launch / 1e9 / peaks["hbm_gbs"],
+                    "launches_per_step": launches_per_step, "avg_launch_us": 1e6 * t_launch}
+        else:
+            achieved = bytes_per_launch / t_launch / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": f"k_dg_{name}",
+                    "peak_kind": peak_kind, "bytes_per_launch": bytes_per_launch,
+                    "launches_per_step": launches_per_step, "avg_launch_us": 1e6 * t_launch}
+    step_bytes = sum(per_step.values())
+
+    # error against the oracle on the timed window: members 0 and nb-1 handed
+    # over at the window's start, the same steps on the oracle
+    errs, cpu = [], None
+    t_or = 0.0
+    if rank == 0 and not args.no_cpu_baseline:
+        for b in sorted({0, nb - 1})[:max(1, args.err_members)]:
+            m = ms_[b]
+            p = D.ParamsDG(ne=ne, dx=m.dx, xl=m.xl, b0=m.b0, b1=m.b1, slide=m.slide, A=m.A, L=m.L, xc0=m.xc0,
+                           s0=m.s0, t0=m.t0, crit=O.CRIT_GLOBAL if args.mode == "global" else O.CRIT_ETA_D,
+                           knh=1e-3, enlarge=1)
+            s = D.StateDG(h0[b], hu0[b], hw0[b])
+            tt = time.perf_counter()
+            for k in range(args.steps):
+                t = t_win + k * dt
+                st_o, _ = D.step(p, t, n_spin + args.warmup + k, dt, s)
+                assert st_o == O.OK
+            t_or += time.perf_counter() - tt
+            scale_u = m.A * math.sqrt(9.81 * (m.b0 + m.b1 * ne * m.dx))
+            errs.append({"member": b, "max_deta_over_a": float(np.max(np.abs(h1[b] - s.h)) / m.A),
+                         "max_dhu_over_a_sqrt_gh": float(np.max(np.abs(hu1[b] - s.hu)) / scale_u),
+                         "max_dhw_over_a_sqrt_gh": float(np.max(np.abs(hw1[b] - s.hw)) / scale_u)})
+        n_or = len(errs) * args.steps
+        cpu = {"value": ne * n_or / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(errs)} member(s) of {ne} elements, the timed window's {args.steps} steps each "
+                         f"({t_or:.1f} s of one host thread), FP64 C DG oracle (banded LDG solve, 2 refinements)"}
+
+    e2e = None
+    if args.e2e_steps > 0:
+        t_now = info2["last"]["t"]
+        hb = [np.empty((nb, 2 * ne)) for _ in range(4)]
+        h, hu, hw, _ = G.get_state()
+        torch.cuda.synchronize()
+        tt = time.perf_counter()
+        for k in range(args.e2e_steps):
+            G.set_state(h, hu, hw, t_now + k * dt)
+            G.step(dt)
+            h, hu, hw, _ = G.get_state()
+        el = time.perf_counter() - tt
+        e2e = {"value": ws * elements * args.e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 8 * 2 * elements, "d2h_bytes_per_step": 4 * 8 * 2 * elements,
+               "steps": args.e2e_steps}
+
+    if rank == 0:
+        out = {
+            "metric": "element-updates/s of the DG-P1 / LDG step incl. the LDG solve", "value": value,
+            "unit": "element-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"DG-P1/LDG 1D slides, {nb} members x {ne} elements, adaptive |eta/d|>1e-3 "
+                                   f"+ 1-element enlargement" if args.mode != "global" else
+                                   f"DG-P1/LDG 1D slides, {nb} members x {ne} elements, global",
+                       "dt": dt, "t_start": t_win, "spin_up_steps": n_spin, "spin_up_s": t_spin,
+                       "mean_marked_elements_per_step": act_mean, "step_bytes_algorithmic": step_bytes,
+                       "l2": "state (4 FP64 fields x 2 nodes) 205 MB per buffer > 129 MB L2; no flush",
+                       "error_vs_oracle": errs},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "timed_region": "nh_dg_run replaying captured CUDA graphs; kernel times from a second, "
+                            "event-profiled pass of the same length",
+            "clocks": clk,
+            "kernel_ms": {k: v[0] for k, v in prof.items() if v[1] > 0},
+            "kernel_launches": {k: v[1] for k, v in prof.items() if v[1] > 0},
+        }
+        print(json.dumps(out))
+    G.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1022,7 +1233,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="landslide_ensemble_2d",
                     choices=["landslide_ensemble_2d", "landslide_2d", "line_soliton_2d", "slide_1d",
-                             "paper_ratios"])
+                             "paper_ratios", "dg_1d"])
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed64"],
                     help="fp64; mixed64 = FP32 state with the FP64 solve; mixed = FP32 Krylov in FP64 "
                          "refinement (1D only).  Default: fp64 (1D), mixed64 (2D)")
@@ -1043,7 +1254,7 @@ def main():
     ap.add_argument("--form-harvest", type=int, default=20)
     ap.add_argument("--form-train", type=int, default=200)
     args = ap.parse_args()
-    two_d = args.workload not in ("slide_1d", "paper_ratios")
+    two_d = args.workload not in ("slide_1d", "paper_ratios", "dg_1d")
     if args.precision is None:
         args.precision = "mixed64" if two_d else "fp64"
     if args.precond is None:
@@ -1058,6 +1269,8 @@ def main():
         args.warmup = 3
     if args.workload == "paper_ratios":
         run_paper_ratios(args)
+    elif args.workload == "dg_1d" and args.impl == "ours":
+        run_dg(args)
     elif args.impl == "reference":
         run_reference_2d(args) if two_d else run_reference(args)
     elif two_d:

@@ -172,69 +172,100 @@ struct PredArgs {
     const DgTime* tc;
 };
 
-// Hydrostatic flux (hu, hu u + g h^2 / 2, hu hw / h) at a node.
-__device__ __forceinline__ void dg_flux(double g, double h, double hu, double hw, double F[3])
+// Nodal flux F(Q) = (hu, hu u + g h^2 / 2, hu hw / h) and the wave speed
+// |u| + sqrt(g h) of one node (Sec. 3.1): one reciprocal of h per node.  The
+// element's volume term and both Rusanov fluxes touching the node reuse them.
+struct NodeFlux {
+    double f0, f1, f2, s;
+};
+
+__device__ __forceinline__ NodeFlux node_flux(double g, double h, double hu, double hw)
 {
-    const double u = hu / h;
-    F[0] = hu;
-    F[1] = hu * u + 0.5 * g * h * h;
-    F[2] = hu * hw / h;
+    const double ih = 1.0 / h, u = hu * ih;
+    NodeFlux F;
+    F.f0 = hu;
+    F.f1 = hu * u + 0.5 * g * h * h;
+    F.f2 = hu * hw * ih;
+    F.s = fabs(u) + sqrt(g * h);
+    return F;
 }
 
-// Rusanov flux between a left and a right state (Sec. 3.1).
-__device__ __forceinline__ void dg_rusanov(double g, double hL, double huL, double hwL, double hR, double huR,
-                                           double hwR, double F[3])
+// The predictor tile: elements [e0, e0 + T); stage 1 runs on [e0 - 1, e0 + T]
+// and reads Q^n of [e0 - 2, e0 + T + 1].  Shared memory (doubles):
+//   q   Q^n nodes of elements e0-2 .. e0+T+1      3 x 2 (T + 4)
+//   qs  Q* nodes of elements e0-1 .. e0+T          3 x 2 (T + 2)
+//   k1  H(Q^n) of the tile's own elements          3 x 2 T
+//   nf  nodal fluxes and speeds of a stage         4 x 2 (T + 4)
+//   fi  interface fluxes of a stage                3 x (T + 3)
+constexpr int kQN = 2 * (kDgTile + 4), kQSN = 2 * (kDgTile + 2), kIF = kDgTile + 3;
+constexpr size_t kPredSmem = sizeof(double) * (3 * kQN + 3 * kQSN + 3 * 2 * kDgTile + 4 * kQN + 3 * kIF + 32);
+
+// One stage's nodal fluxes (nodes [n0, n0 + nn) of the smem array `q` with
+// stride `qn`, the first at global node k0), then interface fluxes for the
+// interfaces left of elements [ea, eb] (interface e between nodes 2e-1 and
+// 2e; walls mirror the end node: (h, -hu, hw)).  Interface e is stored at
+// fi[e - ea]; node k of the stage at nf[k - k0].
+__device__ __forceinline__ void stage_fluxes(const Geo& G, const double* q, int qn, int k0, int kn, int ea, int eb,
+                                             double* nf, double* fi, int tid)
 {
-    double FL[3], FR[3];
-    dg_flux(g, hL, huL, hwL, FL);
-    dg_flux(g, hR, huR, hwR, FR);
-    const double sL = fabs(huL / hL) + sqrt(g * hL), sR = fabs(huR / hR) + sqrt(g * hR);
-    const double s = sL > sR ? sL : sR;
-    F[0] = 0.5 * (FL[0] + FR[0]) - 0.5 * s * (hR - hL);
-    F[1] = 0.5 * (FL[1] + FR[1]) - 0.5 * s * (huR - huL);
-    F[2] = 0.5 * (FL[2] + FR[2]) - 0.5 * s * (hwR - hwL);
+    for (int j = tid; j < kn; j += kDgTile) {
+        const int k = k0 + j;
+        if (k < 0 || k >= 2 * G.ne) continue;
+        const NodeFlux F = node_flux(G.g, q[j], q[qn + j], q[2 * qn + j]);
+        nf[j] = F.f0; nf[kQN + j] = F.f1; nf[2 * kQN + j] = F.f2; nf[3 * kQN + j] = F.s;
+    }
+    __syncthreads();
+    for (int j = tid; j <= eb - ea; j += kDgTile) {
+        const int e = ea + j;
+        if (e < 0 || e > G.ne) continue;
+        // left state: node 2e-1 (or the mirror of node 0), right state: node 2e (or the mirror of node 2ne-1)
+        int kl = 2 * e - 1 - k0, kr = 2 * e - k0;
+        double hL, huL, hwL, hR, huR, hwR, FL0, FL1, FL2, FR0, FR1, FR2, sL, sR;
+        if (e == 0) kl = kr;
+        if (e == G.ne) kr = kl;
+        hL = q[kl]; huL = q[qn + kl]; hwL = q[2 * qn + kl];
+        hR = q[kr]; huR = q[qn + kr]; hwR = q[2 * qn + kr];
+        FL0 = nf[kl]; FL1 = nf[kQN + kl]; FL2 = nf[2 * kQN + kl]; sL = nf[3 * kQN + kl];
+        FR0 = nf[kr]; FR1 = nf[kQN + kr]; FR2 = nf[2 * kQN + kr]; sR = nf[3 * kQN + kr];
+        if (e == 0) { huL = -huL; FL0 = -FL0; FL2 = -FL2; }
+        if (e == G.ne) { huR = -huR; FR0 = -FR0; FR2 = -FR2; }
+        const double s = sL > sR ? sL : sR;
+        fi[j] = 0.5 * (FL0 + FR0) - 0.5 * s * (hR - hL);
+        fi[kIF + j] = 0.5 * (FL1 + FR1) - 0.5 * s * (huR - huL);
+        fi[2 * kIF + j] = 0.5 * (FL2 + FR2) - 0.5 * s * (hwR - hwL);
+    }
+    __syncthreads();
 }
 
-// The semi-discrete operator H(Q) of Sec. 3.1 on element e: nodal values q
-// (3 fields x 2 nodes, [field][node]) and those of its neighbours' touching
-// nodes (ql = right node of e-1, qr = left node of e+1); walls mirror the
-// element's own end node.  out[field][node].
-__device__ __forceinline__ void dg_element_rate(const Geo& G, int e, const double q[3][2], const double ql[3],
-                                                const double qr[3], double dxL, double dxR, double out[3][2])
+// H(Q) of Sec. 3.1 on element e from its nodal fluxes (smem index kk of its
+// left node), its interface fluxes (index ii of its left interface) and the
+// bottom slopes at its nodes: the weak form with the P1 mass matrix inverted,
+// M^{-1} = (2/dx) [[2, -1], [-1, 2]], plus the nodal source g h d_x.
+__device__ __forceinline__ void element_rate(const Geo& G, const double* nf, int kk, const double* fi, int ii,
+                                             double hL, double hR, double dxL, double dxR, double out[3][2])
 {
-    double Fl[3], Fr[3];
-    if (e == 0) dg_rusanov(G.g, q[0][0], -q[1][0], q[2][0], q[0][0], q[1][0], q[2][0], Fl);
-    else dg_rusanov(G.g, ql[0], ql[1], ql[2], q[0][0], q[1][0], q[2][0], Fl);
-    if (e == G.ne - 1) dg_rusanov(G.g, q[0][1], q[1][1], q[2][1], q[0][1], -q[1][1], q[2][1], Fr);
-    else dg_rusanov(G.g, q[0][1], q[1][1], q[2][1], qr[0], qr[1], qr[2], Fr);
-    double FL[3], FR[3];
-    dg_flux(G.g, q[0][0], q[1][0], q[2][0], FL);
-    dg_flux(G.g, q[0][1], q[1][1], q[2][1], FR);
     const double c = 2.0 / G.dx;
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        const double rl = -0.5 * (FL[f] + FR[f]) + Fl[f];
-        const double rr = 0.5 * (FL[f] + FR[f]) - Fr[f];
+        const double FL = nf[f * kQN + kk], FR = nf[f * kQN + kk + 1];
+        const double rl = -0.5 * (FL + FR) + fi[f * kIF + ii];
+        const double rr = 0.5 * (FL + FR) - fi[f * kIF + ii + 1];
         out[f][0] = c * (2.0 * rl - rr);
         out[f][1] = c * (-rl + 2.0 * rr);
     }
-    out[1][0] += G.g * q[0][0] * dxL;
-    out[1][1] += G.g * q[0][1] * dxR;
+    out[1][0] += G.g * hL * dxL;
+    out[1][1] += G.g * hR * dxR;
 }
-
-// Shared-memory layout of the predictor: nodal states of the tile's elements
-// [e0 - 2, e0 + T + 2) (Q^n) and [e0 - 1, e0 + T + 1) (Q* of stage 1), and
-// k1 of the tile's own elements.
-struct PredSmem {
-    double q[3][2 * (kDgTile + 4)];
-    double qs[3][2 * (kDgTile + 2)];
-    double k1[3][2 * kDgTile];
-    double red[32];
-};
 
 __global__ void __launch_bounds__(kDgTile) k_dg_predict(PredArgs a)
 {
-    __shared__ PredSmem S;
+    extern __shared__ double pred_sm[];
+    double* q = pred_sm;                 // [3][kQN]
+    double* qs = q + 3 * kQN;            // [3][kQSN]
+    double* k1 = qs + 3 * kQSN;          // [3][2T]
+    double* nf = k1 + 3 * 2 * kDgTile;   // [4][kQN]
+    double* fi = nf + 4 * kQN;           // [3][kIF]
+    double* red = fi + 3 * kIF;          // [32]
     const Geo& G = a.G;
     const int b = blockIdx.y, e0 = blockIdx.x * kDgTile, tid = threadIdx.x;
     if (a.tc->abort) return;
@@ -242,65 +273,60 @@ __global__ void __launch_bounds__(kDgTile) k_dg_predict(PredArgs a)
     const double dt = a.tc->dt;
     const Slide sl = a.slide[b];
     const DgKin kn = a.kin[b];
-    // load Q^n of elements e0-2 .. e0+T+1 (nodes 2(e0-2) .. 2(e0+T+2)-1)
-    const int n0 = 2 * (e0 - 2), nn = 2 * (kDgTile + 4);
-    for (int j = tid; j < nn; j += kDgTile) {
+    // Q^n of elements e0-2 .. e0+T+1
+    const int n0 = 2 * (e0 - 2);
+    for (int j = tid; j < kQN; j += kDgTile) {
         const int k = n0 + j;
         if (k >= 0 && k < 2 * G.ne) {
-            S.q[0][j] = a.h[mb + k]; S.q[1][j] = a.hu[mb + k]; S.q[2][j] = a.hw[mb + k];
+            q[j] = a.h[mb + k]; q[kQN + j] = a.hu[mb + k]; q[2 * kQN + j] = a.hw[mb + k];
         }
     }
     __syncthreads();
     // stage 1 on elements e0-1 .. e0+T: Q* = Q^n + dt H(Q^n, t^n)
+    stage_fluxes(G, q, kQN, n0, kQN, e0 - 1, e0 + kDgTile + 1, nf, fi, tid);
     for (int j = tid; j < kDgTile + 2; j += kDgTile) {
         const int e = e0 - 1 + j;
         if (e < 0 || e >= G.ne) continue;
-        const int l = 2 * (j + 1);   // smem node index of e's left node in S.q
-        double q[3][2], ql[3], qr[3], out[3][2];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            q[f][0] = S.q[f][l]; q[f][1] = S.q[f][l + 1];
-            ql[f] = e > 0 ? S.q[f][l - 1] : 0.0;
-            qr[f] = e < G.ne - 1 ? S.q[f][l + 2] : 0.0;
-        }
+        const int l = 2 * (j + 1);   // e's left node in q / nf
         const double slope = (a.d0[mb + 2 * e + 1] - a.d0[mb + 2 * e]) / G.dx;
         const double xL = G.x0 + e * G.dx, xR = G.x0 + (e + 1) * G.dx;
-        dg_element_rate(G, e, q, ql, qr, node_dx(slope, xL, sl, kn.s_n), node_dx(slope, xR, sl, kn.s_n), out);
-        const int ls = 2 * j;        // smem node index in S.qs
+        double out[3][2];
+        element_rate(G, nf, l, fi, j, q[l], q[l + 1], node_dx(slope, xL, sl, kn.s_n), node_dx(slope, xR, sl, kn.s_n),
+                     out);
+        const int ls = 2 * j;        // e's left node in qs
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            S.qs[f][ls] = q[f][0] + dt * out[f][0];
-            S.qs[f][ls + 1] = q[f][1] + dt * out[f][1];
+            qs[f * kQSN + ls] = q[f * kQN + l] + dt * out[f][0];
+            qs[f * kQSN + ls + 1] = q[f * kQN + l + 1] + dt * out[f][1];
         }
         if (j >= 1 && j <= kDgTile) {
 #pragma unroll
-            for (int f = 0; f < 3; ++f) { S.k1[f][2 * (j - 1)] = out[f][0]; S.k1[f][2 * (j - 1) + 1] = out[f][1]; }
+            for (int f = 0; f < 3; ++f) {
+                k1[f * 2 * kDgTile + 2 * (j - 1)] = out[f][0];
+                k1[f * 2 * kDgTile + 2 * (j - 1) + 1] = out[f][1];
+            }
         }
     }
     __syncthreads();
     // stage 2 on the tile's own elements: Q~ = Q^n + dt/2 (k1 + H(Q*, t^{n+1}))
+    stage_fluxes(G, qs, kQSN, 2 * (e0 - 1), kQSN, e0, e0 + kDgTile, nf, fi, tid);
     const int e = e0 + tid;
     double mass = 0.0;
     if (e < G.ne) {
-        const int ls = 2 * (tid + 1);
-        double q[3][2], ql[3], qr[3], out[3][2];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            q[f][0] = S.qs[f][ls]; q[f][1] = S.qs[f][ls + 1];
-            ql[f] = e > 0 ? S.qs[f][ls - 1] : 0.0;
-            qr[f] = e < G.ne - 1 ? S.qs[f][ls + 2] : 0.0;
-        }
+        const int ls = 2 * (tid + 1);   // e's left node in qs / nf
         const double d0L = a.d0[mb + 2 * e], d0R = a.d0[mb + 2 * e + 1];
         const double slope = (d0R - d0L) / G.dx;
         const double xL = G.x0 + e * G.dx, xR = G.x0 + (e + 1) * G.dx;
-        dg_element_rate(G, e, q, ql, qr, node_dx(slope, xL, sl, kn.s_n1), node_dx(slope, xR, sl, kn.s_n1), out);
+        double out[3][2];
+        element_rate(G, nf, ls, fi, tid, qs[ls], qs[ls + 1], node_dx(slope, xL, sl, kn.s_n1),
+                     node_dx(slope, xR, sl, kn.s_n1), out);
         const int lq = 2 * (tid + 2);
         double qt[3][2];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
 #pragma unroll
             for (int s = 0; s < 2; ++s)
-                qt[f][s] = S.q[f][lq + s] + 0.5 * dt * (S.k1[f][2 * tid + s] + out[f][s]);
+                qt[f][s] = q[f * kQN + lq + s] + 0.5 * dt * (k1[f * 2 * kDgTile + 2 * tid + s] + out[f][s]);
         }
         const size_t k = mb + 2 * e;
         a.ht[k] = qt[0][0]; a.ht[k + 1] = qt[0][1];
@@ -332,10 +358,10 @@ __global__ void __launch_bounds__(kDgTile) k_dg_predict(PredArgs a)
     }
     // per-CTA mass (summed by k_dg_finish)
     mass = warp_sum(mass);
-    if ((tid & 31) == 0) S.red[tid >> 5] = mass;
+    if ((tid & 31) == 0) red[tid >> 5] = mass;
     __syncthreads();
     if (tid < 32) {
-        double v = tid < kDgTile / 32 ? S.red[tid] : 0.0;
+        double v = tid < kDgTile / 32 ? red[tid] : 0.0;
         v = warp_sum(v);
         if (tid == 0) a.mass_part[(size_t)b * gridDim.x + blockIdx.x] = v;
     }
@@ -1031,7 +1057,7 @@ nh_status enqueue_step(nh_dg* g, cudaStream_t st, int cur)
     pa.d0 = g->d0; pa.slide = g->slide; pa.kin = g->kin; pa.marks = g->marks; pa.mass_part = g->mass_part;
     pa.crit = g->crit; pa.knh = g->knh; pa.tc = g->tc;
     prof_mark(g, NH_DG_K_PREDICT, st);
-    k_dg_predict<<<dim3((g->ne + kDgTile - 1) / kDgTile, g->nb), kDgTile, 0, st>>>(pa);
+    k_dg_predict<<<dim3((g->ne + kDgTile - 1) / kDgTile, g->nb), kDgTile, kPredSmem, st>>>(pa);
     prof_done(g, st);
     prof_mark(g, NH_DG_K_COMPACT, st);
     k_dg_compact<<<g->nb, 1024, 0, st>>>(g->marks, g->mask, g->act, g->nact, g->ne, g->pe,
@@ -1192,6 +1218,8 @@ nh_status nh_dg_create(const nh_dg_desc* desc, const double* d0_host, void* ws, 
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cr_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)kCrSmallSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dg_predict, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kPredSmem);
     if (e != cudaSuccess) { cudaGetLastError(); delete g; return NH_ERR_CUDA; }
     cudaStream_t st = g->stream;
     // zero the whole workspace once (padding lanes stay defined)

@@ -324,3 +324,74 @@ def landslide_ensemble_2d(n_members=32, sizes=tuple(range(256, 1025, 64)), dx=0.
     for w in out:
         w.dt = dt
     return out, dt
+
+
+# ------------------------------------------------------------- DG workloads
+
+@dataclass
+class MemberDG:
+    """One 1D member in the DG-P1 discretisation: ne elements of width dx
+    from xl, static depth b0 + b1 (x - xl) (the form the DG oracle takes),
+    a moving bottom and the nodal initial state (2 ne values per field, node
+    2i = element i's left end)."""
+    ne: int
+    dx: float
+    xl: float
+    b0: float
+    b1: float
+    h: np.ndarray
+    hu: np.ndarray
+    hw: np.ndarray
+    slide: int = 0
+    A: float = 0.0
+    L: float = 1.0
+    xc0: float = 0.0
+    s0: float = 0.0
+    t0: float = 1.0
+    t2: float = 0.0
+
+    def nodes(self):
+        i = np.arange(self.ne)
+        x = np.empty(2 * self.ne)
+        x[0::2] = self.xl + i * self.dx
+        x[1::2] = self.xl + (i + 1) * self.dx
+        return x
+
+    def d0(self):
+        return self.b0 + self.b1 * (self.nodes() - self.xl)
+
+
+@dataclass
+class WorkloadDG:
+    name: str
+    members: list
+    dt: float
+    amplitude: float
+    meta: dict = field(default_factory=dict)
+
+
+def slide_dg_1d(n_members=64, ne=50000, length=40.0, b0=0.05, b1=0.025, A=0.05, L=0.5, s0=2.0, t0=1.0,
+                xc0=1.0, spread=0.3, courant=0.2, seed0=0, g=G):
+    """Batch of 1D moving-bottom slides in DG-P1 form: ne elements over
+    [0, length] on the plane slope d0 = b0 + b1 x (0.05 m to 1.05 m), a
+    Gaussian mound moving as s0 ln cosh(t/t0) from xc0, member k drawing A,
+    L, s0 scaled by U(1 - spread, 1 + spread) from default_rng(seed0 + k);
+    still water at t = 0; dt at Courant number `courant` on the deepest
+    water (the P1 / Heun limit is 1/3)."""
+    dx = length / ne
+    members = []
+    for k in range(n_members):
+        rng = np.random.default_rng(seed0 + k)
+        fa, fl, fs = rng.uniform(1.0 - spread, 1.0 + spread, size=3)
+        m = MemberDG(ne=ne, dx=dx, xl=0.0, b0=b0, b1=b1, h=None, hu=None, hw=None, slide=1,
+                     A=A * fa, L=L * fl, xc0=xc0, s0=s0 * fs, t0=t0)
+        x = m.nodes()
+        xi = (x - xc0) / m.L
+        m.h = m.d0() - m.A * np.exp(-xi * xi)
+        m.hu = np.zeros(2 * ne)
+        m.hw = np.zeros(2 * ne)
+        members.append(m)
+    dt = courant * dx / math.sqrt(g * (b0 + b1 * length))
+    return WorkloadDG("slide_dg_1d", members, dt, A,
+                      meta={"b0": b0, "b1": b1, "A": A, "L": L, "s0": s0, "t0": t0, "xc0": xc0,
+                            "spread": spread, "courant": courant, "seed0": seed0, "length": length})
