@@ -453,16 +453,28 @@ template <typename F>
 __device__ __forceinline__ float lv_apply(const LView& V, int q, F v)
 {
     const int il = q % V.w, jl = q / V.w;
-    float y = 0.f;
+    // every load first (an outside neighbour reads the row's own cell), then
+    // the sum over the neighbours inside: the loads overlap instead of
+    // waiting on each bounds test
+    float c[9], x[9];
+    bool in[9];
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
         int ii = il + slot_dx(s), jj = jl + slot_dy(s);
+        bool ok = true;
         if (V.wx) ii = (ii + V.w) % V.w;
-        else if (ii < 0 || ii >= V.w) continue;
+        else ok = ii >= 0 && ii < V.w;
         if (V.wy) jj = (jj + V.h) % V.h;
-        else if (jj < 0 || jj >= V.h) continue;
-        y += V.c[s * V.cs + q] * v(jj * V.w + ii, ii, jj);
+        else ok = ok && jj >= 0 && jj < V.h;
+        if (!ok) { ii = il; jj = jl; }
+        in[s] = ok;
+        c[s] = V.c[s * V.cs + q];
+        x[s] = v(jj * V.w + ii, ii, jj);
     }
+    float y = 0.f;
+#pragma unroll
+    for (int s = 0; s < 9; ++s)
+        if (in[s]) y += c[s] * x[s];
     return y;
 }
 
@@ -479,10 +491,17 @@ __device__ __forceinline__ float fine_apply(const MgArgs& m, size_t mo, int k, F
     const size_t o = mo + k;
     int nk[9];
     fine_nbrs(m.s, o, nk);
-    float y = m.cf[4 * m.T + o] * v(k);
+    // all loads first (a missing neighbour reads the row itself), then the sum
+    float c[9], x[9];
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+        c[s] = m.cf[s * m.T + o];
+        x[s] = v(s == 4 || nk[s] < 0 ? k : nk[s]);
+    }
+    float y = c[4] * x[4];
 #pragma unroll
     for (int s = 0; s < 9; ++s)
-        if (s != 4 && nk[s] >= 0) y += m.cf[s * m.T + o] * v(nk[s]);
+        if (s != 4 && nk[s] >= 0) y += c[s] * x[s];
     return y;
 }
 
@@ -495,15 +514,26 @@ __device__ __forceinline__ void down_fine(const MgArgs& m, const Geo2& G, size_t
     const int area = V.w * V.h;
     for (int q = t0; q < area; q += stride) {
         const int I = V.i0 + q % V.w, J = V.j0 + q / V.w;
+        // the four children's rows (an absent child evaluates row 0, unused):
+        // their loads overlap
+        int kk[4];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            const int i = 2 * I + (ch & 1), j = 2 * J + (ch >> 1);
+            const bool inb = i < G.nx && j < G.ny;
+            const int kv = m.inv[mo + (inb ? (size_t)j * G.nx + i : 0)];
+            kk[ch] = inb ? kv : -1;
+        }
+        float res[4];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            const int k = kk[ch] >= 0 ? kk[ch] : 0;
+            res[ch] = (float)r[mo + k] - fine_apply(m, mo, k, [&](int jj) { return z0[jj]; });
+        }
         float bsum = 0.f;
-        for (int dj = 0; dj < 2; ++dj)
-            for (int di = 0; di < 2; ++di) {
-                const int i = 2 * I + di, j = 2 * J + dj;
-                if (i >= G.nx || j >= G.ny) continue;
-                const int k = m.inv[mo + (size_t)j * G.nx + i];
-                if (k < 0) continue;
-                bsum += (float)r[mo + k] - fine_apply(m, mo, k, [&](int jj) { return z0[jj]; });
-            }
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch)
+            if (kk[ch] >= 0) bsum += res[ch];
         V.b[q] = bsum;
         V.za[q] = V.c[9 * V.cs + q] * bsum;
     }
@@ -515,15 +545,21 @@ __device__ __forceinline__ void down_coarse(const LView& U, const LView& V, int 
     const int area = V.w * V.h;
     for (int q = t0; q < area; q += stride) {
         const int I = V.i0 + q % V.w, J = V.j0 + q / V.w;
+        // the four children (an absent or empty one evaluates cell 0, unused)
+        float res[4];
+        bool use[4];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            const int ci = 2 * I + (ch & 1) - U.i0, cj = 2 * J + (ch >> 1) - U.j0;
+            const bool inb = ci >= 0 && ci < U.w && cj >= 0 && cj < U.h;
+            const int c = inb ? cj * U.w + ci : 0;
+            use[ch] = inb && U.c[9 * U.cs + c] != 0.f;
+            res[ch] = U.b[c] - lv_apply(U, c, [&](int jj, int, int) { return U.za[jj]; });
+        }
         float bsum = 0.f;
-        for (int dj = 0; dj < 2; ++dj)
-            for (int di = 0; di < 2; ++di) {
-                const int ci = 2 * I + di - U.i0, cj = 2 * J + dj - U.j0;
-                if (ci < 0 || ci >= U.w || cj < 0 || cj >= U.h) continue;
-                const int c = cj * U.w + ci;
-                if (U.c[9 * U.cs + c] == 0.f) continue;   // empty child
-                bsum += U.b[c] - lv_apply(U, c, [&](int jj, int, int) { return U.za[jj]; });
-            }
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch)
+            if (use[ch]) bsum += res[ch];
         V.b[q] = bsum;
         V.za[q] = V.c[9 * V.cs + q] * bsum;
     }
@@ -552,17 +588,25 @@ __device__ __forceinline__ void up_coarse(const LView& V, const LView& U, int t0
 }
 
 // The levels held in the first CTA's shared memory (lloc..nlev), block
-// barriers only: down from level lloc - 1 (or the fine level), the coarsest
-// sweeps, up to lloc; level lloc's result is copied to global memory.
+// barriers only: level lloc's right-hand side and first iterate (computed
+// here from level lloc - 1 or the fine level, or, with `pre`, already formed
+// in global memory by the whole group and copied in), the way down, the
+// coarsest sweeps, up to lloc; level lloc's result is copied to global memory.
 __device__ void mg_local(const MgArgs& m, const MgPlan& P, const Geo2& G, size_t mo, size_t cbase, const double* r,
-                         float* sm)
+                         float* sm, bool pre)
 {
     const int t0 = threadIdx.x, stride = blockDim.x;
     const int L0 = P.lloc, L1 = P.nlev;
     {
         const LView V = lview_smem(sm, P.lev[L0]);
-        if (L0 == 1) down_fine(m, G, mo, r, V, t0, stride);
-        else down_coarse(lview_global(m, P.lev[L0 - 1], cbase), V, t0, stride);
+        if (pre) {
+            const LView Vg = lview_global(m, P.lev[L0], cbase);
+            for (int q = t0; q < V.w * V.h; q += stride) { V.b[q] = Vg.b[q]; V.za[q] = Vg.za[q]; }
+        } else if (L0 == 1) {
+            down_fine(m, G, mo, r, V, t0, stride);
+        } else {
+            down_coarse(lview_global(m, P.lev[L0 - 1], cbase), V, t0, stride);
+        }
     }
     __syncthreads();
     for (int l = L0 + 1; l <= L1; ++l) {
@@ -612,7 +656,17 @@ __device__ bool mg_vcycle(const MgArgs& m, MgGroup& g, const MgPlan& P, const Ge
             }
         }
         if (P.lloc <= P.nlev) {
-            if (g.rank == 0) mg_local(m, P, G, mo, cbase, r, sm);
+            // with several CTAs, the whole group forms level lloc's right-hand
+            // side (the largest step of the shared-memory part) before the
+            // first CTA takes over; the values are the same either way
+            const bool pre = g.G > 1;
+            if (pre) {
+                const LView V = lview_global(m, P.lev[P.lloc], cbase);
+                if (P.lloc == 1) down_fine(m, G, mo, r, V, t0, stride);
+                else down_coarse(lview_global(m, P.lev[P.lloc - 1], cbase), V, t0, stride);
+                if (!mg_sync(g, m.budget, ctl)) return false;
+            }
+            if (g.rank == 0) mg_local(m, P, G, mo, cbase, r, sm, pre);
             if (!mg_sync(g, m.budget, ctl)) return false;
         }
         for (int l = min(lg, P.nlev - 1); l >= 1; --l) {
