@@ -302,6 +302,15 @@ template <typename TS>
 nh_status enqueue_mask_assembly(nh_grid2d* g, cudaStream_t st, int nxt, int lnew, double dt, bool all,
                                 const TimeCtl* tc);
 
+// float4 loads of Q^n and d0s need 16-byte aligned arrays and a member pitch
+// of a multiple of 4 floats (each member's rows then also need nx % 4 == 0,
+// checked in the kernel).
+int fused_vec4(const FusedArgs& fa)
+{
+    auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    return (fa.pitch % 4 == 0 && al(fa.z) && al(fa.hu) && al(fa.hv) && al(fa.hw) && al(fa.d0s)) ? 1 : 0;
+}
+
 // The one-launch FP32 predictor with tile candidate c (kPredTiles[c]): CTAs
 // per member cover its largest tile count, at most 8 per SM over the members.
 template <int TX, int TY>
@@ -362,6 +371,7 @@ nh_status enqueue_front(nh_grid2d* g, cudaStream_t st, int cur, int lnew, double
         fa.oz = as<float>(g->q[nxt][0]); fa.ohu = as<float>(g->q[nxt][1]); fa.ohv = as<float>(g->q[nxt][2]);
         fa.ohw = as<float>(g->q[nxt][3]); fa.m1 = as<float>(g->dn1);
         fa.marks = fused_marks ? g->marks : nullptr; fa.knh = (float)g->knh; fa.dt = dt; fa.tc = tc;
+        fa.vec4 = fused_vec4(fa);
         CK2(launch_fused(g, st, g->ptile, fa));
         if (all) CK2(cudaMemsetAsync(g->marks, 1, T, st));
         else if (g->crit == NH_CRIT_HYDROSTATIC) CK2(cudaMemsetAsync(g->marks, 0, T, st));
@@ -502,6 +512,7 @@ nh_status tune_fused(nh_grid2d* g, double dt)
     fa.oz = as<float>(g->q[nxt][0]); fa.ohu = as<float>(g->q[nxt][1]); fa.ohv = as<float>(g->q[nxt][2]);
     fa.ohw = as<float>(g->q[nxt][3]); fa.m1 = as<float>(g->dn1);
     fa.marks = g->marks; fa.knh = (float)g->knh; fa.dt = dt; fa.tc = nullptr;
+    fa.vec4 = fused_vec4(fa);
     cudaEvent_t e0, e1;
     CK2(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return NH_ERR_CUDA; }

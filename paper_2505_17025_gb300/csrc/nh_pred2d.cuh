@@ -50,6 +50,7 @@ struct FusedArgs {
     float knh;
     double dt;
     const TimeCtl* tc;
+    int vec4;                        // Q^n and d0s 16-byte aligned with a pitch of 4k floats: float4 loads
 };
 
 // Per-CTA FP32 mound evaluator at one time: the slide centre as an integer
@@ -179,25 +180,54 @@ static __global__ void __launch_bounds__(TX * TY, TX * TY <= 256 ? 4 : (TX * TY 
     const int tiles_x = (G.nx + kPX - 1) / kPX, tiles = tiles_x * ((G.ny + kPY - 1) / kPY);
     const float* z = a.z + mo; const float* hu = a.hu + mo; const float* hv = a.hv + mo; const float* hw = a.hw + mo;
     const float* d0s = a.d0s + mo;
+    const bool vec4 = a.vec4 && (G.nx & 3) == 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int i0 = (tile % tiles_x) * kPX, j0 = (tile / tiles_x) * kPY;
         // 1. Q^n and its primitives on the region (mirrored / wrapped)
-        for (int q = threadIdx.x; q < kPA; q += kPThreads) {
-            const int ax = q % kPAX, ay = q / kPAX;
-            int ox, oy;
-            const int ci = g2_index1(G.bcx, G.nx, i0 - 4 + ax, &ox);
-            const int cj = g2_index1(G.bcy, G.ny, j0 - 4 + ay, &oy);
-            const int c = cj * G.nx + ci;
-            const float zc = z[c], m = M0.at(ci, cj), dz = d0s[c];
+        auto put = [&](int q, float zc, float huc, float hvc, float hwc, float dz, float m) {
             const float hc = zc + dz;
             const float rh = 1.0f / hc;
-            const float huc = flip(ox, hu[c]), hvc = flip(oy, hv[c]), hwc = hw[c];
             Az[q] = zc; Ahu[q] = huc; Ahv[q] = hvc; Ahw[q] = hwc;
             Ae[q] = zc + m;
             Ad[q] = dz - m;
             Au[q] = huc * rh;
             Av[q] = hvc * rh;
             Aw[q] = hwc * rh;
+        };
+        auto put_cell = [&](int q, int ax, int ay) {
+            int ox, oy;
+            const int ci = g2_index1(G.bcx, G.nx, i0 - 4 + ax, &ox);
+            const int cj = g2_index1(G.bcy, G.ny, j0 - 4 + ay, &oy);
+            const int c = cj * G.nx + ci;
+            put(q, z[c], flip(ox, hu[c]), flip(oy, hv[c]), hw[c], d0s[c], M0.at(ci, cj));
+        };
+        if (vec4) {
+            // four cells of a row per thread: one float4 per field where the four
+            // lie inside the domain (i0 - 4 + ax is a multiple of 4, so the address
+            // is 16-byte aligned), the per-cell mirrored path elsewhere
+            static_assert(kPAX % 4 == 0, "region rows split into groups of four cells");
+            constexpr int kQ4 = kPAX / 4;
+            for (int q4 = threadIdx.x; q4 < kPA / 4; q4 += kPThreads) {
+                const int ax = (q4 % kQ4) * 4, ay = q4 / kQ4, q = ay * kPAX + ax;
+                const int gi = i0 - 4 + ax, gj = j0 - 4 + ay;
+                if (gi >= 0 && gi + 3 < G.nx && gj >= 0 && gj < G.ny) {
+                    const int c = gj * G.nx + gi;
+                    const float4 z4 = *reinterpret_cast<const float4*>(z + c);
+                    const float4 u4 = *reinterpret_cast<const float4*>(hu + c);
+                    const float4 v4 = *reinterpret_cast<const float4*>(hv + c);
+                    const float4 w4 = *reinterpret_cast<const float4*>(hw + c);
+                    const float4 d4 = *reinterpret_cast<const float4*>(d0s + c);
+                    put(q, z4.x, u4.x, v4.x, w4.x, d4.x, M0.at(gi, gj));
+                    put(q + 1, z4.y, u4.y, v4.y, w4.y, d4.y, M0.at(gi + 1, gj));
+                    put(q + 2, z4.z, u4.z, v4.z, w4.z, d4.z, M0.at(gi + 2, gj));
+                    put(q + 3, z4.w, u4.w, v4.w, w4.w, d4.w, M0.at(gi + 3, gj));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) put_cell(q + e, ax + e, ay);
+                }
+            }
+        } else {
+            for (int q = threadIdx.x; q < kPA; q += kPThreads) put_cell(q, q % kPAX, q / kPAX);
         }
         __syncthreads();
         // 2. stage-1 faces of the stage-1 region (its cell (0, 0) at A (2, 2))
