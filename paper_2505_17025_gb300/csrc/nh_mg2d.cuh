@@ -43,9 +43,9 @@ namespace nh {
 constexpr int kMgThreads = 1024;     // threads per CTA of the multigrid solve
 constexpr int kMgLevels = 12;        // coarse levels at most
 constexpr int kMgCoarsest = 16;      // a level of at most this many cells is the coarsest
-constexpr int kMgSweeps = 7;         // damped-Jacobi sweeps on the coarsest level (odd)
+constexpr int kMgSweeps = 3;         // damped-Jacobi sweeps on the coarsest level (odd)
 constexpr int kMgRowsPerCta = 4096;  // active cells per CTA before a member gets another one
-constexpr float kMgOmega = 0.7f;     // Jacobi damping
+constexpr float kMgOmega = 0.85f;    // Jacobi damping (ensemble: 0.7 -> 30, 0.85 -> 26 PCG iterations per step; 0.95 -> 34, 1.0 fails)
 constexpr float kMgCoarseScale = 1.5f;   // weight of the coarse-level correction (over-correction of the piecewise-constant prolongation)
 constexpr int kMgSmemCells = 3840;   // coarse cells the group's first CTA keeps in shared memory
 constexpr int kMgSmemFloats = 13;    // per such cell: 9 couplings, omega / diagonal, b, two iterates
