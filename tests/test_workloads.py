@@ -45,3 +45,43 @@ def test_two_dimensional_workloads_shapes():
     ls = W.landslide_2d(n=64, dx=0.2)
     assert ls.h.shape == (64, 64) and ls.slide["A"] == 0.1
     assert np.min(ls.d0) >= 0.1 and np.max(ls.d0) <= 2.0
+
+
+def test_dg_slide_workload():
+    """The DG slide batch: linear nodal depths from 0.05 m to 1.05 m, still
+    water over each member's mound, members drawn from their own seeds, dt at
+    Courant 0.2 on the deepest water."""
+    w = W.slide_dg_1d(n_members=3, ne=1000)
+    assert len(w.members) == 3
+    for k, m in enumerate(w.members):
+        x = m.nodes()
+        assert x.shape == (2000,) and x[0] == 0.0 and abs(x[-1] - 40.0) < 1e-12
+        assert np.all(x[1::2] - x[0::2] > 0) and np.array_equal(x[1:-1:2], x[2::2])   # shared end points
+        d0 = m.d0()
+        assert abs(d0[0] - 0.05) < 1e-15 and abs(d0[-1] - 1.05) < 1e-12
+        mound = m.A * np.exp(-((x - m.xc0) / m.L) ** 2)
+        assert np.max(np.abs(m.h - (d0 - mound))) < 1e-15 and np.all(m.h > 0)
+        assert not np.any(m.hu) and not np.any(m.hw)
+        assert 0.7 * 0.05 <= m.A <= 1.3 * 0.05 and 0.7 * 2.0 <= m.s0 <= 1.3 * 2.0
+        one = W.slide_dg_1d(n_members=k + 1, ne=1000).members[k]
+        assert (one.A, one.L, one.s0) == (m.A, m.L, m.s0)
+    assert abs(w.dt - 0.2 * w.members[0].dx / math.sqrt(9.81 * 1.05)) < 1e-15
+
+
+def test_dg_cyclic_reduction_byte_count():
+    """The bench's algorithmic bytes of the DG p-system solve: no global level
+    below 513 rows (all in shared memory: rows in, x out), otherwise each
+    level reads its rows and writes half as many, and the total grows with
+    the marked elements."""
+    import bench
+    red, back = bench._dg_cr_bytes(300, 300)
+    assert back == 0.0 and red == (112.0 + 16.0) * 300
+    red1, back1 = bench._dg_cr_bytes(50000, 50000)
+    red2, back2 = bench._dg_cr_bytes(25000, 50000)
+    assert red1 > red2 > 0 and back1 > back2 > 0
+    # 7 global levels at 50 000 elements (50 000 / 2^7 = 391 <= 512)
+    n, lev = 50000, 0
+    while -(-50000 // (1 << lev)) > 512:
+        lev += 1
+    assert lev == 7
+    assert red1 < 4.0 * 112.0 * 50000 and back1 < 2.0 * 112.0 * 50000
